@@ -1,0 +1,223 @@
+/*
+ * mix.h - C ABI of the GB300 library for spatially mixed molecular dynamics
+ * (force mixing of two local interatomic potentials, arXiv 2502.19081).
+ *
+ * One context holds one trajectory on one CUDA device.  Every step of the hot
+ * path runs in the library's own sm_103a kernels: cell-list neighbour build,
+ * blend weights lambda_i, evaluated sets with one-cutoff buffers, the expensive
+ * many-body (linear cluster expansion) forces on lambda > 0 atoms plus buffer,
+ * the cheap 2+3-body spline forces on lambda < 1 atoms plus buffer, the blend
+ * F_i = w_i F_i^exp + (1 - w_i) F_i^cheap, and velocity-Verlet updates.
+ *
+ * Conventions for every call:
+ *  - Return value: MIX_OK (0) or a negative MIX_E* code; no exceptions cross
+ *    the boundary.  mix_strerror() names a code; mix_last_error() gives the
+ *    context's last message.
+ *  - Device work is enqueued asynchronously on the context's stream.  Errors
+ *    detected by kernels (capacity overflow, non-finite values, an atom leaving
+ *    a non-periodic box) surface at the next synchronising call: mix_sync(),
+ *    the mix_get_* exports, mix_get_state() and the *_host entry points.
+ *  - Ownership: positions, velocities, forces and the workspace are caller-owned
+ *    device buffers that the library borrows from mix_bind() until the next
+ *    mix_bind() or mix_destroy(); it never frees them.  Host arrays passed to
+ *    mix_init() are copied.  The library itself allocates only host memory
+ *    (plus pinned host memory for status reads).
+ *  - Layout: per-atom vectors are [N][4] float64 (x, y, z, unused), 32-byte rows,
+ *    16-byte aligned or better.  Units: Angstrom, fs, eV, amu.
+ *  - A context is not thread-safe; distinct contexts are independent.
+ */
+#ifndef MIX_H
+#define MIX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define MIX_OK 0
+#define MIX_EINVAL (-1)     /* bad argument or unsupported configuration */
+#define MIX_ENOMEM (-2)     /* workspace too small / host allocation failed */
+#define MIX_ECUDA (-3)      /* a CUDA runtime call failed */
+#define MIX_EOVERFLOW (-4)  /* a neighbour count exceeded its capacity */
+#define MIX_ETIMEOUT (-5)   /* a bounded device wait gave up */
+#define MIX_ENUMERIC (-6)   /* a non-finite position, force or energy */
+#define MIX_ESTATE (-7)     /* call out of order (e.g. mix_forces before mix_bind) */
+#define MIX_EBOX (-8)       /* an atom left the box in a non-periodic dimension */
+
+/* arithmetic of the potential evaluations (integration, lambda and force
+ * accumulation are always float64) */
+#define MIX_FP64 0
+#define MIX_FP32 1
+
+/* region shapes (Sec. 4.4: core radius and blend width around a defect) */
+#define MIX_REGION_SPHERE 0    /* distance to a centre point */
+#define MIX_REGION_CYLINDER 1  /* distance to a line through centre along axis */
+
+/* blend functions applied to the linear ramp (Sec. 4.4 names linear and cubic) */
+#define MIX_BLEND_LINEAR 0
+#define MIX_BLEND_CUBIC 1      /* w = lambda^2 (3 - 2 lambda) */
+
+#define MIX_MAX_REGIONS 16
+#define MIX_MAX_NRAD 16
+#define MIX_MAX_LMAX 6
+
+typedef struct mix_ctx mix_ctx;
+
+/* The simulated system.  Periodic dimensions must have box_lo = 0 and at least
+ * three cells of width >= max cutoff + skin, with box_len >= 2 (cutoff + skin)
+ * (minimum image).  Non-periodic dimensions span [box_lo, box_lo + box_len);
+ * an atom outside that range raises MIX_EBOX. */
+typedef struct {
+    int64_t n_atoms;
+    double box_lo[3];
+    double box_len[3];
+    int periodic[3];
+    double mass;            /* amu, single species */
+} mix_system;
+
+/* Expensive potential: a linear atomic cluster expansion (the paper's expensive
+ * potentials are linear ACE, Sec. 2.1, Table 1).  Per site i,
+ *   A_nlm = sum_{j: r_ij < r_cut} R_n(r_ij) Y_lm(r_ij / |r_ij|),
+ *   R_n(r) = T_n(2 r / r_cut - 1) (1 - (r / r_cut)^2)^3  (Chebyshev T_n),
+ *   Y_lm real orthonormal spherical harmonics without Condon-Shortley phase,
+ *   E_i = 1/2 sum_j Vpair(r_ij) + sum_k c_k B_k(i)
+ * with the product basis B of correlation order nu <= nu_max:
+ *   nu = 1: A_n00;  nu = 2: sum_m A_n1lm A_n2lm (n1 <= n2);
+ *   nu = 3: sum_{m1 m2 m3} G(l1 m1, l2 m2, l3 m3) A_n1l1m1 A_n2l2m2 A_n3l3m3,
+ *   G = integral over the sphere of Y_l1m1 Y_l2m2 Y_l3m3, labels (l, n) sorted:
+ *   l1 <= l2 <= l3, n1 <= n2 if l1 == l2, n2 <= n3 if l2 == l3,
+ *   l1 + l2 + l3 even, l3 <= l1 + l2.
+ * Coefficient tables (host, row-major, copied at mix_init):
+ *   c1[n_rad], c2[l_max+1][n_rad][n_rad] (entries n1 <= n2 used),
+ *   c3[l_max+1][l_max+1][l_max+1][n_rad][n_rad][n_rad] (sorted labels used; may
+ *   be NULL when nu_max < 3), pair[16]: cubic B-spline pair coefficients on knots
+ *   (a - 3) r_cut / 13 (NULL = no pair term). */
+typedef struct {
+    double r_cut;
+    int n_rad;              /* 1 .. MIX_MAX_NRAD */
+    int l_max;              /* 0 .. MIX_MAX_LMAX */
+    int nu_max;             /* 1 .. 3 (body order - 1) */
+    const double* c1;
+    const double* c2;
+    const double* c3;
+    const double* pair;
+} mix_ace;
+
+/* Cheap potential: a 2+3-body cubic B-spline (the paper's UF3 family, Sec. 2.1):
+ *   E_i = 1/2 sum_{j: r_ij < r_cut} V2(r_ij)
+ *       + sum_{j<k: r_ij, r_ik < r_cut3} V3(r_ij, r_ik, r_jk),
+ *   V2 = sum_{a<16} c2[a] B_a(r), knots (a - 3) r_cut / 13;
+ *   V3 = sum_{a,b,c<8} c3[a][b][c] B_a(r_ij) B_b(r_ik) B_c(r_jk), knots
+ *   (a - 3) r_cut3 / 5 for the first two arguments and (c - 3) 2 r_cut3 / 5 for
+ *   the third; c3 must be symmetric in (a, b).  r_cut3 <= r_cut. */
+typedef struct {
+    double r_cut;
+    double r_cut3;
+    const double* c2;       /* [16] */
+    const double* c3;       /* [8][8][8] */
+} mix_spline;
+
+typedef struct {
+    int precision;          /* MIX_FP64 or MIX_FP32 */
+    double skin;            /* neighbour-list skin, Angstrom (> 0); lists rebuild
+                               when an atom moved more than skin / 2 */
+    int blend;              /* MIX_BLEND_* */
+    double buffer_exp;      /* buffer radius of the expensive set; <= 0: its cutoff */
+    double buffer_cheap;    /* buffer radius of the cheap set; <= 0: its cutoff */
+    int nbr_cap;            /* neighbour slots per atom; 0: automatic */
+} mix_options;
+
+/* A core region.  d = distance of an atom from the shape (minimum image in
+ * periodic dimensions); lambda = 1 for d < r_core, 1 - (d - r_core) / ramp for
+ * d < r_core + ramp, else 0; the maximum over regions is taken (Alg. 2 takes
+ * the maximum over core atoms; here the core is a geometric shape). */
+typedef struct {
+    int kind;               /* MIX_REGION_* */
+    double centre[3];
+    double axis[3];         /* cylinder direction (normalised by the library) */
+    double r_core;
+    double ramp;
+} mix_region;
+
+typedef struct {
+    int64_t n_core;         /* lambda == 1 */
+    int64_t n_ramp;         /* 0 < lambda < 1 */
+    int64_t n_exp;          /* evaluated with the expensive potential (set + buffer) */
+    int64_t n_cheap;        /* evaluated with the cheap potential (set + buffer) */
+    int64_t rebuilds;       /* neighbour-list builds since mix_bind */
+    int64_t steps;          /* velocity-Verlet steps since mix_bind */
+    int max_neighbours;     /* largest list length seen at the last build */
+    int status_bits;        /* raw device status word */
+} mix_stats;
+
+/* Create a context on the current CUDA device.  `cuda_stream` is a cudaStream_t
+ * (NULL = legacy default stream).  Errors: MIX_EINVAL for unsupported sizes or
+ * a box too small for the cutoff; MIX_ECUDA. */
+int mix_init(const mix_system* sys, const mix_ace* expensive, const mix_spline* cheap,
+             const mix_options* opt, void* cuda_stream, mix_ctx** out);
+
+/* Device workspace the caller must provide to mix_bind (bytes, 256-aligned). */
+int mix_workspace_bytes(const mix_ctx* ctx, size_t* bytes);
+
+/* Borrow caller-owned device buffers: x, v, f are [N][4] float64; workspace has
+ * at least mix_workspace_bytes bytes, 256-byte aligned.  Uploads the potential
+ * tables into the workspace and marks the neighbour lists stale.  Does not read
+ * x, v or f. */
+int mix_bind(mix_ctx* ctx, double* x_dev, double* v_dev, double* f_dev, void* workspace_dev);
+
+/* Set the core regions (at most MIX_MAX_REGIONS; n = 0 gives lambda = 0
+ * everywhere, i.e. the pure cheap potential).  Takes effect at the next force
+ * evaluation.  The paper rebuilds regions every step (Sec. 4.7); lambda is
+ * recomputed at every force evaluation from the current positions. */
+int mix_set_regions(mix_ctx* ctx, const mix_region* regions, int n);
+
+/* f <- blended forces at the current positions (Alg. 4 with the buffer of
+ * Sec. 4.5), rebuilding the neighbour lists first if needed. */
+int mix_forces(mix_ctx* ctx);
+
+/* nsteps velocity-Verlet steps of dt fs:
+ *   v += dt/2 kappa F/m;  x += dt v;  F = mixed forces(x);  v += dt/2 kappa F/m,
+ * kappa = 9.6485332e-3 A fs^-2 per (eV/A/amu).  Forces are evaluated first if
+ * f does not hold the forces of the current positions. */
+int mix_step(mix_ctx* ctx, double dt_fs, int nsteps);
+
+/* End-to-end variant with host buffers: copies x and v ([N][4] float64, ideally
+ * pinned) to the bound device buffers, runs nsteps steps, copies x, v and f
+ * back, and synchronises.  x_host and v_host are updated in place; f_host
+ * (nullable) receives the forces. */
+int mix_step_host(mix_ctx* ctx, double* x_host, double* v_host, double* f_host, double dt_fs, int nsteps);
+
+/* Wait for the context's stream and report device-side errors. */
+int mix_sync(mix_ctx* ctx);
+
+/* Counters of the last evaluation (synchronises). */
+int mix_get_stats(mix_ctx* ctx, mix_stats* stats);
+
+/* Debug / test exports: copy device state into caller host buffers
+ * (synchronising).  Lists are the ones of the last build. */
+int mix_get_cells(mix_ctx* ctx, int* ncell3, int* cell_of /*[N]*/);
+int mix_get_neighbours(mix_ctx* ctx, int* cap_out, int* nnb /*[N] nullable*/, int* nbr /*[N][cap] nullable*/,
+                       int* rev /*[N][cap] nullable*/);
+int mix_get_lambda(mix_ctx* ctx, double* lam /*[N]*/, double* weight /*[N]*/);
+/* flags bit0 lambda > 0, bit1 lambda < 1, bit2 expensive set or buffer,
+ * bit3 cheap set or buffer; act lists ascending. */
+int mix_get_sets(mix_ctx* ctx, uint8_t* flags /*[N]*/, int* act_exp /*[N] nullable*/, int64_t* n_exp,
+                 int* act_cheap /*[N] nullable*/, int64_t* n_cheap);
+int mix_get_site_energies(mix_ctx* ctx, double* e_exp /*[N]*/, double* e_cheap /*[N]*/);
+
+/* Checkpoint: x, v, f, the list reference positions and the step counter.
+ * mix_set_state marks the lists stale (they rebuild at the next evaluation). */
+int mix_get_state(mix_ctx* ctx, double* x, double* v, double* f, int64_t* step);
+int mix_set_state(mix_ctx* ctx, const double* x, const double* v, const double* f, int64_t step, int forces_valid);
+
+int mix_destroy(mix_ctx* ctx);
+const char* mix_strerror(int code);
+const char* mix_last_error(const mix_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MIX_H */

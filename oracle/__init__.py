@@ -5,10 +5,10 @@ benchmark's CPU-baseline leg may call it; the product path never does, and it
 shares no code with the CUDA library (it reads the seeded workload objects by
 attribute and imports nothing from the package).
 
-The C source (oracle.c) follows the paper's steps: region weights (Sec. 4.1,
+The C source (oracle.c) follows the paper's steps: region weights (Sec. 4.4,
 Alg. 2 in its geometric reading), evaluated sets with one-cutoff buffers
-(Sec. 4.2 buffer-set equation, Alg. 3), forces as sums of site-energy
-derivatives (Sec. 4.2 force equation) per potential on its evaluated set,
+(Sec. 4.5 buffer-set equation, Alg. 3), forces as sums of site-energy
+derivatives (Sec. 4.5 force equation) per potential on its evaluated set,
 scaled by the blend weight and summed (Alg. 4), and velocity-Verlet steps.
 
 The two potentials are synthetic, since the paper fixes neither:

@@ -5,14 +5,14 @@
  * never does.  It shares no code with the CUDA library.
  *
  * What it computes, in the paper's order:
- *   - region weights lambda_i (Sec. 4.1, Alg. 1-2, geometric reading);
- *   - the evaluated sets Lambda_k and their buffers (Sec. 4.2, buffer set
+ *   - region weights lambda_i (Sec. 4.4, Alg. 1-2, geometric reading);
+ *   - the evaluated sets Lambda_k and their buffers (Sec. 4.5, buffer set
  *     equation; Alg. 3);
- *   - forces as sums of site-energy derivatives (Sec. 4.2, force equation)
+ *   - forces as sums of site-energy derivatives (Sec. 4.5, force equation)
  *     for each potential restricted to its evaluated set, scaled by the blend
  *     weight and accumulated (Alg. 4);
  *   - the plain definition F = w F_exp,full + (1 - w) F_cheap,full used to
- *     check the above (one-cutoff buffer sufficiency, Sec. 4.2);
+ *     check the above (one-cutoff buffer sufficiency, Sec. 4.5);
  *   - velocity-Verlet NVE steps.
  * Both potentials are synthetic (the paper names the families only: linear ACE
  * and UF3, Sec. 2.1): see the header comment of oracle/__init__.py.
@@ -852,6 +852,35 @@ void or_lambda(void* p, const double* x, double* lam, double* w) {
  *       bit3: evaluated with the cheap potential (Lambda_c or its buffer).
  * Buffer of a set S with radius b: atoms outside S with some member of S
  * closer than b (strict). */
+/* environment of atom i: neighbours within rc (from a fresh list) as r_ij vectors */
+typedef struct {
+    int cap;
+    int* nnb;
+    int* nbr;
+} olist;
+
+static int list_build(const omodel* m, const double* x, double rc, olist* L) {
+    int64_t n = m->n;
+    L->cap = 128;
+    for (;;) {
+        L->nnb = (int*)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+        L->nbr = (int*)malloc(sizeof(int) * (size_t)L->cap * (size_t)(n > 0 ? n : 1));
+        if (!L->nnb || !L->nbr) return OR_ENOMEM;
+        int st = neighbours_cells(&m->box, n, x, rc, L->cap, L->nnb, L->nbr);
+        if (st == OR_EOVERFLOW) {
+            free(L->nnb); free(L->nbr);
+            L->cap *= 2;
+            continue;
+        }
+        return st;
+    }
+}
+
+static void list_free(olist* L) {
+    free(L->nnb);
+    free(L->nbr);
+}
+
 int or_sets(void* p, const double* x, uint8_t* flags) {
     omodel* m = (omodel*)p;
     int64_t n = m->n;
@@ -859,14 +888,15 @@ int or_sets(void* p, const double* x, uint8_t* flags) {
     double* w = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
     or_lambda(p, x, lam, w);
     double rb = m->buf_e > m->buf_c ? m->buf_e : m->buf_c;
-    int cap = 1024;
-    int* nnb = (int*)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
-    int* nbr = (int*)malloc(sizeof(int) * (size_t)cap * (size_t)(n > 0 ? n : 1));
-    int st = neighbours_cells(&m->box, n, x, rb, cap, nnb, nbr);
+    olist NL;
+    int st = list_build(m, x, rb, &NL);
     if (st) {
-        free(lam); free(w); free(nnb); free(nbr);
+        free(lam); free(w);
         return st;
     }
+    int cap = NL.cap;
+    int* nnb = NL.nnb;
+    int* nbr = NL.nbr;
     double be2 = m->buf_e * m->buf_e, bc2 = m->buf_c * m->buf_c;
     for (int64_t i = 0; i < n; ++i) {
         uint8_t f = 0;
@@ -893,35 +923,6 @@ int or_sets(void* p, const double* x, uint8_t* flags) {
     return OR_OK;
 }
 
-/* environment of atom i: neighbours within rc (from a fresh list) as r_ij vectors */
-typedef struct {
-    int cap;
-    int* nnb;
-    int* nbr;
-} olist;
-
-static int list_build(const omodel* m, const double* x, double rc, olist* L) {
-    int64_t n = m->n;
-    L->cap = 256;
-    for (;;) {
-        L->nnb = (int*)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
-        L->nbr = (int*)malloc(sizeof(int) * (size_t)L->cap * (size_t)(n > 0 ? n : 1));
-        if (!L->nnb || !L->nbr) return OR_ENOMEM;
-        int st = neighbours_cells(&m->box, n, x, rc, L->cap, L->nnb, L->nbr);
-        if (st == OR_EOVERFLOW) {
-            free(L->nnb); free(L->nbr);
-            L->cap *= 2;
-            continue;
-        }
-        return st;
-    }
-}
-
-static void list_free(olist* L) {
-    free(L->nnb);
-    free(L->nbr);
-}
-
 /* which: 0 expensive, 1 cheap.  Site energy and pair gradients of atom i. */
 static double site_eval(const omodel* m, int which, const double* x, const olist* L, int64_t i, double* g) {
     int nn = L->nnb[i];
@@ -937,7 +938,7 @@ static double site_eval(const omodel* m, int which, const double* x, const olist
 
 /* Forces of one potential with only the atoms in `active` (NULL = all) as
  * centres: Fp_k = -d(sum_{i active} E_i)/dx_k, written as a scatter of the
- * pair gradients (Sec. 4.2 force equation; Alg. 4 "compute()"). */
+ * pair gradients (Sec. 4.5 force equation; Alg. 4 "compute()"). */
 static int pot_forces(const omodel* m, int which, const double* x, const uint8_t* active, double* Fp,
                       double* Esite) {
     int64_t n = m->n;

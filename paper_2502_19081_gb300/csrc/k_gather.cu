@@ -1,0 +1,103 @@
+// Force assembly and blend (Alg. 4) without atomics, fused with the second
+// half of velocity Verlet.
+//
+// With g^p_ij = dE^p_i / dr_ij stored per list slot by the potential kernels,
+// the force of potential p on atom k restricted to its evaluated set A_p is
+//   Phi^p_k = [k in A_p] sum_j g^p_kj - sum_{i in N(k), i in A_p} g^p_{i, rev(k in i)},
+// the site-energy derivative sum of Sec. 4.5.  Then
+//   F_k = w_k Phi^exp_k + (1 - w_k) Phi^cheap_k,
+// each term evaluated only where its weight is non-zero.  One warp per atom,
+// lanes over the list slots, a fixed-order shuffle reduction in float64.
+#include "mix_launch.h"
+
+namespace mixd {
+
+constexpr int G_WARPS = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(G_WARPS * 32) k_gather(Dev d, int integrate, double h) {
+    using V = typename Vec4<T>::type;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const V* GE = reinterpret_cast<const V*>(d.ge);
+    const V* GC = reinterpret_cast<const V*>(d.gc);
+    const int cap = d.cap;
+    for (int64_t k = (int64_t)blockIdx.x * G_WARPS + warp; k < d.n; k += (int64_t)gridDim.x * G_WARPS) {
+        const double w = d.wgt[k];
+        const int m = d.nnb[k];
+        const int pe = d.pos_e[k], pc = d.pos_c[k];
+        const int* row = d.nbr + k * cap;
+        const int* rv = d.rev + k * cap;
+        double ex = 0, ey = 0, ez = 0, cx = 0, cy = 0, cz = 0;
+        for (int s = lane; s < m; s += 32) {
+            const int j = row[s];
+            const int r = rv[s];
+            if (w > 0.0) {
+                if (pe >= 0) {
+                    const V g = GE[(int64_t)pe * cap + s];
+                    ex += (double)g.x;
+                    ey += (double)g.y;
+                    ez += (double)g.z;
+                }
+                const int pj = d.pos_e[j];
+                if (pj >= 0) {
+                    const V g = GE[(int64_t)pj * cap + r];
+                    ex -= (double)g.x;
+                    ey -= (double)g.y;
+                    ez -= (double)g.z;
+                }
+            }
+            if (w < 1.0) {
+                if (pc >= 0) {
+                    const V g = GC[(int64_t)pc * cap + s];
+                    cx += (double)g.x;
+                    cy += (double)g.y;
+                    cz += (double)g.z;
+                }
+                const int pj = d.pos_c[j];
+                if (pj >= 0) {
+                    const V g = GC[(int64_t)pj * cap + r];
+                    cx -= (double)g.x;
+                    cy -= (double)g.y;
+                    cz -= (double)g.z;
+                }
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            ex += __shfl_down_sync(0xffffffffu, ex, o);
+            ey += __shfl_down_sync(0xffffffffu, ey, o);
+            ez += __shfl_down_sync(0xffffffffu, ez, o);
+            cx += __shfl_down_sync(0xffffffffu, cx, o);
+            cy += __shfl_down_sync(0xffffffffu, cy, o);
+            cz += __shfl_down_sync(0xffffffffu, cz, o);
+        }
+        if (lane == 0) {
+            const double wc = 1.0 - w;
+            double4 F;
+            F.x = (w > 0.0 ? w * ex : 0.0) + (wc > 0.0 ? wc * cx : 0.0);
+            F.y = (w > 0.0 ? w * ey : 0.0) + (wc > 0.0 ? wc * cy : 0.0);
+            F.z = (w > 0.0 ? w * ez : 0.0) + (wc > 0.0 ? wc * cz : 0.0);
+            F.w = 0.0;
+            if (!(isfinite(F.x) && isfinite(F.y) && isfinite(F.z))) set_status(d.status, ST_NONFINITE);
+            d.f[k] = F;
+            if (integrate) {
+                double4 v = d.v[k];
+                v.x = __dadd_rn(v.x, __dmul_rn(h, F.x));
+                v.y = __dadd_rn(v.y, __dmul_rn(h, F.y));
+                v.z = __dadd_rn(v.z, __dmul_rn(h, F.z));
+                d.v[k] = v;
+            }
+        }
+    }
+}
+
+void launch_gather(const Dev& d, int precision, int integrate, double h, cudaStream_t s) {
+    int64_t want = (d.n + G_WARPS - 1) / G_WARPS;
+    int64_t lim = (int64_t)sm_count() * 8;
+    const int grid = (int)(want < lim ? want : lim);
+    if (precision == MIX_FP64)
+        k_gather<double><<<grid > 0 ? grid : 1, G_WARPS * 32, 0, s>>>(d, integrate, h);
+    else
+        k_gather<float><<<grid > 0 ? grid : 1, G_WARPS * 32, 0, s>>>(d, integrate, h);
+}
+
+}  // namespace mixd

@@ -1,0 +1,288 @@
+// Cell list and full neighbour list with a reverse-slot map (the region and
+// force steps reuse one neighbour list, as the paper's region fix reuses the
+// pair style's lists, Sec. 4.4), plus the first half of velocity Verlet and
+// the skin test that decides when the lists are rebuilt.
+//
+// Bit-reproducibility: positions are folded, binned and compared with explicit
+// round-to-nearest operations (no FMA), in the same order as a plain CPU
+// evaluation: d = x_j - x_i; d -= L rint(d / L); r2 = dx*dx + dy*dy + dz*dz;
+// neighbour iff r2 < (rc + skin)^2.  Each row of the list is sorted ascending.
+#include <climits>
+
+#include "mix_launch.h"
+
+namespace mixd {
+
+// v += h F; x += dt v (when integrating); then flag a rebuild if any atom moved
+// more than skin/2 since the last build.  Block 0 resets the per-evaluation
+// counters.
+__global__ void k_disp(Dev d, int integrate, double dt, double h, int force_rebuild) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i == 0) {
+        d.status[SW_NCORE] = 0;
+        d.status[SW_NRAMP] = 0;
+        d.status[SW_NLE] = 0;
+        d.status[SW_NLC] = 0;
+        if (force_rebuild) d.status[SW_REBUILD] = 1;
+    }
+    if (i >= d.n) return;
+    double4 x = d.x[i];
+    if (integrate) {
+        double4 v = d.v[i];
+        const double4 f = d.f[i];
+        v.x = __dadd_rn(v.x, __dmul_rn(h, f.x));
+        v.y = __dadd_rn(v.y, __dmul_rn(h, f.y));
+        v.z = __dadd_rn(v.z, __dmul_rn(h, f.z));
+        x.x = __dadd_rn(x.x, __dmul_rn(dt, v.x));
+        x.y = __dadd_rn(x.y, __dmul_rn(dt, v.y));
+        x.z = __dadd_rn(x.z, __dmul_rn(dt, v.z));
+        d.v[i] = v;
+        d.x[i] = x;
+    }
+    const bool finite = isfinite(x.x) && isfinite(x.y) && isfinite(x.z);
+    if (!finite) {
+        set_status(d.status, ST_NONFINITE);
+        return;
+    }
+    const double xs[3] = {x.x, x.y, x.z};
+    for (int k = 0; k < 3; ++k)
+        if (!d.box.per[k] && (xs[k] < d.box.lo[k] || xs[k] >= d.box.lo[k] + d.box.L[k]))
+            set_status(d.status, ST_OUT_OF_BOX);
+    if (!force_rebuild) {
+        const double4 xb = d.xb[i];
+        const double dx = x.x - xb.x, dy = x.y - xb.y, dz = x.z - xb.z;
+        if (dx * dx + dy * dy + dz * dz > d.half_skin2) d.status[SW_REBUILD] = 1;
+    }
+}
+
+// Fold periodic coordinates into [0, L), bin into cells, count per cell.
+__global__ void k_cell_bin(Dev d) {
+    if (d.status[SW_REBUILD] == 0) return;
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= d.n) return;
+    double4 x = d.x[i];
+    double xs[3] = {x.x, x.y, x.z};
+    for (int k = 0; k < 3; ++k)
+        if (d.box.per[k]) xs[k] = __dsub_rn(xs[k], __dmul_rn(d.box.L[k], floor(__dmul_rn(xs[k], d.box.invL[k]))));
+    x.x = xs[0];
+    x.y = xs[1];
+    x.z = xs[2];
+    d.x[i] = x;
+    const int cx = cell_coord(d.box, d.cells, xs[0], 0);
+    const int cy = cell_coord(d.box, d.cells, xs[1], 1);
+    const int cz = cell_coord(d.box, d.cells, xs[2], 2);
+    const int c = (cz * d.cells.nc[1] + cy) * d.cells.nc[0] + cx;
+    d.cell_of[i] = c;
+    atomicAdd(d.cell_count + c, 1);
+}
+
+// Exclusive scan of the cell counts (one block), zeroing counts and fill slots.
+__global__ void k_cell_scan(Dev d) {
+    if (d.status[SW_REBUILD] == 0) return;
+    __shared__ int wsum[32];
+    __shared__ int carry_s;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    if (tid == 0) {
+        carry_s = 0;
+        d.status[SW_MAXNB] = 0;
+    }
+    __syncthreads();
+    const int nc = d.cells.ncell;
+    for (int base = 0; base < nc; base += blockDim.x) {
+        const int k = base + tid;
+        const int v = k < nc ? d.cell_count[k] : 0;
+        int incl = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            int w = lane < nw ? wsum[lane] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                int t = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += t;
+            }
+            if (lane < nw) wsum[lane] = w;
+        }
+        __syncthreads();
+        const int carry = carry_s;
+        const int excl = carry + (warp > 0 ? wsum[warp - 1] : 0) + incl - v;
+        if (k < nc) {
+            d.cell_start[k] = excl;
+            d.cell_fill[k] = 0;
+            d.cell_count[k] = 0;
+        }
+        __syncthreads();
+        if (tid == blockDim.x - 1) carry_s = excl + v;
+        __syncthreads();
+    }
+    if (tid == 0) d.cell_start[nc] = carry_s;
+}
+
+__global__ void k_cell_fill(Dev d) {
+    if (d.status[SW_REBUILD] == 0) return;
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= d.n) return;
+    const int c = d.cell_of[i];
+    const int slot = d.cell_start[c] + atomicAdd(d.cell_fill + c, 1);
+    d.cell_atoms[slot] = (int)i;
+}
+
+constexpr int NB_WARPS = 4;
+
+// One warp per atom: scan the 27-cell stencil (as up to 18 contiguous runs of
+// cells), keep r2 < rlist2 with a ballot compaction into shared memory, sort
+// the row ascending with a warp bitonic network, write it out.
+__global__ void __launch_bounds__(NB_WARPS * 32) k_neigh_build(Dev d, int capp2) {
+    if (d.status[SW_REBUILD] == 0) return;
+    extern __shared__ int sbuf[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int* buf = sbuf + warp * capp2;
+    const unsigned lt = (1u << lane) - 1u;
+    const int ncx = d.cells.nc[0], ncy = d.cells.nc[1], ncz = d.cells.nc[2];
+    for (int64_t i = (int64_t)blockIdx.x * NB_WARPS + warp; i < d.n; i += (int64_t)gridDim.x * NB_WARPS) {
+        const double4 xi = d.x[i];
+        const int c = d.cell_of[i];
+        const int cx = c % ncx, cy = (c / ncx) % ncy, cz = c / (ncx * ncy);
+        int cnt = 0;
+        for (int dz = -1; dz <= 1; ++dz) {
+            int qz = cz + dz;
+            if (d.box.per[2]) qz = (qz + ncz) % ncz;
+            else if (qz < 0 || qz >= ncz) continue;
+            for (int dy = -1; dy <= 1; ++dy) {
+                int qy = cy + dy;
+                if (d.box.per[1]) qy = (qy + ncy) % ncy;
+                else if (qy < 0 || qy >= ncy) continue;
+                const int row = (qz * ncy + qy) * ncx;
+                // runs of cells along x: [a0, b0] and optionally [a1, b1]
+                int a0, b0, a1 = 1, b1 = 0;
+                if (d.box.per[0]) {
+                    if (cx == 0) { a0 = 0; b0 = 1; a1 = ncx - 1; b1 = ncx - 1; }
+                    else if (cx == ncx - 1) { a0 = ncx - 2; b0 = ncx - 1; a1 = 0; b1 = 0; }
+                    else { a0 = cx - 1; b0 = cx + 1; }
+                } else {
+                    a0 = cx > 0 ? cx - 1 : 0;
+                    b0 = cx < ncx - 1 ? cx + 1 : ncx - 1;
+                }
+                for (int run = 0; run < 2; ++run) {
+                    const int ra = run == 0 ? a0 : a1, rb = run == 0 ? b0 : b1;
+                    if (ra > rb) continue;
+                    const int t0 = d.cell_start[row + ra], t1 = d.cell_start[row + rb + 1];
+                    for (int tb = t0; tb < t1; tb += 32) {
+                        const int t = tb + lane;
+                        bool ok = false;
+                        int j = -1;
+                        if (t < t1) {
+                            j = d.cell_atoms[t];
+                            if (j != (int)i) {
+                                double dd[3];
+                                delta_rn(d.box, xi, d.x[j], dd);
+                                ok = norm2_rn(dd) < d.rlist2;
+                            }
+                        }
+                        const unsigned m = __ballot_sync(0xffffffffu, ok);
+                        if (ok) {
+                            const int p = cnt + __popc(m & lt);
+                            if (p < capp2) buf[p] = j;
+                        }
+                        cnt += __popc(m);
+                    }
+                }
+            }
+        }
+        if (lane == 0) {
+            atomicMax(d.status + SW_MAXNB, cnt);
+            if (cnt > d.cap) set_status(d.status, ST_NBR_OVERFLOW);
+        }
+        const int mlen = cnt < d.cap ? cnt : d.cap;
+        for (int p = mlen + lane; p < capp2; p += 32) buf[p] = INT_MAX;
+        __syncwarp();
+        for (int k = 2; k <= capp2; k <<= 1) {
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int t = lane; t < (capp2 >> 1); t += 32) {
+                    const int a = (t / j) * 2 * j + (t % j);
+                    const int b = a + j;
+                    const bool up = (a & k) == 0;
+                    const int va = buf[a], vb = buf[b];
+                    if ((va > vb) == up) {
+                        buf[a] = vb;
+                        buf[b] = va;
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        int* row = d.nbr + i * (int64_t)d.cap;
+        for (int p = lane; p < mlen; p += 32) row[p] = buf[p];
+        if (lane == 0) {
+            d.nnb[i] = mlen;
+            d.xb[i] = xi;
+        }
+        __syncwarp();
+    }
+}
+
+// rev[i][s] = position of i in the row of j = nbr[i][s] (binary search).
+__global__ void k_neigh_rev(Dev d) {
+    if (d.status[SW_REBUILD] == 0) return;
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t i = idx / d.cap;
+    const int s = (int)(idx - i * d.cap);
+    if (i >= d.n) return;
+    if (s >= d.nnb[i]) return;
+    const int j = d.nbr[idx];
+    const int* row = d.nbr + (int64_t)j * d.cap;
+    int lo = 0, hi = d.nnb[j] - 1, pos = -1;
+    while (lo <= hi) {
+        const int mid = (lo + hi) >> 1;
+        const int v = row[mid];
+        if (v == (int)i) {
+            pos = mid;
+            break;
+        }
+        if (v < (int)i) lo = mid + 1;
+        else hi = mid - 1;
+    }
+    if (pos < 0) {
+        set_status(d.status, ST_REV_MISSING);
+        pos = 0;
+    }
+    d.rev[idx] = pos;
+}
+
+static int g_sms = 0;
+
+int sm_count() {
+    if (g_sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_sms <= 0) g_sms = 1;
+    }
+    return g_sms;
+}
+
+void launch_disp(const Dev& d, cudaStream_t s, int integrate, double dt, double h, int force_rebuild) {
+    const int nb = (int)((d.n + 255) / 256);
+    k_disp<<<nb > 0 ? nb : 1, 256, 0, s>>>(d, integrate, dt, h, force_rebuild);
+}
+
+void launch_build(const Dev& d, cudaStream_t s) {
+    const int nb = (int)((d.n + 255) / 256);
+    k_cell_bin<<<nb > 0 ? nb : 1, 256, 0, s>>>(d);
+    k_cell_scan<<<1, 1024, 0, s>>>(d);
+    k_cell_fill<<<nb > 0 ? nb : 1, 256, 0, s>>>(d);
+    int capp2 = 32;
+    while (capp2 < d.cap) capp2 <<= 1;
+    int64_t want = (d.n + NB_WARPS - 1) / NB_WARPS;
+    int64_t lim = (int64_t)sm_count() * 16;
+    int grid = (int)(want < lim ? want : lim);
+    k_neigh_build<<<grid > 0 ? grid : 1, NB_WARPS * 32, NB_WARPS * capp2 * sizeof(int), s>>>(d, capp2);
+    const int64_t tot = d.n * (int64_t)d.cap;
+    const int nr = (int)((tot + 255) / 256);
+    k_neigh_rev<<<nr > 0 ? nr : 1, 256, 0, s>>>(d);
+}
+
+}  // namespace mixd

@@ -1,0 +1,206 @@
+// Blend weights, evaluated sets and their compaction into ascending index lists.
+//
+// lambda (Sec. 4.4, Alg. 2 in its geometric reading): distance d from each
+// region (sphere: centre; cylinder: axis line; minimum image in periodic
+// dimensions), lambda = 1 for d < r_core, 1 - (d - r_core)/ramp for
+// d < r_core + ramp, else 0, maximum over regions.  Sets (Sec. 4.5, buffer-set
+// equation; Alg. 3): Lambda_exp = {lambda > 0}, Lambda_cheap = {lambda < 1};
+// each is evaluated together with its buffer, the atoms outside it that have a
+// member closer than the buffer radius (strict).  All comparisons use explicit
+// round-to-nearest arithmetic so that the sets are bit-reproducible.
+#include "mix_launch.h"
+
+namespace mixd {
+
+__global__ void k_lambda(Dev d, Regions r) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i == 0 && d.status[SW_REBUILD]) {
+        d.status[SW_REBUILDS] += 1;
+        d.status[SW_REBUILD] = 0;
+    }
+    if (i >= d.n) return;
+    const double4 x = d.x[i];
+    double best = 0.0;
+    for (int k = 0; k < r.n; ++k) {
+        const double* R = r.r[k];
+        const double4 c = make_double4(R[1], R[2], R[3], 0.0);
+        double v[3];
+        delta_rn(d.box, c, x, v);
+        double d2 = norm2_rn(v);
+        if ((int)R[0] == MIX_REGION_CYLINDER) {
+            const double t = __dadd_rn(__dadd_rn(__dmul_rn(v[0], R[4]), __dmul_rn(v[1], R[5])), __dmul_rn(v[2], R[6]));
+            d2 = __dsub_rn(d2, __dmul_rn(t, t));
+            if (d2 < 0.0) d2 = 0.0;
+        }
+        const double dist = __dsqrt_rn(d2);
+        const double rc = R[7], ramp = R[8];
+        double lr;
+        if (dist < rc) lr = 1.0;
+        else if (ramp > 0.0 && dist < __dadd_rn(rc, ramp)) lr = __dsub_rn(1.0, __ddiv_rn(__dsub_rn(dist, rc), ramp));
+        else lr = 0.0;
+        if (lr > best) best = lr;
+    }
+    d.lam[i] = best;
+    double w = best;
+    if (r.blend == MIX_BLEND_CUBIC) w = __dmul_rn(__dmul_rn(best, best), __dsub_rn(3.0, __dmul_rn(2.0, best)));
+    d.wgt[i] = w;
+    d.flags[i] = (uint8_t)((best > 0.0 ? 1 : 0) | (best < 1.0 ? 2 : 0));
+    d.esite_e[i] = 0.0;
+    d.esite_c[i] = 0.0;
+}
+
+constexpr int BUF_WARPS = 8;
+
+// One warp per atom: buffer membership through the neighbour list.
+__global__ void __launch_bounds__(BUF_WARPS * 32) k_buffer(Dev d) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t i = (int64_t)blockIdx.x * BUF_WARPS + warp; i < d.n; i += (int64_t)gridDim.x * BUF_WARPS) {
+        const int f = d.flags[i] & 3;
+        const bool need_e = !(f & 1), need_c = !(f & 2);
+        bool he = false, hc = false;
+        if (need_e || need_c) {
+            const double4 xi = d.x[i];
+            const int m = d.nnb[i];
+            const int* row = d.nbr + i * (int64_t)d.cap;
+            for (int s = lane; s < m; s += 32) {
+                const int j = row[s];
+                const int fj = d.flags[j] & 3;
+                const bool cand_e = need_e && (fj & 1), cand_c = need_c && (fj & 2);
+                if (cand_e || cand_c) {
+                    double dd[3];
+                    delta_rn(d.box, xi, d.x[j], dd);
+                    const double r2 = norm2_rn(dd);
+                    he = he || (cand_e && r2 < d.bufe2);
+                    hc = hc || (cand_c && r2 < d.bufc2);
+                }
+            }
+            he = __any_sync(0xffffffffu, he);
+            hc = __any_sync(0xffffffffu, hc);
+        }
+        if (lane == 0) {
+            const int ae = (f & 1) || he ? 4 : 0;
+            const int ac = (f & 2) || hc ? 8 : 0;
+            d.flags[i] = (uint8_t)(f | ae | ac);
+        }
+    }
+}
+
+// Per-block counts of the two evaluated sets (and of the diagnostic sets).
+__global__ void __launch_bounds__(SCAN_BLOCK) k_count(Dev d) {
+    const int64_t i = blockIdx.x * (int64_t)SCAN_BLOCK + threadIdx.x;
+    int f = 0;
+    double lam = 0.0;
+    if (i < d.n) {
+        f = d.flags[i];
+        lam = d.lam[i];
+    }
+    const bool in = i < d.n;
+    const int ne = __syncthreads_count(in && (f & 4));
+    const int ncheap = __syncthreads_count(in && (f & 8));
+    const int ncore = __syncthreads_count(in && lam == 1.0);
+    const int nramp = __syncthreads_count(in && lam > 0.0 && lam < 1.0);
+    const int nle = __syncthreads_count(in && (f & 1));
+    const int nlc = __syncthreads_count(in && (f & 2));
+    if (threadIdx.x == 0) {
+        d.blk_e[blockIdx.x] = ne;
+        d.blk_c[blockIdx.x] = ncheap;
+        atomicAdd(d.status + SW_NCORE, ncore);
+        atomicAdd(d.status + SW_NRAMP, nramp);
+        atomicAdd(d.status + SW_NLE, nle);
+        atomicAdd(d.status + SW_NLC, nlc);
+    }
+}
+
+// Ordered compaction: act lists ascending, pos maps (-1 when not evaluated).
+__global__ void __launch_bounds__(SCAN_BLOCK) k_scatter(Dev d) {
+    __shared__ int red_e[32], red_c[32];
+    __shared__ int off_e_s, off_c_s;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int b = blockIdx.x;
+    // offset of this block: sum of the counts of the blocks before it
+    int se = 0, sc = 0;
+    for (int k = tid; k < b; k += SCAN_BLOCK) {
+        se += d.blk_e[k];
+        sc += d.blk_c[k];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        se += __shfl_down_sync(0xffffffffu, se, o);
+        sc += __shfl_down_sync(0xffffffffu, sc, o);
+    }
+    if (lane == 0) {
+        red_e[warp] = se;
+        red_c[warp] = sc;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        int a = red_e[lane], c = red_c[lane];
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_down_sync(0xffffffffu, a, o);
+            c += __shfl_down_sync(0xffffffffu, c, o);
+        }
+        if (lane == 0) {
+            off_e_s = a;
+            off_c_s = c;
+        }
+    }
+    __syncthreads();
+    const int64_t i = (int64_t)b * SCAN_BLOCK + tid;
+    const int f = i < d.n ? d.flags[i] : 0;
+    const bool ie = (f & 4) != 0, ic = (f & 8) != 0;
+    const unsigned be = __ballot_sync(0xffffffffu, ie), bc = __ballot_sync(0xffffffffu, ic);
+    const unsigned lt = (1u << lane) - 1u;
+    __syncthreads();
+    if (lane == 0) {
+        red_e[warp] = __popc(be);
+        red_c[warp] = __popc(bc);
+    }
+    __syncthreads();
+    if (warp == 0) {
+        int a = red_e[lane], c = red_c[lane];
+        int ia = a, ic2 = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            int ta = __shfl_up_sync(0xffffffffu, ia, o);
+            int tc = __shfl_up_sync(0xffffffffu, ic2, o);
+            if (lane >= o) {
+                ia += ta;
+                ic2 += tc;
+            }
+        }
+        red_e[lane] = ia - a;   // exclusive per-warp offsets
+        red_c[lane] = ic2 - c;
+        if (lane == 31 && b == (int)gridDim.x - 1) {
+            d.status[SW_NEXP] = off_e_s + ia;
+            d.status[SW_NCHEAP] = off_c_s + ic2;
+        }
+    }
+    __syncthreads();
+    if (i < d.n) {
+        if (ie) {
+            const int p = off_e_s + red_e[warp] + __popc(be & lt);
+            d.act_e[p] = (int)i;
+            d.pos_e[i] = p;
+        } else {
+            d.pos_e[i] = -1;
+        }
+        if (ic) {
+            const int p = off_c_s + red_c[warp] + __popc(bc & lt);
+            d.act_c[p] = (int)i;
+            d.pos_c[i] = p;
+        } else {
+            d.pos_c[i] = -1;
+        }
+    }
+}
+
+void launch_sets(const Dev& d, const Regions& r, cudaStream_t s) {
+    const int nb = (int)((d.n + 255) / 256);
+    k_lambda<<<nb > 0 ? nb : 1, 256, 0, s>>>(d, r);
+    int64_t want = (d.n + BUF_WARPS - 1) / BUF_WARPS;
+    int64_t lim = (int64_t)sm_count() * 8;
+    const int gb = (int)(want < lim ? want : lim);
+    k_buffer<<<gb > 0 ? gb : 1, BUF_WARPS * 32, 0, s>>>(d);
+    k_count<<<d.nblk, SCAN_BLOCK, 0, s>>>(d);
+    k_scatter<<<d.nblk, SCAN_BLOCK, 0, s>>>(d);
+}
+
+}  // namespace mixd

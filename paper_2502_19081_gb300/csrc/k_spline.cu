@@ -1,0 +1,240 @@
+// Cheap potential: a 2+3-body cubic B-spline site energy evaluated on the
+// compacted list of atoms in Lambda_cheap plus its buffer (Sec. 4.5, Alg. 4):
+//   E_i = 1/2 sum_j V2(r_ij) + sum_{j<k; r_ij, r_ik < rc3} V3(r_ij, r_ik, r_jk).
+// One warp per evaluated atom.  Lanes own list slots for the 2-body part and
+// the final write; the 3-body pairs (j, k) are spread over the lanes, their
+// partial derivatives go to a per-warp table, and each lane then sums the
+// rows of its own 3-body neighbour in a fixed order (no atomics, so results
+// are bit-reproducible).
+//   dV3 -> g_j += a_jk u_j + c_jk (r_j - r_k),  a_jk = dV3/d(first argument),
+//          c_jk = (dV3/dr_jk) / r_jk  (c3 symmetric in its first two indices).
+#include "mix_launch.h"
+
+namespace mixd {
+
+constexpr int SPL_WARPS = 4;
+constexpr int SPL_SLOTS = MAX_CAP / 32;     // list slots per lane
+constexpr int T3S = NB3MAX + 1;             // padded row stride of the pair tables
+
+__device__ __forceinline__ double tsqrt3(double x) { return sqrt(x); }
+__device__ __forceinline__ float tsqrt3(float x) { return sqrtf(x); }
+
+template <typename T>
+__device__ __forceinline__ void bspline4(T x, int qmax, int& q, T b[4], T db[4]) {
+    q = (int)floor(x);
+    q = q < 0 ? 0 : (q > qmax ? qmax : q);
+    const T u = x - T(q), w = T(1) - u;
+    const T u2 = u * u, u3 = u2 * u;
+    b[0] = w * w * w * T(1.0 / 6.0);
+    b[1] = (T(3) * u3 - T(6) * u2 + T(4)) * T(1.0 / 6.0);
+    b[2] = (T(-3) * u3 + T(3) * u2 + T(3) * u + T(1)) * T(1.0 / 6.0);
+    b[3] = u3 * T(1.0 / 6.0);
+    db[0] = T(-0.5) * w * w;
+    db[1] = T(1.5) * u2 - T(2) * u;
+    db[2] = T(-1.5) * u2 + u + T(0.5);
+    db[3] = T(0.5) * u2;
+}
+
+template <typename T>
+struct SplWarp {   // per-warp shared scratch
+    int slot[NB3MAX];
+    T v[NB3MAX][4];         // r_ij vector (x, y, z) and |r_ij|
+    T al[NB3MAX * T3S];     // a_jk
+    T cc[NB3MAX * T3S];     // c_jk (symmetric)
+    T g3[NB3MAX][4];
+};
+
+template <typename T>
+__global__ void __launch_bounds__(SPL_WARPS * 32) k_spline(Dev d, SplTab<T> tab) {
+    using V = typename Vec4<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* c3s = reinterpret_cast<T*>(smem_raw);                 // [512]
+    T* c2s = c3s + 512;                                       // [16]
+    SplWarp<T>* ws = reinterpret_cast<SplWarp<T>*>(c2s + 16);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    SplWarp<T>& W = ws[warp];
+    for (int k = threadIdx.x; k < 512; k += blockDim.x) c3s[k] = tab.c3[k];
+    if (threadIdx.x < 16) c2s[threadIdx.x] = tab.c2[threadIdx.x];
+    __syncthreads();
+
+    V* GC = reinterpret_cast<V*>(d.gc);
+    const double rc2 = d.rcc2, rc32 = tab.rc3 * tab.rc3;
+    const T invh2 = (T)(13.0 / tab.rc);
+    const T invh3 = (T)(5.0 / tab.rc3);
+    const T invhc = (T)(5.0 / (2.0 * tab.rc3));
+    const unsigned lt = (1u << lane) - 1u;
+    const int cap = d.cap;
+    const int count = d.status[SW_NCHEAP];
+
+    for (int a = blockIdx.x * SPL_WARPS + warp; a < count; a += gridDim.x * SPL_WARPS) {
+        const int i = d.act_c[a];
+        const double4 xi = d.x[i];
+        const int m = d.nnb[i];
+        const int* row = d.nbr + (int64_t)i * cap;
+        V* grow = GC + (int64_t)a * cap;
+        double epart = 0.0;
+        T g2[SPL_SLOTS][3];
+        int p3[SPL_SLOTS];
+        int n3 = 0;
+#pragma unroll
+        for (int c = 0; c < SPL_SLOTS; ++c) {
+            const int s = c * 32 + lane;
+            g2[c][0] = g2[c][1] = g2[c][2] = T(0);
+            p3[c] = -1;
+            bool is3 = false;
+            double dd[3] = {0, 0, 0}, r = 0;
+            if (c * 32 < m) {
+                if (s < m) {
+                    const double4 xj = d.x[row[s]];
+                    dd[0] = xj.x - xi.x;
+                    dd[1] = xj.y - xi.y;
+                    dd[2] = xj.z - xi.z;
+                    for (int k = 0; k < 3; ++k)
+                        if (d.box.per[k]) dd[k] -= d.box.L[k] * rint(dd[k] * d.box.invL[k]);
+                    const double r2 = dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2];
+                    if (r2 < rc2) {
+                        r = sqrt(r2);
+                        T v, dv;
+                        int q;
+                        T b[4], db[4];
+                        bspline4<T>((T)r * invh2, 12, q, b, db);
+                        v = c2s[q] * b[0] + c2s[q + 1] * b[1] + c2s[q + 2] * b[2] + c2s[q + 3] * b[3];
+                        dv = (c2s[q] * db[0] + c2s[q + 1] * db[1] + c2s[q + 2] * db[2] + c2s[q + 3] * db[3]) * invh2;
+                        epart += 0.5 * (double)v;
+                        const T hp = T(0.5) * dv / (T)r;
+                        g2[c][0] = hp * (T)dd[0];
+                        g2[c][1] = hp * (T)dd[1];
+                        g2[c][2] = hp * (T)dd[2];
+                        is3 = r2 < rc32;
+                    }
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, is3);
+                if (is3) {
+                    const int p = n3 + __popc(bal & lt);
+                    p3[c] = p;
+                    if (p < NB3MAX) {
+                        W.slot[p] = s;
+                        W.v[p][0] = (T)dd[0];
+                        W.v[p][1] = (T)dd[1];
+                        W.v[p][2] = (T)dd[2];
+                        W.v[p][3] = (T)r;
+                    }
+                }
+                n3 += __popc(bal);
+            }
+        }
+        if (n3 > NB3MAX) {
+            if (lane == 0) {
+                set_status(d.status, ST_NB3_OVERFLOW);
+                atomicMax(d.status + SW_NB3MAX, n3);
+            }
+            n3 = NB3MAX;
+        }
+        __syncwarp();
+        // 3-body pairs p < q, flattened over the lanes
+        const int npair = n3 * (n3 - 1) / 2;
+        for (int t = lane; t < npair; t += 32) {
+            int p = 0, tt = t;
+            while (tt >= n3 - 1 - p) {
+                tt -= n3 - 1 - p;
+                ++p;
+            }
+            const int q = p + 1 + tt;
+            const T wx = W.v[q][0] - W.v[p][0], wy = W.v[q][1] - W.v[p][1], wz = W.v[q][2] - W.v[p][2];
+            const T r3 = tsqrt3(wx * wx + wy * wy + wz * wz);
+            int qa, qb, qc;
+            T ba[4], dba[4], bb[4], dbb[4], bc[4], dbc[4];
+            bspline4<T>(W.v[p][3] * invh3, 4, qa, ba, dba);
+            bspline4<T>(W.v[q][3] * invh3, 4, qb, bb, dbb);
+            bspline4<T>(r3 * invhc, 4, qc, bc, dbc);
+            T val = T(0), d1 = T(0), d2 = T(0), d3 = T(0);
+#pragma unroll
+            for (int x = 0; x < 4; ++x) {
+#pragma unroll
+                for (int y = 0; y < 4; ++y) {
+                    const T* cr = c3s + ((qa + x) * 8 + (qb + y)) * 8 + qc;
+                    const T t0 = cr[0] * bc[0] + cr[1] * bc[1] + cr[2] * bc[2] + cr[3] * bc[3];
+                    const T t1 = cr[0] * dbc[0] + cr[1] * dbc[1] + cr[2] * dbc[2] + cr[3] * dbc[3];
+                    val += t0 * ba[x] * bb[y];
+                    d1 += t0 * dba[x] * bb[y];
+                    d2 += t0 * ba[x] * dbb[y];
+                    d3 += t1 * ba[x] * bb[y];
+                }
+            }
+            epart += (double)val;
+            const T c = r3 > T(0) ? d3 * invhc / r3 : T(0);
+            W.al[p * T3S + q] = d1 * invh3;
+            W.al[q * T3S + p] = d2 * invh3;
+            W.cc[p * T3S + q] = c;
+            W.cc[q * T3S + p] = c;
+        }
+        __syncwarp();
+        if (lane < n3) {
+            const int p = lane;
+            T sa = T(0), cx = T(0), cy = T(0), cz = T(0), cs = T(0);
+            for (int q = 0; q < n3; ++q) {
+                if (q == p) continue;
+                const T c = W.cc[p * T3S + q];
+                sa += W.al[p * T3S + q];
+                cs += c;
+                cx += c * W.v[q][0];
+                cy += c * W.v[q][1];
+                cz += c * W.v[q][2];
+            }
+            const T ir = T(1) / W.v[p][3];
+            W.g3[p][0] = sa * W.v[p][0] * ir + cs * W.v[p][0] - cx;
+            W.g3[p][1] = sa * W.v[p][1] * ir + cs * W.v[p][1] - cy;
+            W.g3[p][2] = sa * W.v[p][2] * ir + cs * W.v[p][2] - cz;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int c = 0; c < SPL_SLOTS; ++c) {
+            const int s = c * 32 + lane;
+            if (s < m) {
+                V gv;
+                gv.x = g2[c][0];
+                gv.y = g2[c][1];
+                gv.z = g2[c][2];
+                gv.w = T(0);
+                const int p = p3[c];
+                if (p >= 0 && p < NB3MAX) {
+                    gv.x += W.g3[p][0];
+                    gv.y += W.g3[p][1];
+                    gv.z += W.g3[p][2];
+                }
+                grow[s] = gv;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) epart += __shfl_down_sync(0xffffffffu, epart, o);
+        if (lane == 0) d.esite_c[i] = epart;
+        __syncwarp();
+    }
+}
+
+template <typename T>
+static cudaError_t spl_cfg(int cap, size_t* smem, int* grid) {
+    (void)cap;
+    const size_t bytes = (512 + 16) * sizeof(T) + SPL_WARPS * sizeof(SplWarp<T>);
+    cudaError_t e = cudaFuncSetAttribute(k_spline<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spline<T>, SPL_WARPS * 32, bytes);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    *smem = bytes;
+    *grid = per_sm * sm_count();
+    return cudaSuccess;
+}
+
+cudaError_t spline_configure(int precision, int cap, size_t* smem, int* grid) {
+    return precision == MIX_FP64 ? spl_cfg<double>(cap, smem, grid) : spl_cfg<float>(cap, smem, grid);
+}
+
+void launch_spline(const Dev& d, const void* tab, int precision, size_t smem, int grid, cudaStream_t s) {
+    if (precision == MIX_FP64)
+        k_spline<double><<<grid, SPL_WARPS * 32, smem, s>>>(d, *static_cast<const SplTab<double>*>(tab));
+    else
+        k_spline<float><<<grid, SPL_WARPS * 32, smem, s>>>(d, *static_cast<const SplTab<float>*>(tab));
+}
+
+}  // namespace mixd

@@ -1,0 +1,808 @@
+// Host side of the C ABI declared in include/mix.h: argument checking, the
+// potential tables, the workspace layout and the launch sequence of one force
+// evaluation / velocity-Verlet step.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "mix_launch.h"
+
+using namespace mixd;
+
+namespace {
+
+constexpr double KAPPA = 9.6485332e-3;   // (eV / Angstrom / amu) in Angstrom / fs^2
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// ---------------------------------------------------------------------------
+// real spherical harmonics on the host (same recurrence as the kernels) and
+// Gauss-Legendre quadrature, used to tabulate the Gaunt coefficients
+
+void host_ylm(int L, double x, double y, double z, std::vector<double>& Y) {
+    const int nlm = (L + 1) * (L + 1);
+    Y.assign(nlm, 0.0);
+    std::vector<double> Pi((L + 1) * (L + 2) / 2 + 1, 0.0), C(L + 1), S(L + 1);
+    auto P = [&](int l, int m) -> double& { return Pi[l * (l + 1) / 2 + m]; };
+    P(0, 0) = 1.0;
+    for (int m = 1; m <= L; ++m) P(m, m) = (2.0 * m - 1.0) * P(m - 1, m - 1);
+    for (int m = 0; m < L; ++m) P(m + 1, m) = (2.0 * m + 1.0) * z * P(m, m);
+    for (int m = 0; m <= L; ++m)
+        for (int l = m + 2; l <= L; ++l)
+            P(l, m) = ((2.0 * l - 1.0) * z * P(l - 1, m) - (l + m - 1.0) * P(l - 2, m)) / (double)(l - m);
+    C[0] = 1.0;
+    S[0] = 0.0;
+    for (int m = 1; m <= L; ++m) {
+        C[m] = x * C[m - 1] - y * S[m - 1];
+        S[m] = x * S[m - 1] + y * C[m - 1];
+    }
+    for (int l = 0; l <= L; ++l) {
+        const int o = l * l + l;
+        for (int m = 0; m <= l; ++m) {
+            double f = 1.0;
+            for (int k = l - m + 1; k <= l + m; ++k) f *= (double)k;   // (l+m)!/(l-m)!
+            const double N = std::sqrt((2.0 * l + 1.0) / (4.0 * M_PI) / f);
+            if (m == 0) {
+                Y[o] = N * P(l, 0);
+            } else {
+                Y[o + m] = std::sqrt(2.0) * N * P(l, m) * C[m];
+                Y[o - m] = std::sqrt(2.0) * N * P(l, m) * S[m];
+            }
+        }
+    }
+}
+
+double ylm_norm(int l, int m) {
+    const int mu = m < 0 ? -m : m;
+    double f = 1.0;
+    for (int k = l - mu + 1; k <= l + mu; ++k) f *= (double)k;
+    const double N = std::sqrt((2.0 * l + 1.0) / (4.0 * M_PI) / f);
+    return m == 0 ? N : std::sqrt(2.0) * N;
+}
+
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+    x.resize(n);
+    w.resize(n);
+    for (int i = 0; i < n; ++i) {
+        double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            const double pn = (n == 1) ? z : p1, pm = (n == 1) ? 1.0 : p0;
+            const double dp = n * (z * pn - pm) / (z * z - 1.0);
+            const double dz = pn / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        double p0 = 1.0, p1 = z;
+        for (int k = 2; k <= n; ++k) {
+            const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+            p0 = p1;
+            p1 = p2;
+        }
+        const double pn = (n == 1) ? z : p1, pm = (n == 1) ? 1.0 : p0;
+        const double dp = n * (z * pn - pm) / (z * z - 1.0);
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+// byte arena for the tables uploaded into the workspace
+struct Arena {
+    std::vector<unsigned char> bytes;
+    template <typename T>
+    size_t put(const std::vector<T>& v) {
+        const size_t off = align256(bytes.size());
+        bytes.resize(off + std::max<size_t>(v.size() * sizeof(T), 16));
+        if (!v.empty()) std::memcpy(bytes.data() + off, v.data(), v.size() * sizeof(T));
+        return off;
+    }
+};
+
+template <typename T>
+std::vector<T> conv(const std::vector<double>& v) {
+    return std::vector<T>(v.begin(), v.end());
+}
+
+}  // namespace
+
+struct mix_ctx {
+    mix_system sys;
+    mix_options opt;
+    int precision;
+    // expensive
+    double ace_rc;
+    int n, L, nu;
+    bool has_pair;
+    // cheap
+    double spl_rc, spl_rc3;
+    // regions
+    Regions regions;
+    cudaStream_t stream;
+    Dev dev;
+    double rlist;
+    int cap;
+    // tables (offsets in the arena) and their element-type views
+    Arena arena;
+    size_t o_c1, o_S2, o_W3, o_tau, o_goff, o_gidx, o_gval, o_ylmk, o_pair, o_sc2, o_sc3;
+    int ntau;
+    AceTab<double> ace64;
+    AceTab<float> ace32;
+    SplTab<double> spl64;
+    SplTab<float> spl32;
+    // workspace
+    size_t ws_bytes;
+    size_t off_tab;
+    size_t o_status, o_xb, o_cell_of, o_cell_count, o_cell_start, o_cell_fill, o_cell_atoms, o_nnb, o_nbr, o_rev,
+        o_lam, o_wgt, o_flags, o_act_e, o_act_c, o_pos_e, o_pos_c, o_blk_e, o_blk_c, o_ge, o_gc, o_ee, o_ec;
+    size_t ace_smem, spl_smem;
+    int ace_grid, spl_grid;
+    bool bound;
+    bool need_build;
+    bool forces_valid;
+    int64_t steps;
+    int* pinned;
+    std::string err;
+};
+
+namespace {
+
+int fail(mix_ctx* c, int code, const char* fmt, ...) {
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return code;
+}
+
+int cuda_fail(mix_ctx* c, cudaError_t e, const char* what) {
+    return fail(c, MIX_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Build the element-type independent tables (in double) and pack them.
+int build_tables(mix_ctx* c, const mix_ace* a, const mix_spline* sp) {
+    const int n = a->n_rad, L = a->l_max, L1 = L + 1, nlm = L1 * L1;
+    std::vector<double> c1(a->c1, a->c1 + n);
+    std::vector<double> S2((size_t)L1 * n * n, 0.0);
+    if (a->nu_max >= 2)
+        for (int l = 0; l <= L; ++l)
+            for (int p = 0; p < n; ++p)
+                for (int q = 0; q < n; ++q) {
+                    const double* C2 = a->c2 + (size_t)l * n * n;
+                    const double wpq = p <= q ? C2[p * n + q] : 0.0;
+                    const double wqp = q <= p ? C2[q * n + p] : 0.0;
+                    S2[((size_t)l * n + p) * n + q] = wpq + wqp;
+                }
+    // l-triples and masked nu = 3 coefficients
+    std::vector<int> tau;
+    std::vector<double> W3;
+    std::vector<int> goff, gidx;
+    std::vector<double> gval;
+    if (a->nu_max >= 3) {
+        const int deg = 3 * L;
+        const int nz = deg / 2 + 2, nphi = deg + 2;
+        std::vector<double> gz, gw;
+        gauss_legendre(nz, gz, gw);
+        std::vector<std::vector<double>> Yq;
+        std::vector<double> wq;
+        for (int iz = 0; iz < nz; ++iz)
+            for (int ip = 0; ip < nphi; ++ip) {
+                const double ph = 2.0 * M_PI * ip / nphi;
+                const double s = std::sqrt(std::max(0.0, 1.0 - gz[iz] * gz[iz]));
+                std::vector<double> Y;
+                host_ylm(L, s * std::cos(ph), s * std::sin(ph), gz[iz], Y);
+                Yq.push_back(Y);
+                wq.push_back(gw[iz] * 2.0 * M_PI / nphi);
+            }
+        for (int l1 = 0; l1 <= L; ++l1)
+            for (int l2 = l1; l2 <= L; ++l2)
+                for (int l3 = l2; l3 <= L; ++l3) {
+                    if (((l1 + l2 + l3) & 1) || l3 > l1 + l2) continue;
+                    const int d1 = 2 * l1 + 1, d2 = 2 * l2 + 1, d3 = 2 * l3 + 1;
+                    std::vector<double> G((size_t)d1 * d2 * d3, 0.0);
+                    for (size_t k = 0; k < wq.size(); ++k) {
+                        const std::vector<double>& Y = Yq[k];
+                        for (int m1 = 0; m1 < d1; ++m1)
+                            for (int m2 = 0; m2 < d2; ++m2) {
+                                const double y12 = wq[k] * Y[l1 * l1 + m1] * Y[l2 * l2 + m2];
+                                for (int m3 = 0; m3 < d3; ++m3) G[((size_t)m1 * d2 + m2) * d3 + m3] += y12 * Y[l3 * l3 + m3];
+                            }
+                    }
+                    auto nz_ = [&](int m1, int m2, int m3) { return std::fabs(G[((size_t)m1 * d2 + m2) * d3 + m3]) > 1e-12; };
+                    auto gv = [&](int m1, int m2, int m3) { return G[((size_t)m1 * d2 + m2) * d3 + m3]; };
+                    const int t = (int)(tau.size() / 4);
+                    (void)t;
+                    tau.push_back(l1);
+                    tau.push_back(l2);
+                    tau.push_back(l3);
+                    tau.push_back((int)goff.size());
+                    // ordering by m3 (entries m1 | m2 << 8)
+                    for (int m3 = 0; m3 < d3; ++m3) {
+                        goff.push_back((int)gidx.size());
+                        for (int m1 = 0; m1 < d1; ++m1)
+                            for (int m2 = 0; m2 < d2; ++m2)
+                                if (nz_(m1, m2, m3)) {
+                                    gidx.push_back(m1 | (m2 << 8));
+                                    gval.push_back(gv(m1, m2, m3));
+                                }
+                    }
+                    goff.push_back((int)gidx.size());
+                    // ordering by m1 (entries m2 | m3 << 8)
+                    for (int m1 = 0; m1 < d1; ++m1) {
+                        goff.push_back((int)gidx.size());
+                        for (int m2 = 0; m2 < d2; ++m2)
+                            for (int m3 = 0; m3 < d3; ++m3)
+                                if (nz_(m1, m2, m3)) {
+                                    gidx.push_back(m2 | (m3 << 8));
+                                    gval.push_back(gv(m1, m2, m3));
+                                }
+                    }
+                    goff.push_back((int)gidx.size());
+                    // ordering by m2 (entries m1 | m3 << 8)
+                    for (int m2 = 0; m2 < d2; ++m2) {
+                        goff.push_back((int)gidx.size());
+                        for (int m1 = 0; m1 < d1; ++m1)
+                            for (int m3 = 0; m3 < d3; ++m3)
+                                if (nz_(m1, m2, m3)) {
+                                    gidx.push_back(m1 | (m3 << 8));
+                                    gval.push_back(gv(m1, m2, m3));
+                                }
+                    }
+                    goff.push_back((int)gidx.size());
+                    // masked coefficients
+                    const size_t id = ((size_t)l1 * L1 + l2) * L1 + l3;
+                    const double* C3 = a->c3 + id * n * n * n;
+                    for (int q1 = 0; q1 < n; ++q1)
+                        for (int q2 = 0; q2 < n; ++q2)
+                            for (int q3 = 0; q3 < n; ++q3) {
+                                bool ok = true;
+                                if (l1 == l2 && q2 < q1) ok = false;
+                                if (l2 == l3 && q3 < q2) ok = false;
+                                W3.push_back(ok ? C3[((size_t)q1 * n + q2) * n + q3] : 0.0);
+                            }
+                }
+    }
+    c->ntau = (int)(tau.size() / 4);
+    std::vector<double> ylmk(nlm);
+    for (int l = 0; l <= L; ++l)
+        for (int m = -l; m <= l; ++m) ylmk[l * l + l + m] = ylm_norm(l, m);
+    std::vector<double> pair(16, 0.0);
+    if (a->pair) pair.assign(a->pair, a->pair + 16);
+    std::vector<double> sc2(sp->c2, sp->c2 + 16), sc3(sp->c3, sp->c3 + 512);
+
+    Arena& A = c->arena;
+    A.bytes.clear();
+    if (c->precision == MIX_FP64) {
+        c->o_c1 = A.put(c1);
+        c->o_S2 = A.put(S2);
+        c->o_W3 = A.put(W3);
+        c->o_gval = A.put(gval);
+        c->o_ylmk = A.put(ylmk);
+        c->o_pair = A.put(pair);
+        c->o_sc2 = A.put(sc2);
+        c->o_sc3 = A.put(sc3);
+    } else {
+        c->o_c1 = A.put(conv<float>(c1));
+        c->o_S2 = A.put(conv<float>(S2));
+        c->o_W3 = A.put(conv<float>(W3));
+        c->o_gval = A.put(conv<float>(gval));
+        c->o_ylmk = A.put(conv<float>(ylmk));
+        c->o_pair = A.put(conv<float>(pair));
+        c->o_sc2 = A.put(conv<float>(sc2));
+        c->o_sc3 = A.put(conv<float>(sc3));
+    }
+    c->o_tau = A.put(tau);
+    c->o_goff = A.put(goff);
+    c->o_gidx = A.put(gidx);
+    A.bytes.resize(align256(A.bytes.size()));
+    return MIX_OK;
+}
+
+template <typename T>
+void fill_tabs(mix_ctx* c, unsigned char* base, AceTab<T>& at, SplTab<T>& st) {
+    at.n = c->n;
+    at.L = c->L;
+    at.nu = c->nu;
+    at.nlm = (c->L + 1) * (c->L + 1);
+    at.ntau = c->ntau;
+    at.rc = c->ace_rc;
+    at.c1 = reinterpret_cast<const T*>(base + c->o_c1);
+    at.S2 = reinterpret_cast<const T*>(base + c->o_S2);
+    at.W3 = reinterpret_cast<const T*>(base + c->o_W3);
+    at.tau = reinterpret_cast<const int*>(base + c->o_tau);
+    at.goff = reinterpret_cast<const int*>(base + c->o_goff);
+    at.gidx = reinterpret_cast<const int*>(base + c->o_gidx);
+    at.gval = reinterpret_cast<const T*>(base + c->o_gval);
+    at.ylmk = reinterpret_cast<const T*>(base + c->o_ylmk);
+    at.pair = reinterpret_cast<const T*>(base + c->o_pair);
+    at.has_pair = c->has_pair ? 1 : 0;
+    st.rc = c->spl_rc;
+    st.rc3 = c->spl_rc3;
+    st.c2 = reinterpret_cast<const T*>(base + c->o_sc2);
+    st.c3 = reinterpret_cast<const T*>(base + c->o_sc3);
+}
+
+void layout(mix_ctx* c) {
+    const size_t N = (size_t)c->sys.n_atoms, cap = (size_t)c->cap, nc = (size_t)c->dev.cells.ncell;
+    const size_t v4 = c->precision == MIX_FP64 ? sizeof(double4) : sizeof(float4);
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o = align256(o + std::max<size_t>(bytes, 1));
+        return at;
+    };
+    c->o_status = take(SW_COUNT * sizeof(int));
+    c->o_xb = take(N * sizeof(double4));
+    c->o_cell_of = take(N * 4);
+    c->o_cell_count = take(nc * 4);
+    c->o_cell_start = take((nc + 1) * 4);
+    c->o_cell_fill = take(nc * 4);
+    c->o_cell_atoms = take(N * 4);
+    c->o_nnb = take(N * 4);
+    c->o_nbr = take(N * cap * 4);
+    c->o_rev = take(N * cap * 4);
+    c->o_lam = take(N * 8);
+    c->o_wgt = take(N * 8);
+    c->o_flags = take(N);
+    c->o_act_e = take(N * 4);
+    c->o_act_c = take(N * 4);
+    c->o_pos_e = take(N * 4);
+    c->o_pos_c = take(N * 4);
+    c->o_blk_e = take((size_t)c->dev.nblk * 4);
+    c->o_blk_c = take((size_t)c->dev.nblk * 4);
+    c->o_ge = take(N * cap * v4);
+    c->o_gc = take(N * cap * v4);
+    c->o_ee = take(N * 8);
+    c->o_ec = take(N * 8);
+    c->off_tab = take(c->arena.bytes.size());
+    c->ws_bytes = o;
+}
+
+int check_stream_error(mix_ctx* c, const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, what);
+    return MIX_OK;
+}
+
+// one force evaluation; integrate = 1 wraps it in a velocity-Verlet step
+int evaluate(mix_ctx* c, int integrate, double dt) {
+    const double h = 0.5 * dt * KAPPA / c->sys.mass;
+    cudaStream_t s = c->stream;
+    launch_disp(c->dev, s, integrate, dt, h, c->need_build ? 1 : 0);
+    c->need_build = false;
+    launch_build(c->dev, s);
+    launch_sets(c->dev, c->regions, s);
+    const void* at = c->precision == MIX_FP64 ? (const void*)&c->ace64 : (const void*)&c->ace32;
+    const void* st = c->precision == MIX_FP64 ? (const void*)&c->spl64 : (const void*)&c->spl32;
+    launch_ace(c->dev, at, c->precision, c->L, c->ace_smem, c->ace_grid, s);
+    launch_spline(c->dev, st, c->precision, c->spl_smem, c->spl_grid, s);
+    launch_gather(c->dev, c->precision, integrate, h, s);
+    return check_stream_error(c, "kernel launch");
+}
+
+int read_status(mix_ctx* c) {
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
+    e = cudaMemcpy(c->pinned, c->dev.status, SW_COUNT * sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "status read");
+    const int st = c->pinned[SW_STATUS];
+    if (st & ST_NBR_OVERFLOW)
+        return fail(c, MIX_EOVERFLOW, "neighbour list overflow: %d neighbours, capacity %d", c->pinned[SW_MAXNB], c->cap);
+    if (st & ST_NB3_OVERFLOW)
+        return fail(c, MIX_EOVERFLOW, "three-body neighbours %d exceed %d", c->pinned[SW_NB3MAX], NB3MAX);
+    if (st & ST_NONFINITE) return fail(c, MIX_ENUMERIC, "non-finite position or force");
+    if (st & ST_OUT_OF_BOX) return fail(c, MIX_EBOX, "an atom left the box in a non-periodic dimension");
+    if (st & ST_REV_MISSING) return fail(c, MIX_EINVAL, "asymmetric neighbour list");
+    return MIX_OK;
+}
+
+int copy_out(mix_ctx* c, void* dst, const void* src, size_t bytes) {
+    if (!dst || bytes == 0) return MIX_OK;
+    cudaError_t e = cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpy D2H");
+    return MIX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mix_init(const mix_system* sys, const mix_ace* a, const mix_spline* sp, const mix_options* opt,
+             void* cuda_stream, mix_ctx** out) {
+    if (!out) return MIX_EINVAL;
+    *out = nullptr;
+    if (!sys || !a || !sp || !opt) return MIX_EINVAL;
+    mix_ctx* c = new (std::nothrow) mix_ctx();
+    if (!c) return MIX_ENOMEM;
+    auto bad = [&](const char* msg) {
+        delete c;
+        (void)msg;
+        return MIX_EINVAL;
+    };
+    if (sys->n_atoms < 0 || sys->n_atoms > (int64_t)INT32_MAX / MAX_CAP) return bad("n_atoms");
+    if (!(sys->mass > 0)) return bad("mass");
+    if (a->n_rad < 1 || a->n_rad > MIX_MAX_NRAD || a->l_max < 0 || a->l_max > MIX_MAX_LMAX || a->nu_max < 1 ||
+        a->nu_max > 3 || !(a->r_cut > 0) || !a->c1 || (a->nu_max >= 2 && !a->c2) || (a->nu_max >= 3 && !a->c3))
+        return bad("expensive potential");
+    if (!(sp->r_cut > 0) || !(sp->r_cut3 > 0) || sp->r_cut3 > sp->r_cut || !sp->c2 || !sp->c3)
+        return bad("cheap potential");
+    for (int p = 0; p < 8; ++p)
+        for (int q = 0; q < 8; ++q)
+            for (int r = 0; r < 8; ++r)
+                if (sp->c3[(p * 8 + q) * 8 + r] != sp->c3[(q * 8 + p) * 8 + r]) return bad("c3 not symmetric");
+    if (opt->precision != MIX_FP64 && opt->precision != MIX_FP32) return bad("precision");
+    if (!(opt->skin > 0)) return bad("skin");
+    if (opt->blend != MIX_BLEND_LINEAR && opt->blend != MIX_BLEND_CUBIC) return bad("blend");
+    c->sys = *sys;
+    c->opt = *opt;
+    c->precision = opt->precision;
+    c->ace_rc = a->r_cut;
+    c->n = a->n_rad;
+    c->L = a->l_max;
+    c->nu = a->nu_max;
+    c->has_pair = a->pair != nullptr;
+    c->spl_rc = sp->r_cut;
+    c->spl_rc3 = sp->r_cut3;
+    c->stream = (cudaStream_t)cuda_stream;
+    const double rcmax = std::max(a->r_cut, sp->r_cut);
+    c->rlist = rcmax + opt->skin;
+    const double bufe = opt->buffer_exp > 0 ? opt->buffer_exp : a->r_cut;
+    const double bufc = opt->buffer_cheap > 0 ? opt->buffer_cheap : sp->r_cut;
+    if (bufe > rcmax || bufc > rcmax) return bad("buffer radius beyond the neighbour range");
+
+    Dev& d = c->dev;
+    std::memset(&d, 0, sizeof d);
+    d.n = sys->n_atoms;
+    double vol = 1.0;
+    for (int k = 0; k < 3; ++k) {
+        if (!(sys->box_len[k] > 0)) return bad("box");
+        d.box.lo[k] = sys->box_lo[k];
+        d.box.L[k] = sys->box_len[k];
+        d.box.invL[k] = 1.0 / sys->box_len[k];
+        d.box.per[k] = sys->periodic[k] ? 1 : 0;
+        int ncd = (int)std::floor(sys->box_len[k] / c->rlist);
+        if (d.box.per[k]) {
+            if (sys->box_lo[k] != 0.0) return bad("periodic box_lo must be 0");
+            if (ncd < 3 || sys->box_len[k] < 2.0 * c->rlist) return bad("periodic box too small");
+        } else if (ncd < 1) {
+            ncd = 1;
+        }
+        d.cells.nc[k] = ncd;
+        d.cells.invh[k] = (double)ncd / sys->box_len[k];
+        vol *= sys->box_len[k];
+    }
+    const int64_t ncell = (int64_t)d.cells.nc[0] * d.cells.nc[1] * d.cells.nc[2];
+    if (ncell > (1 << 26)) return bad("too many cells");
+    d.cells.ncell = (int)ncell;
+    if (opt->nbr_cap > 0) {
+        c->cap = opt->nbr_cap;
+    } else {
+        const double rho = vol > 0 ? (double)sys->n_atoms / vol : 0.0;
+        const double expect = rho * 4.0 / 3.0 * M_PI * c->rlist * c->rlist * c->rlist;
+        int cap = (int)std::ceil(1.4 * expect + 16.0);
+        cap = std::max(cap, 64);
+        c->cap = ((cap + 31) / 32) * 32;
+    }
+    if (c->cap > MAX_CAP) c->cap = MAX_CAP;
+    if (c->cap < 1) return bad("nbr_cap");
+    d.cap = c->cap;
+    d.rlist2 = c->rlist * c->rlist;
+    d.half_skin2 = 0.25 * opt->skin * opt->skin;
+    d.rce = a->r_cut;
+    d.rce2 = a->r_cut * a->r_cut;
+    d.rcc = sp->r_cut;
+    d.rcc2 = sp->r_cut * sp->r_cut;
+    d.rc3 = sp->r_cut3;
+    d.bufe2 = bufe * bufe;
+    d.bufc2 = bufc * bufc;
+    const int64_t nblk = (sys->n_atoms + SCAN_BLOCK - 1) / SCAN_BLOCK;
+    d.nblk = (int)(nblk > 0 ? nblk : 1);
+    std::memset(&c->regions, 0, sizeof c->regions);
+    c->regions.blend = opt->blend;
+    int st = build_tables(c, a, sp);
+    if (st) {
+        delete c;
+        return st;
+    }
+    layout(c);
+    cudaError_t e = ace_configure(c->precision, c->L, c->n, c->cap, &c->ace_smem, &c->ace_grid);
+    if (e != cudaSuccess) {
+        delete c;
+        return MIX_ECUDA;
+    }
+    e = spline_configure(c->precision, c->cap, &c->spl_smem, &c->spl_grid);
+    if (e != cudaSuccess) {
+        delete c;
+        return MIX_ECUDA;
+    }
+    e = cudaMallocHost((void**)&c->pinned, SW_COUNT * sizeof(int));
+    if (e != cudaSuccess) {
+        delete c;
+        return MIX_ECUDA;
+    }
+    c->bound = false;
+    c->need_build = true;
+    c->forces_valid = false;
+    c->steps = 0;
+    *out = c;
+    return MIX_OK;
+}
+
+int mix_workspace_bytes(const mix_ctx* c, size_t* bytes) {
+    if (!c || !bytes) return MIX_EINVAL;
+    *bytes = c->ws_bytes;
+    return MIX_OK;
+}
+
+int mix_bind(mix_ctx* c, double* x, double* v, double* f, void* ws) {
+    if (!c) return MIX_EINVAL;
+    if (c->sys.n_atoms > 0 && (!x || !v || !f)) return fail(c, MIX_EINVAL, "null state buffer");
+    if (!ws) return fail(c, MIX_EINVAL, "null workspace");
+    if (((uintptr_t)x | (uintptr_t)v | (uintptr_t)f) & 15) return fail(c, MIX_EINVAL, "state buffers must be 16-byte aligned");
+    if ((uintptr_t)ws & 255) return fail(c, MIX_EINVAL, "workspace must be 256-byte aligned");
+    unsigned char* w = static_cast<unsigned char*>(ws);
+    Dev& d = c->dev;
+    d.x = reinterpret_cast<double4*>(x);
+    d.v = reinterpret_cast<double4*>(v);
+    d.f = reinterpret_cast<double4*>(f);
+    d.status = reinterpret_cast<int*>(w + c->o_status);
+    d.xb = reinterpret_cast<double4*>(w + c->o_xb);
+    d.cell_of = reinterpret_cast<int*>(w + c->o_cell_of);
+    d.cell_count = reinterpret_cast<int*>(w + c->o_cell_count);
+    d.cell_start = reinterpret_cast<int*>(w + c->o_cell_start);
+    d.cell_fill = reinterpret_cast<int*>(w + c->o_cell_fill);
+    d.cell_atoms = reinterpret_cast<int*>(w + c->o_cell_atoms);
+    d.nnb = reinterpret_cast<int*>(w + c->o_nnb);
+    d.nbr = reinterpret_cast<int*>(w + c->o_nbr);
+    d.rev = reinterpret_cast<int*>(w + c->o_rev);
+    d.lam = reinterpret_cast<double*>(w + c->o_lam);
+    d.wgt = reinterpret_cast<double*>(w + c->o_wgt);
+    d.flags = reinterpret_cast<uint8_t*>(w + c->o_flags);
+    d.act_e = reinterpret_cast<int*>(w + c->o_act_e);
+    d.act_c = reinterpret_cast<int*>(w + c->o_act_c);
+    d.pos_e = reinterpret_cast<int*>(w + c->o_pos_e);
+    d.pos_c = reinterpret_cast<int*>(w + c->o_pos_c);
+    d.blk_e = reinterpret_cast<int*>(w + c->o_blk_e);
+    d.blk_c = reinterpret_cast<int*>(w + c->o_blk_c);
+    d.ge = w + c->o_ge;
+    d.gc = w + c->o_gc;
+    d.esite_e = reinterpret_cast<double*>(w + c->o_ee);
+    d.esite_c = reinterpret_cast<double*>(w + c->o_ec);
+    unsigned char* tb = w + c->off_tab;
+    fill_tabs<double>(c, tb, c->ace64, c->spl64);
+    fill_tabs<float>(c, tb, c->ace32, c->spl32);
+    cudaError_t e = cudaMemsetAsync(d.status, 0, SW_COUNT * sizeof(int), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.cell_count, 0, (size_t)d.cells.ncell * 4, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(tb, c->arena.bytes.data(), c->arena.bytes.size(), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "mix_bind");
+    c->bound = true;
+    c->need_build = true;
+    c->forces_valid = false;
+    c->steps = 0;
+    return MIX_OK;
+}
+
+int mix_set_regions(mix_ctx* c, const mix_region* r, int n) {
+    if (!c) return MIX_EINVAL;
+    if (n < 0 || n > MIX_MAX_REGIONS || (n > 0 && !r)) return fail(c, MIX_EINVAL, "region count");
+    Regions R;
+    std::memset(&R, 0, sizeof R);
+    R.n = n;
+    R.blend = c->opt.blend;
+    for (int k = 0; k < n; ++k) {
+        if (r[k].kind != MIX_REGION_SPHERE && r[k].kind != MIX_REGION_CYLINDER)
+            return fail(c, MIX_EINVAL, "region kind");
+        if (!(r[k].r_core >= 0) || !(r[k].ramp >= 0)) return fail(c, MIX_EINVAL, "region radii");
+        double* q = R.r[k];
+        q[0] = r[k].kind;
+        q[1] = r[k].centre[0];
+        q[2] = r[k].centre[1];
+        q[3] = r[k].centre[2];
+        const double ax = r[k].axis[0], ay = r[k].axis[1], az = r[k].axis[2];
+        const double nrm = std::sqrt(ax * ax + ay * ay + az * az);
+        if (r[k].kind == MIX_REGION_CYLINDER && !(nrm > 0)) return fail(c, MIX_EINVAL, "cylinder axis");
+        q[4] = nrm > 0 ? ax / nrm : ax;
+        q[5] = nrm > 0 ? ay / nrm : ay;
+        q[6] = nrm > 0 ? az / nrm : az;
+        q[7] = r[k].r_core;
+        q[8] = r[k].ramp;
+    }
+    c->regions = R;
+    c->forces_valid = false;
+    return MIX_OK;
+}
+
+int mix_forces(mix_ctx* c) {
+    if (!c) return MIX_EINVAL;
+    if (!c->bound) return fail(c, MIX_ESTATE, "mix_forces before mix_bind");
+    int st = evaluate(c, 0, 0.0);
+    if (st) return st;
+    c->forces_valid = true;
+    return MIX_OK;
+}
+
+int mix_step(mix_ctx* c, double dt, int nsteps) {
+    if (!c) return MIX_EINVAL;
+    if (!c->bound) return fail(c, MIX_ESTATE, "mix_step before mix_bind");
+    if (nsteps < 0 || !(dt > 0) || !std::isfinite(dt)) return fail(c, MIX_EINVAL, "dt / nsteps");
+    if (!c->forces_valid) {
+        int st = evaluate(c, 0, 0.0);
+        if (st) return st;
+        c->forces_valid = true;
+    }
+    for (int s = 0; s < nsteps; ++s) {
+        int st = evaluate(c, 1, dt);
+        if (st) return st;
+        c->steps++;
+    }
+    return MIX_OK;
+}
+
+int mix_step_host(mix_ctx* c, double* xh, double* vh, double* fh, double dt, int nsteps) {
+    if (!c) return MIX_EINVAL;
+    if (!c->bound) return fail(c, MIX_ESTATE, "mix_step_host before mix_bind");
+    const size_t bytes = (size_t)c->sys.n_atoms * sizeof(double4);
+    if (bytes && (!xh || !vh)) return fail(c, MIX_EINVAL, "null host buffer");
+    cudaError_t e = cudaMemcpyAsync(c->dev.x, xh, bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->dev.v, vh, bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && fh) e = cudaMemcpyAsync(c->dev.f, fh, bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "mix_step_host upload");
+    c->forces_valid = fh != nullptr;
+    int st = mix_step(c, dt, nsteps);
+    if (st) return st;
+    e = cudaMemcpyAsync(xh, c->dev.x, bytes, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(vh, c->dev.v, bytes, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && fh) e = cudaMemcpyAsync(fh, c->dev.f, bytes, cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "mix_step_host download");
+    return read_status(c);
+}
+
+int mix_sync(mix_ctx* c) {
+    if (!c) return MIX_EINVAL;
+    if (!c->bound) return MIX_OK;
+    return read_status(c);
+}
+
+int mix_get_stats(mix_ctx* c, mix_stats* s) {
+    if (!c || !s) return MIX_EINVAL;
+    if (!c->bound) return fail(c, MIX_ESTATE, "not bound");
+    int st = read_status(c);
+    const int* p = c->pinned;
+    s->n_core = p[SW_NCORE];
+    s->n_ramp = p[SW_NRAMP];
+    s->n_exp = p[SW_NEXP];
+    s->n_cheap = p[SW_NCHEAP];
+    s->rebuilds = p[SW_REBUILDS];
+    s->steps = c->steps;
+    s->max_neighbours = p[SW_MAXNB];
+    s->status_bits = p[SW_STATUS];
+    return st;
+}
+
+int mix_get_cells(mix_ctx* c, int* ncell3, int* cell_of) {
+    if (!c) return MIX_EINVAL;
+    if (!c->bound) return fail(c, MIX_ESTATE, "not bound");
+    int st = read_status(c);
+    if (st) return st;
+    if (ncell3)
+        for (int k = 0; k < 3; ++k) ncell3[k] = c->dev.cells.nc[k];
+    return copy_out(c, cell_of, c->dev.cell_of, (size_t)c->sys.n_atoms * 4);
+}
+
+int mix_get_neighbours(mix_ctx* c, int* cap_out, int* nnb, int* nbr, int* rev) {
+    if (!c) return MIX_EINVAL;
+    if (cap_out) *cap_out = c->cap;
+    if (!c->bound) return fail(c, MIX_ESTATE, "not bound");
+    int st = read_status(c);
+    if (st) return st;
+    const size_t N = (size_t)c->sys.n_atoms;
+    st = copy_out(c, nnb, c->dev.nnb, N * 4);
+    if (!st) st = copy_out(c, nbr, c->dev.nbr, N * c->cap * 4);
+    if (!st) st = copy_out(c, rev, c->dev.rev, N * c->cap * 4);
+    return st;
+}
+
+int mix_get_lambda(mix_ctx* c, double* lam, double* w) {
+    if (!c) return MIX_EINVAL;
+    if (!c->bound) return fail(c, MIX_ESTATE, "not bound");
+    int st = read_status(c);
+    if (st) return st;
+    const size_t N = (size_t)c->sys.n_atoms;
+    st = copy_out(c, lam, c->dev.lam, N * 8);
+    if (!st) st = copy_out(c, w, c->dev.wgt, N * 8);
+    return st;
+}
+
+int mix_get_sets(mix_ctx* c, uint8_t* flags, int* act_e, int64_t* n_e, int* act_c, int64_t* n_c) {
+    if (!c) return MIX_EINVAL;
+    if (!c->bound) return fail(c, MIX_ESTATE, "not bound");
+    int st = read_status(c);
+    if (st) return st;
+    const size_t N = (size_t)c->sys.n_atoms;
+    const int ne = c->pinned[SW_NEXP], nch = c->pinned[SW_NCHEAP];
+    if (n_e) *n_e = ne;
+    if (n_c) *n_c = nch;
+    st = copy_out(c, flags, c->dev.flags, N);
+    if (!st) st = copy_out(c, act_e, c->dev.act_e, (size_t)ne * 4);
+    if (!st) st = copy_out(c, act_c, c->dev.act_c, (size_t)nch * 4);
+    return st;
+}
+
+int mix_get_site_energies(mix_ctx* c, double* ee, double* ec) {
+    if (!c) return MIX_EINVAL;
+    if (!c->bound) return fail(c, MIX_ESTATE, "not bound");
+    int st = read_status(c);
+    if (st) return st;
+    const size_t N = (size_t)c->sys.n_atoms;
+    st = copy_out(c, ee, c->dev.esite_e, N * 8);
+    if (!st) st = copy_out(c, ec, c->dev.esite_c, N * 8);
+    return st;
+}
+
+int mix_get_state(mix_ctx* c, double* x, double* v, double* f, int64_t* step) {
+    if (!c) return MIX_EINVAL;
+    if (!c->bound) return fail(c, MIX_ESTATE, "not bound");
+    int st = read_status(c);
+    const size_t bytes = (size_t)c->sys.n_atoms * sizeof(double4);
+    int s2 = copy_out(c, x, c->dev.x, bytes);
+    if (!s2) s2 = copy_out(c, v, c->dev.v, bytes);
+    if (!s2) s2 = copy_out(c, f, c->dev.f, bytes);
+    if (step) *step = c->steps;
+    return st ? st : s2;
+}
+
+int mix_set_state(mix_ctx* c, const double* x, const double* v, const double* f, int64_t step, int forces_valid) {
+    if (!c) return MIX_EINVAL;
+    if (!c->bound) return fail(c, MIX_ESTATE, "not bound");
+    const size_t bytes = (size_t)c->sys.n_atoms * sizeof(double4);
+    cudaError_t e = cudaSuccess;
+    if (x) e = cudaMemcpyAsync(c->dev.x, x, bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && v) e = cudaMemcpyAsync(c->dev.v, v, bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && f) e = cudaMemcpyAsync(c->dev.f, f, bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "mix_set_state");
+    c->steps = step;
+    c->need_build = true;
+    c->forces_valid = forces_valid && f;
+    return MIX_OK;
+}
+
+int mix_destroy(mix_ctx* c) {
+    if (!c) return MIX_OK;
+    if (c->pinned) cudaFreeHost(c->pinned);
+    delete c;
+    return MIX_OK;
+}
+
+const char* mix_strerror(int code) {
+    switch (code) {
+        case MIX_OK: return "ok";
+        case MIX_EINVAL: return "invalid argument";
+        case MIX_ENOMEM: return "out of memory";
+        case MIX_ECUDA: return "CUDA error";
+        case MIX_EOVERFLOW: return "capacity overflow";
+        case MIX_ETIMEOUT: return "device wait timed out";
+        case MIX_ENUMERIC: return "non-finite value";
+        case MIX_ESTATE: return "call out of order";
+        case MIX_EBOX: return "atom outside a non-periodic box dimension";
+    }
+    return "unknown status";
+}
+
+const char* mix_last_error(const mix_ctx* c) { return c ? c->err.c_str() : ""; }
+
+}  // extern "C"

@@ -1,0 +1,156 @@
+// Internal definitions shared by the library's kernels and its host code.
+// Not part of the public interface (include/mix.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mix.h"
+
+namespace mixd {
+
+// ---------------------------------------------------------------------------
+// status words (int32, start of the workspace)
+enum StatusBits : int {
+    ST_NBR_OVERFLOW = 1,     // a neighbour list exceeded its capacity
+    ST_REV_MISSING = 2,      // list asymmetry (should never happen)
+    ST_NB3_OVERFLOW = 4,     // more than NB3MAX three-body neighbours
+    ST_NONFINITE = 8,        // non-finite position or force
+    ST_OUT_OF_BOX = 16,      // atom outside a non-periodic dimension
+};
+enum StatusWord : int {
+    SW_STATUS = 0,
+    SW_REBUILD = 1,     // 1: lists must be rebuilt in this evaluation
+    SW_MAXNB = 2,       // largest list length at the last build
+    SW_NEXP = 3,        // |A_exp|
+    SW_NCHEAP = 4,      // |A_cheap|
+    SW_REBUILDS = 5,    // number of builds
+    SW_NCORE = 6,
+    SW_NRAMP = 7,
+    SW_NLE = 8,         // lambda > 0
+    SW_NLC = 9,         // lambda < 1
+    SW_NB3MAX = 10,     // largest 3-body neighbour count seen
+    SW_COUNT = 64,
+};
+
+constexpr int NB3MAX = 32;          // three-body neighbours per atom handled on chip
+constexpr int MAX_CAP = 256;        // neighbour slots per atom
+constexpr int SCAN_BLOCK = 1024;    // atoms per block in the set compaction
+
+struct Box {
+    double lo[3], L[3], invL[3];
+    int per[3];
+};
+
+struct Cells {
+    int nc[3];
+    int ncell;
+    double invh[3];
+};
+
+struct Regions {
+    int n;
+    int blend;
+    double r[MIX_MAX_REGIONS][9];   // kind, centre[3], axis[3] (unit), r_core, ramp
+};
+
+// Pointers into the workspace plus scalar parameters, passed by value.
+struct Dev {
+    int64_t n;
+    int cap;
+    Box box;
+    Cells cells;
+    double rlist2;       // (rc_max + skin)^2
+    double half_skin2;   // (skin / 2)^2
+    double rce, rce2;    // expensive cutoff
+    double rcc, rcc2;    // cheap 2-body cutoff
+    double rc3;          // cheap 3-body cutoff
+    double bufe2, bufc2; // buffer radii squared
+    double4* x;
+    double4* v;
+    double4* f;
+    double4* xb;
+    int* status;
+    int* cell_of;
+    int* cell_count;
+    int* cell_start;
+    int* cell_fill;
+    int* cell_atoms;
+    int* nnb;
+    int* nbr;
+    int* rev;
+    double* lam;
+    double* wgt;
+    uint8_t* flags;
+    int* act_e;
+    int* act_c;
+    int* pos_e;
+    int* pos_c;
+    int* blk_e;
+    int* blk_c;
+    void* ge;            // [N][cap] real4: dE_i/dr_ij of the expensive potential
+    void* gc;            // [N][cap] real4: same for the cheap potential
+    double* esite_e;
+    double* esite_c;
+    int nblk;            // blocks of the compaction kernels
+};
+
+template <typename T> struct Vec4;
+template <> struct Vec4<double> { using type = double4; };
+template <> struct Vec4<float> { using type = float4; };
+
+// Expensive-potential tables in the workspace (element type T).
+template <typename T>
+struct AceTab {
+    int n, L, nu, nlm, ntau;
+    double rc;
+    const T* c1;        // [n]
+    const T* S2;        // [L+1][n][n]  symmetric: W2 + W2^T, W2 upper-triangular c2
+    const T* W3;        // [ntau][n][n][n]  masked nu=3 coefficients
+    const int* tau;     // [ntau][4]: l1, l2, l3, index of its first offset row
+    const int* goff;    // offset rows: for each tau, three orderings (by m3, m1, m2),
+                        // each 2l+2 entries (start index per m, then end)
+    const int* gidx;    // [nnz] packed (ma | mb << 8) of the two other m's (0-based)
+    const T* gval;      // [nnz]
+    const T* ylmk;      // [nlm] normalisation of Y_lm times sqrt2 for m != 0
+    const T* pair;      // [16] pair-term B-spline coefficients
+    int has_pair;
+};
+
+template <typename T>
+struct SplTab {
+    double rc, rc3;
+    const T* c2;    // [16]
+    const T* c3;    // [8][8][8]
+};
+
+// ---------------------------------------------------------------------------
+// bit-reproducible geometry: explicit round-to-nearest ops, no FMA contraction
+
+__device__ __forceinline__ double mi_comp(double t, double L, double invL, int per) {
+    if (per) t = __dsub_rn(t, __dmul_rn(L, rint(__dmul_rn(t, invL))));
+    return t;
+}
+
+// d = x_j - x_i with the minimum image in periodic dimensions
+__device__ __forceinline__ void delta_rn(const Box& b, const double4& xi, const double4& xj, double d[3]) {
+    d[0] = mi_comp(__dsub_rn(xj.x, xi.x), b.L[0], b.invL[0], b.per[0]);
+    d[1] = mi_comp(__dsub_rn(xj.y, xi.y), b.L[1], b.invL[1], b.per[1]);
+    d[2] = mi_comp(__dsub_rn(xj.z, xi.z), b.L[2], b.invL[2], b.per[2]);
+}
+
+__device__ __forceinline__ double norm2_rn(const double d[3]) {
+    return __dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2]));
+}
+
+__device__ __forceinline__ int cell_coord(const Box& b, const Cells& c, double x, int d) {
+    double s = __dmul_rn(__dsub_rn(x, b.lo[d]), c.invh[d]);
+    int q = (int)floor(s);
+    q = q < 0 ? 0 : q;
+    q = q > c.nc[d] - 1 ? c.nc[d] - 1 : q;
+    return q;
+}
+
+__device__ __forceinline__ void set_status(int* st, int bits) { atomicOr(st + SW_STATUS, bits); }
+
+}  // namespace mixd

@@ -1,0 +1,28 @@
+// Host-side launchers of the library's kernels (one definition per .cu file).
+#pragma once
+
+#include "mix_dev.cuh"
+
+namespace mixd {
+
+// lists (k_lists.cu)
+void launch_disp(const Dev& d, cudaStream_t s, int integrate, double dt, double h, int force_rebuild);
+void launch_build(const Dev& d, cudaStream_t s);
+
+// weights, sets, compaction (k_sets.cu)
+void launch_sets(const Dev& d, const Regions& r, cudaStream_t s);
+
+// expensive potential (k_ace.cu); returns cudaSuccess or the launch error
+cudaError_t ace_configure(int precision, int L, int n, int cap, size_t* smem, int* grid);
+void launch_ace(const Dev& d, const void* tab, int precision, int L, size_t smem, int grid, cudaStream_t s);
+
+// cheap potential (k_spline.cu)
+cudaError_t spline_configure(int precision, int cap, size_t* smem, int* grid);
+void launch_spline(const Dev& d, const void* tab, int precision, size_t smem, int grid, cudaStream_t s);
+
+// gather + blend + second half-kick (k_gather.cu)
+void launch_gather(const Dev& d, int precision, int integrate, double h, cudaStream_t s);
+
+int sm_count();
+
+}  // namespace mixd

@@ -58,7 +58,7 @@ _SCALES_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "scales.
 @dataclass
 class Region:
     """A core region: points closer than r_core get weight 1, a ramp of width
-    `ramp` follows (Sec. 4.1, Alg. 2 in its geometric reading)."""
+    `ramp` follows (Sec. 4.4, Alg. 2 in its geometric reading)."""
     kind: int
     centre: Tuple[float, float, float]
     axis: Tuple[float, float, float] = (0.0, 0.0, 1.0)

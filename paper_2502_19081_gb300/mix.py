@@ -1,0 +1,319 @@
+"""Python binding of the C ABI in include/mix.h (ctypes; marshalling only).
+
+Every step of the mixed MD path runs in the CUDA library libmix.so built from
+csrc/; this module only converts arguments, owns the torch device buffers the
+library borrows (positions, velocities, forces, workspace) and turns status
+codes into exceptions.  There is no CPU fallback: if the library is missing
+or no CUDA device is present, constructing a Context raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import inputs as I
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libmix.so")
+
+MIX_OK = 0
+MIX_EINVAL = -1
+MIX_ENOMEM = -2
+MIX_ECUDA = -3
+MIX_EOVERFLOW = -4
+MIX_ETIMEOUT = -5
+MIX_ENUMERIC = -6
+MIX_ESTATE = -7
+MIX_EBOX = -8
+
+MIX_FP64 = 0
+MIX_FP32 = 1
+MIX_BLEND_LINEAR = 0
+MIX_BLEND_CUBIC = 1
+
+# functions declared in include/mix.h
+EXPORTS = [
+    "mix_init", "mix_workspace_bytes", "mix_bind", "mix_set_regions", "mix_forces", "mix_step",
+    "mix_step_host", "mix_sync", "mix_get_stats", "mix_get_cells", "mix_get_neighbours",
+    "mix_get_lambda", "mix_get_sets", "mix_get_site_energies", "mix_get_state", "mix_set_state",
+    "mix_destroy", "mix_strerror", "mix_last_error",
+]
+
+
+class MixError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{msg} (status {code})")
+        self.code = code
+
+
+class mix_system(ctypes.Structure):
+    _fields_ = [("n_atoms", ctypes.c_int64), ("box_lo", ctypes.c_double * 3), ("box_len", ctypes.c_double * 3),
+                ("periodic", ctypes.c_int * 3), ("mass", ctypes.c_double)]
+
+
+class mix_ace(ctypes.Structure):
+    _fields_ = [("r_cut", ctypes.c_double), ("n_rad", ctypes.c_int), ("l_max", ctypes.c_int),
+                ("nu_max", ctypes.c_int), ("c1", ctypes.POINTER(ctypes.c_double)),
+                ("c2", ctypes.POINTER(ctypes.c_double)), ("c3", ctypes.POINTER(ctypes.c_double)),
+                ("pair", ctypes.POINTER(ctypes.c_double))]
+
+
+class mix_spline(ctypes.Structure):
+    _fields_ = [("r_cut", ctypes.c_double), ("r_cut3", ctypes.c_double),
+                ("c2", ctypes.POINTER(ctypes.c_double)), ("c3", ctypes.POINTER(ctypes.c_double))]
+
+
+class mix_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("skin", ctypes.c_double), ("blend", ctypes.c_int),
+                ("buffer_exp", ctypes.c_double), ("buffer_cheap", ctypes.c_double), ("nbr_cap", ctypes.c_int)]
+
+
+class mix_region(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("centre", ctypes.c_double * 3), ("axis", ctypes.c_double * 3),
+                ("r_core", ctypes.c_double), ("ramp", ctypes.c_double)]
+
+
+class mix_stats(ctypes.Structure):
+    _fields_ = [("n_core", ctypes.c_int64), ("n_ramp", ctypes.c_int64), ("n_exp", ctypes.c_int64),
+                ("n_cheap", ctypes.c_int64), ("rebuilds", ctypes.c_int64), ("steps", ctypes.c_int64),
+                ("max_neighbours", ctypes.c_int), ("status_bits", ctypes.c_int)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """Load libmix.so (built by build() / __graft_entry__.build()); raises if absent."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                                   "(run python -m paper_2502_19081_gb300.build)")
+            L = ctypes.CDLL(LIB_PATH)
+            P = ctypes.c_void_p
+            dp = ctypes.POINTER(ctypes.c_double)
+            ip = ctypes.POINTER(ctypes.c_int)
+            i64p = ctypes.POINTER(ctypes.c_int64)
+            L.mix_init.argtypes = [ctypes.POINTER(mix_system), ctypes.POINTER(mix_ace), ctypes.POINTER(mix_spline),
+                                   ctypes.POINTER(mix_options), P, ctypes.POINTER(P)]
+            L.mix_workspace_bytes.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
+            L.mix_bind.argtypes = [P, P, P, P, P]
+            L.mix_set_regions.argtypes = [P, ctypes.POINTER(mix_region), ctypes.c_int]
+            L.mix_forces.argtypes = [P]
+            L.mix_step.argtypes = [P, ctypes.c_double, ctypes.c_int]
+            L.mix_step_host.argtypes = [P, dp, dp, dp, ctypes.c_double, ctypes.c_int]
+            L.mix_sync.argtypes = [P]
+            L.mix_get_stats.argtypes = [P, ctypes.POINTER(mix_stats)]
+            L.mix_get_cells.argtypes = [P, ip, ip]
+            L.mix_get_neighbours.argtypes = [P, ip, ip, ip, ip]
+            L.mix_get_lambda.argtypes = [P, dp, dp]
+            L.mix_get_sets.argtypes = [P, ctypes.POINTER(ctypes.c_uint8), ip, i64p, ip, i64p]
+            L.mix_get_site_energies.argtypes = [P, dp, dp]
+            L.mix_get_state.argtypes = [P, dp, dp, dp, i64p]
+            L.mix_set_state.argtypes = [P, dp, dp, dp, ctypes.c_int64, ctypes.c_int]
+            L.mix_destroy.argtypes = [P]
+            L.mix_strerror.restype = ctypes.c_char_p
+            L.mix_strerror.argtypes = [ctypes.c_int]
+            L.mix_last_error.restype = ctypes.c_char_p
+            L.mix_last_error.argtypes = [P]
+            _lib = L
+    return _lib
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _ip(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class Context:
+    """One mixed-MD trajectory on one CUDA device, backed by libmix.so.
+
+    Positions, velocities, forces ([N, 4] float64) and the workspace are torch
+    tensors owned here and lent to the library."""
+
+    def __init__(self, workload: "I.Workload", precision: int = MIX_FP64, device: str = "cuda:0",
+                 nbr_cap: int = 0, blend: int = MIX_BLEND_LINEAR, buffer_exp: float = 0.0,
+                 buffer_cheap: float = 0.0, skin: Optional[float] = None, regions: Optional[Sequence] = None,
+                 stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the mixed-MD path runs only on the GPU")
+        self._torch = torch
+        self.L = lib()
+        self.device = torch.device(device)
+        self.wl = workload
+        s = workload.system
+        self.n = int(s.n)
+        self.precision = precision
+        self._keep = []
+        sysd = mix_system(self.n, (ctypes.c_double * 3)(*s.box_lo), (ctypes.c_double * 3)(*s.box_len),
+                          (ctypes.c_int * 3)(*[int(p) for p in s.periodic]), float(s.mass))
+        a = workload.ace
+        c1, c2, c3, pair = _f64(a.c1), _f64(a.c2), _f64(a.c3), _f64(a.pair)
+        sp = workload.spline
+        s2, s3 = _f64(sp.c2), _f64(sp.c3)
+        self._keep += [c1, c2, c3, pair, s2, s3]
+        aced = mix_ace(float(a.r_cut), int(a.n_rad), int(a.l_max), int(a.nu_max), _dp(c1), _dp(c2), _dp(c3),
+                       _dp(pair))
+        spld = mix_spline(float(sp.r_cut), float(sp.r_cut3), _dp(s2), _dp(s3))
+        opt = mix_options(int(precision), float(workload.skin if skin is None else skin), int(blend),
+                          float(buffer_exp), float(buffer_cheap), int(nbr_cap))
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            h = ctypes.c_void_p()
+            st = self.L.mix_init(ctypes.byref(sysd), ctypes.byref(aced), ctypes.byref(spld), ctypes.byref(opt),
+                                 ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+            if st != MIX_OK:
+                raise MixError(st, "mix_init: " + self.L.mix_strerror(st).decode())
+            self.h = h
+            nb = ctypes.c_size_t()
+            self._check(self.L.mix_workspace_bytes(self.h, ctypes.byref(nb)), "mix_workspace_bytes")
+            self.ws_bytes = int(nb.value)
+            self.x = torch.zeros((max(self.n, 1), 4), dtype=torch.float64, device=self.device)
+            self.v = torch.zeros_like(self.x)
+            self.f = torch.zeros_like(self.x)
+            self.ws = torch.empty(max(self.ws_bytes, 256), dtype=torch.uint8, device=self.device)
+            if self.n:
+                self.x[:self.n].copy_(torch.from_numpy(_f64(s.x)))
+                self.v[:self.n].copy_(torch.from_numpy(_f64(s.v)))
+            torch.cuda.synchronize(self.device)
+            self._check(self.L.mix_bind(self.h, ctypes.c_void_p(self.x.data_ptr()), ctypes.c_void_p(self.v.data_ptr()),
+                                        ctypes.c_void_p(self.f.data_ptr()), ctypes.c_void_p(self.ws.data_ptr())),
+                        "mix_bind")
+            self.set_regions(workload.regions if regions is None else regions)
+        cap = ctypes.c_int()
+        self.L.mix_get_neighbours(self.h, ctypes.byref(cap), None, None, None)
+        self.cap = int(cap.value)
+
+    # -- plumbing -----------------------------------------------------------
+    def _check(self, st: int, what: str):
+        if st != MIX_OK:
+            msg = self.L.mix_last_error(self.h).decode() if getattr(self, "h", None) else ""
+            raise MixError(st, f"{what}: {self.L.mix_strerror(st).decode()}: {msg}")
+
+    def close(self):
+        h = getattr(self, "h", None)
+        if h:
+            self.L.mix_destroy(h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- calls --------------------------------------------------------------
+    def set_regions(self, regions):
+        arr = (mix_region * max(len(regions), 1))()
+        for k, r in enumerate(regions):
+            arr[k] = mix_region(int(r.kind), (ctypes.c_double * 3)(*r.centre), (ctypes.c_double * 3)(*r.axis),
+                                float(r.r_core), float(r.ramp))
+        self._check(self.L.mix_set_regions(self.h, arr, len(regions)), "mix_set_regions")
+
+    def forces(self):
+        self._check(self.L.mix_forces(self.h), "mix_forces")
+        return self.f[:self.n]
+
+    def step(self, dt: float, nsteps: int = 1):
+        self._check(self.L.mix_step(self.h, float(dt), int(nsteps)), "mix_step")
+
+    def step_host(self, x: np.ndarray, v: np.ndarray, f: Optional[np.ndarray], dt: float, nsteps: int = 1):
+        """End-to-end call with host arrays ([N,4] float64, C-contiguous; updated in place)."""
+        self._check(self.L.mix_step_host(self.h, _dp(x), _dp(v), _dp(f) if f is not None else None, float(dt),
+                                         int(nsteps)), "mix_step_host")
+
+    def sync(self):
+        self._check(self.L.mix_sync(self.h), "mix_sync")
+
+    def stats(self, check: bool = True) -> dict:
+        s = mix_stats()
+        st = self.L.mix_get_stats(self.h, ctypes.byref(s))
+        if check:
+            self._check(st, "mix_get_stats")
+        return {k: getattr(s, k) for k, _ in mix_stats._fields_}
+
+    def cells(self):
+        nc = np.zeros(3, dtype=np.int32)
+        cid = np.zeros(max(self.n, 1), dtype=np.int32)
+        self._check(self.L.mix_get_cells(self.h, _ip(nc), _ip(cid)), "mix_get_cells")
+        return nc, cid[:self.n]
+
+    def neighbours(self):
+        nnb = np.zeros(max(self.n, 1), dtype=np.int32)
+        nbr = np.zeros((max(self.n, 1), self.cap), dtype=np.int32)
+        rev = np.zeros((max(self.n, 1), self.cap), dtype=np.int32)
+        cap = ctypes.c_int()
+        self._check(self.L.mix_get_neighbours(self.h, ctypes.byref(cap), _ip(nnb), _ip(nbr), _ip(rev)),
+                    "mix_get_neighbours")
+        return nnb[:self.n], nbr[:self.n], rev[:self.n]
+
+    def lam(self):
+        lam = np.zeros(max(self.n, 1))
+        w = np.zeros(max(self.n, 1))
+        self._check(self.L.mix_get_lambda(self.h, _dp(lam), _dp(w)), "mix_get_lambda")
+        return lam[:self.n], w[:self.n]
+
+    def sets(self):
+        fl = np.zeros(max(self.n, 1), dtype=np.uint8)
+        ae = np.zeros(max(self.n, 1), dtype=np.int32)
+        ac = np.zeros(max(self.n, 1), dtype=np.int32)
+        ne = ctypes.c_int64()
+        nc = ctypes.c_int64()
+        self._check(self.L.mix_get_sets(self.h, fl.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), _ip(ae),
+                                        ctypes.byref(ne), _ip(ac), ctypes.byref(nc)), "mix_get_sets")
+        return fl[:self.n], ae[:ne.value], ac[:nc.value]
+
+    def site_energies(self):
+        ee = np.zeros(max(self.n, 1))
+        ec = np.zeros(max(self.n, 1))
+        self._check(self.L.mix_get_site_energies(self.h, _dp(ee), _dp(ec)), "mix_get_site_energies")
+        return ee[:self.n], ec[:self.n]
+
+    def get_state(self):
+        x = np.zeros((max(self.n, 1), 4))
+        v = np.zeros_like(x)
+        f = np.zeros_like(x)
+        st = ctypes.c_int64()
+        self._check(self.L.mix_get_state(self.h, _dp(x), _dp(v), _dp(f), ctypes.byref(st)), "mix_get_state")
+        return x[:self.n], v[:self.n], f[:self.n], int(st.value)
+
+    def set_state(self, x, v, f=None, step: int = 0):
+        x = _f64(x)
+        v = _f64(v)
+        fa = _f64(f) if f is not None else None
+        self._check(self.L.mix_set_state(self.h, _dp(x), _dp(v), _dp(fa) if fa is not None else None, int(step),
+                                         1 if fa is not None else 0), "mix_set_state")
+
+
+def open_context(workload, precision: int = MIX_FP64, retries: int = 2, **kw) -> Context:
+    """Create a context and evaluate forces once; if the neighbour capacity
+    overflows, recreate it with room for the observed maximum."""
+    cap = kw.pop("nbr_cap", 0)
+    for _ in range(retries + 1):
+        ctx = Context(workload, precision=precision, nbr_cap=cap, **kw)
+        try:
+            ctx.forces()
+            ctx.sync()
+            return ctx
+        except MixError as e:
+            if e.code != MIX_EOVERFLOW:
+                raise
+            st = ctx.stats(check=False)
+            need = max(int(st["max_neighbours"]), ctx.cap + 1)
+            ctx.close()
+            cap = min(256, ((int(need * 1.25) + 31) // 32) * 32)
+    raise MixError(MIX_EOVERFLOW, "neighbour capacity could not be sized")

@@ -4,7 +4,7 @@ Each check compares the oracle with something other than itself: scipy's
 spherical harmonics, quadrature of scipy-built Y products, the addition theorem
 plus sphere quadrature for the many-body basis, scipy B-splines for the cheap
 potential, central finite differences for the gradients (the force equation of
-Sec. 4.2 is a derivative of site energies), and exact invariances.
+Sec. 4.5 is a derivative of site energies), and exact invariances.
 """
 import math
 

@@ -4,11 +4,11 @@
 * weights: closed form of the linear ramp (Alg. 2) at chosen distances, max
   over overlapping regions (Alg. 2 takes the max), cylinder distance;
 * sets: brute-force enumeration of Lambda_k and its buffer (buffer-set
-  equation, Sec. 4.2; Alg. 3);
+  equation, Sec. 4.5; Alg. 3);
 * forces: central differences of the total energy, zero net force, rigid
   translation/rotation/permutation invariance for the pure potentials;
 * mixing: the method (each potential on its set plus a one-cutoff buffer,
-  Alg. 4) equals the plain blend of full forces (buffer sufficiency, Sec. 4.2),
+  Alg. 4) equals the plain blend of full forces (buffer sufficiency, Sec. 4.5),
   with a negative control; lambda = 1 and lambda = 0 reduce to the pure forces;
 * velocity Verlet: time reversibility and the dt^2 energy-error law.
 """
