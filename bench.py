@@ -1,0 +1,415 @@
+#!/usr/bin/env python
+"""Throughput of the spatially mixed MD step (arXiv 2502.19081 force mixing)
+on GB300, in atom-steps/s.
+
+A step is one velocity-Verlet step of the whole hot path: skin test and (when
+needed) cell/neighbour-list rebuild, blend weights, evaluated sets with their
+buffers, expensive potential on its set, cheap potential on its set, atomics-free
+gather + blend, second half-kick.  Workload: bcc Fe 20x20x10 + <110> dumbbell
+(8001 atoms), seeded synthetic positions and potentials.
+
+Timing: W untimed warm-up steps, then K steps; before every timed step a 512 MB
+buffer is written to flush L2 (129 MB), outside the timed interval; each step is
+timed on the device with CUDA events the library records on its stream around
+its kernel groups.  Multi-GPU (torchrun): independent replicas, one per rank,
+no collective on the data path; value = atoms x steps x ranks / max rank time.
+
+--impl reference times the FP64 CPU oracle (the program the GPU path is checked
+against) on the host cores, on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "mixed-MD atom-steps/s, FP64 plain vs FP32/BF16 at ≤1e-3 eV/Å; p50/p99 step ms"
+UNIT = "atom-steps/s"
+GATE = 1e-3
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="fe_dumbbell_8001")
+    p.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    p.add_argument("--secondary-steps", type=int, default=20)
+    p.add_argument("--e2e-steps", type=int, default=20)
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_workload(name: str, rank: int):
+    from paper_2502_19081_gb300 import inputs as I
+    base = {"si_vacancy_215": 1, "fe_dumbbell_8001": 2, "fe_screw_256000": 3}[name]
+    return I.workload(name, seed=base + 1000 * rank)
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work model (per evaluated atom)
+
+
+def exp_flops_per_atom(wl, info, nnb_rc: float) -> float:
+    """Linear ACE: density 2 n nlm Nnb; pair gradients (4 n nlm + 8 nlm) Nnb;
+    nu=2 readout + adjoint 4 n^2 nlm; nu=3 readout 2 nnz(G) n^2 + 2 (2l3+1) n^3
+    per l-triple, three times that with the adjoint."""
+    a = wl.ace
+    n, nlm = a.n_rad, (a.l_max + 1) ** 2
+    f = 2.0 * n * nlm * nnb_rc + (4.0 * n * nlm + 8.0 * nlm) * nnb_rc
+    if a.nu_max >= 2:
+        f += 4.0 * n * n * nlm
+    if a.nu_max >= 3:
+        f += 3.0 * (2.0 * info["gaunt_nnz"] * n * n + 2.0 * info["tau_dim3_sum"] * n ** 3)
+    return f
+
+
+def cheap_flops_per_atom(nnb2: float, n3: float) -> float:
+    """2+3-body spline: about 40 flops per pair and 650 per triplet."""
+    return 40.0 * nnb2 + 650.0 * n3 * (n3 - 1) / 2.0
+
+
+def neighbour_stats(ctx, wl):
+    """Mean neighbours inside each cutoff over the evaluated sets (host-side
+    analysis of the device lists, outside any timed region)."""
+    x, _, _, _ = ctx.get_state()
+    nnb, nbr, _ = ctx.neighbours()
+    fl, ae, ac = ctx.sets()
+    L = wl.system.box_len
+    per = np.array(wl.system.periodic, dtype=bool)
+
+    def counts(idx, rc):
+        if len(idx) == 0:
+            return 0.0
+        out = []
+        for i in idx:
+            js = nbr[i, :nnb[i]]
+            d = x[js, :3] - x[i, :3]
+            d[:, per] -= L[per] * np.rint(d[:, per] / L[per])
+            out.append(int(np.sum(np.sum(d * d, axis=1) < rc * rc)))
+        return float(np.mean(out))
+
+    se = ae if len(ae) <= 4000 else ae[:: max(1, len(ae) // 4000)]
+    sc = ac if len(ac) <= 4000 else ac[:: max(1, len(ac) // 4000)]
+    return {"n_exp": int(len(ae)), "n_cheap": int(len(ac)), "nnb_exp_rc": counts(se, wl.ace.r_cut),
+            "nnb_cheap_rc": counts(sc, wl.spline.r_cut), "n3_cheap": counts(sc, wl.spline.r_cut3)}
+
+
+# ---------------------------------------------------------------------------
+# clocks
+
+
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.path = None
+        self.idx = gpu_index
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.idx)], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+
+
+def run_precision(mix, torch, wl, precision, steps, warmup, flush):
+    ctx = mix.open_context(wl, precision=precision)
+    for _ in range(warmup):
+        ctx.step(wl.dt, 1)
+    ctx.sync()
+    launches0 = ctx.info()["launches"]
+    ctx.profile(True)
+    per_step = []
+    for _ in range(steps):
+        flush()
+        ctx.step(wl.dt, 1)
+        _, last, _ = ctx.get_profile()
+        per_step.append(float(np.sum(last)))
+    tot, _, nev = ctx.get_profile()
+    ctx.profile(False)
+    ctx.sync()
+    launches = ctx.info()["launches"] - launches0
+    return ctx, np.array(per_step), tot, nev, launches
+
+
+def cpu_baseline(wl, seconds: float):
+    """The oracle as it stands (C, OpenMP over sites), on this host's cores, on
+    consecutive mixed velocity-Verlet steps of the same workload."""
+    import oracle
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    oracle.set_threads(cores)
+    m = oracle.Model(wl)
+    x, v = wl.system.x, wl.system.v
+    F, _, _ = m.forces(x, oracle.MODE_METHOD)
+    done = 0
+    t0 = time.perf_counter()
+    while True:
+        x, v, F, _ = m.md(x, v, F, wl.dt, 1, oracle.MODE_METHOD)
+        done += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or done >= 50:
+            break
+    return {"value": wl.system.n * done / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{done} mixed velocity-Verlet steps of {wl.name} ({wl.system.n} atoms), FP64, "
+                      f"OpenMP over sites, {el:.1f} s"}
+
+
+def ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2502_19081_gb300 import build as B
+    from paper_2502_19081_gb300 import mix
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    B.build()
+    wl = make_workload(args.workload, rank)
+    prec = mix.MIX_FP32 if args.precision == "fp32" else mix.MIX_FP64
+    other = mix.MIX_FP64 if prec == mix.MIX_FP32 else mix.MIX_FP32
+    flush_buf = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    def flush():
+        flush_buf.zero_()
+
+    peaks = {p: mix.fma_peak(p) for p in (mix.MIX_FP64, mix.MIX_FP32)}
+
+    # accuracy of the headline precision against the FP64 path at the same positions
+    c64 = mix.open_context(wl, precision=mix.MIX_FP64)
+    x0, _, F64, _ = c64.get_state()
+    nstat = neighbour_stats(c64, wl)
+    info = c64.info()
+    c64.close()
+    cp = mix.open_context(wl, precision=prec)
+    _, _, Fp, _ = cp.get_state()
+    cp.close()
+    ferr = float(np.abs(Fp[:, :3] - F64[:, :3]).max())
+
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    ctx, per, tot, nev, launches = run_precision(mix, torch, wl, prec, args.steps, args.warmup, flush)
+    clk = clocks.stop()
+    total_ms = float(per.sum())
+    t_all = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t_all, op=dist.ReduceOp.MAX)
+    total_max = float(t_all.item())
+    value = wl.system.n * args.steps * world / (total_max * 1e-3)
+
+    # end to end through the host-buffer entry point (pinned host arrays)
+    n = wl.system.n
+    hx = torch.empty((n, 4), dtype=torch.float64, pin_memory=True)
+    hv = torch.empty_like(hx, pin_memory=True)
+    hf = torch.empty_like(hx, pin_memory=True)
+    xs, vs, fs, _ = ctx.get_state()
+    hx.numpy()[:] = xs
+    hv.numpy()[:] = vs
+    hf.numpy()[:] = fs
+    e2e_s = []
+    for _ in range(max(1, args.e2e_steps)):
+        flush()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.step_host(hx.numpy(), hv.numpy(), hf.numpy(), wl.dt, 1)
+        e2e_s.append(time.perf_counter() - t0)
+    e2e_val = n / float(np.mean(e2e_s))
+    ctx.close()
+
+    # the other precision, shorter
+    c2, per2, tot2, nev2, _ = run_precision(mix, torch, wl, other, args.secondary_steps, max(3, args.warmup // 2),
+                                            flush)
+    c2.close()
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    phase_ms = tot / max(nev, 1)
+    dom = int(np.argmax(phase_ms))
+    names = mix.PHASE_NAMES
+    pe = exp_flops_per_atom(wl, info, nstat["nnb_exp_rc"])
+    pc = cheap_flops_per_atom(nstat["nnb_cheap_rc"], nstat["n3_cheap"])
+    peak = peaks[prec]
+    if names[dom] in ("exp", "cheap"):
+        fl = pe * nstat["n_exp"] if names[dom] == "exp" else pc * nstat["n_cheap"]
+        ach = fl / (phase_ms[dom] * 1e-3)
+        roof = {"kernel": "k_ace" if names[dom] == "exp" else "k_spline", "bound": "alu",
+                "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": None, "algorithmic_flops_per_launch": fl,
+                "peak_source": f"measured FMA microbenchmark ({'fp32' if prec == mix.MIX_FP32 else 'fp64'}), "
+                               "mix_fma_peak"}
+    else:
+        peaks_file = os.path.join(ROOT, "MEASURED_PEAKS.json")
+        hbm = json.load(open(peaks_file))["hbm_gbs"] if os.path.exists(peaks_file) else 6800.0
+        byts = n * 400.0
+        ach = byts / (phase_ms[dom] * 1e-3) / 1e9
+        roof = {"kernel": names[dom], "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "traffic": None}
+    kern = {names[p]: {"ms": float(phase_ms[p]), "share": float(phase_ms[p] / phase_ms.sum())}
+            for p in range(len(names))}
+    pname = "f32" if prec == mix.MIX_FP32 else "f64"
+    oname = "f64" if prec == mix.MIX_FP32 else "f32"
+    out = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total_max / args.steps,
+        "p50_ms": float(np.percentile(per, 50)),
+        "p99_ms": float(np.percentile(per, 99)),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": pname,
+        "data": "synthetic (seeded lattice, defect, thermal displacements and potential coefficients)",
+        "config": {"workload": wl.name, "n_atoms": n, "potential_arithmetic": pname, "integration": "f64",
+                   "expensive": f"linear ACE n={wl.ace.n_rad} lmax={wl.ace.l_max} body order {wl.ace.nu_max + 1}",
+                   "cheap": "2+3-body cubic B-spline", "l2": "flushed before every timed step (512 MB write)",
+                   "parallelism": f"replicas x{world}", "evaluated_exp": nstat["n_exp"],
+                   "evaluated_cheap": nstat["n_cheap"]},
+        "force_err_vs_fp64_eV_per_A": ferr,
+        "gate_eV_per_A": GATE,
+        "within_gate": bool(ferr <= GATE),
+        oname + "_path": {"value": wl.system.n * len(per2) / (per2.sum() * 1e-3), "ms_per_step": float(per2.mean()),
+                          "p50_ms": float(np.percentile(per2, 50)), "p99_ms": float(np.percentile(per2, 99)),
+                          "kernels_ms": {names[p]: float(tot2[p] / max(nev2, 1)) for p in range(len(names))}},
+        "roofline": roof,
+        "kernels": kern,
+        "fma_peak_tflops": {"fp64": peaks[mix.MIX_FP64] / 1e12, "fp32": peaks[mix.MIX_FP32] / 1e12},
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 3 * n * 32, "d2h_bytes_per_step": 3 * n * 32,
+                "steps": len(e2e_s), "entry": "mix_step_host (x, v, f in and out, pinned host memory)"},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    if not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
+    print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def reference(args):
+    """The oracle arm: FP64 C oracle on the host cores, same workload and metric."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    wl = make_workload(args.workload, 0)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    oracle.set_threads(cores)
+    m = oracle.Model(wl)
+    x, v = wl.system.x, wl.system.v
+    F, _, _ = m.forces(x, oracle.MODE_METHOD)
+    for _ in range(args.warmup):
+        x, v, F, _ = m.md(x, v, F, wl.dt, 1, oracle.MODE_METHOD)
+    per = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        x, v, F, _ = m.md(x, v, F, wl.dt, 1, oracle.MODE_METHOD)
+        per.append(time.perf_counter() - t0)
+    per = np.array(per)
+    value = wl.system.n * len(per) / per.sum()
+    out = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": float(per.mean() * 1e3),
+        "p50_ms": float(np.percentile(per, 50) * 1e3),
+        "p99_ms": float(np.percentile(per, 99) * 1e3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": wl.name, "n_atoms": wl.system.n, "potential_arithmetic": "f64",
+                   "integration": "f64", "parallelism": "host cores"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{len(per)} mixed velocity-Verlet steps of {wl.name}"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference(args)
+    else:
+        ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -217,6 +217,53 @@ int mix_destroy(mix_ctx* ctx);
 const char* mix_strerror(int code);
 const char* mix_last_error(const mix_ctx* ctx);
 
+/* ------------------------------------------------------------------------ */
+/* Measurement helpers.  The paper has no counterpart: they exist to time the  */
+/* kernels and to state roofline fractions.                                   */
+
+/* Kernel groups of one force evaluation, in launch order. */
+#define MIX_PHASE_DISP 0     /* first half-kick, drift, skin test */
+#define MIX_PHASE_LISTS 1    /* cell list and neighbour list (no-ops unless rebuilding) */
+#define MIX_PHASE_SETS 2     /* weights, buffers, compaction */
+#define MIX_PHASE_EXP 3      /* expensive potential (one kernel) */
+#define MIX_PHASE_CHEAP 4    /* cheap potential (one kernel) */
+#define MIX_PHASE_GATHER 5   /* gather, blend, second half-kick (one kernel) */
+#define MIX_PHASES 6
+
+typedef struct {
+    int nbr_cap;            /* neighbour slots per atom */
+    int n_tau;              /* l-triples of the nu = 3 basis */
+    int64_t gaunt_nnz;      /* non-zero real Gaunt coefficients over all l-triples */
+    int64_t tau_dim3_sum;   /* sum over l-triples of (2 l3 + 1) */
+    int64_t basis_size;     /* number of product-basis functions */
+    size_t workspace_bytes;
+    size_t exp_smem_bytes;  /* dynamic shared memory of the expensive kernel */
+    int exp_grid;           /* its persistent grid (CTAs) */
+    int exp_threads;
+    size_t cheap_smem_bytes;
+    int cheap_grid;
+    int launches_per_evaluation;
+    int64_t launches;       /* kernels enqueued since mix_bind */
+} mix_info;
+
+int mix_get_info(const mix_ctx* ctx, mix_info* info);
+
+/* Enable (1) or disable (0) per-phase timing: CUDA events recorded on the
+ * context stream between the kernel groups of every evaluation.  While
+ * enabled, each evaluation synchronises on its last event so that the
+ * durations can be accumulated.  Enabling resets the accumulators. */
+int mix_profile(mix_ctx* ctx, int enable);
+
+/* Accumulated and last-evaluation durations per phase (milliseconds). */
+int mix_get_profile(mix_ctx* ctx, double* total_ms /*[MIX_PHASES] nullable*/, double* last_ms /*[MIX_PHASES]
+                    nullable*/, int64_t* evaluations);
+
+/* Measured fused multiply-add throughput of this device (flop/s, 2 per FMA)
+ * for MIX_FP64 or MIX_FP32: independent FMA chains on every SM, timed with
+ * CUDA events on `cuda_stream`.  Used as the arithmetic roofline.  Allocates
+ * and frees a small device buffer (one value per block) for its result sink. */
+int mix_fma_peak(int precision, void* cuda_stream, double* flops_per_s);
+
 #ifdef __cplusplus
 }
 #endif

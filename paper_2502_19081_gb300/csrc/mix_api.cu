@@ -16,6 +16,8 @@ using namespace mixd;
 namespace {
 
 constexpr double KAPPA = 9.6485332e-3;   // (eV / Angstrom / amu) in Angstrom / fs^2
+// kernels per evaluation: displacement 1, lists 5, sets 4, expensive 1, cheap 1, gather 1
+constexpr int LAUNCHES_PER_EVAL = 13;
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -145,6 +147,12 @@ struct mix_ctx {
         o_lam, o_wgt, o_flags, o_act_e, o_act_c, o_pos_e, o_pos_c, o_blk_e, o_blk_c, o_ge, o_gc, o_ee, o_ec;
     size_t ace_smem, spl_smem;
     int ace_grid, spl_grid;
+    int64_t gaunt_nnz, tau_d3_sum, basis_size;
+    int64_t launches;
+    bool profiling;
+    cudaEvent_t ev[MIX_PHASES + 1];
+    double prof_total[MIX_PHASES], prof_last[MIX_PHASES];
+    int64_t prof_evals;
     bool bound;
     bool need_build;
     bool forces_valid;
@@ -275,6 +283,19 @@ int build_tables(mix_ctx* c, const mix_ace* a, const mix_spline* sp) {
                 }
     }
     c->ntau = (int)(tau.size() / 4);
+    c->gaunt_nnz = 0;
+    c->tau_d3_sum = 0;
+    int64_t nb3 = 0;
+    for (int t = 0; t < c->ntau; ++t) {
+        const int l1 = tau[4 * t], l2 = tau[4 * t + 1], l3 = tau[4 * t + 2];
+        const int gb = tau[4 * t + 3];
+        c->gaunt_nnz += goff[gb + 2 * l3 + 1] - goff[gb];
+        c->tau_d3_sum += 2 * l3 + 1;
+        const int64_t nn = n;
+        nb3 += (l1 == l2 && l2 == l3) ? nn * (nn + 1) * (nn + 2) / 6
+               : (l1 == l2 || l2 == l3) ? nn * nn * (nn + 1) / 2 : nn * nn * nn;
+    }
+    c->basis_size = n + (a->nu_max >= 2 ? (int64_t)L1 * n * (n + 1) / 2 : 0) + nb3;
     std::vector<double> ylmk(nlm);
     for (int l = 0; l <= L; ++l)
         for (int m = -l; m <= l; ++m) ylmk[l * l + l + m] = ylm_norm(l, m);
@@ -380,16 +401,36 @@ int check_stream_error(mix_ctx* c, const char* what) {
 int evaluate(mix_ctx* c, int integrate, double dt) {
     const double h = 0.5 * dt * KAPPA / c->sys.mass;
     cudaStream_t s = c->stream;
+    const bool prof = c->profiling;
+    if (prof) cudaEventRecord(c->ev[0], s);
     launch_disp(c->dev, s, integrate, dt, h, c->need_build ? 1 : 0);
     c->need_build = false;
+    if (prof) cudaEventRecord(c->ev[1], s);
     launch_build(c->dev, s);
+    if (prof) cudaEventRecord(c->ev[2], s);
     launch_sets(c->dev, c->regions, s);
+    if (prof) cudaEventRecord(c->ev[3], s);
     const void* at = c->precision == MIX_FP64 ? (const void*)&c->ace64 : (const void*)&c->ace32;
     const void* st = c->precision == MIX_FP64 ? (const void*)&c->spl64 : (const void*)&c->spl32;
     launch_ace(c->dev, at, c->precision, c->L, c->ace_smem, c->ace_grid, s);
+    if (prof) cudaEventRecord(c->ev[4], s);
     launch_spline(c->dev, st, c->precision, c->spl_smem, c->spl_grid, s);
+    if (prof) cudaEventRecord(c->ev[5], s);
     launch_gather(c->dev, c->precision, integrate, h, s);
-    return check_stream_error(c, "kernel launch");
+    if (prof) cudaEventRecord(c->ev[6], s);
+    c->launches += LAUNCHES_PER_EVAL;
+    int rc = check_stream_error(c, "kernel launch");
+    if (rc || !prof) return rc;
+    cudaError_t e = cudaEventSynchronize(c->ev[MIX_PHASES]);
+    if (e != cudaSuccess) return cuda_fail(c, e, "profile event");
+    for (int p = 0; p < MIX_PHASES; ++p) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, c->ev[p], c->ev[p + 1]);
+        c->prof_last[p] = ms;
+        c->prof_total[p] += ms;
+    }
+    c->prof_evals++;
+    return MIX_OK;
 }
 
 int read_status(mix_ctx* c) {
@@ -593,6 +634,7 @@ int mix_bind(mix_ctx* c, double* x, double* v, double* f, void* ws) {
     c->need_build = true;
     c->forces_valid = false;
     c->steps = 0;
+    c->launches = 0;
     return MIX_OK;
 }
 
@@ -784,8 +826,61 @@ int mix_set_state(mix_ctx* c, const double* x, const double* v, const double* f,
 int mix_destroy(mix_ctx* c) {
     if (!c) return MIX_OK;
     if (c->pinned) cudaFreeHost(c->pinned);
+    if (c->profiling)
+        for (int p = 0; p <= MIX_PHASES; ++p) cudaEventDestroy(c->ev[p]);
     delete c;
     return MIX_OK;
+}
+
+int mix_get_info(const mix_ctx* c, mix_info* info) {
+    if (!c || !info) return MIX_EINVAL;
+    info->nbr_cap = c->cap;
+    info->n_tau = c->ntau;
+    info->gaunt_nnz = c->gaunt_nnz;
+    info->tau_dim3_sum = c->tau_d3_sum;
+    info->basis_size = c->basis_size;
+    info->workspace_bytes = c->ws_bytes;
+    info->exp_smem_bytes = c->ace_smem;
+    info->exp_grid = c->ace_grid;
+    info->exp_threads = 128;
+    info->cheap_smem_bytes = c->spl_smem;
+    info->cheap_grid = c->spl_grid;
+    info->launches_per_evaluation = LAUNCHES_PER_EVAL;
+    info->launches = c->launches;
+    return MIX_OK;
+}
+
+int mix_profile(mix_ctx* c, int enable) {
+    if (!c) return MIX_EINVAL;
+    if (enable && !c->profiling) {
+        for (int p = 0; p <= MIX_PHASES; ++p) {
+            cudaError_t e = cudaEventCreate(&c->ev[p]);
+            if (e != cudaSuccess) return cuda_fail(c, e, "cudaEventCreate");
+        }
+        c->profiling = true;
+    } else if (!enable && c->profiling) {
+        cudaStreamSynchronize(c->stream);
+        for (int p = 0; p <= MIX_PHASES; ++p) cudaEventDestroy(c->ev[p]);
+        c->profiling = false;
+    }
+    for (int p = 0; p < MIX_PHASES; ++p) c->prof_total[p] = c->prof_last[p] = 0.0;
+    c->prof_evals = 0;
+    return MIX_OK;
+}
+
+int mix_get_profile(mix_ctx* c, double* total_ms, double* last_ms, int64_t* evaluations) {
+    if (!c) return MIX_EINVAL;
+    for (int p = 0; p < MIX_PHASES; ++p) {
+        if (total_ms) total_ms[p] = c->prof_total[p];
+        if (last_ms) last_ms[p] = c->prof_last[p];
+    }
+    if (evaluations) *evaluations = c->prof_evals;
+    return MIX_OK;
+}
+
+int mix_fma_peak(int precision, void* stream, double* flops) {
+    if (!flops || (precision != MIX_FP64 && precision != MIX_FP32)) return MIX_EINVAL;
+    return fma_peak(precision, (cudaStream_t)stream, flops);
 }
 
 const char* mix_strerror(int code) {

@@ -25,4 +25,7 @@ void launch_gather(const Dev& d, int precision, int integrate, double h, cudaStr
 
 int sm_count();
 
+// FMA throughput microbenchmark (k_peak.cu)
+int fma_peak(int precision, cudaStream_t s, double* flops_per_s);
+
 }  // namespace mixd

@@ -40,8 +40,12 @@ EXPORTS = [
     "mix_init", "mix_workspace_bytes", "mix_bind", "mix_set_regions", "mix_forces", "mix_step",
     "mix_step_host", "mix_sync", "mix_get_stats", "mix_get_cells", "mix_get_neighbours",
     "mix_get_lambda", "mix_get_sets", "mix_get_site_energies", "mix_get_state", "mix_set_state",
-    "mix_destroy", "mix_strerror", "mix_last_error",
+    "mix_destroy", "mix_strerror", "mix_last_error", "mix_get_info", "mix_profile", "mix_get_profile",
+    "mix_fma_peak",
 ]
+
+MIX_PHASES = 6
+PHASE_NAMES = ["disp", "lists", "sets", "exp", "cheap", "gather"]
 
 
 class MixError(RuntimeError):
@@ -83,6 +87,15 @@ class mix_stats(ctypes.Structure):
                 ("max_neighbours", ctypes.c_int), ("status_bits", ctypes.c_int)]
 
 
+class mix_info(ctypes.Structure):
+    _fields_ = [("nbr_cap", ctypes.c_int), ("n_tau", ctypes.c_int), ("gaunt_nnz", ctypes.c_int64),
+                ("tau_dim3_sum", ctypes.c_int64), ("basis_size", ctypes.c_int64),
+                ("workspace_bytes", ctypes.c_size_t), ("exp_smem_bytes", ctypes.c_size_t),
+                ("exp_grid", ctypes.c_int), ("exp_threads", ctypes.c_int), ("cheap_smem_bytes", ctypes.c_size_t),
+                ("cheap_grid", ctypes.c_int), ("launches_per_evaluation", ctypes.c_int),
+                ("launches", ctypes.c_int64)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -122,6 +135,10 @@ def lib():
             L.mix_strerror.argtypes = [ctypes.c_int]
             L.mix_last_error.restype = ctypes.c_char_p
             L.mix_last_error.argtypes = [P]
+            L.mix_get_info.argtypes = [P, ctypes.POINTER(mix_info)]
+            L.mix_profile.argtypes = [P, ctypes.c_int]
+            L.mix_get_profile.argtypes = [P, dp, dp, i64p]
+            L.mix_fma_peak.argtypes = [ctypes.c_int, P, dp]
             _lib = L
     return _lib
 
@@ -291,12 +308,39 @@ class Context:
         self._check(self.L.mix_get_state(self.h, _dp(x), _dp(v), _dp(f), ctypes.byref(st)), "mix_get_state")
         return x[:self.n], v[:self.n], f[:self.n], int(st.value)
 
+    def info(self) -> dict:
+        s = mix_info()
+        self._check(self.L.mix_get_info(self.h, ctypes.byref(s)), "mix_get_info")
+        return {k: getattr(s, k) for k, _ in mix_info._fields_}
+
+    def profile(self, enable: bool = True):
+        self._check(self.L.mix_profile(self.h, 1 if enable else 0), "mix_profile")
+
+    def get_profile(self):
+        """(total ms per phase, last-evaluation ms per phase, evaluations)."""
+        tot = np.zeros(MIX_PHASES)
+        last = np.zeros(MIX_PHASES)
+        ev = ctypes.c_int64()
+        self._check(self.L.mix_get_profile(self.h, _dp(tot), _dp(last), ctypes.byref(ev)), "mix_get_profile")
+        return tot, last, int(ev.value)
+
     def set_state(self, x, v, f=None, step: int = 0):
         x = _f64(x)
         v = _f64(v)
         fa = _f64(f) if f is not None else None
         self._check(self.L.mix_set_state(self.h, _dp(x), _dp(v), _dp(fa) if fa is not None else None, int(step),
                                          1 if fa is not None else 0), "mix_set_state")
+
+
+def fma_peak(precision: int, stream=None) -> float:
+    """Measured FMA throughput (flop/s) of the current device."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    out = ctypes.c_double()
+    st = lib().mix_fma_peak(int(precision), ctypes.c_void_p(s.cuda_stream), ctypes.byref(out))
+    if st != MIX_OK:
+        raise MixError(st, "mix_fma_peak")
+    return float(out.value)
 
 
 def open_context(workload, precision: int = MIX_FP64, retries: int = 2, **kw) -> Context:
