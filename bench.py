@@ -62,9 +62,25 @@ def dist_env():
 
 
 def make_workload(name: str, rank: int):
+    """Replica `rank` of the workload: same system, its own thermal draw."""
     from paper_2502_19081_gb300 import inputs as I
     base = {"si_vacancy_215": 1, "fe_dumbbell_8001": 2, "fe_screw_256000": 3}[name]
     return I.workload(name, seed=base + 1000 * rank)
+
+
+def max_over_ranks(total_ms: float, device=None) -> float:
+    """Largest per-rank timed total (the job ends when the slowest replica does)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(n_atoms: int, steps: int, world: int, total_ms_max: float) -> float:
+    """Whole-job atom-steps/s: every rank advanced its own replica `steps` steps."""
+    return n_atoms * steps * world / (total_ms_max * 1e-3)
 
 
 # ---------------------------------------------------------------------------
@@ -253,11 +269,8 @@ def ours(args):
     ctx, per, tot, nev, launches = run_precision(mix, torch, wl, prec, args.steps, args.warmup, flush)
     clk = clocks.stop()
     total_ms = float(per.sum())
-    t_all = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t_all, op=dist.ReduceOp.MAX)
-    total_max = float(t_all.item())
-    value = wl.system.n * args.steps * world / (total_max * 1e-3)
+    total_max = max_over_ranks(total_ms, device="cuda")
+    value = job_throughput(wl.system.n, args.steps, world, total_max)
 
     # end to end through the host-buffer entry point (pinned host arrays)
     n = wl.system.n
