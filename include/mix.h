@@ -264,6 +264,40 @@ int mix_get_profile(mix_ctx* ctx, double* total_ms /*[MIX_PHASES] nullable*/, do
  * and frees a small device buffer (one value per block) for its result sink. */
 int mix_fma_peak(int precision, void* cuda_stream, double* flops_per_s);
 
+/* ------------------------------------------------------------------------ */
+/* Neighbour lists for callers that cannot allocate device memory.  The paper  */
+/* has no counterpart: this is a packaging of the library's own list build.   */
+/*                                                                            */
+/* Some callers may not call cudaMalloc: a plugin inside a host program that  */
+/* owns every device allocation through its own pool, or a time-critical loop */
+/* that cannot take the device-wide synchronisation an allocation implies.    */
+/* This entry point builds the same full, sorted neighbour lists and reverse- */
+/* slot map as a context does (cell list, r2 < r_list^2 with the minimum      */
+/* image, rows ascending), but keeps all of its scratch -- a folded copy of   */
+/* the positions, the cell list, status words -- in one fixed device array    */
+/* inside the library (about 2.5 MB, reserved on every GPU that loads the     */
+/* library until the process exits).  It calls no cudaMalloc, cudaFree or     */
+/* allocating library routine.                                                */
+/*                                                                            */
+/* Inputs and outputs are the caller's device buffers: x_dev [N][4] float64   */
+/* (16-byte aligned, read only), nnb_dev [N], nbr_dev [N][cap], rev_dev       */
+/* [N][cap] int32.  The box follows mix_system's rules.  Limits: N <=         */
+/* MIX_NOALLOC_MAX_ATOMS, cells <= MIX_NOALLOC_MAX_CELLS, 1 <= cap <= 256;     */
+/* anything larger returns MIX_EINVAL before touching the GPU.  A row longer  */
+/* than cap returns MIX_EOVERFLOW (rows are then truncated).                  */
+/*                                                                            */
+/* The call enqueues its work on cuda_stream and waits for it.  The first     */
+/* call on a device looks up the array's device address (cudaGetSymbolAddress */
+/* with that device current); make that first call before any stream capture. */
+/* Every call shares the one array and clears what must start at zero; calls  */
+/* whose work overlaps on the GPU (other streams, other host threads) race on */
+/* it and must be serialised by the caller.                                   */
+#define MIX_NOALLOC_MAX_ATOMS 32768
+#define MIX_NOALLOC_MAX_CELLS 16384
+int mix_neighbours_noalloc(int64_t n_atoms, const double* x_dev, const double* box_lo /*[3]*/,
+                           const double* box_len /*[3]*/, const int* periodic /*[3]*/, double r_list, int cap,
+                           int* nnb_dev, int* nbr_dev, int* rev_dev, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

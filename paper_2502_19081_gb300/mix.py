@@ -139,6 +139,8 @@ def lib():
             L.mix_profile.argtypes = [P, ctypes.c_int]
             L.mix_get_profile.argtypes = [P, dp, dp, i64p]
             L.mix_fma_peak.argtypes = [ctypes.c_int, P, dp]
+            L.mix_neighbours_noalloc.argtypes = [ctypes.c_int64, P, dp, dp, ip, ctypes.c_double, ctypes.c_int,
+                                                 P, P, P, P]
             _lib = L
     return _lib
 
@@ -341,6 +343,22 @@ def fma_peak(precision: int, stream=None) -> float:
     if st != MIX_OK:
         raise MixError(st, "mix_fma_peak")
     return float(out.value)
+
+
+def neighbours_noalloc(x, box_lo, box_len, periodic, r_list: float, cap: int, nnb, nbr, rev, stream=None) -> int:
+    """mix_neighbours_noalloc on torch device tensors: x [N, 4] float64 (read),
+    nnb [N], nbr [N, cap], rev [N, cap] int32 (written).  For callers that may
+    not allocate device memory; returns the status code."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    lo = _f64(box_lo)
+    ln = _f64(box_len)
+    per = np.ascontiguousarray(periodic, dtype=np.int32)
+    n = int(x.shape[0])
+    return int(lib().mix_neighbours_noalloc(n, ctypes.c_void_p(x.data_ptr()), _dp(lo), _dp(ln), _ip(per),
+                                            float(r_list), int(cap), ctypes.c_void_p(nnb.data_ptr()),
+                                            ctypes.c_void_p(nbr.data_ptr()), ctypes.c_void_p(rev.data_ptr()),
+                                            ctypes.c_void_p(s.cuda_stream)))
 
 
 def open_context(workload, precision: int = MIX_FP64, retries: int = 2, **kw) -> Context:
