@@ -128,6 +128,8 @@ typedef struct {
     double buffer_exp;      /* buffer radius of the expensive set; <= 0: its cutoff */
     double buffer_cheap;    /* buffer radius of the cheap set; <= 0: its cutoff */
     int nbr_cap;            /* neighbour slots per atom; 0: automatic */
+    int no_graphs;          /* 0: mix_step replays each step as one captured CUDA
+                               graph launch; nonzero: kernels are launched one by one */
 } mix_options;
 
 /* A core region.  d = distance of an atom from the shape (minimum image in
@@ -275,7 +277,7 @@ int mix_fma_peak(int precision, void* cuda_stream, double* flops_per_s);
 /* slot map as a context does (cell list, r2 < r_list^2 with the minimum      */
 /* image, rows ascending), but keeps all of its scratch -- a folded copy of   */
 /* the positions, the cell list, status words -- in one fixed device array    */
-/* inside the library (about 2.5 MB, reserved on every GPU that loads the     */
+/* inside the library (about 3 MB, reserved on every GPU that loads the       */
 /* library until the process exits).  It calls no cudaMalloc, cudaFree or     */
 /* allocating library routine.                                                */
 /*                                                                            */

@@ -1,0 +1,25 @@
+// Expensive-potential kernel instantiations with double arithmetic (the
+// templates and their description are in k_ace.cuh).
+#include "k_ace.cuh"
+
+namespace mixd {
+
+cudaError_t ace_configure_f64(int L, int n, int cap, size_t* smem, int* grid) {
+    return ace_cfg_t<double>(L, n, cap, smem, grid);
+}
+
+void launch_ace_f64(const Dev& d, const void* tab, int L, size_t smem, int grid, cudaStream_t s) {
+    ace_launch_t<double>(d, *static_cast<const AceTab<double>*>(tab), L, smem, grid, s);
+}
+
+cudaError_t ace_configure(int precision, int L, int n, int cap, size_t* smem, int* grid) {
+    if (cap > MAX_CAP || n > 16) return cudaErrorInvalidValue;
+    return precision == MIX_FP64 ? ace_configure_f64(L, n, cap, smem, grid) : ace_configure_f32(L, n, cap, smem, grid);
+}
+
+void launch_ace(const Dev& d, const void* tab, int precision, int L, size_t smem, int grid, cudaStream_t s) {
+    if (precision == MIX_FP64) launch_ace_f64(d, tab, L, smem, grid, s);
+    else launch_ace_f32(d, tab, L, smem, grid, s);
+}
+
+}  // namespace mixd

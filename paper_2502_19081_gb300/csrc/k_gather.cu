@@ -27,41 +27,43 @@ __global__ void __launch_bounds__(G_WARPS * 32) k_gather(Dev d, int integrate, d
         const int pe = d.pos_e[k], pc = d.pos_c[k];
         const int* row = d.nbr + k * cap;
         const int* rv = d.rev + k * cap;
-        double ex = 0, ey = 0, ez = 0, cx = 0, cy = 0, cz = 0;
+        // each lane sums its few slots in T; lanes are combined in float64 below
+        T tex = T(0), tey = T(0), tez = T(0), tcx = T(0), tcy = T(0), tcz = T(0);
         for (int s = lane; s < m; s += 32) {
             const int j = row[s];
             const int r = rv[s];
             if (w > 0.0) {
                 if (pe >= 0) {
                     const V g = GE[(int64_t)pe * cap + s];
-                    ex += (double)g.x;
-                    ey += (double)g.y;
-                    ez += (double)g.z;
+                    tex += g.x;
+                    tey += g.y;
+                    tez += g.z;
                 }
                 const int pj = d.pos_e[j];
                 if (pj >= 0) {
                     const V g = GE[(int64_t)pj * cap + r];
-                    ex -= (double)g.x;
-                    ey -= (double)g.y;
-                    ez -= (double)g.z;
+                    tex -= g.x;
+                    tey -= g.y;
+                    tez -= g.z;
                 }
             }
             if (w < 1.0) {
                 if (pc >= 0) {
                     const V g = GC[(int64_t)pc * cap + s];
-                    cx += (double)g.x;
-                    cy += (double)g.y;
-                    cz += (double)g.z;
+                    tcx += g.x;
+                    tcy += g.y;
+                    tcz += g.z;
                 }
                 const int pj = d.pos_c[j];
                 if (pj >= 0) {
                     const V g = GC[(int64_t)pj * cap + r];
-                    cx -= (double)g.x;
-                    cy -= (double)g.y;
-                    cz -= (double)g.z;
+                    tcx -= g.x;
+                    tcy -= g.y;
+                    tcz -= g.z;
                 }
             }
         }
+        double ex = tex, ey = tey, ez = tez, cx = tcx, cy = tcy, cz = tcz;
         for (int o = 16; o > 0; o >>= 1) {
             ex += __shfl_down_sync(0xffffffffu, ex, o);
             ey += __shfl_down_sync(0xffffffffu, ey, o);

@@ -68,6 +68,7 @@ __global__ void k_cell_bin(Dev d) {
     x.y = xs[1];
     x.z = xs[2];
     d.x[i] = x;
+    d.xf[i] = make_float4((float)xs[0], (float)xs[1], (float)xs[2], 0.f);
     const int cx = cell_coord(d.box, d.cells, xs[0], 0);
     const int cy = cell_coord(d.box, d.cells, xs[1], 1);
     const int cz = cell_coord(d.box, d.cells, xs[2], 2);
@@ -142,8 +143,15 @@ __global__ void __launch_bounds__(NB_WARPS * 32) k_neigh_build(Dev d, int capp2)
     int* buf = sbuf + warp * capp2;
     const unsigned lt = (1u << lane) - 1u;
     const int ncx = d.cells.nc[0], ncy = d.cells.nc[1], ncz = d.cells.nc[2];
+    // float pre-filter: the float distance is within 2e-5 relative of the
+    // float64 one for boxes up to a few thousand Angstrom, so only candidates
+    // inside a +-2e-4 band around the threshold need the exact float64 test
+    const float lo2 = (float)(d.rlist2 * (1.0 - 2e-4)), hi2 = (float)(d.rlist2 * (1.0 + 2e-4));
+    const float Lf[3] = {(float)d.box.L[0], (float)d.box.L[1], (float)d.box.L[2]};
+    const float iLf[3] = {(float)d.box.invL[0], (float)d.box.invL[1], (float)d.box.invL[2]};
     for (int64_t i = (int64_t)blockIdx.x * NB_WARPS + warp; i < d.n; i += (int64_t)gridDim.x * NB_WARPS) {
         const double4 xi = d.x[i];
+        const float4 xif = d.xf[i];
         const int c = d.cell_of[i];
         const int cx = c % ncx, cy = (c / ncx) % ncy, cz = c / (ncx * ncy);
         int cnt = 0;
@@ -177,9 +185,19 @@ __global__ void __launch_bounds__(NB_WARPS * 32) k_neigh_build(Dev d, int capp2)
                         if (t < t1) {
                             j = d.cell_atoms[t];
                             if (j != (int)i) {
-                                double dd[3];
-                                delta_rn(d.box, xi, d.x[j], dd);
-                                ok = norm2_rn(dd) < d.rlist2;
+                                const float4 xjf = d.xf[j];
+                                float df[3] = {xjf.x - xif.x, xjf.y - xif.y, xjf.z - xif.z};
+#pragma unroll
+                                for (int k = 0; k < 3; ++k)
+                                    if (d.box.per[k]) df[k] -= Lf[k] * rintf(df[k] * iLf[k]);
+                                const float r2f = df[0] * df[0] + df[1] * df[1] + df[2] * df[2];
+                                if (r2f < lo2 && !d.exact_lists) {
+                                    ok = true;
+                                } else if (r2f <= hi2 || d.exact_lists) {
+                                    double dd[3];
+                                    delta_rn(d.box, xi, d.x[j], dd);
+                                    ok = norm2_rn(dd) < d.rlist2;
+                                }
                             }
                         }
                         const unsigned m = __ballot_sync(0xffffffffu, ok);

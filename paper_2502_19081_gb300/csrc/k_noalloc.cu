@@ -25,7 +25,8 @@ constexpr size_t na_al(size_t x) { return (x + 255) & ~(size_t)255; }
 constexpr size_t NA_O_STATUS = 0;
 constexpr size_t NA_O_X = na_al(NA_O_STATUS + SW_COUNT * sizeof(int));
 constexpr size_t NA_O_XB = na_al(NA_O_X + NA_MAX_ATOMS * sizeof(double4));
-constexpr size_t NA_O_CELL_OF = na_al(NA_O_XB + NA_MAX_ATOMS * sizeof(double4));
+constexpr size_t NA_O_XF = na_al(NA_O_XB + NA_MAX_ATOMS * sizeof(double4));
+constexpr size_t NA_O_CELL_OF = na_al(NA_O_XF + NA_MAX_ATOMS * sizeof(float4));
 constexpr size_t NA_O_CELL_ATOMS = na_al(NA_O_CELL_OF + NA_MAX_ATOMS * sizeof(int));
 constexpr size_t NA_O_CELL_COUNT = na_al(NA_O_CELL_ATOMS + NA_MAX_ATOMS * sizeof(int));
 constexpr size_t NA_O_CELL_FILL = na_al(NA_O_CELL_COUNT + NA_MAX_CELLS * sizeof(int));
@@ -103,6 +104,10 @@ extern "C" int mix_neighbours_noalloc(int64_t n_atoms, const double* x_dev, cons
     d.status = reinterpret_cast<int*>(base + NA_O_STATUS);
     d.x = reinterpret_cast<double4*>(base + NA_O_X);
     d.xb = reinterpret_cast<double4*>(base + NA_O_XB);
+    d.xf = reinterpret_cast<float4*>(base + NA_O_XF);
+    double extent = 0.0;
+    for (int k = 0; k < 3; ++k) extent = fmax(extent, fabs(box_lo[k]) + box_len[k]);
+    d.exact_lists = extent > 2000.0 ? 1 : 0;
     d.cell_of = reinterpret_cast<int*>(base + NA_O_CELL_OF);
     d.cell_atoms = reinterpret_cast<int*>(base + NA_O_CELL_ATOMS);
     d.cell_count = reinterpret_cast<int*>(base + NA_O_CELL_COUNT);

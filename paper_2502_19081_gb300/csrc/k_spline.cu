@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(SPL_WARPS * 32) k_spline(Dev d, SplTab<T> tab)
     __syncthreads();
 
     V* GC = reinterpret_cast<V*>(d.gc);
-    const double rc2 = d.rcc2, rc32 = tab.rc3 * tab.rc3;
+    const T rc2 = (T)d.rcc2, rc32 = (T)(tab.rc3 * tab.rc3);
     const T invh2 = (T)(13.0 / tab.rc);
     const T invh3 = (T)(5.0 / tab.rc3);
     const T invhc = (T)(5.0 / (2.0 * tab.rc3));
@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(SPL_WARPS * 32) k_spline(Dev d, SplTab<T> tab)
         const int m = d.nnb[i];
         const int* row = d.nbr + (int64_t)i * cap;
         V* grow = GC + (int64_t)a * cap;
-        double epart = 0.0;
+        T ep = T(0);
         T g2[SPL_SLOTS][3];
         int p3[SPL_SLOTS];
         int n3 = 0;
@@ -82,29 +82,24 @@ __global__ void __launch_bounds__(SPL_WARPS * 32) k_spline(Dev d, SplTab<T> tab)
             g2[c][0] = g2[c][1] = g2[c][2] = T(0);
             p3[c] = -1;
             bool is3 = false;
-            double dd[3] = {0, 0, 0}, r = 0;
+            T dv3[3] = {T(0), T(0), T(0)}, r = T(0);
             if (c * 32 < m) {
                 if (s < m) {
-                    const double4 xj = d.x[row[s]];
-                    dd[0] = xj.x - xi.x;
-                    dd[1] = xj.y - xi.y;
-                    dd[2] = xj.z - xi.z;
-                    for (int k = 0; k < 3; ++k)
-                        if (d.box.per[k]) dd[k] -= d.box.L[k] * rint(dd[k] * d.box.invL[k]);
-                    const double r2 = dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2];
+                    T r2;
+                    pair_vec<T>(d.box, xi, d.x[row[s]], dv3, r2);
                     if (r2 < rc2) {
                         r = sqrt(r2);
                         T v, dv;
                         int q;
                         T b[4], db[4];
-                        bspline4<T>((T)r * invh2, 12, q, b, db);
+                        bspline4<T>(r * invh2, 12, q, b, db);
                         v = c2s[q] * b[0] + c2s[q + 1] * b[1] + c2s[q + 2] * b[2] + c2s[q + 3] * b[3];
                         dv = (c2s[q] * db[0] + c2s[q + 1] * db[1] + c2s[q + 2] * db[2] + c2s[q + 3] * db[3]) * invh2;
-                        epart += 0.5 * (double)v;
-                        const T hp = T(0.5) * dv / (T)r;
-                        g2[c][0] = hp * (T)dd[0];
-                        g2[c][1] = hp * (T)dd[1];
-                        g2[c][2] = hp * (T)dd[2];
+                        ep += T(0.5) * v;
+                        const T hp = T(0.5) * dv / r;
+                        g2[c][0] = hp * dv3[0];
+                        g2[c][1] = hp * dv3[1];
+                        g2[c][2] = hp * dv3[2];
                         is3 = r2 < rc32;
                     }
                 }
@@ -114,10 +109,10 @@ __global__ void __launch_bounds__(SPL_WARPS * 32) k_spline(Dev d, SplTab<T> tab)
                     p3[c] = p;
                     if (p < NB3MAX) {
                         W.slot[p] = s;
-                        W.v[p][0] = (T)dd[0];
-                        W.v[p][1] = (T)dd[1];
-                        W.v[p][2] = (T)dd[2];
-                        W.v[p][3] = (T)r;
+                        W.v[p][0] = dv3[0];
+                        W.v[p][1] = dv3[1];
+                        W.v[p][2] = dv3[2];
+                        W.v[p][3] = r;
                     }
                 }
                 n3 += __popc(bal);
@@ -161,7 +156,7 @@ __global__ void __launch_bounds__(SPL_WARPS * 32) k_spline(Dev d, SplTab<T> tab)
                     d3 += t1 * ba[x] * bb[y];
                 }
             }
-            epart += (double)val;
+            ep += val;
             const T c = r3 > T(0) ? d3 * invhc / r3 : T(0);
             W.al[p * T3S + q] = d1 * invh3;
             W.al[q * T3S + p] = d2 * invh3;
@@ -205,6 +200,7 @@ __global__ void __launch_bounds__(SPL_WARPS * 32) k_spline(Dev d, SplTab<T> tab)
                 grow[s] = gv;
             }
         }
+        double epart = (double)ep;   // float64 across lanes, fixed order
         for (int o = 16; o > 0; o >>= 1) epart += __shfl_down_sync(0xffffffffu, epart, o);
         if (lane == 0) d.esite_c[i] = epart;
         __syncwarp();

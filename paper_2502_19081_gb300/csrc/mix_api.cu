@@ -134,8 +134,8 @@ struct mix_ctx {
     int cap;
     // tables (offsets in the arena) and their element-type views
     Arena arena;
-    size_t o_c1, o_S2, o_W3, o_tau, o_goff, o_gidx, o_gval, o_ylmk, o_pair, o_sc2, o_sc3;
-    int ntau;
+    size_t o_c1, o_S2, o_W3, o_WT3, o_tau, o_goff, o_gidx, o_gval, o_ylmk, o_pair, o_sc2, o_sc3, o_wtoff, o_wtlist;
+    int ntau, np, nq;
     AceTab<double> ace64;
     AceTab<float> ace32;
     SplTab<double> spl64;
@@ -143,13 +143,20 @@ struct mix_ctx {
     // workspace
     size_t ws_bytes;
     size_t off_tab;
-    size_t o_status, o_xb, o_cell_of, o_cell_count, o_cell_start, o_cell_fill, o_cell_atoms, o_nnb, o_nbr, o_rev,
+    size_t o_status, o_xb, o_xf, o_cell_of, o_cell_count, o_cell_start, o_cell_fill, o_cell_atoms, o_nnb, o_nbr, o_rev,
         o_lam, o_wgt, o_flags, o_act_e, o_act_c, o_pos_e, o_pos_c, o_blk_e, o_blk_c, o_ge, o_gc, o_ee, o_ec;
     size_t ace_smem, spl_smem;
     int ace_grid, spl_grid;
     int64_t gaunt_nnz, tau_d3_sum, basis_size;
     int64_t launches;
     bool profiling;
+    bool opt_graphs;
+    cudaStream_t cap_stream;
+    cudaGraph_t graph;
+    cudaGraphExec_t gexec;
+    double graph_dt;
+    bool graph_prof;
+    int64_t graph_regions, regions_version;
     cudaEvent_t ev[MIX_PHASES + 1];
     double prof_total[MIX_PHASES], prof_last[MIX_PHASES];
     int64_t prof_evals;
@@ -296,6 +303,43 @@ int build_tables(mix_ctx* c, const mix_ace* a, const mix_spline* sp) {
                : (l1 == l2 || l2 == l3) ? nn * nn * (nn + 1) / 2 : nn * nn * nn;
     }
     c->basis_size = n + (a->nu_max >= 2 ? (int64_t)L1 * n * (n + 1) / 2 : 0) + nb3;
+    // padded layouts of the nu = 3 coefficients: W[q1 q2][q3] rows of np, and its
+    // transpose W[q3][q1 q2] rows of nq (zeros in the padding)
+    const int np = (n + 3) & ~3, nq = (n * n + 3) & ~3;
+    c->np = np;
+    c->nq = nq;
+    std::vector<double> W3p((size_t)c->ntau * n * n * np, 0.0), WT3((size_t)c->ntau * n * nq, 0.0);
+    for (int t = 0; t < c->ntau; ++t)
+        for (int q12 = 0; q12 < n * n; ++q12)
+            for (int q3 = 0; q3 < n; ++q3) {
+                const double w = W3[((size_t)t * n * n + q12) * n + q3];
+                W3p[((size_t)t * n * n + q12) * np + q3] = w;
+                WT3[((size_t)t * n + q3) * nq + q12] = w;
+            }
+    // l-triples to warps, longest first onto the least loaded warp
+    std::vector<std::pair<double, int>> cost;
+    for (int t = 0; t < c->ntau; ++t) {
+        const int l1 = tau[4 * t], l2 = tau[4 * t + 1], l3 = tau[4 * t + 2], gb = tau[4 * t + 3];
+        const double nnz = goff[gb + 2 * l3 + 1] - goff[gb];
+        const double cst = 4.0 * n * n * n * (2 * l3 + 1) + 6.0 * n * n * nnz + (double)n * n * (2 * l1 + 2 * l2 + 2);
+        cost.push_back({cst, t});
+    }
+    std::sort(cost.begin(), cost.end(), [](const std::pair<double, int>& x, const std::pair<double, int>& y) {
+        return x.first > y.first || (x.first == y.first && x.second < y.second);
+    });
+    std::vector<std::vector<int>> per(ACE_WARPS);
+    std::vector<double> load(ACE_WARPS, 0.0);
+    for (auto& ct : cost) {
+        int w = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        per[w].push_back(ct.second);
+        load[w] += ct.first;
+    }
+    std::vector<int> wt_off(ACE_WARPS + 1, 0), wt_list;
+    for (int w = 0; w < ACE_WARPS; ++w) {
+        wt_off[w] = (int)wt_list.size();
+        for (int t : per[w]) wt_list.push_back(t);
+    }
+    wt_off[ACE_WARPS] = (int)wt_list.size();
     std::vector<double> ylmk(nlm);
     for (int l = 0; l <= L; ++l)
         for (int m = -l; m <= l; ++m) ylmk[l * l + l + m] = ylm_norm(l, m);
@@ -308,7 +352,8 @@ int build_tables(mix_ctx* c, const mix_ace* a, const mix_spline* sp) {
     if (c->precision == MIX_FP64) {
         c->o_c1 = A.put(c1);
         c->o_S2 = A.put(S2);
-        c->o_W3 = A.put(W3);
+        c->o_W3 = A.put(W3p);
+        c->o_WT3 = A.put(WT3);
         c->o_gval = A.put(gval);
         c->o_ylmk = A.put(ylmk);
         c->o_pair = A.put(pair);
@@ -317,7 +362,8 @@ int build_tables(mix_ctx* c, const mix_ace* a, const mix_spline* sp) {
     } else {
         c->o_c1 = A.put(conv<float>(c1));
         c->o_S2 = A.put(conv<float>(S2));
-        c->o_W3 = A.put(conv<float>(W3));
+        c->o_W3 = A.put(conv<float>(W3p));
+        c->o_WT3 = A.put(conv<float>(WT3));
         c->o_gval = A.put(conv<float>(gval));
         c->o_ylmk = A.put(conv<float>(ylmk));
         c->o_pair = A.put(conv<float>(pair));
@@ -327,6 +373,8 @@ int build_tables(mix_ctx* c, const mix_ace* a, const mix_spline* sp) {
     c->o_tau = A.put(tau);
     c->o_goff = A.put(goff);
     c->o_gidx = A.put(gidx);
+    c->o_wtoff = A.put(wt_off);
+    c->o_wtlist = A.put(wt_list);
     A.bytes.resize(align256(A.bytes.size()));
     return MIX_OK;
 }
@@ -338,10 +386,15 @@ void fill_tabs(mix_ctx* c, unsigned char* base, AceTab<T>& at, SplTab<T>& st) {
     at.nu = c->nu;
     at.nlm = (c->L + 1) * (c->L + 1);
     at.ntau = c->ntau;
+    at.np = c->np;
+    at.nq = c->nq;
     at.rc = c->ace_rc;
     at.c1 = reinterpret_cast<const T*>(base + c->o_c1);
     at.S2 = reinterpret_cast<const T*>(base + c->o_S2);
     at.W3 = reinterpret_cast<const T*>(base + c->o_W3);
+    at.WT3 = reinterpret_cast<const T*>(base + c->o_WT3);
+    at.wt_off = reinterpret_cast<const int*>(base + c->o_wtoff);
+    at.wt_list = reinterpret_cast<const int*>(base + c->o_wtlist);
     at.tau = reinterpret_cast<const int*>(base + c->o_tau);
     at.goff = reinterpret_cast<const int*>(base + c->o_goff);
     at.gidx = reinterpret_cast<const int*>(base + c->o_gidx);
@@ -366,6 +419,7 @@ void layout(mix_ctx* c) {
     };
     c->o_status = take(SW_COUNT * sizeof(int));
     c->o_xb = take(N * sizeof(double4));
+    c->o_xf = take(N * sizeof(float4));
     c->o_cell_of = take(N * 4);
     c->o_cell_count = take(nc * 4);
     c->o_cell_start = take((nc + 1) * 4);
@@ -397,27 +451,80 @@ int check_stream_error(mix_ctx* c, const char* what) {
     return MIX_OK;
 }
 
-// one force evaluation; integrate = 1 wraps it in a velocity-Verlet step
-int evaluate(mix_ctx* c, int integrate, double dt) {
+// the kernels of one evaluation, in order, on stream s (events between the
+// phases when profiling)
+// (captured = true: the events become record nodes of the graph being captured)
+void enqueue_evaluation(mix_ctx* c, cudaStream_t s, int integrate, double dt, int force_rebuild, bool prof,
+                        bool captured = false) {
     const double h = 0.5 * dt * KAPPA / c->sys.mass;
-    cudaStream_t s = c->stream;
-    const bool prof = c->profiling;
-    if (prof) cudaEventRecord(c->ev[0], s);
-    launch_disp(c->dev, s, integrate, dt, h, c->need_build ? 1 : 0);
-    c->need_build = false;
-    if (prof) cudaEventRecord(c->ev[1], s);
+    const unsigned ef = captured ? cudaEventRecordExternal : cudaEventRecordDefault;
+    if (prof) cudaEventRecordWithFlags(c->ev[0], s, ef);
+    launch_disp(c->dev, s, integrate, dt, h, force_rebuild);
+    if (prof) cudaEventRecordWithFlags(c->ev[1], s, ef);
     launch_build(c->dev, s);
-    if (prof) cudaEventRecord(c->ev[2], s);
+    if (prof) cudaEventRecordWithFlags(c->ev[2], s, ef);
     launch_sets(c->dev, c->regions, s);
-    if (prof) cudaEventRecord(c->ev[3], s);
+    if (prof) cudaEventRecordWithFlags(c->ev[3], s, ef);
     const void* at = c->precision == MIX_FP64 ? (const void*)&c->ace64 : (const void*)&c->ace32;
     const void* st = c->precision == MIX_FP64 ? (const void*)&c->spl64 : (const void*)&c->spl32;
     launch_ace(c->dev, at, c->precision, c->L, c->ace_smem, c->ace_grid, s);
-    if (prof) cudaEventRecord(c->ev[4], s);
+    if (prof) cudaEventRecordWithFlags(c->ev[4], s, ef);
     launch_spline(c->dev, st, c->precision, c->spl_smem, c->spl_grid, s);
-    if (prof) cudaEventRecord(c->ev[5], s);
+    if (prof) cudaEventRecordWithFlags(c->ev[5], s, ef);
     launch_gather(c->dev, c->precision, integrate, h, s);
-    if (prof) cudaEventRecord(c->ev[6], s);
+    if (prof) cudaEventRecordWithFlags(c->ev[6], s, ef);
+}
+
+void drop_graph(mix_ctx* c) {
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->gexec = nullptr;
+    c->graph = nullptr;
+}
+
+// Capture one velocity-Verlet step (all its kernels, plus the profiling events
+// when enabled) into a CUDA graph on a private stream; replayed by
+// cudaGraphLaunch on the context stream.
+int capture_step(mix_ctx* c, double dt) {
+    drop_graph(c);
+    if (!c->cap_stream) {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_fail(c, e, "capture stream");
+    }
+    cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamBeginCapture");
+    enqueue_evaluation(c, c->cap_stream, 1, dt, 0, c->profiling, true);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(c->cap_stream, &g);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
+    c->graph = g;
+    e = cudaGraphInstantiate(&c->gexec, g, 0);
+    if (e != cudaSuccess) {
+        drop_graph(c);
+        return cuda_fail(c, e, "cudaGraphInstantiate");
+    }
+    c->graph_dt = dt;
+    c->graph_prof = c->profiling;
+    c->graph_regions = c->regions_version;
+    return MIX_OK;
+}
+
+// one force evaluation; integrate = 1 wraps it in a velocity-Verlet step
+int evaluate(mix_ctx* c, int integrate, double dt) {
+    cudaStream_t s = c->stream;
+    const bool prof = c->profiling;
+    const bool use_graph = c->opt_graphs && integrate && !c->need_build;
+    if (use_graph) {
+        if (!c->gexec || c->graph_dt != dt || c->graph_prof != prof || c->graph_regions != c->regions_version) {
+            int st = capture_step(c, dt);
+            if (st) return st;
+        }
+        cudaError_t e = cudaGraphLaunch(c->gexec, s);
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphLaunch");
+    } else {
+        enqueue_evaluation(c, s, integrate, dt, c->need_build ? 1 : 0, prof);
+    }
+    c->need_build = false;
     c->launches += LAUNCHES_PER_EVAL;
     int rc = check_stream_error(c, "kernel launch");
     if (rc || !prof) return rc;
@@ -488,6 +595,7 @@ int mix_init(const mix_system* sys, const mix_ace* a, const mix_spline* sp, cons
     if (opt->blend != MIX_BLEND_LINEAR && opt->blend != MIX_BLEND_CUBIC) return bad("blend");
     c->sys = *sys;
     c->opt = *opt;
+    c->opt_graphs = opt->no_graphs == 0;
     c->precision = opt->precision;
     c->ace_rc = a->r_cut;
     c->n = a->n_rad;
@@ -548,6 +656,9 @@ int mix_init(const mix_system* sys, const mix_ace* a, const mix_spline* sp, cons
     d.rc3 = sp->r_cut3;
     d.bufe2 = bufe * bufe;
     d.bufc2 = bufc * bufc;
+    double extent = 0.0;
+    for (int k = 0; k < 3; ++k) extent = std::max(extent, std::fabs(sys->box_lo[k]) + sys->box_len[k]);
+    d.exact_lists = extent > 2000.0 ? 1 : 0;
     const int64_t nblk = (sys->n_atoms + SCAN_BLOCK - 1) / SCAN_BLOCK;
     d.nblk = (int)(nblk > 0 ? nblk : 1);
     std::memset(&c->regions, 0, sizeof c->regions);
@@ -600,6 +711,7 @@ int mix_bind(mix_ctx* c, double* x, double* v, double* f, void* ws) {
     d.f = reinterpret_cast<double4*>(f);
     d.status = reinterpret_cast<int*>(w + c->o_status);
     d.xb = reinterpret_cast<double4*>(w + c->o_xb);
+    d.xf = reinterpret_cast<float4*>(w + c->o_xf);
     d.cell_of = reinterpret_cast<int*>(w + c->o_cell_of);
     d.cell_count = reinterpret_cast<int*>(w + c->o_cell_count);
     d.cell_start = reinterpret_cast<int*>(w + c->o_cell_start);
@@ -630,6 +742,7 @@ int mix_bind(mix_ctx* c, double* x, double* v, double* f, void* ws) {
         e = cudaMemcpyAsync(tb, c->arena.bytes.data(), c->arena.bytes.size(), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "mix_bind");
+    drop_graph(c);
     c->bound = true;
     c->need_build = true;
     c->forces_valid = false;
@@ -664,6 +777,7 @@ int mix_set_regions(mix_ctx* c, const mix_region* r, int n) {
         q[8] = r[k].ramp;
     }
     c->regions = R;
+    c->regions_version++;
     c->forces_valid = false;
     return MIX_OK;
 }
@@ -825,6 +939,10 @@ int mix_set_state(mix_ctx* c, const double* x, const double* v, const double* f,
 
 int mix_destroy(mix_ctx* c) {
     if (!c) return MIX_OK;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    drop_graph(c);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->pinned) cudaFreeHost(c->pinned);
     if (c->profiling)
         for (int p = 0; p <= MIX_PHASES; ++p) cudaEventDestroy(c->ev[p]);
@@ -852,6 +970,10 @@ int mix_get_info(const mix_ctx* c, mix_info* info) {
 
 int mix_profile(mix_ctx* c, int enable) {
     if (!c) return MIX_EINVAL;
+    if ((enable != 0) != c->profiling) {
+        cudaStreamSynchronize(c->stream);
+        drop_graph(c);
+    }
     if (enable && !c->profiling) {
         for (int p = 0; p <= MIX_PHASES; ++p) {
             cudaError_t e = cudaEventCreate(&c->ev[p]);

@@ -66,10 +66,13 @@ struct Dev {
     double rcc, rcc2;    // cheap 2-body cutoff
     double rc3;          // cheap 3-body cutoff
     double bufe2, bufc2; // buffer radii squared
+    int exact_lists;     // 1: every neighbour candidate takes the float64 test
+                         // (boxes beyond the float pre-filter's error bound)
     double4* x;
     double4* v;
     double4* f;
     double4* xb;
+    float4* xf;          // float copy of the folded positions at the last build
     int* status;
     int* cell_of;
     int* cell_count;
@@ -100,13 +103,20 @@ template <> struct Vec4<double> { using type = double4; };
 template <> struct Vec4<float> { using type = float4; };
 
 // Expensive-potential tables in the workspace (element type T).
+constexpr int ACE_WARPS = 4;        // warps per CTA of the expensive kernel
+
 template <typename T>
 struct AceTab {
     int n, L, nu, nlm, ntau;
+    int np;             // n rounded up to a multiple of 4 (row length of padded tables)
+    int nq;             // n*n rounded up to a multiple of 4
     double rc;
     const T* c1;        // [n]
     const T* S2;        // [L+1][n][n]  symmetric: W2 + W2^T, W2 upper-triangular c2
-    const T* W3;        // [ntau][n][n][n]  masked nu=3 coefficients
+    const T* W3;        // [ntau][n*n][np]  masked nu=3 coefficients W[q1 q2][q3], zero padded
+    const T* WT3;       // [ntau][n][nq]    the same, transposed: W[q3][q1 q2]
+    const int* wt_off;  // [ACE_WARPS + 1] ranges of wt_list handled by each warp
+    const int* wt_list; // [ntau] l-triple indices grouped by warp
     const int* tau;     // [ntau][4]: l1, l2, l3, index of its first offset row
     const int* goff;    // offset rows: for each tau, three orderings (by m3, m1, m2),
                         // each 2l+2 entries (start index per m, then end)
@@ -152,5 +162,19 @@ __device__ __forceinline__ int cell_coord(const Box& b, const Cells& c, double x
 }
 
 __device__ __forceinline__ void set_status(int* st, int bits) { atomicOr(st + SW_STATUS, bits); }
+
+// Pair vector for the potentials: the difference and minimum image in float64
+// (positions are absolute coordinates of up to hundreds of Angstrom), then
+// rounded once to T; length and direction in T.
+template <typename T>
+__device__ __forceinline__ void pair_vec(const Box& b, const double4& xi, const double4& xj, T v[3], T& r2) {
+    const double dd[3] = {xj.x - xi.x, xj.y - xi.y, xj.z - xi.z};
+    for (int k = 0; k < 3; ++k) {
+        double t = dd[k];
+        if (b.per[k]) t = fma(-b.L[k], rint(t * b.invL[k]), t);
+        v[k] = (T)t;
+    }
+    r2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+}
 
 }  // namespace mixd

@@ -12,9 +12,13 @@ void launch_build(const Dev& d, cudaStream_t s);
 // weights, sets, compaction (k_sets.cu)
 void launch_sets(const Dev& d, const Regions& r, cudaStream_t s);
 
-// expensive potential (k_ace.cu); returns cudaSuccess or the launch error
+// expensive potential (k_ace.cuh, k_ace_f32.cu, k_ace_f64.cu); returns cudaSuccess or the launch error
 cudaError_t ace_configure(int precision, int L, int n, int cap, size_t* smem, int* grid);
 void launch_ace(const Dev& d, const void* tab, int precision, int L, size_t smem, int grid, cudaStream_t s);
+cudaError_t ace_configure_f32(int L, int n, int cap, size_t* smem, int* grid);
+cudaError_t ace_configure_f64(int L, int n, int cap, size_t* smem, int* grid);
+void launch_ace_f32(const Dev& d, const void* tab, int L, size_t smem, int grid, cudaStream_t s);
+void launch_ace_f64(const Dev& d, const void* tab, int L, size_t smem, int grid, cudaStream_t s);
 
 // cheap potential (k_spline.cu)
 cudaError_t spline_configure(int precision, int cap, size_t* smem, int* grid);

@@ -73,7 +73,8 @@ class mix_spline(ctypes.Structure):
 
 class mix_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("skin", ctypes.c_double), ("blend", ctypes.c_int),
-                ("buffer_exp", ctypes.c_double), ("buffer_cheap", ctypes.c_double), ("nbr_cap", ctypes.c_int)]
+                ("buffer_exp", ctypes.c_double), ("buffer_cheap", ctypes.c_double), ("nbr_cap", ctypes.c_int),
+                ("no_graphs", ctypes.c_int)]
 
 
 class mix_region(ctypes.Structure):
@@ -166,7 +167,7 @@ class Context:
     def __init__(self, workload: "I.Workload", precision: int = MIX_FP64, device: str = "cuda:0",
                  nbr_cap: int = 0, blend: int = MIX_BLEND_LINEAR, buffer_exp: float = 0.0,
                  buffer_cheap: float = 0.0, skin: Optional[float] = None, regions: Optional[Sequence] = None,
-                 stream=None):
+                 stream=None, graphs: bool = True):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("no CUDA device: the mixed-MD path runs only on the GPU")
@@ -189,7 +190,7 @@ class Context:
                        _dp(pair))
         spld = mix_spline(float(sp.r_cut), float(sp.r_cut3), _dp(s2), _dp(s3))
         opt = mix_options(int(precision), float(workload.skin if skin is None else skin), int(blend),
-                          float(buffer_exp), float(buffer_cheap), int(nbr_cap))
+                          float(buffer_exp), float(buffer_cheap), int(nbr_cap), 0 if graphs else 1)
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
             h = ctypes.c_void_p()
