@@ -89,17 +89,17 @@ def job_throughput(n_atoms: int, steps: int, world: int, total_ms_max: float) ->
 
 def exp_flops_per_atom(wl, info, nnb_rc: float) -> float:
     """Linear ACE: density 2 n nlm Nnb; pair gradients (4 n nlm + 8 nlm) Nnb;
-    nu=2 readout + adjoint 4 n^2 nlm; nu=3 per l-triple: U = W A3 and
-    omega3 = W^T Z (2 (2l3+1) n^3 each), Z, omega1, omega2 (2 nnz(G) n^2 each),
-    E = sum Z U (2 (2l3+1) n^2)."""
+    nu=2 readout + adjoint 4 n^2 nlm; nu=3 readout + adjoint as counted by the
+    library from its l-triples (mix_info.nu3_flops_per_atom: U = W A3 and
+    omega3 = W^T Z, Z, E, and the omega1/omega2 terms that coinciding l's do
+    not make redundant)."""
     a = wl.ace
     n, nlm = a.n_rad, (a.l_max + 1) ** 2
     f = 2.0 * n * nlm * nnb_rc + (4.0 * n * nlm + 8.0 * nlm) * nnb_rc
     if a.nu_max >= 2:
         f += 4.0 * n * n * nlm
     if a.nu_max >= 3:
-        sd3 = info["tau_dim3_sum"]
-        f += 4.0 * sd3 * n ** 3 + 6.0 * info["gaunt_nnz"] * n * n + 2.0 * sd3 * n * n
+        f += float(info["nu3_flops_per_atom"])
     return f
 
 

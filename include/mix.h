@@ -238,6 +238,11 @@ typedef struct {
     int64_t gaunt_nnz;      /* non-zero real Gaunt coefficients over all l-triples */
     int64_t tau_dim3_sum;   /* sum over l-triples of (2 l3 + 1) */
     int64_t basis_size;     /* number of product-basis functions */
+    double nu3_flops_per_atom; /* nu = 3 readout and adjoint per evaluated atom:
+                                  sum over l-triples of U = W A3 and omega3 = W^T Z
+                                  (2 (2l3+1) n^3 each), Z (2 nnz n^2), E (2 (2l3+1) n^2),
+                                  omega1 (2 nnz n^2, unless all l equal) and omega2
+                                  (2 nnz n^2, only for distinct l's) */
     size_t workspace_bytes;
     size_t exp_smem_bytes;  /* dynamic shared memory of the expensive kernel */
     int exp_grid;           /* its persistent grid (CTAs) */

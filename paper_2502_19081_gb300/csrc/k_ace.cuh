@@ -14,6 +14,10 @@
 //        U[q1 q2][m3] = sum_q3 W[q1 q2 q3] A[l3 m3][q3]
 //        Z[q1 q2][m3] = sum_(m1 m2) G A[l1 m1][q1] A[l2 m2][q2]   (Gaunt-sparse)
 //        E += sum Z U;  omega3 += W^T Z;  omega1 += G A2 U;  omega2 += G A1 U;
+//      each lane keeps a few W rows in registers for the U/Z pass; where two
+//      l's coincide W is symmetrised on the host, the adjoints through the
+//      coinciding factors are equal, and one of them is computed and scaled
+//      (omega2 only for distinct l's, omega1 not when all three are equal);
 //   5. omega = sum of the warp copies (fixed order);
 //   6. pair gradients dE_i/dr_ij = u sum_lm sigma_lm Y_lm
 //        + (grad_u p - u (u . grad_u p)) / r,  rho = omega R, sigma = omega R',
@@ -165,20 +169,24 @@ __device__ __forceinline__ void spline16(const T* __restrict__ c, T invh, T r, T
 __host__ __device__ constexpr int ace_pad(int x) { return (x + 3) & ~3; }
 
 // shared-memory layout (element offsets), shared by host sizing and the kernel
+// The density chunk buffers (R, Y of up to ACE_CH neighbours) and the per-warp
+// nu = 3 scratch are never live together and share one region.
 struct AceSmem {
-    int o_u, o_At, o_om, o_cR, o_cY, o_gp, o_w, ws, total;
+    int o_u, o_At, o_om, o_gp, o_w, o_cR, o_cY, ws, total;
     __host__ __device__ AceSmem(int cap, int n, int nq, int L, int NP) {
         const int nlm = (L + 1) * (L + 1);
         const int D = 2 * L + 1;
         o_u = 0;
         o_At = ace_pad(4 * cap);
         o_om = o_At + nlm * NP;
-        o_cR = o_om + nlm * NP;
-        o_cY = o_cR + ACE_CH * NP;
-        o_gp = o_cY + ace_pad(ACE_CH * nlm);
+        o_gp = o_om + nlm * NP;
         o_w = o_gp + 2 * 64 * 4;
-        ws = 2 * D * n * NP + D * nq + nlm * NP;   // per warp: U1, U2, ZT, omega copy
-        total = o_w + ACE_WARPS * ws;
+        o_cR = o_w;
+        o_cY = o_cR + ACE_CH * NP;
+        ws = D * n * NP + D * nq + nlm * NP;   // per warp: U, ZT, omega copy
+        const int chunk = ACE_CH * NP + ace_pad(ACE_CH * nlm);
+        const int wsall = ACE_WARPS * ws;
+        total = o_w + (chunk > wsall ? chunk : wsall);
     }
 };
 
@@ -203,13 +211,9 @@ __global__ void __launch_bounds__(ACE_NT) k_ace(Dev d, AceTab<T> tab) {
     T* s_cR = sm + lay.o_cR;
     T* s_cY = sm + lay.o_cY;
     T* s_gp = sm + lay.o_gp;
-    T* U1 = sm + lay.o_w + warp * lay.ws;
-    T* U2 = U1 + D * n * NP;
-    T* ZT = U2 + D * n * NP;
+    T* U1 = sm + lay.o_w + warp * lay.ws;   // U[m3][q1][q2]
+    T* ZT = U1 + D * n * NP;                // Z[m3][q1 q2]
     T* omw = ZT + D * nq;
-
-    // zero this warp's scratch once: the padding (q >= n, q1 q2 >= n*n) is never written again
-    for (int k = lane; k < lay.ws; k += 32) U1[k] = T(0);
 
     V* GE = reinterpret_cast<V*>(d.ge);
     const T rc2 = (T)d.rce2;
@@ -303,7 +307,9 @@ __global__ void __launch_bounds__(ACE_NT) k_ace(Dev d, AceTab<T> tab) {
             const int o = tid + j * ACE_NT;
             if (o < NLM * NP) s_At[o] = acc[j];
         }
-        for (int k = lane; k < NLM * NP; k += 32) omw[k] = T(0);
+        // the density chunks are dead: zero this warp's scratch (its padding,
+        // q >= n and q1 q2 >= n*n, is read as zeros below and never written)
+        for (int k = lane; k < lay.ws; k += 32) U1[k] = T(0);
         __syncthreads();
 
         // 3. nu = 1 and nu = 2; initialises omega
@@ -338,6 +344,10 @@ __global__ void __launch_bounds__(ACE_NT) k_ace(Dev d, AceTab<T> tab) {
             const int t = tab.wt_list[it];
             const int l1 = tab.tau[4 * t], l2 = tab.tau[4 * t + 1], l3 = tab.tau[4 * t + 2];
             const int gb = tab.tau[4 * t + 3];
+            // coinciding l's (W symmetrised on the host): scale instead of recompute
+            const int mode = tab.tmode[t];
+            const T mult1 = mode == 1 ? T(2) : T(1);
+            const T mult3 = mode == 3 ? T(3) : (mode == 2 ? T(2) : T(1));
             const int d1 = 2 * l1 + 1, d2 = 2 * l2 + 1, d3 = 2 * l3 + 1;
             const T* A1 = s_At + l1 * l1 * NP;
             const T* A2 = s_At + l2 * l2 * NP;
@@ -347,35 +357,66 @@ __global__ void __launch_bounds__(ACE_NT) k_ace(Dev d, AceTab<T> tab) {
             const int* g2o = g1o + d1 + 1;
             const T* W = tab.W3 + (int64_t)t * n * n * NP;
             const T* WT = tab.WT3 + (int64_t)t * n * nq;
-            // U and Z, one (q1, q2) row per lane
-            for (int q12 = lane; q12 < n * n; q12 += 32) {
-                const int q1 = q12 / n, q2 = q12 - q1 * n;
-                T w[NP];
+            // U and Z: each lane holds RC coefficient rows (q1 q2) = base + lane + 32 r
+            // in registers, so every broadcast load of an A row or a Gaunt entry
+            // feeds RC independent accumulations
+            constexpr int RC = sizeof(T) == 4 ? 4 : 2;
+            for (int base = 0; base < n * n; base += 32 * RC) {
+                int q1r[RC], q2r[RC];
+                bool vr[RC];
+                T w[RC][NP];
 #pragma unroll
-                for (int p = 0; p < NP; p += 4) {
-                    const V4<T> v = ldg4<T>(W + q12 * NP + p);
-                    w[p] = v.x;
-                    w[p + 1] = v.y;
-                    w[p + 2] = v.z;
-                    w[p + 3] = v.w;
-                }
-                for (int m3 = 0; m3 < d3; ++m3) {
-                    const T* ar = A3 + m3 * NP;
-                    T u = T(0);
+                for (int r = 0; r < RC; ++r) {
+                    const int q12 = base + lane + 32 * r;
+                    vr[r] = q12 < n * n;
+                    const int qq = vr[r] ? q12 : 0;
+                    q1r[r] = qq / n;
+                    q2r[r] = qq - q1r[r] * n;
 #pragma unroll
                     for (int p = 0; p < NP; p += 4) {
-                        const V4<T> v = ld4<T>(ar + p);
-                        u += w[p] * v.x + w[p + 1] * v.y + w[p + 2] * v.z + w[p + 3] * v.w;
+                        V4<T> v = ldg4<T>(W + qq * NP + p);
+                        if (!vr[r]) v = V4<T>{T(0), T(0), T(0), T(0)};
+                        w[r][p] = v.x;
+                        w[r][p + 1] = v.y;
+                        w[r][p + 2] = v.z;
+                        w[r][p + 3] = v.w;
                     }
-                    T z = T(0);
+                }
+                for (int m3 = 0; m3 < d3; ++m3) {
+                    T a[NP];
+#pragma unroll
+                    for (int p = 0; p < NP; p += 4) {
+                        const V4<T> v = ld4<T>(A3 + m3 * NP + p);
+                        a[p] = v.x;
+                        a[p + 1] = v.y;
+                        a[p + 2] = v.z;
+                        a[p + 3] = v.w;
+                    }
+                    T u[RC], z[RC];
+#pragma unroll
+                    for (int r = 0; r < RC; ++r) {
+                        T s = T(0);
+#pragma unroll
+                        for (int p = 0; p < NP; ++p) s += w[r][p] * a[p];
+                        u[r] = s;
+                        z[r] = T(0);
+                    }
                     for (int e = g3o[m3]; e < g3o[m3 + 1]; ++e) {
-                        const int pk = tab.gidx[e];
-                        z += tab.gval[e] * A1[(pk & 255) * NP + q1] * A2[(pk >> 8) * NP + q2];
+                        const int pk = __ldg(tab.gidx + e);
+                        const T g = __ldg(tab.gval + e);
+                        const T* a1 = A1 + (pk & 255) * NP;
+                        const T* a2 = A2 + (pk >> 8) * NP;
+#pragma unroll
+                        for (int r = 0; r < RC; ++r) z[r] += g * a1[q1r[r]] * a2[q2r[r]];
                     }
-                    U1[(m3 * n + q1) * NP + q2] = u;
-                    U2[(m3 * n + q2) * NP + q1] = u;
-                    ZT[m3 * nq + q12] = z;
-                    ep += u * z;
+#pragma unroll
+                    for (int r = 0; r < RC; ++r) {
+                        if (vr[r]) {
+                            U1[(m3 * n + q1r[r]) * NP + q2r[r]] = u[r];
+                            ZT[m3 * nq + base + lane + 32 * r] = z[r];
+                            ep += u[r] * z[r];
+                        }
+                    }
                 }
             }
             __syncwarp();
@@ -390,11 +431,11 @@ __global__ void __launch_bounds__(ACE_NT) k_ace(Dev d, AceTab<T> tab) {
                     const V4<T> b4 = ld4<T>(zr + p);
                     s += a4.x * b4.x + a4.y * b4.y + a4.z * b4.z + a4.w * b4.w;
                 }
-                omw[(l3 * l3 + m3) * NP + q3] += s;
+                omw[(l3 * l3 + m3) * NP + q3] += mult3 * s;
             }
             __syncwarp();
-            // omega1 += G A2 U
-            for (int o = lane; o < n * d1; o += 32) {
+            // omega1 += G A2 U (equal to omega3 when all three l's coincide)
+            if (mode != 3) for (int o = lane; o < n * d1; o += 32) {
                 const int q1 = o / d1, m1 = o - q1 * d1;
                 T accv = T(0);
                 for (int e = g1o[m1]; e < g1o[m1 + 1]; ++e) {
@@ -410,24 +451,20 @@ __global__ void __launch_bounds__(ACE_NT) k_ace(Dev d, AceTab<T> tab) {
                     }
                     accv += tab.gval[e] * s;
                 }
-                omw[(l1 * l1 + m1) * NP + q1] += accv;
+                omw[(l1 * l1 + m1) * NP + q1] += mult1 * accv;
             }
             __syncwarp();
-            // omega2 += G A1 U
-            for (int o = lane; o < n * d2; o += 32) {
+            // omega2 += G A1 U, needed only when the three l's are distinct
+            // (otherwise it equals omega1 or omega3, already scaled in)
+            if (mode == 0) for (int o = lane; o < n * d2; o += 32) {
                 const int q2 = o / d2, m2 = o - q2 * d2;
                 T accv = T(0);
                 for (int e = g2o[m2]; e < g2o[m2 + 1]; ++e) {
                     const int pk = tab.gidx[e];
                     const T* ar = A1 + (pk & 255) * NP;
-                    const T* ur = U2 + ((pk >> 8) * n + q2) * NP;
+                    const T* ur = U1 + (pk >> 8) * n * NP + q2;
                     T s = T(0);
-#pragma unroll
-                    for (int p = 0; p < NP; p += 4) {
-                        const V4<T> a4 = ld4<T>(ar + p);
-                        const V4<T> b4 = ld4<T>(ur + p);
-                        s += a4.x * b4.x + a4.y * b4.y + a4.z * b4.z + a4.w * b4.w;
-                    }
+                    for (int q1 = 0; q1 < n; ++q1) s += ar[q1] * ur[q1 * NP];
                     accv += tab.gval[e] * s;
                 }
                 omw[(l2 * l2 + m2) * NP + q2] += accv;
@@ -440,7 +477,7 @@ __global__ void __launch_bounds__(ACE_NT) k_ace(Dev d, AceTab<T> tab) {
         for (int o = tid; o < NLM * NP; o += ACE_NT) {
             T s = s_om[o];
 #pragma unroll
-            for (int w = 0; w < ACE_WARPS; ++w) s += sm[lay.o_w + w * lay.ws + 2 * D * n * NP + D * nq + o];
+            for (int w = 0; w < ACE_WARPS; ++w) s += sm[lay.o_w + w * lay.ws + D * n * NP + D * nq + o];
             s_om[o] = s;
         }
         __syncthreads();

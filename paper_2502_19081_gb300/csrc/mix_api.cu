@@ -134,7 +134,8 @@ struct mix_ctx {
     int cap;
     // tables (offsets in the arena) and their element-type views
     Arena arena;
-    size_t o_c1, o_S2, o_W3, o_WT3, o_tau, o_goff, o_gidx, o_gval, o_ylmk, o_pair, o_sc2, o_sc3, o_wtoff, o_wtlist;
+    size_t o_c1, o_S2, o_W3, o_WT3, o_tau, o_goff, o_gidx, o_gval, o_ylmk, o_pair, o_sc2, o_sc3, o_wtoff, o_wtlist,
+        o_tmode;
     int ntau, np, nq;
     AceTab<double> ace64;
     AceTab<float> ace32;
@@ -148,6 +149,7 @@ struct mix_ctx {
     size_t ace_smem, spl_smem;
     int ace_grid, spl_grid;
     int64_t gaunt_nnz, tau_d3_sum, basis_size;
+    double nu3_flops;
     int64_t launches;
     bool profiling;
     bool opt_graphs;
@@ -308,6 +310,41 @@ int build_tables(mix_ctx* c, const mix_ace* a, const mix_spline* sp) {
     const int np = (n + 3) & ~3, nq = (n * n + 3) & ~3;
     c->np = np;
     c->nq = nq;
+    // Where two l's of a triple coincide the Gaunt factor is symmetric in the
+    // matching (l, m) pairs, so the energy only sees the part of W symmetric in
+    // the matching n indices.  Symmetrising W there leaves E unchanged and makes
+    // the adjoints through the coinciding factors equal (the kernel then
+    // computes one and scales it): tau[4t+3] keeps the Gaunt offset row, the
+    // mode goes to tmode[t]: 0 distinct, 1 l1 == l2, 2 l2 == l3, 3 all equal.
+    std::vector<int> tmode(c->ntau, 0);
+    for (int t = 0; t < c->ntau; ++t) {
+        const int l1 = tau[4 * t], l2 = tau[4 * t + 1], l3 = tau[4 * t + 2];
+        const int mode = (l1 == l2 && l2 == l3) ? 3 : (l1 == l2 ? 1 : (l2 == l3 ? 2 : 0));
+        tmode[t] = mode;
+        double* Wt = W3.data() + (size_t)t * n * n * n;
+        std::vector<double> S(Wt, Wt + (size_t)n * n * n);
+        auto at = [&](int a, int b, int cc) -> double { return Wt[((size_t)a * n + b) * n + cc]; };
+        for (int a = 0; a < n; ++a)
+            for (int b = 0; b < n; ++b)
+                for (int cc = 0; cc < n; ++cc) {
+                    double v = at(a, b, cc);
+                    if (mode == 1) v = 0.5 * (at(a, b, cc) + at(b, a, cc));
+                    else if (mode == 2) v = 0.5 * (at(a, b, cc) + at(a, cc, b));
+                    else if (mode == 3)
+                        v = (at(a, b, cc) + at(a, cc, b) + at(b, a, cc) + at(b, cc, a) + at(cc, a, b) + at(cc, b, a)) / 6.0;
+                    S[((size_t)a * n + b) * n + cc] = v;
+                }
+        std::copy(S.begin(), S.end(), Wt);
+    }
+    c->nu3_flops = 0.0;
+    for (int t = 0; t < c->ntau; ++t) {
+        const int l3 = tau[4 * t + 2], gb = tau[4 * t + 3];
+        const double nnz = goff[gb + 2 * l3 + 1] - goff[gb], d3 = 2 * l3 + 1, nn = n;
+        double f = 4.0 * d3 * nn * nn * nn + 2.0 * nnz * nn * nn + 2.0 * d3 * nn * nn;
+        if (tmode[t] != 3) f += 2.0 * nnz * nn * nn;
+        if (tmode[t] == 0) f += 2.0 * nnz * nn * nn;
+        c->nu3_flops += f;
+    }
     std::vector<double> W3p((size_t)c->ntau * n * n * np, 0.0), WT3((size_t)c->ntau * n * nq, 0.0);
     for (int t = 0; t < c->ntau; ++t)
         for (int q12 = 0; q12 < n * n; ++q12)
@@ -375,6 +412,7 @@ int build_tables(mix_ctx* c, const mix_ace* a, const mix_spline* sp) {
     c->o_gidx = A.put(gidx);
     c->o_wtoff = A.put(wt_off);
     c->o_wtlist = A.put(wt_list);
+    c->o_tmode = A.put(tmode);
     A.bytes.resize(align256(A.bytes.size()));
     return MIX_OK;
 }
@@ -395,6 +433,7 @@ void fill_tabs(mix_ctx* c, unsigned char* base, AceTab<T>& at, SplTab<T>& st) {
     at.WT3 = reinterpret_cast<const T*>(base + c->o_WT3);
     at.wt_off = reinterpret_cast<const int*>(base + c->o_wtoff);
     at.wt_list = reinterpret_cast<const int*>(base + c->o_wtlist);
+    at.tmode = reinterpret_cast<const int*>(base + c->o_tmode);
     at.tau = reinterpret_cast<const int*>(base + c->o_tau);
     at.goff = reinterpret_cast<const int*>(base + c->o_goff);
     at.gidx = reinterpret_cast<const int*>(base + c->o_gidx);
@@ -957,6 +996,7 @@ int mix_get_info(const mix_ctx* c, mix_info* info) {
     info->gaunt_nnz = c->gaunt_nnz;
     info->tau_dim3_sum = c->tau_d3_sum;
     info->basis_size = c->basis_size;
+    info->nu3_flops_per_atom = c->nu3_flops;
     info->workspace_bytes = c->ws_bytes;
     info->exp_smem_bytes = c->ace_smem;
     info->exp_grid = c->ace_grid;

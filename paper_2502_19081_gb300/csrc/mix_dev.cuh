@@ -117,6 +117,8 @@ struct AceTab {
     const T* WT3;       // [ntau][n][nq]    the same, transposed: W[q3][q1 q2]
     const int* wt_off;  // [ACE_WARPS + 1] ranges of wt_list handled by each warp
     const int* wt_list; // [ntau] l-triple indices grouped by warp
+    const int* tmode;   // [ntau] 0: l's distinct, 1: l1 == l2, 2: l2 == l3, 3: all equal
+                        // (W3 symmetrised over the matching n indices)
     const int* tau;     // [ntau][4]: l1, l2, l3, index of its first offset row
     const int* goff;    // offset rows: for each tau, three orderings (by m3, m1, m2),
                         // each 2l+2 entries (start index per m, then end)

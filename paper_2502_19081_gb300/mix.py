@@ -91,6 +91,7 @@ class mix_stats(ctypes.Structure):
 class mix_info(ctypes.Structure):
     _fields_ = [("nbr_cap", ctypes.c_int), ("n_tau", ctypes.c_int), ("gaunt_nnz", ctypes.c_int64),
                 ("tau_dim3_sum", ctypes.c_int64), ("basis_size", ctypes.c_int64),
+                ("nu3_flops_per_atom", ctypes.c_double),
                 ("workspace_bytes", ctypes.c_size_t), ("exp_smem_bytes", ctypes.c_size_t),
                 ("exp_grid", ctypes.c_int), ("exp_threads", ctypes.c_int), ("cheap_smem_bytes", ctypes.c_size_t),
                 ("cheap_grid", ctypes.c_int), ("launches_per_evaluation", ctypes.c_int),
