@@ -282,7 +282,7 @@ int mix_fma_peak(int precision, void* cuda_stream, double* flops_per_s);
 /* slot map as a context does (cell list, r2 < r_list^2 with the minimum      */
 /* image, rows ascending), but keeps all of its scratch -- a folded copy of   */
 /* the positions, the cell list, status words -- in one fixed device array    */
-/* inside the library (about 3 MB, reserved on every GPU that loads the       */
+/* inside the library (about 3.6 MB, reserved on every GPU that loads the     */
 /* library until the process exits).  It calls no cudaMalloc, cudaFree or     */
 /* allocating library routine.                                                */
 /*                                                                            */

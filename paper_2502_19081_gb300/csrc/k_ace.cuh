@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(ACE_NT) k_ace(Dev d, AceTab<T> tab) {
 
     for (int a = blockIdx.x; a < count; a += gridDim.x) {
         const int i = d.act_e[a];
-        const double4 xi = d.x[i];
+        const PairFrame<T> pf(d, i);
         const int m = d.nnb[i];
         const int* row = d.nbr + (int64_t)i * cap;
         V* grow = GE + (int64_t)a * cap;
@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(ACE_NT) k_ace(Dev d, AceTab<T> tab) {
             bool ok = false;
             T dv[3] = {T(0), T(0), T(0)}, r2 = T(0);
             if (s < m) {
-                pair_vec<T>(d.box, xi, d.x[row[s]], dv, r2);
+                pf.vec(d, row[s], dv, r2);
                 ok = r2 < rc2;
                 if (!ok) {
                     V z;
@@ -576,8 +576,7 @@ __global__ void __launch_bounds__(ACE_NT) k_ace(Dev d, AceTab<T> tab) {
         }
 
         // site energy (float64, fixed reduction order)
-        double e = (double)ep;
-        for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
+        const double e = warp_sum_to_double(ep);   // fixed order; compensated for float
         if (lane == 0) s_red[warp] = e;
         __syncthreads();
         if (tid == 0) {

@@ -63,15 +63,9 @@ __global__ void __launch_bounds__(G_WARPS * 32) k_gather(Dev d, int integrate, d
                 }
             }
         }
-        double ex = tex, ey = tey, ez = tez, cx = tcx, cy = tcy, cz = tcz;
-        for (int o = 16; o > 0; o >>= 1) {
-            ex += __shfl_down_sync(0xffffffffu, ex, o);
-            ey += __shfl_down_sync(0xffffffffu, ey, o);
-            ez += __shfl_down_sync(0xffffffffu, ez, o);
-            cx += __shfl_down_sync(0xffffffffu, cx, o);
-            cy += __shfl_down_sync(0xffffffffu, cy, o);
-            cz += __shfl_down_sync(0xffffffffu, cz, o);
-        }
+        // lanes combined in a fixed order; float partials with a compensated sum
+        const double ex = warp_sum_to_double(tex), ey = warp_sum_to_double(tey), ez = warp_sum_to_double(tez);
+        const double cx = warp_sum_to_double(tcx), cy = warp_sum_to_double(tcy), cz = warp_sum_to_double(tcz);
         if (lane == 0) {
             const double wc = 1.0 - w;
             double4 F;

@@ -52,6 +52,8 @@ __global__ void k_disp(Dev d, int integrate, double dt, double h, int force_rebu
         const double4 xb = d.xb[i];
         const double dx = x.x - xb.x, dy = x.y - xb.y, dz = x.z - xb.z;
         if (dx * dx + dy * dy + dz * dz > d.half_skin2) d.status[SW_REBUILD] = 1;
+        // relative to the cell of the last build (recomputed by k_cell_bin on rebuilds)
+        if (d.xr) d.xr[i] = cell_relative(d.box, d.cells, x, d.cell3[i]);
     }
 }
 
@@ -74,6 +76,9 @@ __global__ void k_cell_bin(Dev d) {
     const int cz = cell_coord(d.box, d.cells, xs[2], 2);
     const int c = (cz * d.cells.nc[1] + cy) * d.cells.nc[0] + cx;
     d.cell_of[i] = c;
+    const int c3 = cx | (cy << 10) | (cz << 20);
+    d.cell3[i] = c3;
+    d.xr[i] = cell_relative(d.box, d.cells, x, c3);
     atomicAdd(d.cell_count + c, 1);
 }
 

@@ -26,7 +26,9 @@ constexpr size_t NA_O_STATUS = 0;
 constexpr size_t NA_O_X = na_al(NA_O_STATUS + SW_COUNT * sizeof(int));
 constexpr size_t NA_O_XB = na_al(NA_O_X + NA_MAX_ATOMS * sizeof(double4));
 constexpr size_t NA_O_XF = na_al(NA_O_XB + NA_MAX_ATOMS * sizeof(double4));
-constexpr size_t NA_O_CELL_OF = na_al(NA_O_XF + NA_MAX_ATOMS * sizeof(float4));
+constexpr size_t NA_O_XR = na_al(NA_O_XF + NA_MAX_ATOMS * sizeof(float4));
+constexpr size_t NA_O_CELL3 = na_al(NA_O_XR + NA_MAX_ATOMS * sizeof(float4));
+constexpr size_t NA_O_CELL_OF = na_al(NA_O_CELL3 + NA_MAX_ATOMS * sizeof(int));
 constexpr size_t NA_O_CELL_ATOMS = na_al(NA_O_CELL_OF + NA_MAX_ATOMS * sizeof(int));
 constexpr size_t NA_O_CELL_COUNT = na_al(NA_O_CELL_ATOMS + NA_MAX_ATOMS * sizeof(int));
 constexpr size_t NA_O_CELL_FILL = na_al(NA_O_CELL_COUNT + NA_MAX_CELLS * sizeof(int));
@@ -92,6 +94,9 @@ extern "C" int mix_neighbours_noalloc(int64_t n_atoms, const double* x_dev, cons
         }
         d.cells.nc[k] = nc;
         d.cells.invh[k] = (double)nc / box_len[k];
+        d.cells.h[k] = box_len[k] / (double)nc;
+        d.cells.hf[k] = (float)d.cells.h[k];
+        if (nc > 1023) return MIX_EINVAL;
         ncell *= nc;
     }
     if (ncell > NA_MAX_CELLS) return MIX_EINVAL;
@@ -105,6 +110,8 @@ extern "C" int mix_neighbours_noalloc(int64_t n_atoms, const double* x_dev, cons
     d.x = reinterpret_cast<double4*>(base + NA_O_X);
     d.xb = reinterpret_cast<double4*>(base + NA_O_XB);
     d.xf = reinterpret_cast<float4*>(base + NA_O_XF);
+    d.xr = reinterpret_cast<float4*>(base + NA_O_XR);
+    d.cell3 = reinterpret_cast<int*>(base + NA_O_CELL3);
     double extent = 0.0;
     for (int k = 0; k < 3; ++k) extent = fmax(extent, fabs(box_lo[k]) + box_len[k]);
     d.exact_lists = extent > 2000.0 ? 1 : 0;

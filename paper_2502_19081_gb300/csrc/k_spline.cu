@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(SPL_WARPS * 32) k_spline(Dev d, SplTab<T> tab)
 
     for (int a = blockIdx.x * SPL_WARPS + warp; a < count; a += gridDim.x * SPL_WARPS) {
         const int i = d.act_c[a];
-        const double4 xi = d.x[i];
+        const PairFrame<T> pf(d, i);
         const int m = d.nnb[i];
         const int* row = d.nbr + (int64_t)i * cap;
         V* grow = GC + (int64_t)a * cap;
@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(SPL_WARPS * 32) k_spline(Dev d, SplTab<T> tab)
             if (c * 32 < m) {
                 if (s < m) {
                     T r2;
-                    pair_vec<T>(d.box, xi, d.x[row[s]], dv3, r2);
+                    pf.vec(d, row[s], dv3, r2);
                     if (r2 < rc2) {
                         r = sqrt(r2);
                         T v, dv;
@@ -200,8 +200,7 @@ __global__ void __launch_bounds__(SPL_WARPS * 32) k_spline(Dev d, SplTab<T> tab)
                 grow[s] = gv;
             }
         }
-        double epart = (double)ep;   // float64 across lanes, fixed order
-        for (int o = 16; o > 0; o >>= 1) epart += __shfl_down_sync(0xffffffffu, epart, o);
+        const double epart = warp_sum_to_double(ep);   // fixed order; compensated for float
         if (lane == 0) d.esite_c[i] = epart;
         __syncwarp();
     }

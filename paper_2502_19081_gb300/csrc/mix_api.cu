@@ -144,7 +144,7 @@ struct mix_ctx {
     // workspace
     size_t ws_bytes;
     size_t off_tab;
-    size_t o_status, o_xb, o_xf, o_cell_of, o_cell_count, o_cell_start, o_cell_fill, o_cell_atoms, o_nnb, o_nbr, o_rev,
+    size_t o_status, o_xb, o_xf, o_xr, o_cell3, o_cell_of, o_cell_count, o_cell_start, o_cell_fill, o_cell_atoms, o_nnb, o_nbr, o_rev,
         o_lam, o_wgt, o_flags, o_act_e, o_act_c, o_pos_e, o_pos_c, o_blk_e, o_blk_c, o_ge, o_gc, o_ee, o_ec;
     size_t ace_smem, spl_smem;
     int ace_grid, spl_grid;
@@ -459,6 +459,8 @@ void layout(mix_ctx* c) {
     c->o_status = take(SW_COUNT * sizeof(int));
     c->o_xb = take(N * sizeof(double4));
     c->o_xf = take(N * sizeof(float4));
+    c->o_xr = take(N * sizeof(float4));
+    c->o_cell3 = take(N * sizeof(int));
     c->o_cell_of = take(N * 4);
     c->o_cell_count = take(nc * 4);
     c->o_cell_start = take((nc + 1) * 4);
@@ -669,6 +671,9 @@ int mix_init(const mix_system* sys, const mix_ace* a, const mix_spline* sp, cons
         }
         d.cells.nc[k] = ncd;
         d.cells.invh[k] = (double)ncd / sys->box_len[k];
+        d.cells.h[k] = sys->box_len[k] / (double)ncd;
+        d.cells.hf[k] = (float)d.cells.h[k];
+        if (ncd > 1023) return bad("more than 1023 cells along one dimension");
         vol *= sys->box_len[k];
     }
     const int64_t ncell = (int64_t)d.cells.nc[0] * d.cells.nc[1] * d.cells.nc[2];
@@ -751,6 +756,8 @@ int mix_bind(mix_ctx* c, double* x, double* v, double* f, void* ws) {
     d.status = reinterpret_cast<int*>(w + c->o_status);
     d.xb = reinterpret_cast<double4*>(w + c->o_xb);
     d.xf = reinterpret_cast<float4*>(w + c->o_xf);
+    d.xr = reinterpret_cast<float4*>(w + c->o_xr);
+    d.cell3 = reinterpret_cast<int*>(w + c->o_cell3);
     d.cell_of = reinterpret_cast<int*>(w + c->o_cell_of);
     d.cell_count = reinterpret_cast<int*>(w + c->o_cell_count);
     d.cell_start = reinterpret_cast<int*>(w + c->o_cell_start);

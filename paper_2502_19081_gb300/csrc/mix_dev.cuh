@@ -46,7 +46,18 @@ struct Cells {
     int nc[3];
     int ncell;
     double invh[3];
+    double h[3];     // cell widths L / nc
+    float hf[3];
 };
+
+// position relative to the origin of cell (cx, cy, cz), rounded once to float
+__device__ __forceinline__ float4 cell_relative(const Box& b, const Cells& c, const double4& x, int c3) {
+    const int cc[3] = {c3 & 1023, (c3 >> 10) & 1023, (c3 >> 20) & 1023};
+    const double xs[3] = {x.x, x.y, x.z};
+    float r[3];
+    for (int k = 0; k < 3; ++k) r[k] = (float)(xs[k] - (b.lo[k] + (double)cc[k] * c.h[k]));
+    return make_float4(r[0], r[1], r[2], 0.f);
+}
 
 struct Regions {
     int n;
@@ -73,6 +84,8 @@ struct Dev {
     double4* f;
     double4* xb;
     float4* xf;          // float copy of the folded positions at the last build
+    float4* xr;          // position minus the origin of its cell (cell of the last build), float
+    int* cell3;          // cell coordinates of the last build, packed cx | cy << 10 | cz << 20
     int* status;
     int* cell_of;
     int* cell_count;
@@ -165,6 +178,29 @@ __device__ __forceinline__ int cell_coord(const Box& b, const Cells& c, double x
 
 __device__ __forceinline__ void set_status(int* st, int bits) { atomicOr(st + SW_STATUS, bits); }
 
+// Warp-wide sum delivered to lane 0 as float64, lanes combined in a fixed
+// order.  float64 inputs are summed in float64; float inputs are summed in
+// float with a compensation term (Knuth's TwoSum at every step), so the float
+// path keeps double-like accuracy for the sum without float64 arithmetic per
+// lane (float64 runs at 1/62 of float on GB300).
+__device__ __forceinline__ double warp_sum_to_double(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_sum_to_double(float v) {
+    float s = v, c = 0.f;
+    for (int o = 16; o > 0; o >>= 1) {
+        const float s2 = __shfl_down_sync(0xffffffffu, s, o);
+        const float c2 = __shfl_down_sync(0xffffffffu, c, o);
+        const float t = __fadd_rn(s, s2);
+        const float bb = __fsub_rn(t, s);
+        const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bb)), __fsub_rn(s2, bb));
+        s = t;
+        c = __fadd_rn(__fadd_rn(c, c2), e);
+    }
+    return (double)s + (double)c;
+}
+
 // Pair vector for the potentials: the difference and minimum image in float64
 // (positions are absolute coordinates of up to hundreds of Angstrom), then
 // rounded once to T; length and direction in T.
@@ -178,5 +214,43 @@ __device__ __forceinline__ void pair_vec(const Box& b, const double4& xi, const 
     }
     r2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
 }
+
+// Pair vectors of atom i in the kernel's arithmetic.  float64: pair_vec above.
+// float: from cell-relative float positions, x_j - x_i = xr_j - xr_i + dc h with
+// dc the cell offset (in {-1, 0, 1} per dimension for list neighbours, wrapped
+// in periodic dimensions), so no float64 operation is spent per pair.
+template <typename T>
+struct PairFrame;
+
+template <>
+struct PairFrame<double> {
+    double4 xi;
+    __device__ __forceinline__ PairFrame(const Dev& d, int i) : xi(d.x[i]) {}
+    __device__ __forceinline__ void vec(const Dev& d, int j, double v[3], double& r2) const {
+        pair_vec<double>(d.box, xi, d.x[j], v, r2);
+    }
+};
+
+template <>
+struct PairFrame<float> {
+    float4 xri;
+    int ci;
+    __device__ __forceinline__ PairFrame(const Dev& d, int i) : xri(d.xr[i]), ci(d.cell3[i]) {}
+    __device__ __forceinline__ void vec(const Dev& d, int j, float v[3], float& r2) const {
+        const float4 xrj = d.xr[j];
+        const int cj = d.cell3[j];
+        const float a[3] = {xrj.x - xri.x, xrj.y - xri.y, xrj.z - xri.z};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            int dc = ((cj >> (10 * k)) & 1023) - ((ci >> (10 * k)) & 1023);
+            if (d.box.per[k]) {
+                if (dc > 1) dc -= d.cells.nc[k];
+                else if (dc < -1) dc += d.cells.nc[k];
+            }
+            v[k] = a[k] + (float)dc * d.cells.hf[k];
+        }
+        r2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+    }
+};
 
 }  // namespace mixd
