@@ -251,6 +251,9 @@ typedef struct {
     int cheap_grid;
     int launches_per_evaluation;
     int64_t launches;       /* kernels enqueued since mix_bind */
+    int gather_grid;        /* CTAs of the gather kernel */
+    int build_grid;         /* CTAs of the neighbour-list kernel */
+    int buffer_grid;        /* CTAs of the buffer-scan kernel */
 } mix_info;
 
 int mix_get_info(const mix_ctx* ctx, mix_info* info);
@@ -270,6 +273,43 @@ int mix_get_profile(mix_ctx* ctx, double* total_ms /*[MIX_PHASES] nullable*/, do
  * CUDA events on `cuda_stream`.  Used as the arithmetic roofline.  Allocates
  * and frees a small device buffer (one value per block) for its result sink. */
 int mix_fma_peak(int precision, void* cuda_stream, double* flops_per_s);
+
+/* ------------------------------------------------------------------------ */
+/* Launch-shape autotuning and batches of trajectories.  The paper has no      */
+/* counterpart (its runs are single LAMMPS jobs); these serve many independent */
+/* defect cells on one GPU.                                                   */
+
+/* Autotune one bound context: times force evaluations at the current
+ * positions (which leave x, v and f unchanged) while varying, one at a time,
+ * the persistent grid of each potential kernel and the grids of the gather and
+ * buffer kernels, and keeps the fastest shapes (reported by mix_get_info).
+ * reps: timed evaluations per candidate (median). */
+int mix_tune(mix_ctx* ctx, int reps);
+
+typedef struct mix_batch mix_batch;
+
+/* Group n bound contexts that were all created on `cuda_stream`.  The batch
+ * borrows them: keep them alive until mix_batch_destroy.  Each step of the
+ * batch is one CUDA graph launch whose child graphs, one per member, have no
+ * dependencies on one another, so the members' kernels overlap on the device.
+ * Results equal those of stepping each member alone. */
+int mix_batch_create(mix_ctx* const* members, int n, void* cuda_stream, mix_batch** out);
+
+/* nsteps velocity-Verlet steps of every member (members whose forces are not
+ * current, or whose lists are stale, are first evaluated individually). */
+int mix_batch_step(mix_batch* b, double dt_fs, int nsteps);
+
+/* Wait for the batch and report the first member error (mix_batch_last_error
+ * names the member). */
+int mix_batch_sync(mix_batch* b);
+
+/* Autotune the batch: for grid divisors 1, 2, 4, 8, 16 applied to every
+ * member's persistent and gather grids, times launches of a graph of all
+ * members' force evaluations (state unchanged) and keeps the fastest divisor. */
+int mix_batch_tune(mix_batch* b, int reps, int* chosen_divisor);
+
+int mix_batch_destroy(mix_batch* b);
+const char* mix_batch_last_error(const mix_batch* b);
 
 /* ------------------------------------------------------------------------ */
 /* Neighbour lists for callers that cannot allocate device memory.  The paper  */

@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(G_WARPS * 32) k_gather(Dev d, int integrate, d
 
 void launch_gather(const Dev& d, int precision, int integrate, double h, cudaStream_t s) {
     int64_t want = (d.n + G_WARPS - 1) / G_WARPS;
-    int64_t lim = (int64_t)sm_count() * 8;
+    int64_t lim = d.grid_gather > 0 ? d.grid_gather : (int64_t)sm_count() * 8;
     const int grid = (int)(want < lim ? want : lim);
     if (precision == MIX_FP64)
         k_gather<double><<<grid > 0 ? grid : 1, G_WARPS * 32, 0, s>>>(d, integrate, h);

@@ -300,7 +300,7 @@ void launch_build(const Dev& d, cudaStream_t s) {
     int capp2 = 32;
     while (capp2 < d.cap) capp2 <<= 1;
     int64_t want = (d.n + NB_WARPS - 1) / NB_WARPS;
-    int64_t lim = (int64_t)sm_count() * 16;
+    int64_t lim = d.grid_build > 0 ? d.grid_build : (int64_t)sm_count() * 16;
     int grid = (int)(want < lim ? want : lim);
     k_neigh_build<<<grid > 0 ? grid : 1, NB_WARPS * 32, NB_WARPS * capp2 * sizeof(int), s>>>(d, capp2);
     const int64_t tot = d.n * (int64_t)d.cap;

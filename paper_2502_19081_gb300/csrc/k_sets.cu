@@ -196,7 +196,7 @@ void launch_sets(const Dev& d, const Regions& r, cudaStream_t s) {
     const int nb = (int)((d.n + 255) / 256);
     k_lambda<<<nb > 0 ? nb : 1, 256, 0, s>>>(d, r);
     int64_t want = (d.n + BUF_WARPS - 1) / BUF_WARPS;
-    int64_t lim = (int64_t)sm_count() * 8;
+    int64_t lim = d.grid_buffer > 0 ? d.grid_buffer : (int64_t)sm_count() * 8;
     const int gb = (int)(want < lim ? want : lim);
     k_buffer<<<gb > 0 ? gb : 1, BUF_WARPS * 32, 0, s>>>(d);
     k_count<<<d.nblk, SCAN_BLOCK, 0, s>>>(d);

@@ -148,6 +148,7 @@ struct mix_ctx {
         o_lam, o_wgt, o_flags, o_act_e, o_act_c, o_pos_e, o_pos_c, o_blk_e, o_blk_c, o_ge, o_gc, o_ee, o_ec;
     size_t ace_smem, spl_smem;
     int ace_grid, spl_grid;
+    int ace_grid_max, spl_grid_max;   // resident CTAs at full occupancy
     int64_t gaunt_nnz, tau_d3_sum, basis_size;
     double nu3_flops;
     int64_t launches;
@@ -719,6 +720,8 @@ int mix_init(const mix_system* sys, const mix_ace* a, const mix_spline* sp, cons
         return MIX_ECUDA;
     }
     e = spline_configure(c->precision, c->cap, &c->spl_smem, &c->spl_grid);
+    c->ace_grid_max = c->ace_grid;
+    c->spl_grid_max = c->spl_grid;
     if (e != cudaSuccess) {
         delete c;
         return MIX_ECUDA;
@@ -1012,6 +1015,9 @@ int mix_get_info(const mix_ctx* c, mix_info* info) {
     info->cheap_grid = c->spl_grid;
     info->launches_per_evaluation = LAUNCHES_PER_EVAL;
     info->launches = c->launches;
+    info->gather_grid = c->dev.grid_gather;
+    info->build_grid = c->dev.grid_build;
+    info->buffer_grid = c->dev.grid_buffer;
     return MIX_OK;
 }
 
@@ -1068,5 +1074,287 @@ const char* mix_strerror(int code) {
 }
 
 const char* mix_last_error(const mix_ctx* c) { return c ? c->err.c_str() : ""; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// autotuning and batches
+
+namespace {
+
+// median duration (ms) of `reps` force evaluations at the current positions
+// (integrate = 0 leaves x, v and f as they are), after one untimed evaluation
+int time_force_evals(mix_ctx* c, int reps, float* ms) {
+    int st = evaluate(c, 0, 0.0);
+    if (st) return st;
+    c->forces_valid = true;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return fail(c, MIX_ECUDA, "event");
+    std::vector<float> v;
+    for (int r = 0; r < reps; ++r) {
+        cudaEventRecord(e0, c->stream);
+        enqueue_evaluation(c, c->stream, 0, 0.0, 0, false);
+        cudaEventRecord(e1, c->stream);
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return cuda_fail(c, e, "tuning");
+        }
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        v.push_back(t);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    std::sort(v.begin(), v.end());
+    *ms = v.empty() ? 0.f : v[v.size() / 2];
+    return check_stream_error(c, "tuning");
+}
+
+// Coordinate descent over candidate values of one launch parameter.
+int tune_param(mix_ctx* c, int reps, int* param, const std::vector<int>& cand) {
+    int best = *param;
+    float tbest = 1e30f;
+    for (int v : cand) {
+        if (v < 1) continue;
+        *param = v;
+        float t = 0.f;
+        int st = time_force_evals(c, reps, &t);
+        if (st) return st;
+        if (t < tbest) {
+            tbest = t;
+            best = v;
+        }
+    }
+    *param = best;
+    return MIX_OK;
+}
+
+void set_grid_divisor(mix_ctx* c, int div) {
+    c->ace_grid = std::max(1, c->ace_grid_max / div);
+    c->spl_grid = std::max(1, c->spl_grid_max / div);
+    c->dev.grid_gather = std::max(1, sm_count() * 8 / div);
+    c->dev.grid_buffer = std::max(1, sm_count() * 8 / div);
+    drop_graph(c);
+}
+
+// one member evaluation captured into a (not instantiated) graph
+int member_graph(mix_ctx* c, int integrate, double dt, cudaGraph_t* g) {
+    if (!c->cap_stream) {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_fail(c, e, "capture stream");
+    }
+    cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamBeginCapture");
+    enqueue_evaluation(c, c->cap_stream, integrate, dt, 0, false, true);
+    e = cudaStreamEndCapture(c->cap_stream, g);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
+    return MIX_OK;
+}
+
+}  // namespace
+
+struct mix_batch {
+    std::vector<mix_ctx*> m;
+    std::vector<int64_t> regions_seen;
+    cudaStream_t stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    double dt = 0.0;
+    int divisor = 1;
+    std::string err;
+};
+
+namespace {
+
+int bfail(mix_batch* b, int code, const std::string& msg) {
+    b->err = msg;
+    return code;
+}
+
+void batch_drop(mix_batch* b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+}
+
+// parent graph with one independent child graph per member
+int batch_graph(mix_batch* b, int integrate, double dt, cudaGraph_t* graph, cudaGraphExec_t* exec) {
+    cudaGraph_t parent = nullptr;
+    cudaError_t e = cudaGraphCreate(&parent, 0);
+    if (e != cudaSuccess) return bfail(b, MIX_ECUDA, "cudaGraphCreate");
+    for (size_t k = 0; k < b->m.size(); ++k) {
+        mix_ctx* c = b->m[k];
+        cudaGraph_t g = nullptr;
+        int st = member_graph(c, integrate, dt, &g);
+        if (st) {
+            cudaGraphDestroy(parent);
+            return bfail(b, st, "member " + std::to_string(k) + ": " + c->err);
+        }
+        cudaGraphNode_t node;
+        e = cudaGraphAddChildGraphNode(&node, parent, nullptr, 0, g);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(parent);
+            return bfail(b, MIX_ECUDA, std::string("cudaGraphAddChildGraphNode: ") + cudaGetErrorString(e));
+        }
+    }
+    e = cudaGraphInstantiate(exec, parent, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(parent);
+        return bfail(b, MIX_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    }
+    *graph = parent;
+    return MIX_OK;
+}
+
+// evaluate members whose forces or lists are not current, one by one
+int batch_prepare(mix_batch* b) {
+    for (size_t k = 0; k < b->m.size(); ++k) {
+        mix_ctx* c = b->m[k];
+        if (!c->bound) return bfail(b, MIX_ESTATE, "member " + std::to_string(k) + " is not bound");
+        if (c->need_build || !c->forces_valid) {
+            int st = evaluate(c, 0, 0.0);
+            if (st) return bfail(b, st, "member " + std::to_string(k) + ": " + c->err);
+            c->forces_valid = true;
+        }
+    }
+    return MIX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mix_tune(mix_ctx* c, int reps) {
+    if (!c) return MIX_EINVAL;
+    if (!c->bound) return fail(c, MIX_ESTATE, "mix_tune before mix_bind");
+    if (reps < 1) reps = 3;
+    const int sms = sm_count();
+    std::vector<int> ga = {c->ace_grid_max, c->ace_grid_max * 3 / 4, c->ace_grid_max / 2, c->ace_grid_max / 4};
+    std::vector<int> gs = {c->spl_grid_max, c->spl_grid_max / 2, c->spl_grid_max / 4};
+    std::vector<int> gg = {sms * 2, sms * 4, sms * 8, sms * 16};
+    int st = tune_param(c, reps, &c->ace_grid, ga);
+    if (!st) st = tune_param(c, reps, &c->spl_grid, gs);
+    if (!st) st = tune_param(c, reps, &c->dev.grid_gather, gg);
+    if (!st) st = tune_param(c, reps, &c->dev.grid_buffer, gg);
+    drop_graph(c);
+    return st;
+}
+
+int mix_batch_create(mix_ctx* const* members, int n, void* stream, mix_batch** out) {
+    if (!out || n < 1 || !members) return MIX_EINVAL;
+    *out = nullptr;
+    mix_batch* b = new (std::nothrow) mix_batch();
+    if (!b) return MIX_ENOMEM;
+    b->stream = (cudaStream_t)stream;
+    for (int k = 0; k < n; ++k) {
+        mix_ctx* c = members[k];
+        if (!c || c->stream != b->stream) {
+            delete b;
+            return MIX_EINVAL;
+        }
+        b->m.push_back(c);
+        b->regions_seen.push_back(c->regions_version);
+    }
+    *out = b;
+    return MIX_OK;
+}
+
+int mix_batch_step(mix_batch* b, double dt, int nsteps) {
+    if (!b) return MIX_EINVAL;
+    if (nsteps < 0 || !(dt > 0) || !std::isfinite(dt)) return bfail(b, MIX_EINVAL, "dt / nsteps");
+    int st = batch_prepare(b);
+    if (st) return st;
+    bool stale = !b->exec || b->dt != dt;
+    for (size_t k = 0; k < b->m.size(); ++k)
+        if (b->regions_seen[k] != b->m[k]->regions_version) stale = true;
+    if (stale) {
+        batch_drop(b);
+        st = batch_graph(b, 1, dt, &b->graph, &b->exec);
+        if (st) return st;
+        b->dt = dt;
+        for (size_t k = 0; k < b->m.size(); ++k) b->regions_seen[k] = b->m[k]->regions_version;
+    }
+    for (int s = 0; s < nsteps; ++s) {
+        cudaError_t e = cudaGraphLaunch(b->exec, b->stream);
+        if (e != cudaSuccess) return bfail(b, MIX_ECUDA, std::string("cudaGraphLaunch: ") + cudaGetErrorString(e));
+    }
+    for (mix_ctx* c : b->m) {
+        c->steps += nsteps;
+        c->launches += (int64_t)LAUNCHES_PER_EVAL * nsteps;
+    }
+    return MIX_OK;
+}
+
+int mix_batch_sync(mix_batch* b) {
+    if (!b) return MIX_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(b, MIX_ECUDA, std::string("cudaStreamSynchronize: ") + cudaGetErrorString(e));
+    for (size_t k = 0; k < b->m.size(); ++k) {
+        int st = read_status(b->m[k]);
+        if (st) return bfail(b, st, "member " + std::to_string(k) + ": " + b->m[k]->err);
+    }
+    return MIX_OK;
+}
+
+int mix_batch_tune(mix_batch* b, int reps, int* chosen) {
+    if (!b) return MIX_EINVAL;
+    if (reps < 1) reps = 3;
+    int st = batch_prepare(b);
+    if (st) return st;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return bfail(b, MIX_ECUDA, "event");
+    int best = 1;
+    float tbest = 1e30f;
+    for (int div : {1, 2, 4, 8, 16}) {
+        for (mix_ctx* c : b->m) set_grid_divisor(c, div);
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t x = nullptr;
+        st = batch_graph(b, 0, 0.0, &g, &x);
+        if (st) break;
+        std::vector<float> v;
+        cudaGraphLaunch(x, b->stream);
+        for (int r = 0; r < reps; ++r) {
+            cudaEventRecord(e0, b->stream);
+            cudaGraphLaunch(x, b->stream);
+            cudaEventRecord(e1, b->stream);
+            cudaEventSynchronize(e1);
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            v.push_back(t);
+        }
+        cudaGraphExecDestroy(x);
+        cudaGraphDestroy(g);
+        std::sort(v.begin(), v.end());
+        const float t = v[v.size() / 2];
+        if (t < tbest) {
+            tbest = t;
+            best = div;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (mix_ctx* c : b->m) set_grid_divisor(c, best);
+    batch_drop(b);
+    b->divisor = best;
+    if (chosen) *chosen = best;
+    cudaError_t e = cudaGetLastError();
+    if (!st && e != cudaSuccess) st = bfail(b, MIX_ECUDA, cudaGetErrorString(e));
+    return st;
+}
+
+int mix_batch_destroy(mix_batch* b) {
+    if (!b) return MIX_OK;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    batch_drop(b);
+    delete b;
+    return MIX_OK;
+}
+
+const char* mix_batch_last_error(const mix_batch* b) { return b ? b->err.c_str() : ""; }
 
 }  // extern "C"

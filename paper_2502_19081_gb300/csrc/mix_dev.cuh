@@ -109,6 +109,10 @@ struct Dev {
     double* esite_e;
     double* esite_c;
     int nblk;            // blocks of the compaction kernels
+    // launch shapes chosen by the autotuner (0: default)
+    int grid_build;      // CTAs of the neighbour-list build (4 warps each)
+    int grid_buffer;     // CTAs of the buffer scan (8 warps each)
+    int grid_gather;     // CTAs of the gather (8 warps each)
 };
 
 template <typename T> struct Vec4;

@@ -396,6 +396,57 @@ def fe_screw(seed: int = 3, n_atoms: int = 256000, nrep_z: int = 26, sigma: floa
                     description="bcc Fe screw-dislocation cylinder (256000 atoms)")
 
 
+def si_replica(seed: int, n_target: int, defect: str, temp_k: float, ace: Ace = None,
+               spline: Spline = None) -> Workload:
+    """One Si defect cell of a batch: the diamond k1 x k2 x k3 box (k >= 3) whose
+    atom count is nearest n_target, then a vacancy (atom nearest the centre
+    removed) or a tetrahedral interstitial (atom added at the empty (1/2,1/2,1/2)a
+    site nearest the centre); Maxwell-Boltzmann velocities at temp_k; core sphere
+    6 A + ramp 2 A at the defect with the C1 potentials (shared when given)."""
+    a = 5.431
+    rng = np.random.default_rng(seed)
+    k = max(3, int(round((n_target / 8.0) ** (1.0 / 3.0))))
+    k3 = max(3, int(round(n_target / (8.0 * k * k))))
+    q = diamond_lattice(k, k, k3)                          # a/4 units
+    ctr = np.array([2 * k, 2 * k, 2 * k3])
+    if defect == "vacancy":
+        d2 = np.sum((q - ctr) ** 2, axis=1)
+        idx = int(np.argmin(d2))
+        site = q[idx] * (a / 4.0)
+        q = np.delete(q, idx, axis=0)
+        pos = q * (a / 4.0)
+    else:
+        # empty tetrahedral sites: (1/2,1/2,1/2)a + fcc translations, i.e. 2 + 4*cell + fcc offsets
+        cell = np.array([k // 2, k // 2, k3 // 2])
+        site = ((cell * 4 + np.array([2, 2, 2])) * (a / 4.0))
+        pos = np.concatenate([q * (a / 4.0), site[None, :]])
+    pos = pos + rng.normal(0.0, 0.05, pos.shape)
+    L = np.array([k * a, k * a, k3 * a])
+    pos = wrap_into_box(pos, L, (1, 1, 1))
+    v = maxwell_boltzmann(rng, pos.shape[0], MASS_SI, temp_k)
+    sysm = System(x=_pack(pos), v=v, mass=MASS_SI, box_lo=np.zeros(3), box_len=L, periodic=(1, 1, 1))
+    if ace is None or spline is None:
+        ace, spline = element_potentials("Si", np.random.default_rng(1), 5.0, 8, 3, 3)
+    reg = [Region(REGION_SPHERE, tuple(site), (0.0, 0.0, 1.0), 6.0, 2.0)]
+    return Workload(f"si_replica_{seed}", sysm, reg, ace, spline, skin=0.3, dt=1.0, steps=200,
+                    precision=PRECISION_FP32, seed=seed, extra={"defect": defect, "temp_k": temp_k})
+
+
+def si_replicas(n_replicas: int = 256, seed: int = 4, n_min: int = 1000, n_max: int = 20000):
+    """The batch of independent Si defect cells: sizes log-uniform on
+    [n_min, n_max], vacancy or interstitial with equal probability,
+    temperatures uniform on [300, 1500] K; one shared pair of potentials."""
+    rng = np.random.default_rng(seed)
+    ace, spl = element_potentials("Si", np.random.default_rng(1), 5.0, 8, 3, 3)
+    out = []
+    for r in range(n_replicas):
+        n_t = int(round(math.exp(rng.uniform(math.log(n_min), math.log(n_max)))))
+        defect = "vacancy" if rng.uniform() < 0.5 else "interstitial"
+        temp = float(rng.uniform(300.0, 1500.0))
+        out.append(si_replica(seed * 100000 + r, n_t, defect, temp, ace, spl))
+    return out
+
+
 WORKLOADS = {
     "si_vacancy_215": si_vacancy,
     "fe_dumbbell_8001": fe_dumbbell,

@@ -41,7 +41,8 @@ EXPORTS = [
     "mix_step_host", "mix_sync", "mix_get_stats", "mix_get_cells", "mix_get_neighbours",
     "mix_get_lambda", "mix_get_sets", "mix_get_site_energies", "mix_get_state", "mix_set_state",
     "mix_destroy", "mix_strerror", "mix_last_error", "mix_get_info", "mix_profile", "mix_get_profile",
-    "mix_fma_peak",
+    "mix_fma_peak", "mix_tune", "mix_batch_create", "mix_batch_step", "mix_batch_sync", "mix_batch_tune",
+    "mix_batch_destroy", "mix_batch_last_error",
 ]
 
 MIX_PHASES = 6
@@ -95,7 +96,8 @@ class mix_info(ctypes.Structure):
                 ("workspace_bytes", ctypes.c_size_t), ("exp_smem_bytes", ctypes.c_size_t),
                 ("exp_grid", ctypes.c_int), ("exp_threads", ctypes.c_int), ("cheap_smem_bytes", ctypes.c_size_t),
                 ("cheap_grid", ctypes.c_int), ("launches_per_evaluation", ctypes.c_int),
-                ("launches", ctypes.c_int64)]
+                ("launches", ctypes.c_int64), ("gather_grid", ctypes.c_int), ("build_grid", ctypes.c_int),
+                ("buffer_grid", ctypes.c_int)]
 
 
 _lock = threading.Lock()
@@ -143,6 +145,14 @@ def lib():
             L.mix_fma_peak.argtypes = [ctypes.c_int, P, dp]
             L.mix_neighbours_noalloc.argtypes = [ctypes.c_int64, P, dp, dp, ip, ctypes.c_double, ctypes.c_int,
                                                  P, P, P, P]
+            L.mix_tune.argtypes = [P, ctypes.c_int]
+            L.mix_batch_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, P, ctypes.POINTER(P)]
+            L.mix_batch_step.argtypes = [P, ctypes.c_double, ctypes.c_int]
+            L.mix_batch_sync.argtypes = [P]
+            L.mix_batch_tune.argtypes = [P, ctypes.c_int, ip]
+            L.mix_batch_destroy.argtypes = [P]
+            L.mix_batch_last_error.restype = ctypes.c_char_p
+            L.mix_batch_last_error.argtypes = [P]
             _lib = L
     return _lib
 
@@ -312,6 +322,10 @@ class Context:
         self._check(self.L.mix_get_state(self.h, _dp(x), _dp(v), _dp(f), ctypes.byref(st)), "mix_get_state")
         return x[:self.n], v[:self.n], f[:self.n], int(st.value)
 
+    def tune(self, reps: int = 3):
+        """Autotune the launch shapes on the current positions (state unchanged)."""
+        self._check(self.L.mix_tune(self.h, int(reps)), "mix_tune")
+
     def info(self) -> dict:
         s = mix_info()
         self._check(self.L.mix_get_info(self.h, ctypes.byref(s)), "mix_get_info")
@@ -334,6 +348,53 @@ class Context:
         fa = _f64(f) if f is not None else None
         self._check(self.L.mix_set_state(self.h, _dp(x), _dp(v), _dp(fa) if fa is not None else None, int(step),
                                          1 if fa is not None else 0), "mix_set_state")
+
+
+class Batch:
+    """Independent trajectories advanced together: one CUDA graph launch per
+    step, one child graph per member (mix_batch_*).  Members are Contexts
+    created on the same stream; the batch keeps them alive."""
+
+    def __init__(self, contexts: Sequence[Context]):
+        if not contexts:
+            raise ValueError("empty batch")
+        self.L = lib()
+        self.members = list(contexts)
+        stream = self.members[0].stream
+        arr = (ctypes.c_void_p * len(self.members))(*[c.h.value for c in self.members])
+        h = ctypes.c_void_p()
+        st = self.L.mix_batch_create(arr, len(self.members), ctypes.c_void_p(stream.cuda_stream), ctypes.byref(h))
+        if st != MIX_OK:
+            raise MixError(st, "mix_batch_create (members must be bound and share one stream)")
+        self.h = h
+
+    def _check(self, st: int, what: str):
+        if st != MIX_OK:
+            raise MixError(st, f"{what}: {self.L.mix_strerror(st).decode()}: "
+                               f"{self.L.mix_batch_last_error(self.h).decode()}")
+
+    def step(self, dt: float, nsteps: int = 1):
+        self._check(self.L.mix_batch_step(self.h, float(dt), int(nsteps)), "mix_batch_step")
+
+    def sync(self):
+        self._check(self.L.mix_batch_sync(self.h), "mix_batch_sync")
+
+    def tune(self, reps: int = 3) -> int:
+        out = ctypes.c_int()
+        self._check(self.L.mix_batch_tune(self.h, int(reps), ctypes.byref(out)), "mix_batch_tune")
+        return int(out.value)
+
+    def close(self):
+        h = getattr(self, "h", None)
+        if h:
+            self.L.mix_batch_destroy(h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def fma_peak(precision: int, stream=None) -> float:

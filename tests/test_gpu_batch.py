@@ -1,0 +1,94 @@
+"""Batches and autotuning through the C ABI (GPU).
+
+A batch advances independent replicas with one graph launch per step; each
+member must end bit-identical to the same replica stepped alone (kernels are
+deterministic and no kernel reads another member's data).  Autotuning times
+force evaluations only and must leave the state unchanged.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2502_19081_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mx():
+    from paper_2502_19081_gb300 import build, mix
+    build.build()
+    return mix
+
+
+def _replicas():
+    ace, spl = I.element_potentials("Si", np.random.default_rng(1), 5.0, 8, 3, 3)
+    specs = [(300, "vacancy", 300.0), (700, "interstitial", 900.0), (1500, "vacancy", 1500.0),
+             (2500, "interstitial", 600.0), (450, "vacancy", 1200.0), (1100, "interstitial", 450.0)]
+    return [I.si_replica(50 + k, n, dfc, t, ace, spl) for k, (n, dfc, t) in enumerate(specs)]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_batch_equals_members_alone(mx, prec):
+    wls = _replicas()
+    alone = []
+    for wl in wls:
+        c = mx.open_context(wl, precision=prec)
+        c.step(1.0, 20)
+        alone.append(c.get_state())
+        c.close()
+    members = [mx.open_context(wl, precision=prec) for wl in wls]
+    b = mx.Batch(members)
+    b.step(1.0, 8)
+    b.step(1.0, 12)
+    b.sync()
+    for c, (xa, va, fa, sa) in zip(members, alone):
+        x, v, f, s = c.get_state()
+        assert s == sa == 20
+        assert np.array_equal(x, xa) and np.array_equal(v, va) and np.array_equal(f, fa)
+    b.close()
+
+
+def test_batch_tune_keeps_results(mx):
+    wls = _replicas()[:4]
+    members = [mx.open_context(wl, precision=1) for wl in wls]
+    before = [c.get_state() for c in members]
+    b = mx.Batch(members)
+    div = b.tune(reps=2)
+    assert div in (1, 2, 4, 8, 16)
+    for c, st in zip(members, before):
+        x, v, f, _ = c.get_state()
+        assert np.array_equal(x, st[0]) and np.array_equal(v, st[1]) and np.array_equal(f, st[2])
+    b.step(1.0, 10)
+    b.sync()
+    for wl, c in zip(wls, members):
+        a = mx.open_context(wl, precision=1)
+        a.step(1.0, 10)
+        xa, va, fa, _ = a.get_state()
+        x, v, f, _ = c.get_state()
+        assert np.array_equal(x, xa) and np.array_equal(f, fa)
+    b.close()
+
+
+def test_context_tune_keeps_state_and_parity(mx):
+    wl = I.fe_dumbbell()
+    c = mx.open_context(wl)
+    x0, v0, f0, _ = c.get_state()
+    c.tune(reps=2)
+    x1, v1, f1, _ = c.get_state()
+    assert np.array_equal(x0, x1) and np.array_equal(v0, v1)
+    assert np.abs(f1 - f0).max() < 1e-13
+    info = c.info()
+    assert info["exp_grid"] >= 1 and info["gather_grid"] >= 1
+    c.step(1.0, 5)
+    x, _, F, _ = c.get_state()
+    FB, _, _ = oracle.Model(wl).forces(x, oracle.MODE_METHOD)
+    assert np.abs(F[:, :3] - FB[:, :3]).max() < 1e-10
+
+
+def test_replica_forces_match_oracle(mx):
+    for wl in _replicas()[:3]:
+        c = mx.open_context(wl, precision=1)
+        x, _, F, _ = c.get_state()
+        FB, _, _ = oracle.Model(wl).forces(x, oracle.MODE_METHOD)
+        assert np.abs(F[:, :3] - FB[:, :3]).max() <= 1e-3
