@@ -105,6 +105,8 @@ def lib():
             L.or_site.argtypes = [P, ctypes.c_int, ctypes.c_int, dp, dp, dp]
             L.or_density.argtypes = [P, ctypes.c_int, dp, dp]
             L.or_md.argtypes = [P, dp, dp, dp, ctypes.c_double, ctypes.c_int, ctypes.c_int, dp]
+            L.or_set_atomic.argtypes = [P, ctypes.POINTER(ctypes.c_uint8), ctypes.c_double, ctypes.c_double]
+            L.or_coordination.argtypes = [P, dp, ctypes.c_double, ip]
             L.or_set_threads.argtypes = [ctypes.c_int]
             L.or_get_threads.restype = ctypes.c_int
             _lib = L
@@ -225,6 +227,33 @@ class Model:
         if h:
             lib().or_model_free(h)
             self._h = None
+
+    def set_atomic(self, seeds=None, r_core: float = 0.0, r_blend: float = 0.0):
+        """Weights from seed atoms (Alg. 1-2); seeds: indices or a [N] mask, None
+        returns to the geometric regions."""
+        if seeds is None:
+            lib().or_set_atomic(self._h, None, 0.0, 0.0)
+            return
+        mask = np.zeros(max(self.n, 1), dtype=np.uint8)
+        s = np.asarray(seeds)
+        if s.dtype == bool or (s.size == self.n and set(np.unique(s)) <= {0, 1} and s.dtype != np.int64):
+            mask[:self.n] = s.astype(np.uint8)
+        else:
+            mask[s.astype(np.int64)] = 1
+        self._keep.append(mask)
+        st = lib().or_set_atomic(self._h, mask.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), float(r_core),
+                                 float(r_blend))
+        if st:
+            raise ValueError(f"or_set_atomic status {st}")
+
+    def coordination(self, x, r: float) -> np.ndarray:
+        """Number of neighbours closer than r of every atom."""
+        x = _pos(x)
+        z = np.zeros(max(self.n, 1), dtype=np.int32)
+        st = lib().or_coordination(self._h, _d(x), float(r), _i(z))
+        if st:
+            raise ValueError(f"or_coordination status {st}")
+        return z[:self.n]
 
     def basis_count(self) -> int:
         return int(lib().or_model_basis_count(self._h))

@@ -747,6 +747,9 @@ typedef struct {
     double reg[MAXREG][9]; /* kind, c[3], axis[3] (unit), r_core, ramp */
     int blend;             /* 0 linear, 1 cubic (smoothstep of the linear ramp) */
     double buf_e, buf_c;
+    int atomic;            /* 1: weights from seed atoms (Alg. 1-2) instead of regions */
+    uint8_t* seed;         /* [n] seed atoms */
+    double a_core, a_blend;
 } omodel;
 
 void* or_model_new(int64_t n, const double* lo, const double* L, const int* per, double mass, double ace_rc,
@@ -788,6 +791,7 @@ void or_model_free(void* p) {
     if (!m) return;
     ace_free(m->ace);
     free(m->spl);
+    free(m->seed);
     free(m);
 }
 
@@ -842,9 +846,103 @@ static void lambda_one(const omodel* m, const double* x, double* lam, double* w)
         *w = best;
 }
 
+typedef struct {
+    int cap;
+    int* nnb;
+    int* nbr;
+} olist;
+static int list_build(const omodel* m, const double* x, double rc, olist* L);
+static void list_free(olist* L);
+
+/* Weights from seed atoms, Alg. 1 then Alg. 2 as written: every seed and every
+ * neighbour of a seed closer than r_core is a core atom with weight 1; then for
+ * every core atom i and neighbour j closer than r_blend the weight of j becomes
+ * max(weight, 1 - r_ij / r_blend).  Distances compared squared (r2 < r_core^2,
+ * r2 < r_blend^2), r = sqrt(r2). */
+static int lambda_atomic(const omodel* m, const double* x, double* lam) {
+    int64_t n = m->n;
+    size_t nz = (size_t)(n > 0 ? n : 1);
+    uint8_t* core = (uint8_t*)calloc(nz, 1);
+    for (int64_t i = 0; i < n; ++i) lam[i] = 0.0;
+    olist L;
+    double rmax = m->a_core > m->a_blend ? m->a_core : m->a_blend;
+    int st = list_build(m, x, rmax, &L);
+    if (st) {
+        free(core);
+        return st;
+    }
+    double rc2 = m->a_core * m->a_core, rb2 = m->a_blend * m->a_blend;
+    for (int64_t i = 0; i < n; ++i) {
+        if (!m->seed[i]) continue;
+        core[i] = 1;
+        lam[i] = 1.0;
+        for (int k = 0; k < L.nnb[i]; ++k) {
+            int j = L.nbr[(size_t)L.cap * i + k];
+            double d[3];
+            box_delta(&m->box, x + 4 * i, x + 4 * (int64_t)j, d);
+            if (norm2(d) < rc2) {
+                core[j] = 1;
+                lam[j] = 1.0;
+            }
+        }
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        if (!core[i]) continue;
+        for (int k = 0; k < L.nnb[i]; ++k) {
+            int j = L.nbr[(size_t)L.cap * i + k];
+            double d[3];
+            box_delta(&m->box, x + 4 * i, x + 4 * (int64_t)j, d);
+            double r2 = norm2(d);
+            if (r2 < rb2) {
+                double v = 1.0 - sqrt(r2) / m->a_blend;
+                if (v > lam[j]) lam[j] = v;
+            }
+        }
+    }
+    list_free(&L);
+    free(core);
+    return OR_OK;
+}
+
 void or_lambda(void* p, const double* x, double* lam, double* w) {
     omodel* m = (omodel*)p;
+    if (m->atomic) {
+        lambda_atomic(m, x, lam);
+        for (int64_t i = 0; i < m->n; ++i) {
+            double b = lam[i];
+            w[i] = m->blend == 1 ? b * b * (3.0 - 2.0 * b) : b;
+        }
+        return;
+    }
     for (int64_t i = 0; i < m->n; ++i) lambda_one(m, x + 4 * i, lam + i, w + i);
+}
+
+/* Switch the model to seed-atom weights (seed: [n] 0/1, NULL switches back to
+ * the geometric regions). */
+int or_set_atomic(void* p, const uint8_t* seed, double r_core, double r_blend) {
+    omodel* m = (omodel*)p;
+    free(m->seed);
+    m->seed = NULL;
+    m->atomic = 0;
+    if (!seed) return OR_OK;
+    if (!(r_core >= 0) || !(r_blend >= 0)) return OR_EINVAL;
+    m->seed = (uint8_t*)malloc((size_t)(m->n > 0 ? m->n : 1));
+    memcpy(m->seed, seed, (size_t)m->n);
+    m->a_core = r_core;
+    m->a_blend = r_blend;
+    m->atomic = 1;
+    return OR_OK;
+}
+
+/* Coordination: number of neighbours closer than r (strict) of every atom. */
+int or_coordination(void* p, const double* x, double r, int* z) {
+    omodel* m = (omodel*)p;
+    olist L;
+    int st = list_build(m, x, r, &L);
+    if (st) return st;
+    for (int64_t i = 0; i < m->n; ++i) z[i] = L.nnb[i];
+    list_free(&L);
+    return OR_OK;
 }
 
 /* flags bit0: lambda > 0 (Lambda_e), bit1: lambda < 1 (Lambda_c),
@@ -853,12 +951,6 @@ void or_lambda(void* p, const double* x, double* lam, double* w) {
  * Buffer of a set S with radius b: atoms outside S with some member of S
  * closer than b (strict). */
 /* environment of atom i: neighbours within rc (from a fresh list) as r_ij vectors */
-typedef struct {
-    int cap;
-    int* nnb;
-    int* nbr;
-} olist;
-
 static int list_build(const omodel* m, const double* x, double rc, olist* L) {
     int64_t n = m->n;
     L->cap = 128;
