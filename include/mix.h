@@ -176,6 +176,35 @@ int mix_bind(mix_ctx* ctx, double* x_dev, double* v_dev, double* f_dev, void* wo
  * recomputed at every force evaluation from the current positions. */
 int mix_set_regions(mix_ctx* ctx, const mix_region* regions, int n);
 
+/* Weights from seed atoms instead of regions (Alg. 1 and 2 of Sec. 4.4):
+ * the seeds and every atom closer than r_core to a seed are core atoms
+ * (lambda = 1); any other atom takes the largest 1 - r/r_blend over core atoms
+ * closer than r_blend (lambda = 0 without one).  Distances are compared as
+ * r^2 < r_core^2 and r^2 < r_blend^2 in float64, r = sqrt(r^2), with the
+ * minimum image; the blend option (linear / cubic) applies to lambda as with
+ * regions.  seeds: host array of n_seeds atom indices (duplicates allowed);
+ * the mask is copied to the device before returning.  r_core and r_blend lie
+ * in [0, largest cutoff] (both are found through the neighbour lists).
+ * MIX_EINVAL for an index outside [0, N) or a radius out of range;
+ * MIX_ESTATE before mix_bind.  mix_set_regions switches back to regions. */
+int mix_set_seeds(mix_ctx* ctx, const int* seeds, int n_seeds, double r_core, double r_blend);
+
+/* Seeds chosen on the device from the coordination number z_i (neighbours
+ * closer than r_coord, strict), the defect criterion of the silicon vacancy
+ * runs (Sec. 4.6): an atom is a seed when the mean of z_i lies in
+ * [z_lo, z_hi].  The first force evaluation after this call seeds from its own
+ * counts; after that z_i is summed over `period` evaluations and the seeds
+ * are refreshed from the mean at the end of each period.  Core and blend
+ * weights then follow mix_set_seeds.  r_coord, r_core, r_blend lie in
+ * [0, largest cutoff]; period >= 1; z_lo <= z_hi.  MIX_EINVAL otherwise;
+ * MIX_ESTATE before mix_bind. */
+int mix_set_seed_rule(mix_ctx* ctx, double r_coord, double z_lo, double z_hi, int period, double r_core,
+                      double r_blend);
+
+/* Seed mask of the last evaluation ([N] 0/1, nullable) and the number of seeds
+ * (nullable); synchronises. */
+int mix_get_seeds(mix_ctx* ctx, uint8_t* seed /*[N]*/, int64_t* n_seeds);
+
 /* f <- blended forces at the current positions (Alg. 4 with the buffer of
  * Sec. 4.5), rebuilding the neighbour lists first if needed. */
 int mix_forces(mix_ctx* ctx);

@@ -49,6 +49,119 @@ __global__ void k_lambda(Dev d, Regions r) {
     d.esite_c[i] = 0.0;
 }
 
+// --- weights from seed atoms (Alg. 1-2), in gather form: each atom looks at its
+// own neighbours, which yields the same sets of candidates as the scatter loops
+// of the algorithms, so the results (flags and maxima) are identical.
+
+constexpr int SEED_WARPS = 8;
+
+// Coordination: neighbours closer than r_coord.  The first evaluation after the
+// rule is set seeds from its own counts; after that the counts are summed over
+// `period` evaluations and the seeds refreshed from their mean at the end of
+// each period (the sums then restart).
+__global__ void __launch_bounds__(SEED_WARPS * 32) k_coord(Dev d, SeedRule sr) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int evals = d.status[SW_EVALS];
+    const bool refresh = evals % sr.period == 0;
+    const double navg = evals == 0 ? 1.0 : (double)sr.period;
+    for (int64_t i = (int64_t)blockIdx.x * SEED_WARPS + warp; i < d.n; i += (int64_t)gridDim.x * SEED_WARPS) {
+        const double4 xi = d.x[i];
+        const int m = d.nnb[i];
+        const int* row = d.nbr + i * (int64_t)d.cap;
+        int cnt = 0;
+        for (int s = lane; s < m; s += 32) {
+            double dd[3];
+            delta_rn(d.box, xi, d.x[row[s]], dd);
+            cnt += norm2_rn(dd) < sr.rz2 ? 1 : 0;
+        }
+        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+        if (lane == 0) {
+            const int z = d.zsum[i] + cnt;
+            if (refresh) {
+                const double avg = (double)z / navg;
+                const bool s = avg >= sr.zlo && avg <= sr.zhi;
+                d.seed[i] = s ? 1 : 0;
+                d.zsum[i] = 0;
+            } else {
+                d.zsum[i] = z;
+            }
+        }
+    }
+}
+
+// Alg. 1: core = seeds and atoms closer than r_core to a seed.
+__global__ void __launch_bounds__(SEED_WARPS * 32) k_core(Dev d, SeedRule sr) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        d.status[SW_EVALS] += 1;
+        d.status[SW_NSEED] = 0;
+    }
+    for (int64_t j = (int64_t)blockIdx.x * SEED_WARPS + warp; j < d.n; j += (int64_t)gridDim.x * SEED_WARPS) {
+        bool c = d.seed[j] != 0;
+        if (!c) {
+            const double4 xj = d.x[j];
+            const int m = d.nnb[j];
+            const int* row = d.nbr + j * (int64_t)d.cap;
+            for (int s = lane; s < m; s += 32) {
+                const int i = row[s];
+                if (d.seed[i]) {
+                    double dd[3];
+                    delta_rn(d.box, xj, d.x[i], dd);
+                    c = c || norm2_rn(dd) < sr.rcore2;
+                }
+            }
+            c = __any_sync(0xffffffffu, c);
+        }
+        if (lane == 0) d.core[j] = c ? 1 : 0;
+    }
+}
+
+// Alg. 2: weight 1 on core atoms, else the largest 1 - r/r_blend over core
+// neighbours closer than r_blend (0 without one).
+__global__ void __launch_bounds__(SEED_WARPS * 32) k_blend(Dev d, SeedRule sr) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && d.status[SW_REBUILD]) {
+        d.status[SW_REBUILDS] += 1;
+        d.status[SW_REBUILD] = 0;
+    }
+    for (int64_t j = (int64_t)blockIdx.x * SEED_WARPS + warp; j < d.n; j += (int64_t)gridDim.x * SEED_WARPS) {
+        double best = 0.0;
+        if (d.core[j]) {
+            best = 1.0;
+        } else {
+            const double4 xj = d.x[j];
+            const int m = d.nnb[j];
+            const int* row = d.nbr + j * (int64_t)d.cap;
+            for (int s = lane; s < m; s += 32) {
+                const int i = row[s];
+                if (d.core[i]) {
+                    double dd[3];
+                    delta_rn(d.box, xj, d.x[i], dd);
+                    const double r2 = norm2_rn(dd);
+                    if (r2 < sr.rblend2) {
+                        const double v = __dsub_rn(1.0, __ddiv_rn(__dsqrt_rn(r2), sr.rblend));
+                        best = v > best ? v : best;
+                    }
+                }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const double t = __shfl_down_sync(0xffffffffu, best, o);
+                best = t > best ? t : best;
+            }
+        }
+        if (lane == 0) {
+            d.lam[j] = best;
+            double w = best;
+            if (sr.blend == MIX_BLEND_CUBIC) w = __dmul_rn(__dmul_rn(best, best), __dsub_rn(3.0, __dmul_rn(2.0, best)));
+            d.wgt[j] = w;
+            d.flags[j] = (uint8_t)((best > 0.0 ? 1 : 0) | (best < 1.0 ? 2 : 0));
+            d.esite_e[j] = 0.0;
+            d.esite_c[j] = 0.0;
+            if (d.seed[j]) atomicAdd(d.status + SW_NSEED, 1);
+        }
+    }
+}
+
 constexpr int BUF_WARPS = 8;
 
 // One warp per atom: buffer membership through the neighbour list.
@@ -192,9 +305,20 @@ __global__ void __launch_bounds__(SCAN_BLOCK) k_scatter(Dev d) {
     }
 }
 
-void launch_sets(const Dev& d, const Regions& r, cudaStream_t s) {
+int sets_launches(const SeedRule& sr) { return sr.mode == 0 ? 4 : (sr.mode == 1 ? 5 : 6); }
+
+void launch_sets(const Dev& d, const Regions& r, const SeedRule& sr, cudaStream_t s) {
     const int nb = (int)((d.n + 255) / 256);
-    k_lambda<<<nb > 0 ? nb : 1, 256, 0, s>>>(d, r);
+    if (sr.mode == 0) {
+        k_lambda<<<nb > 0 ? nb : 1, 256, 0, s>>>(d, r);
+    } else {
+        int64_t want = (d.n + SEED_WARPS - 1) / SEED_WARPS;
+        int64_t lim = (int64_t)sm_count() * 8;
+        const int gs = (int)(want < lim ? want : lim);
+        if (sr.mode == 2) k_coord<<<gs > 0 ? gs : 1, SEED_WARPS * 32, 0, s>>>(d, sr);
+        k_core<<<gs > 0 ? gs : 1, SEED_WARPS * 32, 0, s>>>(d, sr);
+        k_blend<<<gs > 0 ? gs : 1, SEED_WARPS * 32, 0, s>>>(d, sr);
+    }
     int64_t want = (d.n + BUF_WARPS - 1) / BUF_WARPS;
     int64_t lim = d.grid_buffer > 0 ? d.grid_buffer : (int64_t)sm_count() * 8;
     const int gb = (int)(want < lim ? want : lim);

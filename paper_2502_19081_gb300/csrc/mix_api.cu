@@ -17,6 +17,7 @@ namespace {
 
 constexpr double KAPPA = 9.6485332e-3;   // (eV / Angstrom / amu) in Angstrom / fs^2
 // kernels per evaluation: displacement 1, lists 5, sets 4, expensive 1, cheap 1, gather 1
+// (13 with geometric regions; the seed-atom modes add one or two)
 constexpr int LAUNCHES_PER_EVAL = 13;
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -128,6 +129,7 @@ struct mix_ctx {
     double spl_rc, spl_rc3;
     // regions
     Regions regions;
+    SeedRule seedrule;
     cudaStream_t stream;
     Dev dev;
     double rlist;
@@ -145,7 +147,8 @@ struct mix_ctx {
     size_t ws_bytes;
     size_t off_tab;
     size_t o_status, o_xb, o_xf, o_xr, o_cell3, o_cell_of, o_cell_count, o_cell_start, o_cell_fill, o_cell_atoms, o_nnb, o_nbr, o_rev,
-        o_lam, o_wgt, o_flags, o_act_e, o_act_c, o_pos_e, o_pos_c, o_blk_e, o_blk_c, o_ge, o_gc, o_ee, o_ec;
+        o_lam, o_wgt, o_flags, o_act_e, o_act_c, o_pos_e, o_pos_c, o_blk_e, o_blk_c, o_ge, o_gc, o_ee, o_ec,
+        o_seed, o_core, o_zsum;
     size_t ace_smem, spl_smem;
     int ace_grid, spl_grid;
     int ace_grid_max, spl_grid_max;   // resident CTAs at full occupancy
@@ -483,6 +486,9 @@ void layout(mix_ctx* c) {
     c->o_gc = take(N * cap * v4);
     c->o_ee = take(N * 8);
     c->o_ec = take(N * 8);
+    c->o_seed = take(N);
+    c->o_core = take(N);
+    c->o_zsum = take(N * 4);
     c->off_tab = take(c->arena.bytes.size());
     c->ws_bytes = o;
 }
@@ -492,6 +498,8 @@ int check_stream_error(mix_ctx* c, const char* what) {
     if (e != cudaSuccess) return cuda_fail(c, e, what);
     return MIX_OK;
 }
+
+int evals_launches(const mix_ctx* c) { return LAUNCHES_PER_EVAL - 4 + sets_launches(c->seedrule); }
 
 // the kernels of one evaluation, in order, on stream s (events between the
 // phases when profiling)
@@ -505,7 +513,7 @@ void enqueue_evaluation(mix_ctx* c, cudaStream_t s, int integrate, double dt, in
     if (prof) cudaEventRecordWithFlags(c->ev[1], s, ef);
     launch_build(c->dev, s);
     if (prof) cudaEventRecordWithFlags(c->ev[2], s, ef);
-    launch_sets(c->dev, c->regions, s);
+    launch_sets(c->dev, c->regions, c->seedrule, s);
     if (prof) cudaEventRecordWithFlags(c->ev[3], s, ef);
     const void* at = c->precision == MIX_FP64 ? (const void*)&c->ace64 : (const void*)&c->ace32;
     const void* st = c->precision == MIX_FP64 ? (const void*)&c->spl64 : (const void*)&c->spl32;
@@ -567,7 +575,7 @@ int evaluate(mix_ctx* c, int integrate, double dt) {
         enqueue_evaluation(c, s, integrate, dt, c->need_build ? 1 : 0, prof);
     }
     c->need_build = false;
-    c->launches += LAUNCHES_PER_EVAL;
+    c->launches += evals_launches(c);
     int rc = check_stream_error(c, "kernel launch");
     if (rc || !prof) return rc;
     cudaError_t e = cudaEventSynchronize(c->ev[MIX_PHASES]);
@@ -782,11 +790,15 @@ int mix_bind(mix_ctx* c, double* x, double* v, double* f, void* ws) {
     d.gc = w + c->o_gc;
     d.esite_e = reinterpret_cast<double*>(w + c->o_ee);
     d.esite_c = reinterpret_cast<double*>(w + c->o_ec);
+    d.seed = reinterpret_cast<uint8_t*>(w + c->o_seed);
+    d.core = reinterpret_cast<uint8_t*>(w + c->o_core);
+    d.zsum = reinterpret_cast<int*>(w + c->o_zsum);
     unsigned char* tb = w + c->off_tab;
     fill_tabs<double>(c, tb, c->ace64, c->spl64);
     fill_tabs<float>(c, tb, c->ace32, c->spl32);
     cudaError_t e = cudaMemsetAsync(d.status, 0, SW_COUNT * sizeof(int), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.cell_count, 0, (size_t)d.cells.ncell * 4, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.seed, 0, (size_t)d.n, c->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(tb, c->arena.bytes.data(), c->arena.bytes.size(), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -826,6 +838,7 @@ int mix_set_regions(mix_ctx* c, const mix_region* r, int n) {
         q[8] = r[k].ramp;
     }
     c->regions = R;
+    c->seedrule.mode = 0;
     c->regions_version++;
     c->forces_valid = false;
     return MIX_OK;
@@ -1013,7 +1026,7 @@ int mix_get_info(const mix_ctx* c, mix_info* info) {
     info->exp_threads = 128;
     info->cheap_smem_bytes = c->spl_smem;
     info->cheap_grid = c->spl_grid;
-    info->launches_per_evaluation = LAUNCHES_PER_EVAL;
+    info->launches_per_evaluation = evals_launches(c);
     info->launches = c->launches;
     info->gather_grid = c->dev.grid_gather;
     info->build_grid = c->dev.grid_build;
@@ -1139,6 +1152,38 @@ void set_grid_divisor(mix_ctx* c, int div) {
     drop_graph(c);
 }
 
+// Seed state advanced by every evaluation under the coordination rule; the
+// tuners' extra evaluations must leave it as they found it.
+struct SeedSave {
+    bool active = false;
+    std::vector<uint8_t> seed;
+    std::vector<int> zsum;
+    int evals = 0;
+};
+
+int seed_save(mix_ctx* c, SeedSave* s) {
+    s->active = c->seedrule.mode == 2;
+    if (!s->active) return MIX_OK;
+    const size_t N = (size_t)c->sys.n_atoms;
+    s->seed.resize(N);
+    s->zsum.resize(N);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess && N) e = cudaMemcpy(s->seed.data(), c->dev.seed, N, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && N) e = cudaMemcpy(s->zsum.data(), c->dev.zsum, N * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&s->evals, c->dev.status + SW_EVALS, 4, cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? MIX_OK : cuda_fail(c, e, "seed state save");
+}
+
+int seed_restore(mix_ctx* c, const SeedSave& s) {
+    if (!s.active) return MIX_OK;
+    const size_t N = (size_t)c->sys.n_atoms;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess && N) e = cudaMemcpy(c->dev.seed, s.seed.data(), N, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && N) e = cudaMemcpy(c->dev.zsum, s.zsum.data(), N * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->dev.status + SW_EVALS, &s.evals, 4, cudaMemcpyHostToDevice);
+    return e == cudaSuccess ? MIX_OK : cuda_fail(c, e, "seed state restore");
+}
+
 // one member evaluation captured into a (not instantiated) graph
 int member_graph(mix_ctx* c, int integrate, double dt, cudaGraph_t* g) {
     if (!c->cap_stream) {
@@ -1236,12 +1281,15 @@ int mix_tune(mix_ctx* c, int reps) {
     std::vector<int> ga = {c->ace_grid_max, c->ace_grid_max * 3 / 4, c->ace_grid_max / 2, c->ace_grid_max / 4};
     std::vector<int> gs = {c->spl_grid_max, c->spl_grid_max / 2, c->spl_grid_max / 4};
     std::vector<int> gg = {sms * 2, sms * 4, sms * 8, sms * 16};
-    int st = tune_param(c, reps, &c->ace_grid, ga);
+    SeedSave saved;
+    int st = seed_save(c, &saved);
+    if (!st) st = tune_param(c, reps, &c->ace_grid, ga);
     if (!st) st = tune_param(c, reps, &c->spl_grid, gs);
     if (!st) st = tune_param(c, reps, &c->dev.grid_gather, gg);
     if (!st) st = tune_param(c, reps, &c->dev.grid_buffer, gg);
     drop_graph(c);
-    return st;
+    const int st2 = seed_restore(c, saved);
+    return st ? st : st2;
 }
 
 int mix_batch_create(mix_ctx* const* members, int n, void* stream, mix_batch** out) {
@@ -1284,7 +1332,7 @@ int mix_batch_step(mix_batch* b, double dt, int nsteps) {
     }
     for (mix_ctx* c : b->m) {
         c->steps += nsteps;
-        c->launches += (int64_t)LAUNCHES_PER_EVAL * nsteps;
+        c->launches += (int64_t)evals_launches(c) * nsteps;
     }
     return MIX_OK;
 }
@@ -1305,6 +1353,9 @@ int mix_batch_tune(mix_batch* b, int reps, int* chosen) {
     if (reps < 1) reps = 3;
     int st = batch_prepare(b);
     if (st) return st;
+    std::vector<SeedSave> saved(b->m.size());
+    for (size_t k = 0; k < b->m.size() && !st; ++k) st = seed_save(b->m[k], &saved[k]);
+    if (st) return bfail(b, st, "seed state save");
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return bfail(b, MIX_ECUDA, "event");
@@ -1342,6 +1393,10 @@ int mix_batch_tune(mix_batch* b, int reps, int* chosen) {
     batch_drop(b);
     b->divisor = best;
     if (chosen) *chosen = best;
+    for (size_t k = 0; k < b->m.size(); ++k) {
+        const int sr = seed_restore(b->m[k], saved[k]);
+        if (!st && sr) st = bfail(b, sr, "seed state restore");
+    }
     cudaError_t e = cudaGetLastError();
     if (!st && e != cudaSuccess) st = bfail(b, MIX_ECUDA, cudaGetErrorString(e));
     return st;
@@ -1356,5 +1411,90 @@ int mix_batch_destroy(mix_batch* b) {
 }
 
 const char* mix_batch_last_error(const mix_batch* b) { return b ? b->err.c_str() : ""; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// weights from seed atoms (Alg. 1-2)
+
+namespace {
+
+int seed_radii_ok(mix_ctx* c, double a, double b) {
+    const double rmax = c->rlist - c->opt.skin;   // pairs closer than this are always in the lists
+    if (!(a >= 0) || !(b >= 0) || a > rmax || b > rmax)
+        return fail(c, MIX_EINVAL, "seed radii must lie in [0, %.4g] (the largest cutoff)", rmax);
+    return MIX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mix_set_seeds(mix_ctx* c, const int* seeds, int n_seeds, double r_core, double r_blend) {
+    if (!c) return MIX_EINVAL;
+    if (!c->bound) return fail(c, MIX_ESTATE, "mix_set_seeds before mix_bind");
+    if (n_seeds < 0 || (n_seeds > 0 && !seeds)) return fail(c, MIX_EINVAL, "seed list");
+    int st = seed_radii_ok(c, r_core, r_blend);
+    if (st) return st;
+    const int64_t N = c->sys.n_atoms;
+    std::vector<uint8_t> mask((size_t)(N > 0 ? N : 1), 0);
+    for (int k = 0; k < n_seeds; ++k) {
+        if (seeds[k] < 0 || seeds[k] >= N) return fail(c, MIX_EINVAL, "seed index %d out of range", seeds[k]);
+        mask[seeds[k]] = 1;
+    }
+    cudaError_t e = cudaMemcpyAsync(c->dev.seed, mask.data(), (size_t)N, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "mix_set_seeds");
+    SeedRule& r = c->seedrule;
+    r = SeedRule();
+    r.mode = 1;
+    r.blend = c->opt.blend;
+    r.rcore2 = r_core * r_core;
+    r.rblend2 = r_blend * r_blend;
+    r.rblend = r_blend;
+    r.period = 1;
+    c->regions_version++;
+    c->forces_valid = false;
+    return MIX_OK;
+}
+
+int mix_set_seed_rule(mix_ctx* c, double r_coord, double z_lo, double z_hi, int period, double r_core,
+                      double r_blend) {
+    if (!c) return MIX_EINVAL;
+    if (!c->bound) return fail(c, MIX_ESTATE, "mix_set_seed_rule before mix_bind");
+    if (period < 1 || !(z_lo <= z_hi)) return fail(c, MIX_EINVAL, "period >= 1 and z_lo <= z_hi");
+    int st = seed_radii_ok(c, r_core, r_blend);
+    if (!st) st = seed_radii_ok(c, r_coord, 0.0);
+    if (st) return st;
+    const size_t N = (size_t)c->sys.n_atoms;
+    cudaError_t e = cudaMemsetAsync(c->dev.zsum, 0, N * 4, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->dev.seed, 0, N, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->dev.status + SW_EVALS, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "mix_set_seed_rule");
+    SeedRule& r = c->seedrule;
+    r = SeedRule();
+    r.mode = 2;
+    r.blend = c->opt.blend;
+    r.rcore2 = r_core * r_core;
+    r.rblend2 = r_blend * r_blend;
+    r.rblend = r_blend;
+    r.rz2 = r_coord * r_coord;
+    r.zlo = z_lo;
+    r.zhi = z_hi;
+    r.period = period;
+    c->regions_version++;
+    c->forces_valid = false;
+    return MIX_OK;
+}
+
+int mix_get_seeds(mix_ctx* c, uint8_t* seed, int64_t* n_seeds) {
+    if (!c) return MIX_EINVAL;
+    if (!c->bound) return fail(c, MIX_ESTATE, "not bound");
+    int st = read_status(c);
+    if (st) return st;
+    if (n_seeds) *n_seeds = c->pinned[SW_NSEED];
+    return copy_out(c, seed, c->dev.seed, (size_t)c->sys.n_atoms);
+}
 
 }  // extern "C"

@@ -30,6 +30,8 @@ enum StatusWord : int {
     SW_NLE = 8,         // lambda > 0
     SW_NLC = 9,         // lambda < 1
     SW_NB3MAX = 10,     // largest 3-body neighbour count seen
+    SW_EVALS = 11,      // evaluations since the seed rule was set (coordination averaging)
+    SW_NSEED = 12,      // number of seed atoms
     SW_COUNT = 64,
 };
 
@@ -63,6 +65,16 @@ struct Regions {
     int n;
     int blend;
     double r[MIX_MAX_REGIONS][9];   // kind, centre[3], axis[3] (unit), r_core, ramp
+};
+
+// Weights from seed atoms instead of geometric regions (Alg. 1-2).
+struct SeedRule {
+    int mode;          // 0: geometric regions; 1: explicit seeds; 2: seeds from coordination
+    int blend;         // MIX_BLEND_*
+    double rcore2, rblend2, rblend;
+    double rz2;        // coordination radius squared
+    double zlo, zhi;   // seed when the averaged coordination lies in [zlo, zhi]
+    int period;        // evaluations averaged per seed refresh
 };
 
 // Pointers into the workspace plus scalar parameters, passed by value.
@@ -108,6 +120,9 @@ struct Dev {
     void* gc;            // [N][cap] real4: same for the cheap potential
     double* esite_e;
     double* esite_c;
+    uint8_t* seed;       // [N] seed atoms (seed-atom weights)
+    uint8_t* core;       // [N] core atoms
+    int* zsum;           // [N] coordination summed over the current averaging period
     int nblk;            // blocks of the compaction kernels
     // launch shapes chosen by the autotuner (0: default)
     int grid_build;      // CTAs of the neighbour-list build (4 warps each)

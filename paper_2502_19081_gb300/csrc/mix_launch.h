@@ -10,7 +10,8 @@ void launch_disp(const Dev& d, cudaStream_t s, int integrate, double dt, double 
 void launch_build(const Dev& d, cudaStream_t s);
 
 // weights, sets, compaction (k_sets.cu)
-void launch_sets(const Dev& d, const Regions& r, cudaStream_t s);
+void launch_sets(const Dev& d, const Regions& r, const SeedRule& sr, cudaStream_t s);
+int sets_launches(const SeedRule& sr);   // kernels launch_sets enqueues
 
 // expensive potential (k_ace.cuh, k_ace_f32.cu, k_ace_f64.cu); returns cudaSuccess or the launch error
 cudaError_t ace_configure(int precision, int L, int n, int cap, size_t* smem, int* grid);

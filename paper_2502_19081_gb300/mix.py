@@ -42,7 +42,7 @@ EXPORTS = [
     "mix_get_lambda", "mix_get_sets", "mix_get_site_energies", "mix_get_state", "mix_set_state",
     "mix_destroy", "mix_strerror", "mix_last_error", "mix_get_info", "mix_profile", "mix_get_profile",
     "mix_fma_peak", "mix_tune", "mix_batch_create", "mix_batch_step", "mix_batch_sync", "mix_batch_tune",
-    "mix_batch_destroy", "mix_batch_last_error",
+    "mix_batch_destroy", "mix_batch_last_error", "mix_set_seeds", "mix_set_seed_rule", "mix_get_seeds",
 ]
 
 MIX_PHASES = 6
@@ -122,6 +122,10 @@ def lib():
             L.mix_workspace_bytes.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
             L.mix_bind.argtypes = [P, P, P, P, P]
             L.mix_set_regions.argtypes = [P, ctypes.POINTER(mix_region), ctypes.c_int]
+            L.mix_set_seeds.argtypes = [P, ip, ctypes.c_int, ctypes.c_double, ctypes.c_double]
+            L.mix_set_seed_rule.argtypes = [P, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                            ctypes.c_double, ctypes.c_double]
+            L.mix_get_seeds.argtypes = [P, ctypes.POINTER(ctypes.c_uint8), i64p]
             L.mix_forces.argtypes = [P]
             L.mix_step.argtypes = [P, ctypes.c_double, ctypes.c_int]
             L.mix_step_host.argtypes = [P, dp, dp, dp, ctypes.c_double, ctypes.c_int]
@@ -254,6 +258,26 @@ class Context:
             arr[k] = mix_region(int(r.kind), (ctypes.c_double * 3)(*r.centre), (ctypes.c_double * 3)(*r.axis),
                                 float(r.r_core), float(r.ramp))
         self._check(self.L.mix_set_regions(self.h, arr, len(regions)), "mix_set_regions")
+
+    def set_seeds(self, seeds, r_core: float, r_blend: float):
+        """Weights from explicit seed atoms (Alg. 1-2)."""
+        idx = np.ascontiguousarray(np.asarray(seeds, dtype=np.int32).reshape(-1))
+        buf = idx if idx.size else np.zeros(1, dtype=np.int32)
+        self._check(self.L.mix_set_seeds(self.h, _ip(buf), int(idx.size), float(r_core), float(r_blend)),
+                    "mix_set_seeds")
+
+    def set_seed_rule(self, r_coord: float, z_lo: float, z_hi: float, period: int, r_core: float,
+                      r_blend: float):
+        """Seeds from the (period-averaged) coordination number, then Alg. 1-2."""
+        self._check(self.L.mix_set_seed_rule(self.h, float(r_coord), float(z_lo), float(z_hi), int(period),
+                                             float(r_core), float(r_blend)), "mix_set_seed_rule")
+
+    def seeds(self):
+        m = np.zeros(max(self.n, 1), dtype=np.uint8)
+        k = ctypes.c_int64()
+        self._check(self.L.mix_get_seeds(self.h, m.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), ctypes.byref(k)),
+                    "mix_get_seeds")
+        return m[:self.n], k.value
 
     def forces(self):
         self._check(self.L.mix_forces(self.h), "mix_forces")
