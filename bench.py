@@ -231,6 +231,27 @@ def cpu_baseline(wl, seconds: float):
                       f"OpenMP over sites, {el:.1f} s"}
 
 
+def profiled_traffic(profile: str, sources) -> "int | None":
+    """DRAM bytes per launch from a committed ncu summary, or None when the
+    kernel's sources changed since the capture (hash recorded in the summary)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", profile)
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    vals = {}
+    for line in text.splitlines():
+        if ":" in line and line.split(":", 1)[0] in ("traffic_bytes_per_launch", "kernel_source_sha256_16"):
+            k, v = line.split(":", 1)
+            vals[k] = v.strip()
+    h = hashlib.sha256()
+    for src in sources:
+        h.update(open(os.path.join(ROOT, "paper_2502_19081_gb300", "csrc", src), "rb").read())
+    if vals.get("kernel_source_sha256_16") != h.hexdigest()[:16] or "traffic_bytes_per_launch" not in vals:
+        return None
+    return int(vals["traffic_bytes_per_launch"])
+
+
 def ours(args):
     import torch
     import torch.distributed as dist
@@ -315,7 +336,10 @@ def ours(args):
         ach = fl / (phase_ms[dom] * 1e-3)
         roof = {"kernel": "k_ace" if names[dom] == "exp" else "k_spline", "bound": "alu",
                 "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": None, "algorithmic_flops_per_launch": fl,
+                "traffic": (profiled_traffic("k_ace_fe_dumbbell_8001.md", ("k_ace.cuh", "k_ace_f32.cu"))
+                            if names[dom] == "exp" and prec == mix.MIX_FP32 and wl.name == "fe_dumbbell_8001"
+                            else None),
+                "algorithmic_flops_per_launch": fl,
                 "peak_source": f"measured FMA microbenchmark ({'fp32' if prec == mix.MIX_FP32 else 'fp64'}), "
                                "mix_fma_peak"}
     else:
