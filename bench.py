@@ -51,6 +51,10 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=20)
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--serve-seconds", type=float, default=60.0)
+    p.add_argument("--serve-rate", type=float, default=20.0)
+    p.add_argument("--serve-atoms", type=int, default=2_000_000)
+    p.add_argument("--serve-queue", type=int, default=8)
     return p.parse_args()
 
 
@@ -440,6 +444,99 @@ def batch_bench(args):
     print(json.dumps(out), flush=True)
 
 
+def serve_bench(args):
+    """Serving: a Poisson stream of requests (20 per second; Si or Fe cells of
+    1e3 to 5e5 atoms, log-uniform; 100 to 2000 steps, log-uniform; core 1 to
+    10 % of the atoms; FP32 potentials, FP64 integration) served for a bounded
+    wall-clock window by the library's server (mix_server_*): admission by
+    device memory and an active-atom cap, continuous batching, one step per
+    tick.  value = atom-steps served per second of the window; the per-step
+    latency is the device time of each batched step; queueing delay is
+    admission time minus arrival time.  Requests that arrived but are not yet
+    handed to the server wait in a client-side backlog (system generation is
+    deferred until the server queue has room), counted as queued."""
+    import collections
+    import torch
+    from paper_2502_19081_gb300 import build as B
+    from paper_2502_19081_gb300 import inputs as I
+    from paper_2502_19081_gb300 import mix
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    B.build()
+    pots = I.serve_potentials()
+    stream = list(I.serve_stream(seed=5 + 1000 * rank, rate=args.serve_rate, duration=args.serve_seconds))
+    offered = sum(r["n_target"] * r["nsteps"] for r in stream) / args.serve_seconds
+    srv = mix.Server(1.0, max_active_atoms=args.serve_atoms)
+    pending = collections.deque(stream)
+    backlog = collections.deque()
+    arrival = {}
+    step_ms, atoms_per_step, qdelay, done = [], [], [], []
+    served = 0.0
+    server_queued = 0
+    clocks = Clocks(local)
+    clocks.start()
+    t_now = 0.0
+    t0 = time.perf_counter()
+    while True:
+        t_now = time.perf_counter() - t0
+        if t_now >= args.serve_seconds:
+            break
+        while pending and pending[0]["t"] <= t_now:
+            backlog.append(pending.popleft())
+        while backlog and server_queued < args.serve_queue:
+            r = backlog.popleft()
+            wl = I.serve_request(r["seed"], r["element"], r["n_target"], r["core_frac"], r["temp_k"], pots)
+            rid = srv.submit(wl, r["nsteps"], precision=mix.MIX_FP32)
+            arrival[rid] = r["t"]
+            server_queued += 1
+        t = srv.tick(1)
+        server_queued = t["queued"]
+        if t["steps"]:
+            step_ms.append(t["step_ms"])
+            atoms_per_step.append(t["active_atoms"])
+            served += t["active_atoms"] * t["steps"]
+        for rid in list(arrival):
+            info = srv.request(rid)
+            if info["state"] in (mix.MIX_REQ_DONE, mix.MIX_REQ_FAILED):
+                qdelay.append(info["t_admit"] - arrival[rid] if info["t_admit"] >= 0 else float("nan"))
+                done.append((rid, info["state"], info["steps_done"], info["status"]))
+                try:
+                    srv.fetch(rid)
+                except mix.MixError:
+                    pass
+                del arrival[rid]
+        if t["active"] == 0 and t["queued"] == 0 and not backlog and pending:
+            time.sleep(max(0.0, min(pending[0]["t"] - (time.perf_counter() - t0), 0.05)))
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    active_delay = []
+    for rid, ta in arrival.items():
+        info = srv.request(rid)
+        if info["t_admit"] >= 0:
+            active_delay.append(info["t_admit"] - ta)
+    srv.close()
+    per = np.array(step_ms) if step_ms else np.zeros(1)
+    qd = np.array([q for q in qdelay + active_delay if q == q]) if (qdelay or active_delay) else np.zeros(1)
+    out = {"metric": "served atom-steps/s, Poisson request stream (continuous batching)",
+           "value": served / wall, "unit": UNIT, "n_gpus": world, "steps": len(step_ms), "warmup": 0,
+           "ms_per_step": float(per.mean()), "p50_ms": float(np.percentile(per, 50)),
+           "p99_ms": float(np.percentile(per, 99)), "higher_is_better": True, "dtype": "f32",
+           "config": {"workload": "serve_poisson", "rate_per_s": args.serve_rate, "window_s": args.serve_seconds,
+                      "max_active_atoms": args.serve_atoms, "server_queue": args.serve_queue,
+                      "potential_arithmetic": "f32", "integration": "f64",
+                      "l2": "working set > L2 (no flush)"},
+           "offered_atom_steps_per_s": offered,
+           "arrived": len(stream) - len(pending), "completed": sum(1 for d in done if d[1] == mix.MIX_REQ_DONE),
+           "failed": sum(1 for d in done if d[1] == mix.MIX_REQ_FAILED),
+           "failed_by_status": dict(collections.Counter(
+               mix.lib().mix_strerror(d[3]).decode() for d in done if d[1] == mix.MIX_REQ_FAILED)),
+           "admitted": len(done) + len(active_delay),
+           "queue_delay_s": {"p50": float(np.percentile(qd, 50)), "p99": float(np.percentile(qd, 99))},
+           "mean_active_atoms": float(np.mean(atoms_per_step)) if atoms_per_step else 0.0,
+           "clocks": clk}
+    print(json.dumps(out), flush=True)
+
+
 def reference(args):
     """The oracle arm: FP64 C oracle on the host cores, same workload and metric."""
     rank, world, _ = dist_env()
@@ -493,6 +590,8 @@ def main():
         reference(args)
     elif args.workload == "si_replicas_256":
         batch_bench(args)
+    elif args.workload == "serve_poisson":
+        serve_bench(args)
     else:
         ours(args)
 

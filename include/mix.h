@@ -341,6 +341,89 @@ int mix_batch_destroy(mix_batch* b);
 const char* mix_batch_last_error(const mix_batch* b);
 
 /* ------------------------------------------------------------------------ */
+/* Serving: many independent mixed-MD trajectories (requests) arriving over  */
+/* time share one GPU.  The paper runs one trajectory at a time; this layer  */
+/* packages the context and batch calls above for a stream of requests:      */
+/* requests wait in a queue in arrival order, are admitted while their       */
+/* device memory fits the server's budget (and the optional caps below), run */
+/* together in one batched step graph (continuous batching: the batch is     */
+/* rebuilt whenever a request joins or leaves), keep their state on the      */
+/* device between steps, and leave when their step count is reached.  Each   */
+/* request's results are those of the same context run alone (the batch     */
+/* runs every member's own kernels on its own buffers).                      */
+typedef struct mix_server mix_server;
+
+typedef struct {
+    double dt_fs;             /* time step of every request */
+    size_t hbm_budget;        /* device bytes the requests may hold (0: free memory at creation minus hbm_reserve) */
+    size_t hbm_reserve;       /* bytes kept free when hbm_budget = 0 (0: 2 GiB) */
+    int64_t max_active_atoms; /* admission cap on atoms stepped together (0: none); a request larger than the
+                                 cap is admitted only when nothing else runs */
+    int max_active;           /* cap on concurrent requests (0: none) */
+    int fifo;                 /* 1: strict arrival order; 0: a later request that fits may pass a blocked one */
+} mix_server_options;
+
+enum { MIX_REQ_QUEUED = 0, MIX_REQ_ACTIVE = 1, MIX_REQ_DONE = 2, MIX_REQ_FAILED = 3 };
+
+typedef struct {
+    int state;                /* MIX_REQ_* */
+    int status;               /* MIX_OK, or the error that failed the request */
+    int64_t n_atoms;
+    int64_t steps_done, steps_total;
+    size_t device_bytes;      /* x, v, f and workspace */
+    double t_submit, t_admit, t_done;   /* seconds on the server's clock (-1: not yet) */
+} mix_request_info;
+
+typedef struct {
+    int admitted, retired, failed;      /* by this tick */
+    int active, queued;                 /* after this tick */
+    int64_t active_atoms;               /* atoms stepped by this tick */
+    int steps;                          /* steps run by this tick */
+    size_t bytes_in_use;
+    double step_ms;                     /* device time per step of the batched step graph */
+    double admit_ms;                    /* host time of admission (allocation, upload, first forces) */
+    double rebuild_ms;                  /* host time spent rebuilding the batch graph (after a join or leave) */
+    double t;                           /* server clock at the end of the tick (s) */
+} mix_tick_info;
+
+/* All requests' work goes to cuda_stream.  MIX_ENOMEM when no budget is left. */
+int mix_server_create(const mix_server_options* opt, void* cuda_stream, mix_server** out);
+
+/* Queue a request: system, potentials, options (as for mix_init; the server's
+ * stream is used), regions (as mix_set_regions), host x and v ([N][4] float64,
+ * copied), nsteps >= 0.  The context is created here (host tables); device
+ * memory is taken at admission.  MIX_ENOMEM if the request can never fit the
+ * budget; other errors as mix_init.  *id receives the request's id (>= 1). */
+int mix_server_submit(mix_server* s, const mix_system* sys, const mix_ace* expensive, const mix_spline* cheap,
+                      const mix_options* opt, const mix_region* regions, int n_regions, const double* x_host,
+                      const double* v_host, int64_t nsteps, int64_t* id);
+
+/* Admit what fits, run min(max_steps, the fewest steps any active request has
+ * left) batched steps (max_steps >= 1), retire finished requests (their final
+ * x, v, f are copied to host memory and their device memory is released),
+ * and fail requests whose own status reports an error (the others go on).
+ * Synchronises.  info is nullable. */
+int mix_server_tick(mix_server* s, int max_steps, mix_tick_info* info);
+
+int mix_server_request(mix_server* s, int64_t id, mix_request_info* info);
+
+/* Copy a finished request's final state ([N][4] float64 host arrays, each
+ * nullable) and forget the request.  MIX_ESTATE if it is not DONE or FAILED
+ * (a failed request returns its status and copies nothing). */
+int mix_server_fetch(mix_server* s, int64_t id, double* x_host, double* v_host, double* f_host);
+
+int mix_server_destroy(mix_server* s);
+const char* mix_server_last_error(const mix_server* s);
+
+/* The admission rule alone (host only, no GPU): queued requests in arrival
+ * order with device bytes need[k] and atoms[k]; bytes_free left in the
+ * budget; atoms_free left under max_active_atoms (< 0: no cap); active
+ * requests now running; max_active (0: none); fifo as above.  admit[k] = 1
+ * for each admitted request; returns how many. */
+int mix_admission_plan(const size_t* need, const int64_t* atoms, int n_queued, size_t bytes_free, int64_t atoms_free,
+                       int active, int max_active, int fifo, int* admit);
+
+/* ------------------------------------------------------------------------ */
 /* Neighbour lists for callers that cannot allocate device memory.  The paper  */
 /* has no counterpart: this is a packaging of the library's own list build.   */
 /*                                                                            */

@@ -593,7 +593,7 @@ inline cudaError_t ace_cfg(int n, int cap, size_t* smem, int* grid) {
     const int nq = (n * n + 3) & ~3;
     const AceSmem lay(cap, n, nq, L, NP);
     const size_t bytes = (size_t)lay.total * sizeof(T);
-    cudaError_t e = cudaFuncSetAttribute(k_ace<T, L, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cudaError_t e = raise_smem_limit((const void*)k_ace<T, L, NP>, bytes);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ace<T, L, NP>, ACE_NT, bytes);

@@ -9,6 +9,8 @@
 // neighbour iff r2 < (rc + skin)^2.  Each row of the list is sorted ascending.
 #include <climits>
 
+#include <mutex>
+
 #include "mix_launch.h"
 
 namespace mixd {
@@ -285,6 +287,16 @@ int sm_count() {
         if (g_sms <= 0) g_sms = 1;
     }
     return g_sms;
+}
+
+cudaError_t raise_smem_limit(const void* func, size_t bytes) {
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, func);
+    if (e != cudaSuccess) return e;
+    if ((size_t)fa.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
+    return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 void launch_disp(const Dev& d, cudaStream_t s, int integrate, double dt, double h, int force_rebuild) {

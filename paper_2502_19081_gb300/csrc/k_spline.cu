@@ -210,7 +210,7 @@ template <typename T>
 static cudaError_t spl_cfg(int cap, size_t* smem, int* grid) {
     (void)cap;
     const size_t bytes = (512 + 16) * sizeof(T) + SPL_WARPS * sizeof(SplWarp<T>);
-    cudaError_t e = cudaFuncSetAttribute(k_spline<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cudaError_t e = raise_smem_limit((const void*)k_spline<T>, bytes);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spline<T>, SPL_WARPS * 32, bytes);

@@ -30,6 +30,11 @@ void launch_gather(const Dev& d, int precision, int integrate, double h, cudaStr
 
 int sm_count();
 
+// Raise (never lower) a kernel's dynamic shared-memory limit to `bytes`.  The
+// limit belongs to the kernel, not to a context: contexts of different sizes
+// share kernel instantiations, so one context must not shrink another's limit.
+cudaError_t raise_smem_limit(const void* func, size_t bytes);
+
 // FMA throughput microbenchmark (k_peak.cu)
 int fma_peak(int precision, cudaStream_t s, double* flops_per_s);
 

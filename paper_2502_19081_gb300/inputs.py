@@ -124,23 +124,19 @@ def diamond_lattice(nx: int, ny: int, nz: int) -> np.ndarray:
     """Integer coordinates (units of a/4) of a diamond supercell, z-major order."""
     fcc = np.array([[0, 0, 0], [0, 2, 2], [2, 0, 2], [2, 2, 0]])
     basis = np.concatenate([fcc, fcc + 1])
-    pts = []
-    for ix in range(nx):
-        for iy in range(ny):
-            for iz in range(nz):
-                pts.append(basis + 4 * np.array([ix, iy, iz]))
-    return np.concatenate(pts).astype(np.int64)
+    return (basis[None, :, :] + 4 * _cell_grid(nx, ny, nz)[:, None, :]).reshape(-1, 3).astype(np.int64)
+
+
+def _cell_grid(nx: int, ny: int, nz: int) -> np.ndarray:
+    """Cell indices (ix, iy, iz), ix slowest and iz fastest."""
+    g = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
+    return np.stack(g, axis=-1).reshape(-1, 3)
 
 
 def bcc_lattice(nx: int, ny: int, nz: int) -> np.ndarray:
     """Integer coordinates (units of a/2) of a bcc supercell."""
     basis = np.array([[0, 0, 0], [1, 1, 1]])
-    pts = []
-    for ix in range(nx):
-        for iy in range(ny):
-            for iz in range(nz):
-                pts.append(basis + 2 * np.array([ix, iy, iz]))
-    return np.concatenate(pts).astype(np.int64)
+    return (basis[None, :, :] + 2 * _cell_grid(nx, ny, nz)[:, None, :]).reshape(-1, 3).astype(np.int64)
 
 
 def _pack(pos3: np.ndarray) -> np.ndarray:
@@ -445,6 +441,71 @@ def si_replicas(n_replicas: int = 256, seed: int = 4, n_min: int = 1000, n_max: 
         temp = float(rng.uniform(300.0, 1500.0))
         out.append(si_replica(seed * 100000 + r, n_t, defect, temp, ace, spl))
     return out
+
+
+def serve_potentials():
+    """The two potential pairs of the request stream: Si with the silicon
+    vacancy cell's recipe (rc 5 A, n 8, lmax 3, body order 3) and Fe with the
+    dumbbell cell's recipe (rc 5.5 A, n 10, lmax 4, body order 4)."""
+    si = element_potentials("Si", np.random.default_rng(1), 5.0, 8, 3, 3)
+    fe = element_potentials("Fe", np.random.default_rng(2), 5.5, 10, 4, 4)
+    return {"Si": si, "Fe": fe}
+
+
+def serve_request(seed: int, element: str, n_target: int, core_frac: float, temp_k: float, pots) -> Workload:
+    """One request: the periodic diamond (Si, 8 atoms per cell) or bcc (Fe, 2
+    per cell) box of k x k x k3 cells (k >= 3) whose atom count is nearest
+    n_target, minus the site nearest the centre (a vacancy), thermal sigma
+    0.05 A, Maxwell-Boltzmann velocities at temp_k; a core sphere at the
+    vacancy holding the fraction core_frac of the atoms,
+    r_core = (3 f N / (4 pi rho))^(1/3), ramp 2 A (Si) or 3 A (Fe)."""
+    rng = np.random.default_rng(seed)
+    if element == "Si":
+        a, per_cell, unit, mass, ramp = 5.431, 8, 4.0, MASS_SI, 2.0
+    else:
+        a, per_cell, unit, mass, ramp = 2.855, 2, 2.0, MASS_FE, 3.0
+    k = max(3, int(round((n_target / per_cell) ** (1.0 / 3.0))))
+    k3 = max(3, int(round(n_target / (per_cell * k * k))))
+    q = diamond_lattice(k, k, k3) if element == "Si" else bcc_lattice(k, k, k3)
+    ctr = np.array([k, k, k3]) * (unit / 2.0)
+    idx = int(np.argmin(np.sum((q - ctr) ** 2, axis=1)))
+    site = q[idx] * (a / unit)
+    pos = np.delete(q, idx, axis=0) * (a / unit)
+    pos = pos + rng.normal(0.0, 0.05, pos.shape)
+    L = np.array([k * a, k * a, k3 * a])
+    pos = wrap_into_box(pos, L, (1, 1, 1))
+    n = pos.shape[0]
+    rho = n / float(np.prod(L))
+    r_core = (3.0 * core_frac * n / (4.0 * math.pi * rho)) ** (1.0 / 3.0)
+    sysm = System(x=_pack(pos), v=maxwell_boltzmann(rng, n, mass, temp_k), mass=mass, box_lo=np.zeros(3),
+                  box_len=L, periodic=(1, 1, 1))
+    ace, spl = pots[element]
+    reg = [Region(REGION_SPHERE, tuple(site), (0.0, 0.0, 1.0), r_core, ramp)]
+    return Workload(f"request_{element}_{n}_{seed}", sysm, reg, ace, spl, skin=0.3, dt=1.0, steps=0,
+                    precision=PRECISION_FP32, seed=seed,
+                    extra={"core_frac": core_frac, "temp_k": temp_k, "element": element})
+
+
+def serve_stream(seed: int = 5, rate: float = 20.0, duration: float = 600.0, n_min: float = 1e3,
+                 n_max: float = 5e5, len_min: float = 100.0, len_max: float = 2000.0):
+    """Request specifications of a Poisson arrival process: exponential gaps of
+    mean 1/rate seconds up to `duration`; Si or Fe with equal probability; atom
+    counts and trajectory lengths log-uniform on [n_min, n_max] and
+    [len_min, len_max]; core fraction uniform on [1 %, 10 %]; temperature
+    uniform on [300, 1500] K.  Yields dicts (t, seed, element, n_target,
+    core_frac, temp_k, nsteps); serve_request builds the system."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    k = 0
+    while True:
+        t += float(rng.exponential(1.0 / rate))
+        if t > duration:
+            return
+        yield {"t": t, "seed": seed * 1000003 + k, "element": "Si" if rng.uniform() < 0.5 else "Fe",
+               "n_target": int(round(math.exp(rng.uniform(math.log(n_min), math.log(n_max))))),
+               "core_frac": float(rng.uniform(0.01, 0.10)), "temp_k": float(rng.uniform(300.0, 1500.0)),
+               "nsteps": int(round(math.exp(rng.uniform(math.log(len_min), math.log(len_max)))))}
+        k += 1
 
 
 WORKLOADS = {

@@ -43,6 +43,8 @@ EXPORTS = [
     "mix_destroy", "mix_strerror", "mix_last_error", "mix_get_info", "mix_profile", "mix_get_profile",
     "mix_fma_peak", "mix_tune", "mix_batch_create", "mix_batch_step", "mix_batch_sync", "mix_batch_tune",
     "mix_batch_destroy", "mix_batch_last_error", "mix_set_seeds", "mix_set_seed_rule", "mix_get_seeds",
+    "mix_server_create", "mix_server_submit", "mix_server_tick", "mix_server_request", "mix_server_fetch",
+    "mix_server_destroy", "mix_server_last_error", "mix_admission_plan",
 ]
 
 MIX_PHASES = 6
@@ -100,6 +102,26 @@ class mix_info(ctypes.Structure):
                 ("buffer_grid", ctypes.c_int)]
 
 
+class mix_server_options(ctypes.Structure):
+    _fields_ = [("dt_fs", ctypes.c_double), ("hbm_budget", ctypes.c_size_t), ("hbm_reserve", ctypes.c_size_t),
+                ("max_active_atoms", ctypes.c_int64), ("max_active", ctypes.c_int), ("fifo", ctypes.c_int)]
+
+
+class mix_request_info(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int), ("status", ctypes.c_int), ("n_atoms", ctypes.c_int64),
+                ("steps_done", ctypes.c_int64), ("steps_total", ctypes.c_int64), ("device_bytes", ctypes.c_size_t),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+class mix_tick_info(ctypes.Structure):
+    _fields_ = [("admitted", ctypes.c_int), ("retired", ctypes.c_int), ("failed", ctypes.c_int),
+                ("active", ctypes.c_int), ("queued", ctypes.c_int), ("active_atoms", ctypes.c_int64),
+                ("steps", ctypes.c_int), ("bytes_in_use", ctypes.c_size_t), ("step_ms", ctypes.c_double),
+                ("admit_ms", ctypes.c_double), ("rebuild_ms", ctypes.c_double), ("t", ctypes.c_double)]
+
+
+MIX_REQ_QUEUED, MIX_REQ_ACTIVE, MIX_REQ_DONE, MIX_REQ_FAILED = 0, 1, 2, 3
+
 _lock = threading.Lock()
 _lib = None
 
@@ -127,6 +149,18 @@ def lib():
                                             ctypes.c_double, ctypes.c_double]
             L.mix_get_seeds.argtypes = [P, ctypes.POINTER(ctypes.c_uint8), i64p]
             L.mix_forces.argtypes = [P]
+            L.mix_server_create.argtypes = [ctypes.POINTER(mix_server_options), P, ctypes.POINTER(P)]
+            L.mix_server_submit.argtypes = [P, ctypes.POINTER(mix_system), ctypes.POINTER(mix_ace),
+                                            ctypes.POINTER(mix_spline), ctypes.POINTER(mix_options),
+                                            ctypes.POINTER(mix_region), ctypes.c_int, dp, dp, ctypes.c_int64, i64p]
+            L.mix_server_tick.argtypes = [P, ctypes.c_int, ctypes.POINTER(mix_tick_info)]
+            L.mix_server_request.argtypes = [P, ctypes.c_int64, ctypes.POINTER(mix_request_info)]
+            L.mix_server_fetch.argtypes = [P, ctypes.c_int64, dp, dp, dp]
+            L.mix_server_destroy.argtypes = [P]
+            L.mix_server_last_error.restype = ctypes.c_char_p
+            L.mix_server_last_error.argtypes = [P]
+            L.mix_admission_plan.argtypes = [ctypes.POINTER(ctypes.c_size_t), i64p, ctypes.c_int, ctypes.c_size_t,
+                                             ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ip]
             L.mix_step.argtypes = [P, ctypes.c_double, ctypes.c_int]
             L.mix_step_host.argtypes = [P, dp, dp, dp, ctypes.c_double, ctypes.c_int]
             L.mix_sync.argtypes = [P]
@@ -173,6 +207,34 @@ def _f64(a) -> np.ndarray:
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
+def _init_structs(workload, precision, nbr_cap=0, blend=MIX_BLEND_LINEAR, buffer_exp=0.0, buffer_cheap=0.0,
+                  skin=None, graphs=True):
+    """mix_init arguments for a workload; the returned list keeps the arrays alive."""
+    s = workload.system
+    keep = []
+    sysd = mix_system(int(s.n), (ctypes.c_double * 3)(*s.box_lo), (ctypes.c_double * 3)(*s.box_len),
+                      (ctypes.c_int * 3)(*[int(p) for p in s.periodic]), float(s.mass))
+    a = workload.ace
+    c1, c2, c3, pair = _f64(a.c1), _f64(a.c2), _f64(a.c3), _f64(a.pair)
+    sp = workload.spline
+    s2, s3 = _f64(sp.c2), _f64(sp.c3)
+    keep += [c1, c2, c3, pair, s2, s3]
+    aced = mix_ace(float(a.r_cut), int(a.n_rad), int(a.l_max), int(a.nu_max), _dp(c1), _dp(c2), _dp(c3),
+                   _dp(pair))
+    spld = mix_spline(float(sp.r_cut), float(sp.r_cut3), _dp(s2), _dp(s3))
+    opt = mix_options(int(precision), float(workload.skin if skin is None else skin), int(blend),
+                      float(buffer_exp), float(buffer_cheap), int(nbr_cap), 0 if graphs else 1)
+    return sysd, aced, spld, opt, keep
+
+
+def _regions_array(regions):
+    arr = (mix_region * max(len(regions), 1))()
+    for k, r in enumerate(regions):
+        arr[k] = mix_region(int(r.kind), (ctypes.c_double * 3)(*r.centre), (ctypes.c_double * 3)(*r.axis),
+                            float(r.r_core), float(r.ramp))
+    return arr
+
+
 class Context:
     """One mixed-MD trajectory on one CUDA device, backed by libmix.so.
 
@@ -193,19 +255,8 @@ class Context:
         s = workload.system
         self.n = int(s.n)
         self.precision = precision
-        self._keep = []
-        sysd = mix_system(self.n, (ctypes.c_double * 3)(*s.box_lo), (ctypes.c_double * 3)(*s.box_len),
-                          (ctypes.c_int * 3)(*[int(p) for p in s.periodic]), float(s.mass))
-        a = workload.ace
-        c1, c2, c3, pair = _f64(a.c1), _f64(a.c2), _f64(a.c3), _f64(a.pair)
-        sp = workload.spline
-        s2, s3 = _f64(sp.c2), _f64(sp.c3)
-        self._keep += [c1, c2, c3, pair, s2, s3]
-        aced = mix_ace(float(a.r_cut), int(a.n_rad), int(a.l_max), int(a.nu_max), _dp(c1), _dp(c2), _dp(c3),
-                       _dp(pair))
-        spld = mix_spline(float(sp.r_cut), float(sp.r_cut3), _dp(s2), _dp(s3))
-        opt = mix_options(int(precision), float(workload.skin if skin is None else skin), int(blend),
-                          float(buffer_exp), float(buffer_cheap), int(nbr_cap), 0 if graphs else 1)
+        sysd, aced, spld, opt, self._keep = _init_structs(workload, precision, nbr_cap, blend, buffer_exp,
+                                                          buffer_cheap, skin, graphs)
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
             h = ctypes.c_void_p()
@@ -253,10 +304,7 @@ class Context:
 
     # -- calls --------------------------------------------------------------
     def set_regions(self, regions):
-        arr = (mix_region * max(len(regions), 1))()
-        for k, r in enumerate(regions):
-            arr[k] = mix_region(int(r.kind), (ctypes.c_double * 3)(*r.centre), (ctypes.c_double * 3)(*r.axis),
-                                float(r.r_core), float(r.ramp))
+        arr = _regions_array(regions)
         self._check(self.L.mix_set_regions(self.h, arr, len(regions)), "mix_set_regions")
 
     def set_seeds(self, seeds, r_core: float, r_blend: float):
@@ -446,6 +494,95 @@ def neighbours_noalloc(x, box_lo, box_len, periodic, r_list: float, cap: int, nn
                                             float(r_list), int(cap), ctypes.c_void_p(nnb.data_ptr()),
                                             ctypes.c_void_p(nbr.data_ptr()), ctypes.c_void_p(rev.data_ptr()),
                                             ctypes.c_void_p(s.cuda_stream)))
+
+
+def admission_plan(need, atoms, bytes_free: int, atoms_free: int = -1, active: int = 0, max_active: int = 0,
+                   fifo: bool = True):
+    """The server's admission rule alone (host only): admit flags per queued request."""
+    L = lib()
+    k = len(need)
+    nd = (ctypes.c_size_t * max(k, 1))(*[int(v) for v in need])
+    at = np.ascontiguousarray(np.asarray(atoms, dtype=np.int64).reshape(-1)) if k else np.zeros(1, np.int64)
+    out = np.zeros(max(k, 1), dtype=np.int32)
+    cnt = L.mix_admission_plan(nd, at.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), k, int(bytes_free),
+                               int(atoms_free), int(active), int(max_active), 1 if fifo else 0, _ip(out))
+    if cnt < 0:
+        raise MixError(cnt, "mix_admission_plan")
+    return out[:k].astype(bool)
+
+
+class Server:
+    """A request queue served by continuous batching on one device (libmix.so's
+    mix_server_*): requests are admitted while their device memory fits the
+    budget, stepped together, and retired with their final state on the host."""
+
+    def __init__(self, dt: float, hbm_budget: int = 0, hbm_reserve: int = 0, max_active_atoms: int = 0,
+                 max_active: int = 0, fifo: bool = True, device: str = "cuda:0", stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the serving path runs only on the GPU")
+        self.L = lib()
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        o = mix_server_options(float(dt), int(hbm_budget), int(hbm_reserve), int(max_active_atoms),
+                               int(max_active), 1 if fifo else 0)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            st = self.L.mix_server_create(ctypes.byref(o), ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        if st != MIX_OK:
+            raise MixError(st, "mix_server_create: " + self.L.mix_strerror(st).decode())
+        self.h = h
+        self.n = {}
+
+    def _check(self, st: int, what: str):
+        if st != MIX_OK:
+            msg = self.L.mix_server_last_error(self.h).decode() if self.h else ""
+            raise MixError(st, f"{what}: {self.L.mix_strerror(st).decode()}: {msg}")
+
+    def submit(self, workload, nsteps: int, precision: int = MIX_FP32, nbr_cap: int = 0,
+               blend: int = MIX_BLEND_LINEAR, skin: Optional[float] = None, regions=None) -> int:
+        sysd, aced, spld, opt, keep = _init_structs(workload, precision, nbr_cap, blend, 0.0, 0.0, skin, True)
+        regs = workload.regions if regions is None else regions
+        arr = _regions_array(regs)
+        s = workload.system
+        x = np.ascontiguousarray(np.asarray(s.x, dtype=np.float64).reshape(-1, 4)) if s.n else np.zeros((1, 4))
+        v = np.ascontiguousarray(np.asarray(s.v, dtype=np.float64).reshape(-1, 4)) if s.n else np.zeros((1, 4))
+        rid = ctypes.c_int64()
+        self._check(self.L.mix_server_submit(self.h, ctypes.byref(sysd), ctypes.byref(aced), ctypes.byref(spld),
+                                             ctypes.byref(opt), arr, len(regs), _dp(x), _dp(v), int(nsteps),
+                                             ctypes.byref(rid)), "mix_server_submit")
+        self.n[int(rid.value)] = int(s.n)
+        return int(rid.value)
+
+    def tick(self, max_steps: int = 1) -> dict:
+        t = mix_tick_info()
+        self._check(self.L.mix_server_tick(self.h, int(max_steps), ctypes.byref(t)), "mix_server_tick")
+        return {k: getattr(t, k) for k, _ in mix_tick_info._fields_}
+
+    def request(self, rid: int) -> dict:
+        r = mix_request_info()
+        self._check(self.L.mix_server_request(self.h, int(rid), ctypes.byref(r)), "mix_server_request")
+        return {k: getattr(r, k) for k, _ in mix_request_info._fields_}
+
+    def fetch(self, rid: int):
+        n = self.n.get(int(rid), 0)
+        x = np.zeros((max(n, 1), 4))
+        v = np.zeros_like(x)
+        f = np.zeros_like(x)
+        self._check(self.L.mix_server_fetch(self.h, int(rid), _dp(x), _dp(v), _dp(f)), "mix_server_fetch")
+        self.n.pop(int(rid), None)
+        return x[:n], v[:n], f[:n]
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.mix_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def open_context(workload, precision: int = MIX_FP64, retries: int = 2, **kw) -> Context:

@@ -286,3 +286,19 @@ def test_screw_cylinder_full_size_sampled(mx):
         pick += list(rng.choice(idx, 2, replace=False))
     Fs = om.forces_sampled(x, np.array(pick))
     assert _max_abs(F[pick, :3], Fs[:, :3]) < TOL64
+
+
+def test_contexts_of_different_capacity_share_kernels(mx):
+    """The expensive kernel's shared-memory size grows with the neighbour
+    capacity; a context created later with a smaller capacity must not shrink
+    the limit an earlier, larger one launches with."""
+    wl = I.small_fe_box(16)
+    big = mx.open_context(wl, nbr_cap=256)
+    small = mx.open_context(wl, nbr_cap=96)
+    big.forces()
+    big.sync()
+    x, _, F, _ = big.get_state()
+    FB, _, _ = oracle.Model(wl).forces(x, oracle.MODE_METHOD)
+    assert _max_abs(F[:, :3], FB[:, :3]) < TOL64
+    xs, _, Fs, _ = small.get_state()
+    assert np.array_equal(Fs, F)
