@@ -14,15 +14,18 @@
 //        U[q1 q2][m3] = sum_q3 W[q1 q2 q3] A[l3 m3][q3]
 //        Z[q1 q2][m3] = sum_(m1 m2) G A[l1 m1][q1] A[l2 m2][q2]   (Gaunt-sparse)
 //        E += sum Z U;  omega3 += W^T Z;  omega1 += G A2 U;  omega2 += G A1 U;
-//      each lane keeps a few W rows in registers for the U/Z pass; where two
-//      l's coincide W is symmetrised on the host, the adjoints through the
+//      in the U/Z pass a lane owns one q1 and a block of qb consecutive q2
+//      (the W rows of that block sit in registers), so each Gaunt entry costs
+//      one packed table load, one scalar A1 load and one vector A2 load for qb
+//      accumulations; omega3 = W^T Z with a lane per output; where
+//      two l's coincide W is symmetrised on the host, the adjoints through the
 //      coinciding factors are equal, and one of them is computed and scaled
 //      (omega2 only for distinct l's, omega1 not when all three are equal);
 //   5. omega = sum of the warp copies (fixed order);
 //   6. pair gradients dE_i/dr_ij = u sum_lm sigma_lm Y_lm
 //        + (grad_u p - u (u . grad_u p)) / r,  rho = omega R, sigma = omega R',
-//      R, R', Y recomputed per neighbour in registers, the lm sum split over two
-//      warps; written per list slot.
+//      R, R', Y recomputed per neighbour in registers, the lm sum split over
+//      pairs of warps; written per list slot.
 // Per-atom arrays are stored transposed ([lm][q], q padded to NP = 4k with
 // zeros) so that the inner products run over 4-wide vector loads with no index
 // division.  Site energy partial sums are kept in T per thread and reduced in
@@ -33,7 +36,6 @@
 
 namespace mixd {
 
-constexpr int ACE_NT = ACE_WARPS * 32;   // threads per CTA
 constexpr int ACE_CH = 64;               // neighbours per density chunk
 
 template <typename T> struct V4;
@@ -69,6 +71,42 @@ __device__ __forceinline__ V4<double> ldg4<double>(const double* p) {
     const double2 a = __ldg(reinterpret_cast<const double2*>(p));
     const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
     return {a.x, a.y, b.x, b.y};
+}
+
+// one Gaunt entry through the read-only path (one 8- or 16-byte load)
+__device__ __forceinline__ void ld_gent(const GEnt<float>* p, int& pk, float& g) {
+    const int2 v = __ldg(reinterpret_cast<const int2*>(p));
+    pk = v.x;
+    g = __int_as_float(v.y);
+}
+__device__ __forceinline__ void ld_gent(const GEnt<double>* p, int& pk, double& g) {
+    const int4 v = __ldg(reinterpret_cast<const int4*>(p));
+    pk = v.x;
+    g = __hiloint2double(v.w, v.z);
+}
+
+// QB consecutive values from shared memory (QB in {1, 2, 4}, aligned to QB)
+template <typename T, int QB>
+__device__ __forceinline__ void ld_blk(const T* p, T* out) {
+    if constexpr (QB == 4) {
+        const V4<T> v = ld4<T>(p);
+        out[0] = v.x;
+        out[1] = v.y;
+        out[2] = v.z;
+        out[3] = v.w;
+    } else if constexpr (QB == 2) {
+        if constexpr (sizeof(T) == 4) {
+            const float2 v = *reinterpret_cast<const float2*>(p);
+            out[0] = v.x;
+            out[1] = v.y;
+        } else {
+            const double2 v = *reinterpret_cast<const double2*>(p);
+            out[0] = v.x;
+            out[1] = v.y;
+        }
+    } else {
+        out[0] = p[0];
+    }
 }
 
 // Pi[l][m] = d^m P_l / dz^m for 0 <= m <= l <= L (flattened l(l+1)/2 + m),
@@ -173,37 +211,127 @@ __host__ __device__ constexpr int ace_pad(int x) { return (x + 3) & ~3; }
 // nu = 3 scratch are never live together and share one region.
 struct AceSmem {
     int o_u, o_At, o_om, o_gp, o_w, o_cR, o_cY, ws, total;
-    __host__ __device__ AceSmem(int cap, int n, int nq, int L, int NP) {
+    __host__ __device__ AceSmem(int cap, int n, int nq, int L, int NP, int W) {
         const int nlm = (L + 1) * (L + 1);
         const int D = 2 * L + 1;
         o_u = 0;
         o_At = ace_pad(4 * cap);
         o_om = o_At + nlm * NP;
         o_gp = o_om + nlm * NP;
-        o_w = o_gp + 2 * 64 * 4;
+        o_w = o_gp + 2 * (16 * W) * 4;         // gradient partials: 2 halves x 16 W neighbours
         o_cR = o_w;
         o_cY = o_cR + ACE_CH * NP;
         ws = D * n * NP + D * nq + nlm * NP;   // per warp: U, ZT, omega copy
         const int chunk = ACE_CH * NP + ace_pad(ACE_CH * nlm);
-        const int wsall = ACE_WARPS * ws;
+        const int wsall = W * ws;
         total = o_w + (chunk > wsall ? chunk : wsall);
     }
 };
 
+// nu = 3, U and Z of one l-triple for this warp.  Lane units are (q1, block of
+// QB consecutive q2); the m3 loop is uniform over the warp so every Gaunt
+// entry and A3 row load is a broadcast.
+//   U[m3][q1][q2] = sum_q3 W[q1 q2][q3] A3[m3][q3]      (stored, q2 padded to NP)
+//   Z[m3][q1 n + q2] = sum_(m1 m2) G A1[m1][q1] A2[m2][q2]
+//   ep += sum U Z
+// Without U (all three l's equal: no adjoint needs U) only Z is formed and the
+// energy is taken in the omega3 pass as sum A3 (W^T Z), the same sum reordered.
+template <typename T, int NP, int QB, bool WITHU>
+__device__ __forceinline__ void nu3_uz(const T* __restrict__ W, const T* A1, const T* A2, const T* A3,
+                                       const int* g3o, const GEnt<T>* __restrict__ gent, int n, int nq, int d3,
+                                       int lane, T* U1, T* ZT, T& ep) {
+    constexpr int nqb = NP / QB;
+    const int units = n * nqb;
+    for (int u0 = 0; u0 < units; u0 += 32) {
+        const int u = u0 + lane;
+        const bool uv = u < units;
+        const int uu = uv ? u : 0;
+        const int q1 = uu / nqb;
+        const int q2 = (uu - q1 * nqb) * QB;
+        T w[QB][NP];
+#pragma unroll
+        for (int r = 0; r < QB; ++r) {
+            if (!WITHU) break;
+            const bool ok = uv && q2 + r < n;
+            const T* wr = W + (q1 * n + (ok ? q2 + r : 0)) * NP;
+#pragma unroll
+            for (int p = 0; p < NP; p += 4) {
+                V4<T> v = ldg4<T>(wr + p);
+                if (!ok) v = V4<T>{T(0), T(0), T(0), T(0)};
+                w[r][p] = v.x;
+                w[r][p + 1] = v.y;
+                w[r][p + 2] = v.z;
+                w[r][p + 3] = v.w;
+            }
+        }
+        for (int m3 = 0; m3 < d3; ++m3) {
+            T uo[QB], z[QB];
+#pragma unroll
+            for (int r = 0; r < QB; ++r) {
+                uo[r] = T(0);
+                z[r] = T(0);
+            }
+            if (WITHU) {
+                T a[NP];
+#pragma unroll
+                for (int p = 0; p < NP; p += 4) {
+                    const V4<T> v = ld4<T>(A3 + m3 * NP + p);
+                    a[p] = v.x;
+                    a[p + 1] = v.y;
+                    a[p + 2] = v.z;
+                    a[p + 3] = v.w;
+                }
+#pragma unroll
+                for (int r = 0; r < QB; ++r) {
+                    T s = T(0);
+#pragma unroll
+                    for (int p = 0; p < NP; ++p) s += w[r][p] * a[p];
+                    uo[r] = s;
+                }
+            }
+            const int e1 = g3o[m3 + 1];
+            for (int e = g3o[m3]; e < e1; ++e) {
+                int pk;
+                T g;
+                ld_gent(gent + e, pk, g);
+                const T ga = g * A1[(pk & 255) * NP + q1];
+                T a2[QB];
+                ld_blk<T, QB>(A2 + (pk >> 8) * NP + q2, a2);
+#pragma unroll
+                for (int r = 0; r < QB; ++r) z[r] += ga * a2[r];
+            }
+            if (uv) {
+#pragma unroll
+                for (int r = 0; r < QB; ++r) {
+                    if (WITHU) U1[(m3 * n + q1) * NP + q2 + r] = uo[r];
+                    if (q2 + r < n) {
+                        ZT[m3 * nq + q1 * n + q2 + r] = z[r];
+                        if (WITHU) ep += uo[r] * z[r];
+                    }
+                }
+            }
+        }
+    }
+}
+
 template <typename T, int L, int NP>
-__global__ void __launch_bounds__(ACE_NT) k_ace(Dev d, AceTab<T> tab) {
+__global__ void __launch_bounds__(ace_warps<T>() * 32, ace_min_ctas<T>()) k_ace(Dev d, AceTab<T> tab) {
+    constexpr int WN = ace_warps<T>();
+    constexpr int NT = WN * 32;
     constexpr int NLM = (L + 1) * (L + 1);
     constexpr int D = 2 * L + 1;
-    constexpr int NOUT = (NLM * NP + ACE_NT - 1) / ACE_NT;
+    constexpr int NOUT = (NLM * NP + NT - 1) / NT;
+    constexpr int QM = sizeof(T) == 4 ? 4 : 2;     // largest q2 block of the U/Z pass
+    constexpr int PER = 16 * WN;                   // neighbours per gradient pass
     using V = typename Vec4<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_slot[MAX_CAP];
-    __shared__ int s_wcnt[ACE_WARPS];
-    __shared__ double s_red[ACE_WARPS];
+    __shared__ int s_wcnt[WN];
+    __shared__ double s_red[WN];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int n = tab.n, nq = tab.nq, cap = d.cap;
-    const AceSmem lay(cap, n, nq, L, NP);
+    const AceSmem lay(cap, n, nq, L, NP, WN);
     T* sm = reinterpret_cast<T*>(smem_raw);
     T* s_u = sm + lay.o_u;
     T* s_At = sm + lay.o_At;
@@ -233,7 +361,7 @@ __global__ void __launch_bounds__(ACE_NT) k_ace(Dev d, AceTab<T> tab) {
 
         // 1. neighbours inside the cutoff, ordered compaction
         int nb = 0;
-        for (int base = 0; base < m; base += ACE_NT) {
+        for (int base = 0; base < m; base += NT) {
             const int s = base + tid;
             bool ok = false;
             T dv[3] = {T(0), T(0), T(0)}, r2 = T(0);
@@ -251,7 +379,7 @@ __global__ void __launch_bounds__(ACE_NT) k_ace(Dev d, AceTab<T> tab) {
             __syncthreads();
             int off = nb, tot = 0;
 #pragma unroll
-            for (int w = 0; w < ACE_WARPS; ++w) {
+            for (int w = 0; w < WN; ++w) {
                 if (w < warp) off += s_wcnt[w];
                 tot += s_wcnt[w];
             }
@@ -275,7 +403,7 @@ __global__ void __launch_bounds__(ACE_NT) k_ace(Dev d, AceTab<T> tab) {
         for (int j = 0; j < NOUT; ++j) acc[j] = T(0);
         for (int k0 = 0; k0 < nb; k0 += ACE_CH) {
             const int kc = nb - k0 < ACE_CH ? nb - k0 : ACE_CH;
-            for (int kl = tid; kl < kc; kl += ACE_NT) {
+            for (int kl = tid; kl < kc; kl += NT) {
                 const int k = k0 + kl;
                 const T r = s_u[4 * k + 3];
                 T R[NP], dR[NP];
@@ -292,7 +420,7 @@ __global__ void __launch_bounds__(ACE_NT) k_ace(Dev d, AceTab<T> tab) {
             __syncthreads();
 #pragma unroll
             for (int j = 0; j < NOUT; ++j) {
-                const int o = tid + j * ACE_NT;
+                const int o = tid + j * NT;
                 if (o < NLM * NP) {
                     const int lm = o / NP, q = o - lm * NP;
                     T s = acc[j];
@@ -304,7 +432,7 @@ __global__ void __launch_bounds__(ACE_NT) k_ace(Dev d, AceTab<T> tab) {
         }
 #pragma unroll
         for (int j = 0; j < NOUT; ++j) {
-            const int o = tid + j * ACE_NT;
+            const int o = tid + j * NT;
             if (o < NLM * NP) s_At[o] = acc[j];
         }
         // the density chunks are dead: zero this warp's scratch (its padding,
@@ -315,7 +443,7 @@ __global__ void __launch_bounds__(ACE_NT) k_ace(Dev d, AceTab<T> tab) {
         // 3. nu = 1 and nu = 2; initialises omega
 #pragma unroll
         for (int j = 0; j < NOUT; ++j) {
-            const int o = tid + j * ACE_NT;
+            const int o = tid + j * NT;
             if (o < NLM * NP) {
                 const int lm = o / NP, q = o - lm * NP;
                 T val = T(0);
@@ -357,68 +485,9 @@ __global__ void __launch_bounds__(ACE_NT) k_ace(Dev d, AceTab<T> tab) {
             const int* g2o = g1o + d1 + 1;
             const T* W = tab.W3 + (int64_t)t * n * n * NP;
             const T* WT = tab.WT3 + (int64_t)t * n * nq;
-            // U and Z: each lane holds RC coefficient rows (q1 q2) = base + lane + 32 r
-            // in registers, so every broadcast load of an A row or a Gaunt entry
-            // feeds RC independent accumulations
-            constexpr int RC = sizeof(T) == 4 ? 4 : 2;
-            for (int base = 0; base < n * n; base += 32 * RC) {
-                int q1r[RC], q2r[RC];
-                bool vr[RC];
-                T w[RC][NP];
-#pragma unroll
-                for (int r = 0; r < RC; ++r) {
-                    const int q12 = base + lane + 32 * r;
-                    vr[r] = q12 < n * n;
-                    const int qq = vr[r] ? q12 : 0;
-                    q1r[r] = qq / n;
-                    q2r[r] = qq - q1r[r] * n;
-#pragma unroll
-                    for (int p = 0; p < NP; p += 4) {
-                        V4<T> v = ldg4<T>(W + qq * NP + p);
-                        if (!vr[r]) v = V4<T>{T(0), T(0), T(0), T(0)};
-                        w[r][p] = v.x;
-                        w[r][p + 1] = v.y;
-                        w[r][p + 2] = v.z;
-                        w[r][p + 3] = v.w;
-                    }
-                }
-                for (int m3 = 0; m3 < d3; ++m3) {
-                    T a[NP];
-#pragma unroll
-                    for (int p = 0; p < NP; p += 4) {
-                        const V4<T> v = ld4<T>(A3 + m3 * NP + p);
-                        a[p] = v.x;
-                        a[p + 1] = v.y;
-                        a[p + 2] = v.z;
-                        a[p + 3] = v.w;
-                    }
-                    T u[RC], z[RC];
-#pragma unroll
-                    for (int r = 0; r < RC; ++r) {
-                        T s = T(0);
-#pragma unroll
-                        for (int p = 0; p < NP; ++p) s += w[r][p] * a[p];
-                        u[r] = s;
-                        z[r] = T(0);
-                    }
-                    for (int e = g3o[m3]; e < g3o[m3 + 1]; ++e) {
-                        const int pk = __ldg(tab.gidx + e);
-                        const T g = __ldg(tab.gval + e);
-                        const T* a1 = A1 + (pk & 255) * NP;
-                        const T* a2 = A2 + (pk >> 8) * NP;
-#pragma unroll
-                        for (int r = 0; r < RC; ++r) z[r] += g * a1[q1r[r]] * a2[q2r[r]];
-                    }
-#pragma unroll
-                    for (int r = 0; r < RC; ++r) {
-                        if (vr[r]) {
-                            U1[(m3 * n + q1r[r]) * NP + q2r[r]] = u[r];
-                            ZT[m3 * nq + base + lane + 32 * r] = z[r];
-                            ep += u[r] * z[r];
-                        }
-                    }
-                }
-            }
+            if (mode == 3) nu3_uz<T, NP, QM, false>(W, A1, A2, A3, g3o, tab.gent, n, nq, d3, lane, U1, ZT, ep);
+            else if (tab.qb == QM) nu3_uz<T, NP, QM, true>(W, A1, A2, A3, g3o, tab.gent, n, nq, d3, lane, U1, ZT, ep);
+            else nu3_uz<T, NP, QM / 2, true>(W, A1, A2, A3, g3o, tab.gent, n, nq, d3, lane, U1, ZT, ep);
             __syncwarp();
             // omega3 += W^T Z
             for (int o = lane; o < n * d3; o += 32) {
@@ -432,14 +501,18 @@ __global__ void __launch_bounds__(ACE_NT) k_ace(Dev d, AceTab<T> tab) {
                     s += a4.x * b4.x + a4.y * b4.y + a4.z * b4.z + a4.w * b4.w;
                 }
                 omw[(l3 * l3 + m3) * NP + q3] += mult3 * s;
+                if (mode == 3) ep += A3[m3 * NP + q3] * s;
             }
             __syncwarp();
             // omega1 += G A2 U (equal to omega3 when all three l's coincide)
+            // (lanes in m1-major order: lanes sharing m1 share the Gaunt loop and its loads)
             if (mode != 3) for (int o = lane; o < n * d1; o += 32) {
-                const int q1 = o / d1, m1 = o - q1 * d1;
+                const int m1 = o / n, q1 = o - m1 * n;
                 T accv = T(0);
                 for (int e = g1o[m1]; e < g1o[m1 + 1]; ++e) {
-                    const int pk = tab.gidx[e];
+                    int pk;
+                    T gv;
+                    ld_gent(tab.gent + e, pk, gv);
                     const T* ar = A2 + (pk & 255) * NP;
                     const T* ur = U1 + ((pk >> 8) * n + q1) * NP;
                     T s = T(0);
@@ -449,7 +522,7 @@ __global__ void __launch_bounds__(ACE_NT) k_ace(Dev d, AceTab<T> tab) {
                         const V4<T> b4 = ld4<T>(ur + p);
                         s += a4.x * b4.x + a4.y * b4.y + a4.z * b4.z + a4.w * b4.w;
                     }
-                    accv += tab.gval[e] * s;
+                    accv += gv * s;
                 }
                 omw[(l1 * l1 + m1) * NP + q1] += mult1 * accv;
             }
@@ -457,15 +530,17 @@ __global__ void __launch_bounds__(ACE_NT) k_ace(Dev d, AceTab<T> tab) {
             // omega2 += G A1 U, needed only when the three l's are distinct
             // (otherwise it equals omega1 or omega3, already scaled in)
             if (mode == 0) for (int o = lane; o < n * d2; o += 32) {
-                const int q2 = o / d2, m2 = o - q2 * d2;
+                const int m2 = o / n, q2 = o - m2 * n;
                 T accv = T(0);
                 for (int e = g2o[m2]; e < g2o[m2 + 1]; ++e) {
-                    const int pk = tab.gidx[e];
+                    int pk;
+                    T gv;
+                    ld_gent(tab.gent + e, pk, gv);
                     const T* ar = A1 + (pk & 255) * NP;
                     const T* ur = U1 + (pk >> 8) * n * NP + q2;
                     T s = T(0);
                     for (int q1 = 0; q1 < n; ++q1) s += ar[q1] * ur[q1 * NP];
-                    accv += tab.gval[e] * s;
+                    accv += gv * s;
                 }
                 omw[(l2 * l2 + m2) * NP + q2] += accv;
             }
@@ -474,18 +549,18 @@ __global__ void __launch_bounds__(ACE_NT) k_ace(Dev d, AceTab<T> tab) {
         __syncthreads();
 
         // 5. omega = nu<=2 part + the warp copies, in a fixed order
-        for (int o = tid; o < NLM * NP; o += ACE_NT) {
+        for (int o = tid; o < NLM * NP; o += NT) {
             T s = s_om[o];
 #pragma unroll
-            for (int w = 0; w < ACE_WARPS; ++w) s += sm[lay.o_w + w * lay.ws + D * n * NP + D * nq + o];
+            for (int w = 0; w < WN; ++w) s += sm[lay.o_w + w * lay.ws + D * n * NP + D * nq + o];
             s_om[o] = s;
         }
         __syncthreads();
 
-        // 6. pair gradients: warps (0,1) take neighbours k0..k0+31, warps (2,3) the next 32;
+        // 6. pair gradients: warp pair (2s, 2s+1) takes neighbours k0 + 32 s .. k0 + 32 s + 31;
         //    the two warps of a pair split the lm sum by parity
         const int half = warp & 1, sub = warp >> 1;
-        for (int k0 = 0; k0 < nb; k0 += 64) {
+        for (int k0 = 0; k0 < nb; k0 += PER) {
             const int kl = sub * 32 + lane;
             const int k = k0 + kl;
             T sy = T(0), Gx = T(0), Gy = T(0), Gz = T(0);
@@ -541,16 +616,16 @@ __global__ void __launch_bounds__(ACE_NT) k_ace(Dev d, AceTab<T> tab) {
                     }
                 }
             }
-            T* gp = s_gp + (half * 64 + kl) * 4;
+            T* gp = s_gp + (half * PER + kl) * 4;
             gp[0] = sy;
             gp[1] = Gx;
             gp[2] = Gy;
             gp[3] = Gz;
             __syncthreads();
-            if (tid < 64 && k0 + tid < nb) {
+            if (tid < PER && k0 + tid < nb) {
                 const int kk = k0 + tid;
                 const T* g0 = s_gp + tid * 4;
-                const T* g1 = s_gp + (64 + tid) * 4;
+                const T* g1 = s_gp + (PER + tid) * 4;
                 const T x = s_u[4 * kk], y = s_u[4 * kk + 1], z = s_u[4 * kk + 2], r = s_u[4 * kk + 3];
                 const T syt = g0[0] + g1[0];
                 const T gxt = g0[1] + g1[1], gyt = g0[2] + g1[2], gzt = g0[3] + g1[3];
@@ -581,7 +656,7 @@ __global__ void __launch_bounds__(ACE_NT) k_ace(Dev d, AceTab<T> tab) {
         __syncthreads();
         if (tid == 0) {
             double es = 0.0;
-            for (int w = 0; w < ACE_WARPS; ++w) es += s_red[w];
+            for (int w = 0; w < WN; ++w) es += s_red[w];
             d.esite_e[i] = es;
         }
         __syncthreads();
@@ -591,12 +666,12 @@ __global__ void __launch_bounds__(ACE_NT) k_ace(Dev d, AceTab<T> tab) {
 template <typename T, int L, int NP>
 inline cudaError_t ace_cfg(int n, int cap, size_t* smem, int* grid) {
     const int nq = (n * n + 3) & ~3;
-    const AceSmem lay(cap, n, nq, L, NP);
+    const AceSmem lay(cap, n, nq, L, NP, ace_warps<T>());
     const size_t bytes = (size_t)lay.total * sizeof(T);
     cudaError_t e = raise_smem_limit((const void*)k_ace<T, L, NP>, bytes);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ace<T, L, NP>, ACE_NT, bytes);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ace<T, L, NP>, ace_warps<T>() * 32, bytes);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     *smem = bytes;
@@ -629,13 +704,13 @@ inline cudaError_t ace_cfg_t(int L, int n, int cap, size_t* smem, int* grid) {
 template <typename T, int NP>
 inline void ace_launch_l(const Dev& d, const AceTab<T>& tab, int L, size_t smem, int grid, cudaStream_t s) {
     switch (L) {
-        case 0: k_ace<T, 0, NP><<<grid, ACE_NT, smem, s>>>(d, tab); break;
-        case 1: k_ace<T, 1, NP><<<grid, ACE_NT, smem, s>>>(d, tab); break;
-        case 2: k_ace<T, 2, NP><<<grid, ACE_NT, smem, s>>>(d, tab); break;
-        case 3: k_ace<T, 3, NP><<<grid, ACE_NT, smem, s>>>(d, tab); break;
-        case 4: k_ace<T, 4, NP><<<grid, ACE_NT, smem, s>>>(d, tab); break;
-        case 5: k_ace<T, 5, NP><<<grid, ACE_NT, smem, s>>>(d, tab); break;
-        case 6: k_ace<T, 6, NP><<<grid, ACE_NT, smem, s>>>(d, tab); break;
+        case 0: k_ace<T, 0, NP><<<grid, ace_warps<T>() * 32, smem, s>>>(d, tab); break;
+        case 1: k_ace<T, 1, NP><<<grid, ace_warps<T>() * 32, smem, s>>>(d, tab); break;
+        case 2: k_ace<T, 2, NP><<<grid, ace_warps<T>() * 32, smem, s>>>(d, tab); break;
+        case 3: k_ace<T, 3, NP><<<grid, ace_warps<T>() * 32, smem, s>>>(d, tab); break;
+        case 4: k_ace<T, 4, NP><<<grid, ace_warps<T>() * 32, smem, s>>>(d, tab); break;
+        case 5: k_ace<T, 5, NP><<<grid, ace_warps<T>() * 32, smem, s>>>(d, tab); break;
+        case 6: k_ace<T, 6, NP><<<grid, ace_warps<T>() * 32, smem, s>>>(d, tab); break;
     }
 }
 

@@ -115,6 +115,17 @@ std::vector<T> conv(const std::vector<double>& v) {
     return std::vector<T>(v.begin(), v.end());
 }
 
+template <typename T>
+std::vector<GEnt<T>> gaunt_entries(const std::vector<int>& idx, const std::vector<double>& val) {
+    std::vector<GEnt<T>> out(idx.size());
+    for (size_t k = 0; k < idx.size(); ++k) {
+        std::memset(&out[k], 0, sizeof(GEnt<T>));
+        out[k].pk = idx[k];
+        out[k].g = (T)val[k];
+    }
+    return out;
+}
+
 }  // namespace
 
 struct mix_ctx {
@@ -136,9 +147,9 @@ struct mix_ctx {
     int cap;
     // tables (offsets in the arena) and their element-type views
     Arena arena;
-    size_t o_c1, o_S2, o_W3, o_WT3, o_tau, o_goff, o_gidx, o_gval, o_ylmk, o_pair, o_sc2, o_sc3, o_wtoff, o_wtlist,
+    size_t o_c1, o_S2, o_W3, o_WT3, o_tau, o_goff, o_gent, o_ylmk, o_pair, o_sc2, o_sc3, o_wtoff, o_wtlist,
         o_tmode;
-    int ntau, np, nq;
+    int ntau, np, nq, qb;
     AceTab<double> ace64;
     AceTab<float> ace32;
     SplTab<double> spl64;
@@ -368,19 +379,30 @@ int build_tables(mix_ctx* c, const mix_ace* a, const mix_spline* sp) {
     std::sort(cost.begin(), cost.end(), [](const std::pair<double, int>& x, const std::pair<double, int>& y) {
         return x.first > y.first || (x.first == y.first && x.second < y.second);
     });
-    std::vector<std::vector<int>> per(ACE_WARPS);
-    std::vector<double> load(ACE_WARPS, 0.0);
+    const int warps = c->precision == MIX_FP64 ? ace_warps<double>() : ace_warps<float>();
+    std::vector<std::vector<int>> per(warps);
+    std::vector<double> load(warps, 0.0);
     for (auto& ct : cost) {
         int w = (int)(std::min_element(load.begin(), load.end()) - load.begin());
         per[w].push_back(ct.second);
         load[w] += ct.first;
     }
-    std::vector<int> wt_off(ACE_WARPS + 1, 0), wt_list;
-    for (int w = 0; w < ACE_WARPS; ++w) {
+    std::vector<int> wt_off(warps + 1, 0), wt_list;
+    for (int w = 0; w < warps; ++w) {
         wt_off[w] = (int)wt_list.size();
         for (int t : per[w]) wt_list.push_back(t);
     }
-    wt_off[ACE_WARPS] = (int)wt_list.size();
+    wt_off[warps] = (int)wt_list.size();
+    // q2 block of the U/Z pass: the largest block (4 float, 2 float64) or half
+    // of it, whichever fills the warp's lanes better over n * np / qb units
+    {
+        const int qm = c->precision == MIX_FP64 ? 2 : 4;
+        auto eff = [&](int qb) {
+            const int units = n * (np / qb);
+            return (double)units / (32.0 * ((units + 31) / 32));
+        };
+        c->qb = eff(qm / 2) > eff(qm) + 1e-12 ? qm / 2 : qm;
+    }
     std::vector<double> ylmk(nlm);
     for (int l = 0; l <= L; ++l)
         for (int m = -l; m <= l; ++m) ylmk[l * l + l + m] = ylm_norm(l, m);
@@ -395,7 +417,7 @@ int build_tables(mix_ctx* c, const mix_ace* a, const mix_spline* sp) {
         c->o_S2 = A.put(S2);
         c->o_W3 = A.put(W3p);
         c->o_WT3 = A.put(WT3);
-        c->o_gval = A.put(gval);
+        c->o_gent = A.put(gaunt_entries<double>(gidx, gval));
         c->o_ylmk = A.put(ylmk);
         c->o_pair = A.put(pair);
         c->o_sc2 = A.put(sc2);
@@ -405,7 +427,7 @@ int build_tables(mix_ctx* c, const mix_ace* a, const mix_spline* sp) {
         c->o_S2 = A.put(conv<float>(S2));
         c->o_W3 = A.put(conv<float>(W3p));
         c->o_WT3 = A.put(conv<float>(WT3));
-        c->o_gval = A.put(conv<float>(gval));
+        c->o_gent = A.put(gaunt_entries<float>(gidx, gval));
         c->o_ylmk = A.put(conv<float>(ylmk));
         c->o_pair = A.put(conv<float>(pair));
         c->o_sc2 = A.put(conv<float>(sc2));
@@ -413,7 +435,6 @@ int build_tables(mix_ctx* c, const mix_ace* a, const mix_spline* sp) {
     }
     c->o_tau = A.put(tau);
     c->o_goff = A.put(goff);
-    c->o_gidx = A.put(gidx);
     c->o_wtoff = A.put(wt_off);
     c->o_wtlist = A.put(wt_list);
     c->o_tmode = A.put(tmode);
@@ -440,8 +461,8 @@ void fill_tabs(mix_ctx* c, unsigned char* base, AceTab<T>& at, SplTab<T>& st) {
     at.tmode = reinterpret_cast<const int*>(base + c->o_tmode);
     at.tau = reinterpret_cast<const int*>(base + c->o_tau);
     at.goff = reinterpret_cast<const int*>(base + c->o_goff);
-    at.gidx = reinterpret_cast<const int*>(base + c->o_gidx);
-    at.gval = reinterpret_cast<const T*>(base + c->o_gval);
+    at.gent = reinterpret_cast<const GEnt<T>*>(base + c->o_gent);
+    at.qb = c->qb;
     at.ylmk = reinterpret_cast<const T*>(base + c->o_ylmk);
     at.pair = reinterpret_cast<const T*>(base + c->o_pair);
     at.has_pair = c->has_pair ? 1 : 0;
@@ -1023,7 +1044,7 @@ int mix_get_info(const mix_ctx* c, mix_info* info) {
     info->workspace_bytes = c->ws_bytes;
     info->exp_smem_bytes = c->ace_smem;
     info->exp_grid = c->ace_grid;
-    info->exp_threads = 128;
+    info->exp_threads = 32 * (c->precision == MIX_FP64 ? ace_warps<double>() : ace_warps<float>());
     info->cheap_smem_bytes = c->spl_smem;
     info->cheap_grid = c->spl_grid;
     info->launches_per_evaluation = evals_launches(c);

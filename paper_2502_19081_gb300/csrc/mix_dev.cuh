@@ -135,27 +135,45 @@ template <> struct Vec4<double> { using type = double4; };
 template <> struct Vec4<float> { using type = float4; };
 
 // Expensive-potential tables in the workspace (element type T).
-constexpr int ACE_WARPS = 4;        // warps per CTA of the expensive kernel
+// Warps per CTA of the expensive kernel (both element types), and the CTAs per
+// SM the float kernel is compiled for: 5 x 4 warps (registers capped at 102 a
+// thread, shared memory ~43 KB a CTA) measured faster than 2 x 8 or 4 x 4.
+template <typename T>
+__host__ __device__ constexpr int ace_warps() {
+    return 4;
+}
+template <typename T>
+__host__ __device__ constexpr int ace_min_ctas() {
+    return sizeof(T) == 4 ? 5 : 1;
+}
+
+// One Gaunt coefficient with the packed m indices of its two other factors
+// (ma | mb << 8, 0-based), loaded as one 8- or 16-byte word.
+template <typename T>
+struct __align__(sizeof(T) == 4 ? 8 : 16) GEnt {
+    int pk;
+    T g;
+};
 
 template <typename T>
 struct AceTab {
     int n, L, nu, nlm, ntau;
     int np;             // n rounded up to a multiple of 4 (row length of padded tables)
     int nq;             // n*n rounded up to a multiple of 4
+    int qb;             // q2 block per lane in the nu = 3 U/Z pass (divides np)
     double rc;
     const T* c1;        // [n]
     const T* S2;        // [L+1][n][n]  symmetric: W2 + W2^T, W2 upper-triangular c2
     const T* W3;        // [ntau][n*n][np]  masked nu=3 coefficients W[q1 q2][q3], zero padded
     const T* WT3;       // [ntau][n][nq]    the same, transposed: W[q3][q1 q2]
-    const int* wt_off;  // [ACE_WARPS + 1] ranges of wt_list handled by each warp
+    const int* wt_off;  // [warps + 1] ranges of wt_list handled by each warp
     const int* wt_list; // [ntau] l-triple indices grouped by warp
     const int* tmode;   // [ntau] 0: l's distinct, 1: l1 == l2, 2: l2 == l3, 3: all equal
                         // (W3 symmetrised over the matching n indices)
     const int* tau;     // [ntau][4]: l1, l2, l3, index of its first offset row
     const int* goff;    // offset rows: for each tau, three orderings (by m3, m1, m2),
                         // each 2l+2 entries (start index per m, then end)
-    const int* gidx;    // [nnz] packed (ma | mb << 8) of the two other m's (0-based)
-    const T* gval;      // [nnz]
+    const GEnt<T>* gent;  // [nnz] Gaunt coefficients in those orderings
     const T* ylmk;      // [nlm] normalisation of Y_lm times sqrt2 for m != 0
     const T* pair;      // [16] pair-term B-spline coefficients
     int has_pair;
