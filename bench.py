@@ -432,13 +432,30 @@ def batch_bench(args):
     b.sync()
     per = np.array([a.elapsed_time(c) for a, c in zip(e0, e1)])
     natoms = sum(wl.system.n for wl in wls)
+    binfo = b.info()
+    # the same batch stepped as one child graph per member, for comparison
+    b.set_fused(False)
+    b.step(1.0, 2)
+    torch.cuda.synchronize()
+    ch0, ch1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    nch = max(3, min(10, args.steps))
+    ch0.record(s)
+    b.step(1.0, nch)
+    ch1.record(s)
+    torch.cuda.synchronize()
+    child_ms = ch0.elapsed_time(ch1) / nch
+    b.set_fused(True)
     out = {"metric": METRIC, "value": natoms * args.steps / (per.sum() * 1e-3), "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(per.mean()),
            "p50_ms": float(np.percentile(per, 50)), "p99_ms": float(np.percentile(per, 99)),
            "higher_is_better": True, "dtype": "f32",
            "config": {"workload": "si_replicas_256", "n_atoms": natoms, "replicas": len(wls),
                       "potential_arithmetic": "f32", "integration": "f64", "grid_divisor": div,
+                      "step": "fused: one launch per kernel for all replicas" if binfo["fused"]
+                      else "one child graph per replica",
                       "l2": "working set > L2 (no flush)"},
+           "gpu_launches": binfo["launches"],
+           "child_graph_ms_per_step": child_ms,
            "clocks": clk}
     b.close()
     print(json.dumps(out), flush=True)

@@ -20,8 +20,9 @@
  *  - Ownership: positions, velocities, forces and the workspace are caller-owned
  *    device buffers that the library borrows from mix_bind() until the next
  *    mix_bind() or mix_destroy(); it never frees them.  Host arrays passed to
- *    mix_init() are copied.  The library itself allocates only host memory
- *    (plus pinned host memory for status reads).
+ *    mix_init() are copied.  A context allocates only host memory (plus pinned
+ *    host memory for status reads); a batch's fused step and the serving layer
+ *    allocate device memory of their own, described at their calls.
  *  - Layout: per-atom vectors are [N][4] float64 (x, y, z, unused), 32-byte rows,
  *    16-byte aligned or better.  Units: Angstrom, fs, eV, amu.
  *  - A context is not thread-safe; distinct contexts are independent.
@@ -339,6 +340,24 @@ int mix_batch_tune(mix_batch* b, int reps, int* chosen_divisor);
 
 int mix_batch_destroy(mix_batch* b);
 const char* mix_batch_last_error(const mix_batch* b);
+
+/* Fused step (default on): when every member uses one precision and geometric
+ * regions (mix_set_regions), a step is one launch per kernel for all members
+ * together -- blocks are assigned to members by tables built when the batch
+ * graph is (re)built, and the potentials walk flattened lists of every
+ * member's evaluated atoms -- instead of one child graph per member.  Results
+ * are identical either way.  The fused step allocates its own device arrays
+ * (member descriptors, block tables, work lists: about 16 bytes per atom plus
+ * 16 bytes per block) when its graph is built; mix_batch_destroy frees them.
+ * Members with seed-atom weights fall back to child graphs.  Launch shapes of
+ * the fused step do not use mix_batch_tune's divisor. */
+int mix_batch_set_fused(mix_batch* b, int fused);
+
+/* fused: 1 if the current step graph is the fused one; groups: kernel
+ * instantiation groups of the expensive potential (members sharing lmax and
+ * padded radial count); launches: kernels launched by fused steps so far.
+ * Each pointer nullable. */
+int mix_batch_info(const mix_batch* b, int* fused, int* groups, int64_t* launches);
 
 /* ------------------------------------------------------------------------ */
 /* Serving: many independent mixed-MD trajectories (requests) arriving over  */

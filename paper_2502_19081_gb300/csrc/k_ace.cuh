@@ -25,7 +25,8 @@
 //   6. pair gradients dE_i/dr_ij = u sum_lm sigma_lm Y_lm
 //        + (grad_u p - u (u . grad_u p)) / r,  rho = omega R, sigma = omega R',
 //      R, R', Y recomputed per neighbour in registers, the lm sum split over
-//      pairs of warps; written per list slot.
+//      pairs of warps; written per list slot, to the atom's own row and to the
+//      partner's incoming row (slot rev, stamped with the evaluation count).
 // Per-atom arrays are stored transposed ([lm][q], q padded to NP = 4k with
 // zeros) so that the inner products run over 4-wide vector loads with no index
 // division.  Site energy partial sums are kept in T per thread and reduced in
@@ -314,8 +315,10 @@ __device__ __forceinline__ void nu3_uz(const T* __restrict__ W, const T* A1, con
     }
 }
 
+// One evaluated atom (index a of the system's expensive list), by the whole CTA.
 template <typename T, int L, int NP>
-__global__ void __launch_bounds__(ace_warps<T>() * 32, ace_min_ctas<T>()) k_ace(Dev d, AceTab<T> tab) {
+__device__ __forceinline__ void ace_atom(const Dev& d, const AceTab<T>& tab, int a, unsigned char* smem_raw,
+                                         int* s_slot, int* s_wcnt, double* s_red) {
     constexpr int WN = ace_warps<T>();
     constexpr int NT = WN * 32;
     constexpr int NLM = (L + 1) * (L + 1);
@@ -324,11 +327,6 @@ __global__ void __launch_bounds__(ace_warps<T>() * 32, ace_min_ctas<T>()) k_ace(
     constexpr int QM = sizeof(T) == 4 ? 4 : 2;     // largest q2 block of the U/Z pass
     constexpr int PER = 16 * WN;                   // neighbours per gradient pass
     using V = typename Vec4<T>::type;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int s_slot[MAX_CAP];
-    __shared__ int s_wcnt[WN];
-    __shared__ double s_red[WN];
-
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int n = tab.n, nq = tab.nq, cap = d.cap;
     const AceSmem lay(cap, n, nq, L, NP, WN);
@@ -344,20 +342,20 @@ __global__ void __launch_bounds__(ace_warps<T>() * 32, ace_min_ctas<T>()) k_ace(
     T* omw = ZT + D * nq;
 
     V* GE = reinterpret_cast<V*>(d.ge);
+    V* GIN = reinterpret_cast<V*>(d.ge_in);
+    const int stamp = d.status[SW_EPOCH];
     const T rc2 = (T)d.rce2;
     const T rc = (T)tab.rc;
     const T invrc = T(1) / rc;
     const T invh = T(13) / rc;
-    const int count = d.status[SW_NEXP];
     const unsigned lt = (1u << lane) - 1u;
-    __syncthreads();
-
-    for (int a = blockIdx.x; a < count; a += gridDim.x) {
+    {
         const int i = d.act_e[a];
         const PairFrame<T> pf(d, i);
         const int m = d.nnb[i];
         const int* row = d.nbr + (int64_t)i * cap;
-        V* grow = GE + (int64_t)a * cap;
+        const int* rvr = d.rev + (int64_t)i * cap;
+        V* grow = GE + (int64_t)i * cap;
 
         // 1. neighbours inside the cutoff, ordered compaction
         int nb = 0;
@@ -372,6 +370,8 @@ __global__ void __launch_bounds__(ace_warps<T>() * 32, ace_min_ctas<T>()) k_ace(
                     V z;
                     z.x = z.y = z.z = z.w = T(0);
                     grow[s] = z;
+                    z.w = stamp_as(T(0), stamp);
+                    GIN[(int64_t)row[s] * cap + rvr[s]] = z;   // the partner's incoming row
                 }
             }
             const unsigned bal = __ballot_sync(0xffffffffu, ok);
@@ -645,14 +645,17 @@ __global__ void __launch_bounds__(ace_warps<T>() * 32, ace_min_ctas<T>()) k_ace(
                 gv.y = g[1];
                 gv.z = g[2];
                 gv.w = T(0);
-                grow[s_slot[kk]] = gv;
+                const int slot = s_slot[kk];
+                grow[slot] = gv;
+                gv.w = stamp_as(T(0), stamp);
+                GIN[(int64_t)row[slot] * cap + rvr[slot]] = gv;
             }
             __syncthreads();
         }
 
         // site energy (float64, fixed reduction order)
-        const double e = warp_sum_to_double(ep);   // fixed order; compensated for float
-        if (lane == 0) s_red[warp] = e;
+        const auto e = warp_sum(ep);   // fixed order; compensated for float
+        if (lane == 0) s_red[warp] = lane0_double(e);
         __syncthreads();
         if (tid == 0) {
             double es = 0.0;
@@ -660,6 +663,52 @@ __global__ void __launch_bounds__(ace_warps<T>() * 32, ace_min_ctas<T>()) k_ace(
             d.esite_e[i] = es;
         }
         __syncthreads();
+    }
+}
+
+template <typename T, int L, int NP>
+__global__ void __launch_bounds__(ace_warps<T>() * 32, ace_min_ctas<T>()) k_ace(Dev d, AceTab<T> tab) {
+    constexpr int WN = ace_warps<T>();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_slot[MAX_CAP];
+    __shared__ int s_wcnt[WN];
+    __shared__ double s_red[WN];
+    const int count = d.status[SW_NEXP];
+    for (int a = blockIdx.x; a < count; a += gridDim.x) ace_atom<T, L, NP>(d, tab, a, smem_raw, s_slot, s_wcnt, s_red);
+}
+
+// Many systems: walks the flattened list {system, index in its expensive list}
+// of one group of systems sharing (T, L, NP); the CTA reloads the system's Dev
+// and tables into shared memory when the system changes.
+template <typename T>
+struct AceBatch {
+    const Dev* devs;
+    const AceTab<T>* tabs;
+    const int2* list;
+    const int* count;
+};
+
+template <typename T, int L, int NP>
+__global__ void __launch_bounds__(ace_warps<T>() * 32, ace_min_ctas<T>()) kb_ace(AceBatch<T> b) {
+    constexpr int WN = ace_warps<T>();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_slot[MAX_CAP];
+    __shared__ int s_wcnt[WN];
+    __shared__ double s_red[WN];
+    __shared__ Dev s_dev;
+    __shared__ AceTab<T> s_tab;
+    const int count = *b.count;
+    int cur = -1;
+    for (int g = blockIdx.x; g < count; g += gridDim.x) {
+        const int2 e = b.list[g];
+        if (e.x != cur) {
+            __syncthreads();
+            load_dev(&s_dev, b.devs + e.x);
+            copy_shared(&s_tab, b.tabs + e.x);
+            __syncthreads();
+            cur = e.x;
+        }
+        ace_atom<T, L, NP>(s_dev, s_tab, e.y, smem_raw, s_slot, s_wcnt, s_red);
     }
 }
 
@@ -712,6 +761,66 @@ inline void ace_launch_l(const Dev& d, const AceTab<T>& tab, int L, size_t smem,
         case 5: k_ace<T, 5, NP><<<grid, ace_warps<T>() * 32, smem, s>>>(d, tab); break;
         case 6: k_ace<T, 6, NP><<<grid, ace_warps<T>() * 32, smem, s>>>(d, tab); break;
     }
+}
+
+// multi-system launches of one (T, L, NP) group
+template <typename T, int L, int NP>
+inline cudaError_t ace_batch_cfg(int n, int cap, size_t* smem, int* grid) {
+    const int nq = (n * n + 3) & ~3;
+    const AceSmem lay(cap, n, nq, L, NP, ace_warps<T>());
+    const size_t bytes = (size_t)lay.total * sizeof(T);
+    cudaError_t e = raise_smem_limit((const void*)kb_ace<T, L, NP>, bytes);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kb_ace<T, L, NP>, ace_warps<T>() * 32, bytes);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    *smem = bytes;
+    *grid = per_sm * sm_count();
+    return cudaSuccess;
+}
+
+template <typename T, int NP>
+inline cudaError_t ace_batch_cfg_l(int L, int n, int cap, size_t* smem, int* grid) {
+    switch (L) {
+        case 0: return ace_batch_cfg<T, 0, NP>(n, cap, smem, grid);
+        case 1: return ace_batch_cfg<T, 1, NP>(n, cap, smem, grid);
+        case 2: return ace_batch_cfg<T, 2, NP>(n, cap, smem, grid);
+        case 3: return ace_batch_cfg<T, 3, NP>(n, cap, smem, grid);
+        case 4: return ace_batch_cfg<T, 4, NP>(n, cap, smem, grid);
+        case 5: return ace_batch_cfg<T, 5, NP>(n, cap, smem, grid);
+        case 6: return ace_batch_cfg<T, 6, NP>(n, cap, smem, grid);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+inline cudaError_t ace_batch_cfg_t(int L, int n, int cap, size_t* smem, int* grid) {
+    if (n <= 4) return ace_batch_cfg_l<T, 4>(L, n, cap, smem, grid);
+    if (n <= 8) return ace_batch_cfg_l<T, 8>(L, n, cap, smem, grid);
+    if (n <= 12) return ace_batch_cfg_l<T, 12>(L, n, cap, smem, grid);
+    return ace_batch_cfg_l<T, 16>(L, n, cap, smem, grid);
+}
+
+template <typename T, int NP>
+inline void ace_batch_launch_l(const AceBatch<T>& b, int L, size_t smem, int grid, cudaStream_t s) {
+    switch (L) {
+        case 0: kb_ace<T, 0, NP><<<grid, ace_warps<T>() * 32, smem, s>>>(b); break;
+        case 1: kb_ace<T, 1, NP><<<grid, ace_warps<T>() * 32, smem, s>>>(b); break;
+        case 2: kb_ace<T, 2, NP><<<grid, ace_warps<T>() * 32, smem, s>>>(b); break;
+        case 3: kb_ace<T, 3, NP><<<grid, ace_warps<T>() * 32, smem, s>>>(b); break;
+        case 4: kb_ace<T, 4, NP><<<grid, ace_warps<T>() * 32, smem, s>>>(b); break;
+        case 5: kb_ace<T, 5, NP><<<grid, ace_warps<T>() * 32, smem, s>>>(b); break;
+        case 6: kb_ace<T, 6, NP><<<grid, ace_warps<T>() * 32, smem, s>>>(b); break;
+    }
+}
+
+template <typename T>
+inline void ace_batch_launch_t(const AceBatch<T>& b, int n, int L, size_t smem, int grid, cudaStream_t s) {
+    if (n <= 4) ace_batch_launch_l<T, 4>(b, L, smem, grid, s);
+    else if (n <= 8) ace_batch_launch_l<T, 8>(b, L, smem, grid, s);
+    else if (n <= 12) ace_batch_launch_l<T, 12>(b, L, smem, grid, s);
+    else ace_batch_launch_l<T, 16>(b, L, smem, grid, s);
 }
 
 template <typename T>

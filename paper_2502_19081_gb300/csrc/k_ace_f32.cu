@@ -12,4 +12,14 @@ void launch_ace_f32(const Dev& d, const void* tab, int L, size_t smem, int grid,
     ace_launch_t<float>(d, *static_cast<const AceTab<float>*>(tab), L, smem, grid, s);
 }
 
+cudaError_t ace_batch_configure_f32(int L, int n, int cap, size_t* smem, int* grid) {
+    return ace_batch_cfg_t<float>(L, n, cap, smem, grid);
+}
+
+void launch_ace_batch_f32(const Dev* devs, const void* tabs, const int2* list, const int* count, int n, int L,
+                          size_t smem, int grid, cudaStream_t s) {
+    AceBatch<float> b{devs, static_cast<const AceTab<float>*>(tabs), list, count};
+    ace_batch_launch_t<float>(b, n, L, smem, grid, s);
+}
+
 }  // namespace mixd

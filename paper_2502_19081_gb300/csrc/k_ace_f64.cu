@@ -12,6 +12,16 @@ void launch_ace_f64(const Dev& d, const void* tab, int L, size_t smem, int grid,
     ace_launch_t<double>(d, *static_cast<const AceTab<double>*>(tab), L, smem, grid, s);
 }
 
+cudaError_t ace_batch_configure_f64(int L, int n, int cap, size_t* smem, int* grid) {
+    return ace_batch_cfg_t<double>(L, n, cap, smem, grid);
+}
+
+void launch_ace_batch_f64(const Dev* devs, const void* tabs, const int2* list, const int* count, int n, int L,
+                          size_t smem, int grid, cudaStream_t s) {
+    AceBatch<double> b{devs, static_cast<const AceTab<double>*>(tabs), list, count};
+    ace_batch_launch_t<double>(b, n, L, smem, grid, s);
+}
+
 cudaError_t ace_configure(int precision, int L, int n, int cap, size_t* smem, int* grid) {
     if (cap > MAX_CAP || n > 16) return cudaErrorInvalidValue;
     return precision == MIX_FP64 ? ace_configure_f64(L, n, cap, smem, grid) : ace_configure_f32(L, n, cap, smem, grid);
@@ -20,6 +30,22 @@ cudaError_t ace_configure(int precision, int L, int n, int cap, size_t* smem, in
 void launch_ace(const Dev& d, const void* tab, int precision, int L, size_t smem, int grid, cudaStream_t s) {
     if (precision == MIX_FP64) launch_ace_f64(d, tab, L, smem, grid, s);
     else launch_ace_f32(d, tab, L, smem, grid, s);
+}
+
+}  // namespace mixd
+
+namespace mixd {
+
+cudaError_t ace_batch_configure(int precision, int L, int n, int cap, size_t* smem, int* grid) {
+    if (cap > MAX_CAP || n > 16) return cudaErrorInvalidValue;
+    return precision == MIX_FP64 ? ace_batch_configure_f64(L, n, cap, smem, grid)
+                                 : ace_batch_configure_f32(L, n, cap, smem, grid);
+}
+
+void launch_ace_batch(int precision, const Dev* devs, const void* tabs, const int2* list, const int* count, int n,
+                      int L, size_t smem, int grid, cudaStream_t s) {
+    if (precision == MIX_FP64) launch_ace_batch_f64(devs, tabs, list, count, n, L, smem, grid, s);
+    else launch_ace_batch_f32(devs, tabs, list, count, n, L, smem, grid, s);
 }
 
 }  // namespace mixd

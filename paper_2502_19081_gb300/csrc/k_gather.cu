@@ -1,9 +1,11 @@
 // Force assembly and blend (Alg. 4) without atomics, fused with the second
 // half of velocity Verlet.
 //
-// With g^p_ij = dE^p_i / dr_ij stored per list slot by the potential kernels,
-// the force of potential p on atom k restricted to its evaluated set A_p is
+// With g^p_ij = dE^p_i / dr_ij stored per list slot by the potential kernels
+// (in atom i's own row, and in atom j's incoming row at the slot of i), the
+// force of potential p on atom k restricted to its evaluated set A_p is
 //   Phi^p_k = [k in A_p] sum_j g^p_kj - sum_{i in N(k), i in A_p} g^p_{i, rev(k in i)},
+// two coalesced rows per potential and atom.
 // the site-energy derivative sum of Sec. 4.5.  Then
 //   F_k = w_k Phi^exp_k + (1 - w_k) Phi^cheap_k,
 // each term evaluated only where its weight is non-zero.  One warp per atom,
@@ -14,59 +16,94 @@ namespace mixd {
 
 constexpr int G_WARPS = 8;
 
+constexpr int G_ATOMS = 32;   // most atoms a warp gathers before finishing them lane-parallel
+
 template <typename T>
-__global__ void __launch_bounds__(G_WARPS * 32) k_gather(Dev d, int integrate, double h) {
+using GSum = decltype(warp_sum(T(0)));
+
+// A warp gathers ga <= G_ATOMS atoms one after another (lanes over list slots, float
+// or float64 sums per potential and component, compensated for float) and parks
+// the six lane-0 sums per atom in shared memory; then lane t finishes atom t in
+// float64 (blend, non-finite check, second half-kick).  The float64 pipe of this
+// part runs at 1/64 of the float rate, so one float64 instruction should serve
+// many atoms, not one; ga trades that against the number of warps a small
+// system can keep busy.
+template <typename T>
+__device__ __forceinline__ void gather_body(const Dev& d, int bx, int gx, int integrate, double h, int ga,
+                                            GSum<T>* park) {
     using V = typename Vec4<T>::type;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    GSum<T>* pk = park + warp * G_ATOMS * 6;
     const V* GE = reinterpret_cast<const V*>(d.ge);
     const V* GC = reinterpret_cast<const V*>(d.gc);
+    const V* GEI = reinterpret_cast<const V*>(d.ge_in);
+    const V* GCI = reinterpret_cast<const V*>(d.gc_in);
     const int cap = d.cap;
-    for (int64_t k = (int64_t)blockIdx.x * G_WARPS + warp; k < d.n; k += (int64_t)gridDim.x * G_WARPS) {
-        const double w = d.wgt[k];
-        const int m = d.nnb[k];
-        const int pe = d.pos_e[k], pc = d.pos_c[k];
-        const int* row = d.nbr + k * cap;
-        const int* rv = d.rev + k * cap;
-        // each lane sums its few slots in T; lanes are combined in float64 below
-        T tex = T(0), tey = T(0), tez = T(0), tcx = T(0), tcy = T(0), tcz = T(0);
-        for (int s = lane; s < m; s += 32) {
-            const int j = row[s];
-            const int r = rv[s];
-            if (w > 0.0) {
-                if (pe >= 0) {
-                    const V g = GE[(int64_t)pe * cap + s];
-                    tex += g.x;
-                    tey += g.y;
-                    tez += g.z;
+    const int stamp = d.status[SW_EPOCH];
+    const int64_t step = (int64_t)gx * G_WARPS * ga;
+    for (int64_t k0 = ((int64_t)bx * G_WARPS + warp) * ga; k0 < d.n; k0 += step) {
+        const int na = (int)(d.n - k0 < ga ? d.n - k0 : ga);
+        for (int a = 0; a < na; ++a) {
+            const int64_t k = k0 + a;
+            const int m = d.nnb[k];
+            const int fk = d.flags[k];
+            const bool own_e = (fk & 4) != 0, own_c = (fk & 8) != 0;
+            // w > 0 iff lambda > 0 and w < 1 iff lambda < 1 (flags bits 0, 1)
+            const bool use_e = (fk & 1) != 0, use_c = (fk & 2) != 0;
+            const int64_t base = k * cap;
+            // own row: dE_k/dr_kj; incoming row: dE_j/dr_jk, present when j was
+            // evaluated in this evaluation (its stamp is current)
+            T tex = T(0), tey = T(0), tez = T(0), tcx = T(0), tcy = T(0), tcz = T(0);
+            for (int s = lane; s < m; s += 32) {
+                if (use_e) {
+                    if (own_e) {
+                        const V g = GE[base + s];
+                        tex += g.x;
+                        tey += g.y;
+                        tez += g.z;
+                    }
+                    const V g = GEI[base + s];
+                    if (stamp_is(g.w, stamp)) {
+                        tex -= g.x;
+                        tey -= g.y;
+                        tez -= g.z;
+                    }
                 }
-                const int pj = d.pos_e[j];
-                if (pj >= 0) {
-                    const V g = GE[(int64_t)pj * cap + r];
-                    tex -= g.x;
-                    tey -= g.y;
-                    tez -= g.z;
+                if (use_c) {
+                    if (own_c) {
+                        const V g = GC[base + s];
+                        tcx += g.x;
+                        tcy += g.y;
+                        tcz += g.z;
+                    }
+                    const V g = GCI[base + s];
+                    if (stamp_is(g.w, stamp)) {
+                        tcx -= g.x;
+                        tcy -= g.y;
+                        tcz -= g.z;
+                    }
                 }
             }
-            if (w < 1.0) {
-                if (pc >= 0) {
-                    const V g = GC[(int64_t)pc * cap + s];
-                    tcx += g.x;
-                    tcy += g.y;
-                    tcz += g.z;
-                }
-                const int pj = d.pos_c[j];
-                if (pj >= 0) {
-                    const V g = GC[(int64_t)pj * cap + r];
-                    tcx -= g.x;
-                    tcy -= g.y;
-                    tcz -= g.z;
-                }
+            // lanes combined in a fixed order
+            const GSum<T> r0 = warp_sum(tex), r1 = warp_sum(tey), r2 = warp_sum(tez);
+            const GSum<T> r3 = warp_sum(tcx), r4 = warp_sum(tcy), r5 = warp_sum(tcz);
+            if (lane == 0) {
+                GSum<T>* q = pk + a * 6;
+                q[0] = r0;
+                q[1] = r1;
+                q[2] = r2;
+                q[3] = r3;
+                q[4] = r4;
+                q[5] = r5;
             }
         }
-        // lanes combined in a fixed order; float partials with a compensated sum
-        const double ex = warp_sum_to_double(tex), ey = warp_sum_to_double(tey), ez = warp_sum_to_double(tez);
-        const double cx = warp_sum_to_double(tcx), cy = warp_sum_to_double(tcy), cz = warp_sum_to_double(tcz);
-        if (lane == 0) {
+        __syncwarp();
+        if (lane < na) {
+            const int64_t k = k0 + lane;
+            const GSum<T>* q = pk + lane * 6;
+            const double ex = lane0_double(q[0]), ey = lane0_double(q[1]), ez = lane0_double(q[2]);
+            const double cx = lane0_double(q[3]), cy = lane0_double(q[4]), cz = lane0_double(q[5]);
+            const double w = d.wgt[k];
             const double wc = 1.0 - w;
             double4 F;
             F.x = (w > 0.0 ? w * ex : 0.0) + (wc > 0.0 ? wc * cx : 0.0);
@@ -83,17 +120,43 @@ __global__ void __launch_bounds__(G_WARPS * 32) k_gather(Dev d, int integrate, d
                 d.v[k] = v;
             }
         }
+        __syncwarp();
     }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(G_WARPS * 32) k_gather(Dev d, int integrate, double h, int ga) {
+    __shared__ GSum<T> park[G_WARPS * G_ATOMS * 6];
+    gather_body<T>(d, blockIdx.x, gridDim.x, integrate, h, ga, park);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(G_WARPS * 32) kb_gather(BatchArgs ba, int integrate, double dt) {
+    __shared__ GSum<T> park[G_WARPS * G_ATOMS * 6];
+    MIX_BATCH_BLOCK(ba)
+    gather_body<T>(s_dev, s_ent.y, s_ent.z, integrate, half_kick(dt, s_dev.mass), G_ATOMS, park);
+}
+
+void launch_gather_batch(const BatchPlan& p, int precision, int integrate, double dt, cudaStream_t s) {
+    if (precision == MIX_FP64)
+        kb_gather<double><<<p.nblk[BT_GATHER], G_WARPS * 32, 0, s>>>(p.ba[BT_GATHER], integrate, dt);
+    else
+        kb_gather<float><<<p.nblk[BT_GATHER], G_WARPS * 32, 0, s>>>(p.ba[BT_GATHER], integrate, dt);
+}
+
 void launch_gather(const Dev& d, int precision, int integrate, double h, cudaStream_t s) {
-    int64_t want = (d.n + G_WARPS - 1) / G_WARPS;
+    // atoms per warp: enough warps for about half occupancy, at most G_ATOMS
+    const int64_t warps_wanted = (int64_t)sm_count() * 32;
+    int ga = (int)((d.n + warps_wanted - 1) / warps_wanted);
+    ga = ga < 1 ? 1 : (ga > G_ATOMS ? G_ATOMS : ga);
+    const int64_t per_block = (int64_t)G_WARPS * ga;
+    int64_t want = (d.n + per_block - 1) / per_block;
     int64_t lim = d.grid_gather > 0 ? d.grid_gather : (int64_t)sm_count() * 8;
     const int grid = (int)(want < lim ? want : lim);
     if (precision == MIX_FP64)
-        k_gather<double><<<grid > 0 ? grid : 1, G_WARPS * 32, 0, s>>>(d, integrate, h);
+        k_gather<double><<<grid > 0 ? grid : 1, G_WARPS * 32, 0, s>>>(d, integrate, h, ga);
     else
-        k_gather<float><<<grid > 0 ? grid : 1, G_WARPS * 32, 0, s>>>(d, integrate, h);
+        k_gather<float><<<grid > 0 ? grid : 1, G_WARPS * 32, 0, s>>>(d, integrate, h, ga);
 }
 
 }  // namespace mixd

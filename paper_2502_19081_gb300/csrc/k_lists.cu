@@ -16,54 +16,60 @@
 namespace mixd {
 
 // v += h F; x += dt v (when integrating); then flag a rebuild if any atom moved
-// more than skin/2 since the last build.  Block 0 resets the per-evaluation
-// counters.
-__global__ void k_disp(Dev d, int integrate, double dt, double h, int force_rebuild) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i == 0) {
-        d.status[SW_NCORE] = 0;
-        d.status[SW_NRAMP] = 0;
-        d.status[SW_NLE] = 0;
-        d.status[SW_NLC] = 0;
-        if (force_rebuild) d.status[SW_REBUILD] = 1;
-    }
-    if (i >= d.n) return;
-    double4 x = d.x[i];
-    if (integrate) {
-        double4 v = d.v[i];
-        const double4 f = d.f[i];
-        v.x = __dadd_rn(v.x, __dmul_rn(h, f.x));
-        v.y = __dadd_rn(v.y, __dmul_rn(h, f.y));
-        v.z = __dadd_rn(v.z, __dmul_rn(h, f.z));
-        x.x = __dadd_rn(x.x, __dmul_rn(dt, v.x));
-        x.y = __dadd_rn(x.y, __dmul_rn(dt, v.y));
-        x.z = __dadd_rn(x.z, __dmul_rn(dt, v.z));
-        d.v[i] = v;
-        d.x[i] = x;
-    }
-    const bool finite = isfinite(x.x) && isfinite(x.y) && isfinite(x.z);
-    if (!finite) {
-        set_status(d.status, ST_NONFINITE);
-        return;
-    }
-    const double xs[3] = {x.x, x.y, x.z};
-    for (int k = 0; k < 3; ++k)
-        if (!d.box.per[k] && (xs[k] < d.box.lo[k] || xs[k] >= d.box.lo[k] + d.box.L[k]))
-            set_status(d.status, ST_OUT_OF_BOX);
-    if (!force_rebuild) {
-        const double4 xb = d.xb[i];
-        const double dx = x.x - xb.x, dy = x.y - xb.y, dz = x.z - xb.z;
-        if (dx * dx + dy * dy + dz * dz > d.half_skin2) d.status[SW_REBUILD] = 1;
-        // relative to the cell of the last build (recomputed by k_cell_bin on rebuilds)
-        if (d.xr) d.xr[i] = cell_relative(d.box, d.cells, x, d.cell3[i]);
+// more than skin/2 since the last build.  Atom 0's thread resets the
+// per-evaluation counters.  (Bodies take the system d, this block's index bx
+// among the gx blocks working on d, and stride over d's atoms.)
+__device__ __forceinline__ void disp_body(const Dev& d, int bx, int gx, int integrate, double dt, double h,
+                                          int force_rebuild) {
+    const int64_t stride = (int64_t)gx * blockDim.x;
+    for (int64_t i = bx * (int64_t)blockDim.x + threadIdx.x;; i += stride) {
+        if (i == 0) {
+            d.status[SW_NCORE] = 0;
+            d.status[SW_NRAMP] = 0;
+            d.status[SW_NLE] = 0;
+            d.status[SW_NLC] = 0;
+            d.status[SW_EPOCH] += 1;
+            if (force_rebuild) d.status[SW_REBUILD] = 1;
+        }
+        if (i >= d.n) return;
+        double4 x = d.x[i];
+        if (integrate) {
+            double4 v = d.v[i];
+            const double4 f = d.f[i];
+            v.x = __dadd_rn(v.x, __dmul_rn(h, f.x));
+            v.y = __dadd_rn(v.y, __dmul_rn(h, f.y));
+            v.z = __dadd_rn(v.z, __dmul_rn(h, f.z));
+            x.x = __dadd_rn(x.x, __dmul_rn(dt, v.x));
+            x.y = __dadd_rn(x.y, __dmul_rn(dt, v.y));
+            x.z = __dadd_rn(x.z, __dmul_rn(dt, v.z));
+            d.v[i] = v;
+            d.x[i] = x;
+        }
+        const bool finite = isfinite(x.x) && isfinite(x.y) && isfinite(x.z);
+        if (!finite) {
+            set_status(d.status, ST_NONFINITE);
+            continue;
+        }
+        const double xs[3] = {x.x, x.y, x.z};
+        for (int k = 0; k < 3; ++k)
+            if (!d.box.per[k] && (xs[k] < d.box.lo[k] || xs[k] >= d.box.lo[k] + d.box.L[k]))
+                set_status(d.status, ST_OUT_OF_BOX);
+        if (!force_rebuild) {
+            const double4 xb = d.xb[i];
+            const double dx = x.x - xb.x, dy = x.y - xb.y, dz = x.z - xb.z;
+            if (dx * dx + dy * dy + dz * dz > d.half_skin2) d.status[SW_REBUILD] = 1;
+            // relative to the cell of the last build (recomputed by k_cell_bin on rebuilds)
+            if (d.xr) d.xr[i] = cell_relative(d.box, d.cells, x, d.cell3[i]);
+        }
     }
 }
 
+__global__ void k_disp(Dev d, int integrate, double dt, double h, int force_rebuild) {
+    disp_body(d, blockIdx.x, gridDim.x, integrate, dt, h, force_rebuild);
+}
+
 // Fold periodic coordinates into [0, L), bin into cells, count per cell.
-__global__ void k_cell_bin(Dev d) {
-    if (d.status[SW_REBUILD] == 0) return;
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= d.n) return;
+__device__ __forceinline__ void cell_bin_atom(const Dev& d, int64_t i) {
     double4 x = d.x[i];
     double xs[3] = {x.x, x.y, x.z};
     for (int k = 0; k < 3; ++k)
@@ -84,8 +90,15 @@ __global__ void k_cell_bin(Dev d) {
     atomicAdd(d.cell_count + c, 1);
 }
 
+__device__ __forceinline__ void cell_bin_body(const Dev& d, int bx, int gx) {
+    if (d.status[SW_REBUILD] == 0) return;
+    for (int64_t i = bx * (int64_t)blockDim.x + threadIdx.x; i < d.n; i += (int64_t)gx * blockDim.x)
+        cell_bin_atom(d, i);
+}
+__global__ void k_cell_bin(Dev d) { cell_bin_body(d, blockIdx.x, gridDim.x); }
+
 // Exclusive scan of the cell counts (one block), zeroing counts and fill slots.
-__global__ void k_cell_scan(Dev d) {
+__device__ __forceinline__ void cell_scan_body(const Dev& d) {
     if (d.status[SW_REBUILD] == 0) return;
     __shared__ int wsum[32];
     __shared__ int carry_s;
@@ -128,24 +141,31 @@ __global__ void k_cell_scan(Dev d) {
     }
     if (tid == 0) d.cell_start[nc] = carry_s;
 }
+__global__ void k_cell_scan(Dev d) { cell_scan_body(d); }
 
-__global__ void k_cell_fill(Dev d) {
+__device__ __forceinline__ void cell_fill_body(const Dev& d, int bx, int gx) {
     if (d.status[SW_REBUILD] == 0) return;
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= d.n) return;
-    const int c = d.cell_of[i];
-    const int slot = d.cell_start[c] + atomicAdd(d.cell_fill + c, 1);
-    d.cell_atoms[slot] = (int)i;
+    for (int64_t i = bx * (int64_t)blockDim.x + threadIdx.x; i < d.n; i += (int64_t)gx * blockDim.x) {
+        const int c = d.cell_of[i];
+        const int slot = d.cell_start[c] + atomicAdd(d.cell_fill + c, 1);
+        d.cell_atoms[slot] = (int)i;
+    }
 }
+__global__ void k_cell_fill(Dev d) { cell_fill_body(d, blockIdx.x, gridDim.x); }
 
 constexpr int NB_WARPS = 4;
 
 // One warp per atom: scan the 27-cell stencil (as up to 18 contiguous runs of
 // cells), keep r2 < rlist2 with a ballot compaction into shared memory, sort
 // the row ascending with a warp bitonic network, write it out.
-__global__ void __launch_bounds__(NB_WARPS * 32) k_neigh_build(Dev d, int capp2) {
+__device__ __forceinline__ int pow2_cap(int cap) {
+    int c = 32;
+    while (c < cap) c <<= 1;
+    return c;
+}
+
+__device__ __forceinline__ void neigh_build_body(const Dev& d, int bx, int gx, int capp2, int* sbuf) {
     if (d.status[SW_REBUILD] == 0) return;
-    extern __shared__ int sbuf[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int* buf = sbuf + warp * capp2;
     const unsigned lt = (1u << lane) - 1u;
@@ -156,7 +176,7 @@ __global__ void __launch_bounds__(NB_WARPS * 32) k_neigh_build(Dev d, int capp2)
     const float lo2 = (float)(d.rlist2 * (1.0 - 2e-4)), hi2 = (float)(d.rlist2 * (1.0 + 2e-4));
     const float Lf[3] = {(float)d.box.L[0], (float)d.box.L[1], (float)d.box.L[2]};
     const float iLf[3] = {(float)d.box.invL[0], (float)d.box.invL[1], (float)d.box.invL[2]};
-    for (int64_t i = (int64_t)blockIdx.x * NB_WARPS + warp; i < d.n; i += (int64_t)gridDim.x * NB_WARPS) {
+    for (int64_t i = (int64_t)bx * NB_WARPS + warp; i < d.n; i += (int64_t)gx * NB_WARPS) {
         const double4 xi = d.x[i];
         const float4 xif = d.xf[i];
         const int c = d.cell_of[i];
@@ -249,13 +269,15 @@ __global__ void __launch_bounds__(NB_WARPS * 32) k_neigh_build(Dev d, int capp2)
     }
 }
 
+__global__ void __launch_bounds__(NB_WARPS * 32) k_neigh_build(Dev d, int capp2) {
+    extern __shared__ int sbuf[];
+    neigh_build_body(d, blockIdx.x, gridDim.x, capp2, sbuf);
+}
+
 // rev[i][s] = position of i in the row of j = nbr[i][s] (binary search).
-__global__ void k_neigh_rev(Dev d) {
-    if (d.status[SW_REBUILD] == 0) return;
-    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+__device__ __forceinline__ void neigh_rev_slot(const Dev& d, int64_t idx) {
     const int64_t i = idx / d.cap;
     const int s = (int)(idx - i * d.cap);
-    if (i >= d.n) return;
     if (s >= d.nnb[i]) return;
     const int j = d.nbr[idx];
     const int* row = d.nbr + (int64_t)j * d.cap;
@@ -275,6 +297,43 @@ __global__ void k_neigh_rev(Dev d) {
         pos = 0;
     }
     d.rev[idx] = pos;
+}
+
+__device__ __forceinline__ void neigh_rev_body(const Dev& d, int bx, int gx) {
+    if (d.status[SW_REBUILD] == 0) return;
+    const int64_t tot = d.n * (int64_t)d.cap;
+    for (int64_t idx = bx * (int64_t)blockDim.x + threadIdx.x; idx < tot; idx += (int64_t)gx * blockDim.x)
+        neigh_rev_slot(d, idx);
+}
+__global__ void k_neigh_rev(Dev d) { neigh_rev_body(d, blockIdx.x, gridDim.x); }
+
+// ---------------------------------------------------------------------------
+// multi-system versions (one launch for all systems of a batch)
+
+__global__ void kb_disp(BatchArgs ba, int integrate, double dt, int force_rebuild) {
+    MIX_BATCH_BLOCK(ba)
+    disp_body(s_dev, s_ent.y, s_ent.z, integrate, dt, half_kick(dt, s_dev.mass), force_rebuild);
+}
+__global__ void kb_cell_bin(BatchArgs ba) {
+    MIX_BATCH_BLOCK_REBUILD(ba)
+    cell_bin_body(s_dev, s_ent.y, s_ent.z);
+}
+__global__ void kb_cell_scan(BatchArgs ba) {
+    MIX_BATCH_BLOCK_REBUILD(ba)
+    cell_scan_body(s_dev);
+}
+__global__ void kb_cell_fill(BatchArgs ba) {
+    MIX_BATCH_BLOCK_REBUILD(ba)
+    cell_fill_body(s_dev, s_ent.y, s_ent.z);
+}
+__global__ void __launch_bounds__(NB_WARPS * 32) kb_neigh_build(BatchArgs ba) {
+    extern __shared__ int sbuf[];
+    MIX_BATCH_BLOCK_REBUILD(ba)
+    neigh_build_body(s_dev, s_ent.y, s_ent.z, pow2_cap(s_dev.cap), sbuf);
+}
+__global__ void kb_neigh_rev(BatchArgs ba) {
+    MIX_BATCH_BLOCK_REBUILD(ba)
+    neigh_rev_body(s_dev, s_ent.y, s_ent.z);
 }
 
 static int g_sms = 0;
@@ -318,6 +377,18 @@ void launch_build(const Dev& d, cudaStream_t s) {
     const int64_t tot = d.n * (int64_t)d.cap;
     const int nr = (int)((tot + 255) / 256);
     k_neigh_rev<<<nr > 0 ? nr : 1, 256, 0, s>>>(d);
+}
+
+void launch_disp_batch(const BatchPlan& p, cudaStream_t s, int integrate, double dt, int force_rebuild) {
+    kb_disp<<<p.nblk[BT_ATOM], 256, 0, s>>>(p.ba[BT_ATOM], integrate, dt, force_rebuild);
+}
+
+void launch_build_batch(const BatchPlan& p, cudaStream_t s) {
+    kb_cell_bin<<<p.nblk[BT_ATOM], 256, 0, s>>>(p.ba[BT_ATOM]);
+    kb_cell_scan<<<p.nblk[BT_ONE], 1024, 0, s>>>(p.ba[BT_ONE]);
+    kb_cell_fill<<<p.nblk[BT_ATOM], 256, 0, s>>>(p.ba[BT_ATOM]);
+    kb_neigh_build<<<p.nblk[BT_NB], NB_WARPS * 32, NB_WARPS * p.capp2 * sizeof(int), s>>>(p.ba[BT_NB]);
+    kb_neigh_rev<<<p.nblk[BT_REV], 256, 0, s>>>(p.ba[BT_REV]);
 }
 
 }  // namespace mixd

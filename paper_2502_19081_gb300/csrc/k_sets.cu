@@ -12,13 +12,22 @@
 
 namespace mixd {
 
-__global__ void k_lambda(Dev d, Regions r) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i == 0 && d.status[SW_REBUILD]) {
-        d.status[SW_REBUILDS] += 1;
-        d.status[SW_REBUILD] = 0;
+__device__ __forceinline__ void lambda_atom(const Dev& d, const Regions& r, int64_t i);
+
+__device__ __forceinline__ void lambda_body(const Dev& d, const Regions& r, int bx, int gx) {
+    for (int64_t i = bx * (int64_t)blockDim.x + threadIdx.x;; i += (int64_t)gx * blockDim.x) {
+        if (i == 0 && d.status[SW_REBUILD]) {
+            d.status[SW_REBUILDS] += 1;
+            d.status[SW_REBUILD] = 0;
+        }
+        if (i >= d.n) return;
+        lambda_atom(d, r, i);
     }
-    if (i >= d.n) return;
+}
+
+__global__ void k_lambda(Dev d, Regions r) { lambda_body(d, r, blockIdx.x, gridDim.x); }
+
+__device__ __forceinline__ void lambda_atom(const Dev& d, const Regions& r, int64_t i) {
     const double4 x = d.x[i];
     double best = 0.0;
     for (int k = 0; k < r.n; ++k) {
@@ -165,9 +174,9 @@ __global__ void __launch_bounds__(SEED_WARPS * 32) k_blend(Dev d, SeedRule sr) {
 constexpr int BUF_WARPS = 8;
 
 // One warp per atom: buffer membership through the neighbour list.
-__global__ void __launch_bounds__(BUF_WARPS * 32) k_buffer(Dev d) {
+__device__ __forceinline__ void buffer_body(const Dev& d, int bx, int gx) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int64_t i = (int64_t)blockIdx.x * BUF_WARPS + warp; i < d.n; i += (int64_t)gridDim.x * BUF_WARPS) {
+    for (int64_t i = (int64_t)bx * BUF_WARPS + warp; i < d.n; i += (int64_t)gx * BUF_WARPS) {
         const int f = d.flags[i] & 3;
         const bool need_e = !(f & 1), need_c = !(f & 2);
         bool he = false, hc = false;
@@ -197,10 +206,11 @@ __global__ void __launch_bounds__(BUF_WARPS * 32) k_buffer(Dev d) {
         }
     }
 }
+__global__ void __launch_bounds__(BUF_WARPS * 32) k_buffer(Dev d) { buffer_body(d, blockIdx.x, gridDim.x); }
 
 // Per-block counts of the two evaluated sets (and of the diagnostic sets).
-__global__ void __launch_bounds__(SCAN_BLOCK) k_count(Dev d) {
-    const int64_t i = blockIdx.x * (int64_t)SCAN_BLOCK + threadIdx.x;
+__device__ __forceinline__ void count_body(const Dev& d, int bx) {
+    const int64_t i = bx * (int64_t)SCAN_BLOCK + threadIdx.x;
     int f = 0;
     double lam = 0.0;
     if (i < d.n) {
@@ -215,21 +225,22 @@ __global__ void __launch_bounds__(SCAN_BLOCK) k_count(Dev d) {
     const int nle = __syncthreads_count(in && (f & 1));
     const int nlc = __syncthreads_count(in && (f & 2));
     if (threadIdx.x == 0) {
-        d.blk_e[blockIdx.x] = ne;
-        d.blk_c[blockIdx.x] = ncheap;
+        d.blk_e[bx] = ne;
+        d.blk_c[bx] = ncheap;
         atomicAdd(d.status + SW_NCORE, ncore);
         atomicAdd(d.status + SW_NRAMP, nramp);
         atomicAdd(d.status + SW_NLE, nle);
         atomicAdd(d.status + SW_NLC, nlc);
     }
 }
+__global__ void __launch_bounds__(SCAN_BLOCK) k_count(Dev d) { count_body(d, blockIdx.x); }
 
 // Ordered compaction: act lists ascending, pos maps (-1 when not evaluated).
-__global__ void __launch_bounds__(SCAN_BLOCK) k_scatter(Dev d) {
+__device__ __forceinline__ void scatter_body(const Dev& d, int bx, int gx) {
     __shared__ int red_e[32], red_c[32];
     __shared__ int off_e_s, off_c_s;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int b = blockIdx.x;
+    const int b = bx;
     // offset of this block: sum of the counts of the blocks before it
     int se = 0, sc = 0;
     for (int k = tid; k < b; k += SCAN_BLOCK) {
@@ -281,7 +292,7 @@ __global__ void __launch_bounds__(SCAN_BLOCK) k_scatter(Dev d) {
         }
         red_e[lane] = ia - a;   // exclusive per-warp offsets
         red_c[lane] = ic2 - c;
-        if (lane == 31 && b == (int)gridDim.x - 1) {
+        if (lane == 31 && b == gx - 1) {
             d.status[SW_NEXP] = off_e_s + ia;
             d.status[SW_NCHEAP] = off_c_s + ic2;
         }
@@ -302,6 +313,69 @@ __global__ void __launch_bounds__(SCAN_BLOCK) k_scatter(Dev d) {
         } else {
             d.pos_c[i] = -1;
         }
+    }
+}
+__global__ void __launch_bounds__(SCAN_BLOCK) k_scatter(Dev d) { scatter_body(d, blockIdx.x, gridDim.x); }
+
+// ---------------------------------------------------------------------------
+// multi-system versions (geometric regions only)
+
+__global__ void kb_lambda(BatchArgs ba, const Regions* __restrict__ regions) {
+    MIX_BATCH_BLOCK(ba)
+    lambda_body(s_dev, regions[s_ent.x], s_ent.y, s_ent.z);
+}
+__global__ void __launch_bounds__(BUF_WARPS * 32) kb_buffer(BatchArgs ba) {
+    MIX_BATCH_BLOCK(ba)
+    buffer_body(s_dev, s_ent.y, s_ent.z);
+}
+__global__ void __launch_bounds__(SCAN_BLOCK) kb_count(BatchArgs ba) {
+    MIX_BATCH_BLOCK(ba)
+    count_body(s_dev, s_ent.y);
+}
+__global__ void __launch_bounds__(SCAN_BLOCK) kb_scatter(BatchArgs ba) {
+    MIX_BATCH_BLOCK(ba)
+    scatter_body(s_dev, s_ent.y, s_ent.z);
+}
+
+// Flattened lists of the evaluated atoms of every system: block s writes
+// {s, k} for k below its expensive (cheap) count at the sum of the counts of
+// the systems before it (within its expensive group; all systems for cheap).
+// The last system of a group writes the group's total; the last system the
+// cheap total.
+__global__ void kb_flatten(FlatArgs f) {
+    __shared__ int red[2][32];
+    const int s = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int g = f.egroup[s];
+    int oe = 0, oc = 0;
+    for (int t = tid; t < s; t += blockDim.x) {
+        const int* st = f.devs[t].status;
+        if (f.egroup[t] == g) oe += st[SW_NEXP];
+        oc += st[SW_NCHEAP];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        oe += __shfl_down_sync(0xffffffffu, oe, o);
+        oc += __shfl_down_sync(0xffffffffu, oc, o);
+    }
+    if (lane == 0) {
+        red[0][warp] = oe;
+        red[1][warp] = oc;
+    }
+    __syncthreads();
+    oe = 0;
+    oc = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        oe += red[0][w];
+        oc += red[1][w];
+    }
+    const int* st = f.devs[s].status;
+    const int ne = st[SW_NEXP], nc = st[SW_NCHEAP];
+    int2* le = f.list_e + f.ebase[g] + oe;
+    int2* lc = f.list_c + oc;
+    for (int k = tid; k < ne; k += blockDim.x) le[k] = make_int2(s, k);
+    for (int k = tid; k < nc; k += blockDim.x) lc[k] = make_int2(s, k);
+    if (tid == 0) {
+        if (f.elast[s]) f.counts[g] = oe + ne;
+        if (s == f.nsys - 1) f.counts[f.ngrp] = oc + nc;
     }
 }
 
@@ -325,6 +399,18 @@ void launch_sets(const Dev& d, const Regions& r, const SeedRule& sr, cudaStream_
     k_buffer<<<gb > 0 ? gb : 1, BUF_WARPS * 32, 0, s>>>(d);
     k_count<<<d.nblk, SCAN_BLOCK, 0, s>>>(d);
     k_scatter<<<d.nblk, SCAN_BLOCK, 0, s>>>(d);
+}
+
+}  // namespace mixd
+
+namespace mixd {
+
+void launch_sets_batch(const BatchPlan& p, cudaStream_t s) {
+    kb_lambda<<<p.nblk[BT_ATOM], 256, 0, s>>>(p.ba[BT_ATOM], p.regions);
+    kb_buffer<<<p.nblk[BT_WARP8], BUF_WARPS * 32, 0, s>>>(p.ba[BT_WARP8]);
+    kb_count<<<p.nblk[BT_SCAN], SCAN_BLOCK, 0, s>>>(p.ba[BT_SCAN]);
+    kb_scatter<<<p.nblk[BT_SCAN], SCAN_BLOCK, 0, s>>>(p.ba[BT_SCAN]);
+    kb_flatten<<<p.flat.nsys, 256, 0, s>>>(p.flat);
 }
 
 }  // namespace mixd

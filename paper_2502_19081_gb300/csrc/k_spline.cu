@@ -13,7 +13,6 @@
 namespace mixd {
 
 constexpr int SPL_WARPS = 4;
-constexpr int SPL_SLOTS = MAX_CAP / 32;     // list slots per lane
 constexpr int T3S = NB3MAX + 1;             // padded row stride of the pair tables
 
 __device__ __forceinline__ double tsqrt3(double x) { return sqrt(x); }
@@ -39,84 +38,81 @@ template <typename T>
 struct SplWarp {   // per-warp shared scratch
     int slot[NB3MAX];
     T v[NB3MAX][4];         // r_ij vector (x, y, z) and |r_ij|
+    T g2[NB3MAX][4];        // 2-body part of dE_i/dr_ij of the 3-body neighbours
     T al[NB3MAX * T3S];     // a_jk
     T cc[NB3MAX * T3S];     // c_jk (symmetric)
-    T g3[NB3MAX][4];
 };
 
+// One evaluated atom (index a of the system's cheap list), by one warp; the
+// coefficient tables c2s, c3s may sit in shared or global memory.
 template <typename T>
-__global__ void __launch_bounds__(SPL_WARPS * 32) k_spline(Dev d, SplTab<T> tab) {
+__device__ __forceinline__ void spline_atom(const Dev& d, const SplTab<T>& tab, int a, const T* c2s, const T* c3s,
+                                            SplWarp<T>& W) {
     using V = typename Vec4<T>::type;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* c3s = reinterpret_cast<T*>(smem_raw);                 // [512]
-    T* c2s = c3s + 512;                                       // [16]
-    SplWarp<T>* ws = reinterpret_cast<SplWarp<T>*>(c2s + 16);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    SplWarp<T>& W = ws[warp];
-    for (int k = threadIdx.x; k < 512; k += blockDim.x) c3s[k] = tab.c3[k];
-    if (threadIdx.x < 16) c2s[threadIdx.x] = tab.c2[threadIdx.x];
-    __syncthreads();
-
+    const int lane = threadIdx.x & 31;
     V* GC = reinterpret_cast<V*>(d.gc);
-    const T rc2 = (T)d.rcc2, rc32 = (T)(tab.rc3 * tab.rc3);
-    const T invh2 = (T)(13.0 / tab.rc);
-    const T invh3 = (T)(5.0 / tab.rc3);
-    const T invhc = (T)(5.0 / (2.0 * tab.rc3));
+    V* GIN = reinterpret_cast<V*>(d.gc_in);
+    const int stamp = d.status[SW_EPOCH];
+    const T rc2 = tab.rc2, rc32 = tab.rc32;
+    const T invh2 = tab.invh2, invh3 = tab.invh3, invhc = tab.invhc;
     const unsigned lt = (1u << lane) - 1u;
     const int cap = d.cap;
-    const int count = d.status[SW_NCHEAP];
-
-    for (int a = blockIdx.x * SPL_WARPS + warp; a < count; a += gridDim.x * SPL_WARPS) {
+    {
         const int i = d.act_c[a];
         const PairFrame<T> pf(d, i);
         const int m = d.nnb[i];
         const int* row = d.nbr + (int64_t)i * cap;
-        V* grow = GC + (int64_t)a * cap;
+        const int* rvr = d.rev + (int64_t)i * cap;
+        V* grow = GC + (int64_t)i * cap;
         T ep = T(0);
-        T g2[SPL_SLOTS][3];
-        int p3[SPL_SLOTS];
         int n3 = 0;
-#pragma unroll
-        for (int c = 0; c < SPL_SLOTS; ++c) {
+        // 2-body part; a slot without 3-body terms is final here (own row and the
+        // partner's incoming row); a 3-body slot waits in the warp's table
+        for (int c = 0; c * 32 < m; ++c) {
             const int s = c * 32 + lane;
-            g2[c][0] = g2[c][1] = g2[c][2] = T(0);
-            p3[c] = -1;
             bool is3 = false;
-            T dv3[3] = {T(0), T(0), T(0)}, r = T(0);
-            if (c * 32 < m) {
-                if (s < m) {
-                    T r2;
-                    pf.vec(d, row[s], dv3, r2);
-                    if (r2 < rc2) {
-                        r = sqrt(r2);
-                        T v, dv;
-                        int q;
-                        T b[4], db[4];
-                        bspline4<T>(r * invh2, 12, q, b, db);
-                        v = c2s[q] * b[0] + c2s[q + 1] * b[1] + c2s[q + 2] * b[2] + c2s[q + 3] * b[3];
-                        dv = (c2s[q] * db[0] + c2s[q + 1] * db[1] + c2s[q + 2] * db[2] + c2s[q + 3] * db[3]) * invh2;
-                        ep += T(0.5) * v;
-                        const T hp = T(0.5) * dv / r;
-                        g2[c][0] = hp * dv3[0];
-                        g2[c][1] = hp * dv3[1];
-                        g2[c][2] = hp * dv3[2];
-                        is3 = r2 < rc32;
-                    }
+            T dv3[3] = {T(0), T(0), T(0)}, r = T(0), g2[3] = {T(0), T(0), T(0)};
+            if (s < m) {
+                T r2;
+                pf.vec(d, row[s], dv3, r2);
+                if (r2 < rc2) {
+                    r = sqrt(r2);
+                    T v, dv;
+                    int q;
+                    T b[4], db[4];
+                    bspline4<T>(r * invh2, 12, q, b, db);
+                    v = c2s[q] * b[0] + c2s[q + 1] * b[1] + c2s[q + 2] * b[2] + c2s[q + 3] * b[3];
+                    dv = (c2s[q] * db[0] + c2s[q + 1] * db[1] + c2s[q + 2] * db[2] + c2s[q + 3] * db[3]) * invh2;
+                    ep += T(0.5) * v;
+                    const T hp = T(0.5) * dv / r;
+                    g2[0] = hp * dv3[0];
+                    g2[1] = hp * dv3[1];
+                    g2[2] = hp * dv3[2];
+                    is3 = r2 < rc32;
                 }
-                const unsigned bal = __ballot_sync(0xffffffffu, is3);
-                if (is3) {
-                    const int p = n3 + __popc(bal & lt);
-                    p3[c] = p;
-                    if (p < NB3MAX) {
-                        W.slot[p] = s;
-                        W.v[p][0] = dv3[0];
-                        W.v[p][1] = dv3[1];
-                        W.v[p][2] = dv3[2];
-                        W.v[p][3] = r;
-                    }
-                }
-                n3 += __popc(bal);
             }
+            const unsigned bal = __ballot_sync(0xffffffffu, is3);
+            const int p = is3 ? n3 + __popc(bal & lt) : -1;
+            if (is3 && p < NB3MAX) {
+                W.slot[p] = s;
+                W.v[p][0] = dv3[0];
+                W.v[p][1] = dv3[1];
+                W.v[p][2] = dv3[2];
+                W.v[p][3] = r;
+                W.g2[p][0] = g2[0];
+                W.g2[p][1] = g2[1];
+                W.g2[p][2] = g2[2];
+            } else if (s < m) {
+                V gv;
+                gv.x = g2[0];
+                gv.y = g2[1];
+                gv.z = g2[2];
+                gv.w = T(0);
+                grow[s] = gv;
+                gv.w = stamp_as(T(0), stamp);
+                GIN[(int64_t)row[s] * cap + rvr[s]] = gv;   // the partner's incoming row
+            }
+            n3 += __popc(bal);
         }
         if (n3 > NB3MAX) {
             if (lane == 0) {
@@ -164,6 +160,7 @@ __global__ void __launch_bounds__(SPL_WARPS * 32) k_spline(Dev d, SplTab<T> tab)
             W.cc[q * T3S + p] = c;
         }
         __syncwarp();
+        // 3-body slots: 2-body part plus the sum over the other 3-body neighbours
         if (lane < n3) {
             const int p = lane;
             T sa = T(0), cx = T(0), cy = T(0), cz = T(0), cs = T(0);
@@ -177,33 +174,81 @@ __global__ void __launch_bounds__(SPL_WARPS * 32) k_spline(Dev d, SplTab<T> tab)
                 cz += c * W.v[q][2];
             }
             const T ir = T(1) / W.v[p][3];
-            W.g3[p][0] = sa * W.v[p][0] * ir + cs * W.v[p][0] - cx;
-            W.g3[p][1] = sa * W.v[p][1] * ir + cs * W.v[p][1] - cy;
-            W.g3[p][2] = sa * W.v[p][2] * ir + cs * W.v[p][2] - cz;
+            V gv;
+            gv.x = W.g2[p][0] + (sa * W.v[p][0] * ir + cs * W.v[p][0] - cx);
+            gv.y = W.g2[p][1] + (sa * W.v[p][1] * ir + cs * W.v[p][1] - cy);
+            gv.z = W.g2[p][2] + (sa * W.v[p][2] * ir + cs * W.v[p][2] - cz);
+            gv.w = T(0);
+            const int s = W.slot[p];
+            grow[s] = gv;
+            gv.w = stamp_as(T(0), stamp);
+            GIN[(int64_t)row[s] * cap + rvr[s]] = gv;
         }
         __syncwarp();
-#pragma unroll
-        for (int c = 0; c < SPL_SLOTS; ++c) {
-            const int s = c * 32 + lane;
-            if (s < m) {
-                V gv;
-                gv.x = g2[c][0];
-                gv.y = g2[c][1];
-                gv.z = g2[c][2];
-                gv.w = T(0);
-                const int p = p3[c];
-                if (p >= 0 && p < NB3MAX) {
-                    gv.x += W.g3[p][0];
-                    gv.y += W.g3[p][1];
-                    gv.z += W.g3[p][2];
-                }
-                grow[s] = gv;
-            }
-        }
-        const double epart = warp_sum_to_double(ep);   // fixed order; compensated for float
-        if (lane == 0) d.esite_c[i] = epart;
+        const auto epart = warp_sum(ep);   // fixed order; compensated for float
+        if (lane == 0) d.esite_c[i] = lane0_double(epart);
         __syncwarp();
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(SPL_WARPS * 32) k_spline(Dev d, SplTab<T> tab) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* c3s = reinterpret_cast<T*>(smem_raw);                 // [512]
+    T* c2s = c3s + 512;                                       // [16]
+    SplWarp<T>* ws = reinterpret_cast<SplWarp<T>*>(c2s + 16);
+    const int warp = threadIdx.x >> 5;
+    for (int k = threadIdx.x; k < 512; k += blockDim.x) c3s[k] = tab.c3[k];
+    if (threadIdx.x < 16) c2s[threadIdx.x] = tab.c2[threadIdx.x];
+    __syncthreads();
+    const int count = d.status[SW_NCHEAP];
+    for (int a = blockIdx.x * SPL_WARPS + warp; a < count; a += gridDim.x * SPL_WARPS)
+        spline_atom<T>(d, tab, a, c2s, c3s, ws[warp]);
+}
+
+// Many systems: a warp per entry {system, index} of the flattened cheap list;
+// the system's parameters and coefficient tables are read through L1.
+template <typename T>
+__global__ void __launch_bounds__(SPL_WARPS * 32) kb_spline(const Dev* __restrict__ devs,
+                                                           const SplTab<T>* __restrict__ tabs,
+                                                           const int2* __restrict__ list, const int* count_p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SplWarp<T>* ws = reinterpret_cast<SplWarp<T>*>(smem_raw);
+    const int warp = threadIdx.x >> 5;
+    const int count = *count_p;
+    for (int g = blockIdx.x * SPL_WARPS + warp; g < count; g += gridDim.x * SPL_WARPS) {
+        const int2 e = list[g];
+        const SplTab<T>& tab = tabs[e.x];
+        spline_atom<T>(devs[e.x], tab, e.y, tab.c2, tab.c3, ws[warp]);
+    }
+}
+
+template <typename T>
+static cudaError_t spl_batch_cfg(size_t* smem, int* grid) {
+    const size_t bytes = SPL_WARPS * sizeof(SplWarp<T>);
+    cudaError_t e = raise_smem_limit((const void*)kb_spline<T>, bytes);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kb_spline<T>, SPL_WARPS * 32, bytes);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    *smem = bytes;
+    *grid = per_sm * sm_count();
+    return cudaSuccess;
+}
+
+cudaError_t spline_batch_configure(int precision, size_t* smem, int* grid) {
+    return precision == MIX_FP64 ? spl_batch_cfg<double>(smem, grid) : spl_batch_cfg<float>(smem, grid);
+}
+
+void launch_spline_batch(int precision, const Dev* devs, const void* tabs, const int2* list, const int* count,
+                         size_t smem, int grid, cudaStream_t s) {
+    if (precision == MIX_FP64)
+        kb_spline<double><<<grid, SPL_WARPS * 32, smem, s>>>(devs, static_cast<const SplTab<double>*>(tabs), list,
+                                                             count);
+    else
+        kb_spline<float><<<grid, SPL_WARPS * 32, smem, s>>>(devs, static_cast<const SplTab<float>*>(tabs), list,
+                                                            count);
 }
 
 template <typename T>

@@ -15,7 +15,6 @@ using namespace mixd;
 
 namespace {
 
-constexpr double KAPPA = 9.6485332e-3;   // (eV / Angstrom / amu) in Angstrom / fs^2
 // kernels per evaluation: displacement 1, lists 5, sets 4, expensive 1, cheap 1, gather 1
 // (13 with geometric regions; the seed-atom modes add one or two)
 constexpr int LAUNCHES_PER_EVAL = 13;
@@ -158,7 +157,7 @@ struct mix_ctx {
     size_t ws_bytes;
     size_t off_tab;
     size_t o_status, o_xb, o_xf, o_xr, o_cell3, o_cell_of, o_cell_count, o_cell_start, o_cell_fill, o_cell_atoms, o_nnb, o_nbr, o_rev,
-        o_lam, o_wgt, o_flags, o_act_e, o_act_c, o_pos_e, o_pos_c, o_blk_e, o_blk_c, o_ge, o_gc, o_ee, o_ec,
+        o_lam, o_wgt, o_flags, o_act_e, o_act_c, o_pos_e, o_pos_c, o_blk_e, o_blk_c, o_ge, o_gc, o_gei, o_gci, o_ee, o_ec,
         o_seed, o_core, o_zsum;
     size_t ace_smem, spl_smem;
     int ace_grid, spl_grid;
@@ -470,6 +469,11 @@ void fill_tabs(mix_ctx* c, unsigned char* base, AceTab<T>& at, SplTab<T>& st) {
     st.rc3 = c->spl_rc3;
     st.c2 = reinterpret_cast<const T*>(base + c->o_sc2);
     st.c3 = reinterpret_cast<const T*>(base + c->o_sc3);
+    st.rc2 = (T)(c->dev.rcc2);
+    st.rc32 = (T)(c->spl_rc3 * c->spl_rc3);
+    st.invh2 = (T)(13.0 / c->spl_rc);
+    st.invh3 = (T)(5.0 / c->spl_rc3);
+    st.invhc = (T)(5.0 / (2.0 * c->spl_rc3));
 }
 
 void layout(mix_ctx* c) {
@@ -505,6 +509,8 @@ void layout(mix_ctx* c) {
     c->o_blk_c = take((size_t)c->dev.nblk * 4);
     c->o_ge = take(N * cap * v4);
     c->o_gc = take(N * cap * v4);
+    c->o_gei = take(N * cap * v4);
+    c->o_gci = take(N * cap * v4);
     c->o_ee = take(N * 8);
     c->o_ec = take(N * 8);
     c->o_seed = take(N);
@@ -527,7 +533,7 @@ int evals_launches(const mix_ctx* c) { return LAUNCHES_PER_EVAL - 4 + sets_launc
 // (captured = true: the events become record nodes of the graph being captured)
 void enqueue_evaluation(mix_ctx* c, cudaStream_t s, int integrate, double dt, int force_rebuild, bool prof,
                         bool captured = false) {
-    const double h = 0.5 * dt * KAPPA / c->sys.mass;
+    const double h = half_kick(dt, c->sys.mass);
     const unsigned ef = captured ? cudaEventRecordExternal : cudaEventRecordDefault;
     if (prof) cudaEventRecordWithFlags(c->ev[0], s, ef);
     launch_disp(c->dev, s, integrate, dt, h, force_rebuild);
@@ -685,6 +691,7 @@ int mix_init(const mix_system* sys, const mix_ace* a, const mix_spline* sp, cons
     Dev& d = c->dev;
     std::memset(&d, 0, sizeof d);
     d.n = sys->n_atoms;
+    d.mass = sys->mass;
     double vol = 1.0;
     for (int k = 0; k < 3; ++k) {
         if (!(sys->box_len[k] > 0)) return bad("box");
@@ -809,6 +816,8 @@ int mix_bind(mix_ctx* c, double* x, double* v, double* f, void* ws) {
     d.blk_c = reinterpret_cast<int*>(w + c->o_blk_c);
     d.ge = w + c->o_ge;
     d.gc = w + c->o_gc;
+    d.ge_in = w + c->o_gei;
+    d.gc_in = w + c->o_gci;
     d.esite_e = reinterpret_cast<double*>(w + c->o_ee);
     d.esite_c = reinterpret_cast<double*>(w + c->o_ec);
     d.seed = reinterpret_cast<uint8_t*>(w + c->o_seed);
@@ -820,12 +829,16 @@ int mix_bind(mix_ctx* c, double* x, double* v, double* f, void* ws) {
     cudaError_t e = cudaMemsetAsync(d.status, 0, SW_COUNT * sizeof(int), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.cell_count, 0, (size_t)d.cells.ncell * 4, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.seed, 0, (size_t)d.n, c->stream);
+    // incoming rows carry the epoch of the evaluation that wrote them; zero is never current
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.ge_in, 0, c->o_gci - c->o_gei, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.gc_in, 0, c->o_gci - c->o_gei, c->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(tb, c->arena.bytes.data(), c->arena.bytes.size(), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "mix_bind");
     drop_graph(c);
     c->bound = true;
+    c->regions_version++;      // batches holding this context re-read its buffers
     c->need_build = true;
     c->forces_valid = false;
     c->steps = 0;
@@ -1230,6 +1243,25 @@ struct mix_batch {
     double dt = 0.0;
     int divisor = 1;
     std::string err;
+    // fused multi-system step: one launch per kernel for all members
+    int want_fused = 1;              // use it whenever the members allow
+    bool graph_fused = false;        // the current graph is the fused step
+    cudaStream_t cap_stream = nullptr;
+    unsigned char* dmem = nullptr;   // plan arrays (device)
+    BatchPlan plan{};
+    int precision = 0;
+    struct Group {
+        int L, n, cap;
+        size_t base, smem;
+        int grid;
+    };
+    std::vector<Group> groups;
+    const Dev* ddevs = nullptr;
+    const void* dace = nullptr;
+    const void* dspl = nullptr;
+    size_t spl_smem = 0;
+    int spl_grid = 0;
+    int64_t launches = 0;            // kernels launched by fused steps
 };
 
 namespace {
@@ -1273,6 +1305,193 @@ int batch_graph(mix_batch* b, int integrate, double dt, cudaGraph_t* graph, cuda
         return bfail(b, MIX_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
     }
     *graph = parent;
+    return MIX_OK;
+}
+
+// --- fused multi-system step ------------------------------------------------
+
+// The fused step needs one arithmetic for all members and the geometric form
+// of the weights (the seed-atom kernels have no batched version).
+bool fused_eligible(const mix_batch* b) {
+    if (!b->want_fused || b->m.empty()) return false;
+    for (const mix_ctx* c : b->m)
+        if (!c->bound || c->precision != b->m[0]->precision || c->seedrule.mode != 0) return false;
+    return true;
+}
+
+void fused_free(mix_batch* b) {
+    if (b->dmem) cudaFree(b->dmem);
+    b->dmem = nullptr;
+}
+
+// Host-built plan: per-system parameter arrays, one block table per launch
+// granularity, the expensive groups (systems sharing L and the padded radial
+// count) and the flattened work lists, all in one device allocation.
+int fused_build(mix_batch* b) {
+    const int ns = (int)b->m.size();
+    b->precision = b->m[0]->precision;
+    const bool f64 = b->precision == MIX_FP64;
+    std::vector<Dev> devs(ns);
+    std::vector<Regions> regs(ns);
+    for (int s = 0; s < ns; ++s) {
+        devs[s] = b->m[s]->dev;
+        regs[s] = b->m[s]->regions;
+    }
+    // expensive groups
+    auto npad = [](int n) { return n <= 4 ? 4 : n <= 8 ? 8 : n <= 12 ? 12 : 16; };
+    std::vector<int> egroup(ns), elast(ns, 0);
+    b->groups.clear();
+    std::vector<int64_t> gatoms;
+    for (int s = 0; s < ns; ++s) {
+        const mix_ctx* c = b->m[s];
+        int g = -1;
+        for (size_t k = 0; k < b->groups.size(); ++k)
+            if (b->groups[k].L == c->L && npad(b->groups[k].n) == npad(c->n)) g = (int)k;
+        if (g < 0) {
+            b->groups.push_back({c->L, c->n, c->cap, 0, 0, 0});
+            gatoms.push_back(0);
+            g = (int)b->groups.size() - 1;
+        }
+        b->groups[g].n = std::max(b->groups[g].n, c->n);
+        b->groups[g].cap = std::max(b->groups[g].cap, c->cap);
+        gatoms[g] += c->sys.n_atoms;
+        egroup[s] = g;
+    }
+    for (int s = 0; s < ns; ++s) {
+        bool last = true;
+        for (int t = s + 1; t < ns; ++t)
+            if (egroup[t] == egroup[s]) last = false;
+        elast[s] = last ? 1 : 0;
+    }
+    const int ng = (int)b->groups.size();
+    std::vector<int> ebase(ng);
+    int64_t tot = 0, acc = 0;
+    for (int g = 0; g < ng; ++g) {
+        ebase[g] = (int)acc;
+        b->groups[g].base = (size_t)acc;
+        acc += gatoms[g];
+    }
+    tot = acc;
+    if (tot > INT32_MAX / 2) return bfail(b, MIX_EINVAL, "batch too large for one fused step");
+    // block tables
+    std::vector<std::vector<int4>> tabs(BT_COUNT);
+    int capp2 = 32;
+    for (int s = 0; s < ns; ++s) {
+        const Dev& d = devs[s];
+        const int64_t n = d.n;
+        auto blocks = [](int64_t units, int64_t per) { return (int)std::max<int64_t>(1, (units + per - 1) / per); };
+        const int gx[BT_COUNT] = {blocks(n, 1024), 1, blocks(n, 32), blocks(n * (int64_t)d.cap, 2048),
+                                  blocks(n, 32), std::max(1, d.nblk), blocks(n, 256)};
+        for (int k = 0; k < BT_COUNT; ++k)
+            for (int bx = 0; bx < gx[k]; ++bx) tabs[k].push_back(make_int4(s, bx, gx[k], 0));
+        while (capp2 < d.cap) capp2 <<= 1;
+    }
+    // one device allocation for everything
+    const size_t tsz = f64 ? sizeof(AceTab<double>) : sizeof(AceTab<float>);
+    const size_t ssz = f64 ? sizeof(SplTab<double>) : sizeof(SplTab<float>);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = off;
+        off = align256(off + std::max<size_t>(bytes, 16));
+        return at;
+    };
+    const size_t o_devs = take(ns * sizeof(Dev)), o_regs = take(ns * sizeof(Regions)), o_ace = take(ns * tsz),
+                 o_spl = take(ns * ssz), o_eg = take(ns * 4), o_el = take(ns * 4), o_eb = take(ng * 4),
+                 o_cnt = take((ng + 1) * 4), o_le = take(tot * sizeof(int2)), o_lc = take(tot * sizeof(int2));
+    size_t o_tab[BT_COUNT];
+    for (int k = 0; k < BT_COUNT; ++k) o_tab[k] = take(tabs[k].size() * sizeof(int4));
+    fused_free(b);
+    cudaError_t e = cudaMalloc(&b->dmem, off);
+    if (e != cudaSuccess) {
+        b->dmem = nullptr;
+        return bfail(b, MIX_ENOMEM, std::string("fused batch arrays: ") + cudaGetErrorString(e));
+    }
+    std::vector<unsigned char> host(off, 0);
+    auto put = [&](size_t o, const void* src, size_t bytes) {
+        if (bytes) std::memcpy(host.data() + o, src, bytes);
+    };
+    put(o_devs, devs.data(), ns * sizeof(Dev));
+    put(o_regs, regs.data(), ns * sizeof(Regions));
+    for (int s = 0; s < ns; ++s) {
+        const mix_ctx* c = b->m[s];
+        if (f64) {
+            put(o_ace + s * tsz, &c->ace64, tsz);
+            put(o_spl + s * ssz, &c->spl64, ssz);
+        } else {
+            put(o_ace + s * tsz, &c->ace32, tsz);
+            put(o_spl + s * ssz, &c->spl32, ssz);
+        }
+    }
+    put(o_eg, egroup.data(), ns * 4);
+    put(o_el, elast.data(), ns * 4);
+    put(o_eb, ebase.data(), ng * 4);
+    for (int k = 0; k < BT_COUNT; ++k) put(o_tab[k], tabs[k].data(), tabs[k].size() * sizeof(int4));
+    e = cudaMemcpy(b->dmem, host.data(), off, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return bfail(b, MIX_ECUDA, std::string("fused batch upload: ") + cudaGetErrorString(e));
+    unsigned char* base = b->dmem;
+    BatchPlan& P = b->plan;
+    b->ddevs = reinterpret_cast<const Dev*>(base + o_devs);
+    b->dace = base + o_ace;
+    b->dspl = base + o_spl;
+    for (int k = 0; k < BT_COUNT; ++k) {
+        P.ba[k].devs = b->ddevs;
+        P.ba[k].tab = reinterpret_cast<const int4*>(base + o_tab[k]);
+        P.nblk[k] = (int)tabs[k].size();
+    }
+    P.regions = reinterpret_cast<const Regions*>(base + o_regs);
+    P.capp2 = capp2;
+    FlatArgs& F = P.flat;
+    F.devs = b->ddevs;
+    F.nsys = ns;
+    F.ngrp = ng;
+    F.egroup = reinterpret_cast<const int*>(base + o_eg);
+    F.elast = reinterpret_cast<const int*>(base + o_el);
+    F.ebase = reinterpret_cast<const int*>(base + o_eb);
+    F.list_e = reinterpret_cast<int2*>(base + o_le);
+    F.list_c = reinterpret_cast<int2*>(base + o_lc);
+    F.counts = reinterpret_cast<int*>(base + o_cnt);
+    // launch shapes of the potentials
+    for (mix_batch::Group& g : b->groups) {
+        e = ace_batch_configure(b->precision, g.L, g.n, g.cap, &g.smem, &g.grid);
+        if (e != cudaSuccess) return bfail(b, MIX_ECUDA, std::string("fused expensive kernel: ") + cudaGetErrorString(e));
+    }
+    e = spline_batch_configure(b->precision, &b->spl_smem, &b->spl_grid);
+    if (e != cudaSuccess) return bfail(b, MIX_ECUDA, std::string("fused cheap kernel: ") + cudaGetErrorString(e));
+    return MIX_OK;
+}
+
+int fused_launches(const mix_batch* b) { return 15 + (int)b->groups.size(); }
+
+// one fused step (or force evaluation) captured on the batch's private stream
+int fused_graph(mix_batch* b, int integrate, double dt, cudaGraph_t* graph, cudaGraphExec_t* exec) {
+    if (!b->cap_stream) {
+        cudaError_t e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return bfail(b, MIX_ECUDA, "capture stream");
+    }
+    cudaStream_t s = b->cap_stream;
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return bfail(b, MIX_ECUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e));
+    const BatchPlan& P = b->plan;
+    launch_disp_batch(P, s, integrate, dt, 0);
+    launch_build_batch(P, s);
+    launch_sets_batch(P, s);
+    for (size_t g = 0; g < b->groups.size(); ++g) {
+        const mix_batch::Group& G = b->groups[g];
+        launch_ace_batch(b->precision, b->ddevs, b->dace, P.flat.list_e + G.base, P.flat.counts + g, G.n, G.L, G.smem,
+                         G.grid, s);
+    }
+    launch_spline_batch(b->precision, b->ddevs, b->dspl, P.flat.list_c, P.flat.counts + b->groups.size(), b->spl_smem,
+                        b->spl_grid, s);
+    launch_gather_batch(P, b->precision, integrate, dt, s);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(s, &g);
+    if (e != cudaSuccess) return bfail(b, MIX_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(exec, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return bfail(b, MIX_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    }
+    *graph = g;
     return MIX_OK;
 }
 
@@ -1337,13 +1556,21 @@ int mix_batch_step(mix_batch* b, double dt, int nsteps) {
     if (nsteps < 0 || !(dt > 0) || !std::isfinite(dt)) return bfail(b, MIX_EINVAL, "dt / nsteps");
     int st = batch_prepare(b);
     if (st) return st;
-    bool stale = !b->exec || b->dt != dt;
+    const bool fused = fused_eligible(b);
+    bool stale = !b->exec || b->dt != dt || b->graph_fused != fused;
     for (size_t k = 0; k < b->m.size(); ++k)
         if (b->regions_seen[k] != b->m[k]->regions_version) stale = true;
     if (stale) {
         batch_drop(b);
-        st = batch_graph(b, 1, dt, &b->graph, &b->exec);
+        if (fused) {
+            // the plan snapshots the members' device descriptors: rebuilt with the graph
+            st = fused_build(b);
+            if (!st) st = fused_graph(b, 1, dt, &b->graph, &b->exec);
+        } else {
+            st = batch_graph(b, 1, dt, &b->graph, &b->exec);
+        }
         if (st) return st;
+        b->graph_fused = fused;
         b->dt = dt;
         for (size_t k = 0; k < b->m.size(); ++k) b->regions_seen[k] = b->m[k]->regions_version;
     }
@@ -1353,8 +1580,9 @@ int mix_batch_step(mix_batch* b, double dt, int nsteps) {
     }
     for (mix_ctx* c : b->m) {
         c->steps += nsteps;
-        c->launches += (int64_t)evals_launches(c) * nsteps;
+        if (!fused) c->launches += (int64_t)evals_launches(c) * nsteps;
     }
+    if (fused) b->launches += (int64_t)fused_launches(b) * nsteps;
     return MIX_OK;
 }
 
@@ -1427,7 +1655,23 @@ int mix_batch_destroy(mix_batch* b) {
     if (!b) return MIX_OK;
     if (b->stream) cudaStreamSynchronize(b->stream);
     batch_drop(b);
+    fused_free(b);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     delete b;
+    return MIX_OK;
+}
+
+int mix_batch_set_fused(mix_batch* b, int fused) {
+    if (!b) return MIX_EINVAL;
+    b->want_fused = fused ? 1 : 0;
+    return MIX_OK;
+}
+
+int mix_batch_info(const mix_batch* b, int* fused, int* groups, int64_t* launches) {
+    if (!b) return MIX_EINVAL;
+    if (fused) *fused = b->graph_fused ? 1 : 0;
+    if (groups) *groups = (int)b->groups.size();
+    if (launches) *launches = b->launches;
     return MIX_OK;
 }
 

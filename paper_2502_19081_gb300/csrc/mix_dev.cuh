@@ -32,6 +32,7 @@ enum StatusWord : int {
     SW_NB3MAX = 10,     // largest 3-body neighbour count seen
     SW_EVALS = 11,      // evaluations since the seed rule was set (coordination averaging)
     SW_NSEED = 12,      // number of seed atoms
+    SW_EPOCH = 13,      // force evaluations since binding (stamps the incoming gradient rows)
     SW_COUNT = 64,
 };
 
@@ -78,9 +79,18 @@ struct SeedRule {
 };
 
 // Pointers into the workspace plus scalar parameters, passed by value.
+constexpr double MIX_KAPPA = 9.6485332e-3;   // (eV / Angstrom / amu) in Angstrom / fs^2
+
+// half-kick factor of velocity Verlet, h = dt/2 kappa / m (one expression for
+// every caller, so single and batched steps round identically)
+__host__ __device__ __forceinline__ double half_kick(double dt, double mass) {
+    return 0.5 * dt * MIX_KAPPA / mass;
+}
+
 struct Dev {
     int64_t n;
     int cap;
+    double mass;         // amu
     Box box;
     Cells cells;
     double rlist2;       // (rc_max + skin)^2
@@ -116,8 +126,10 @@ struct Dev {
     int* pos_c;
     int* blk_e;
     int* blk_c;
-    void* ge;            // [N][cap] real4: dE_i/dr_ij of the expensive potential
+    void* ge;            // [N][cap] real4: dE_i/dr_ij of the expensive potential, row of atom i
     void* gc;            // [N][cap] real4: same for the cheap potential
+    void* ge_in;         // [N][cap] real4: row of atom j, slot rev: the partner's dE_i/dr_ij,
+    void* gc_in;         //   w = the evaluation (epoch) that wrote it; same for the cheap potential
     double* esite_e;
     double* esite_c;
     uint8_t* seed;       // [N] seed atoms (seed-atom weights)
@@ -129,6 +141,54 @@ struct Dev {
     int grid_buffer;     // CTAs of the buffer scan (8 warps each)
     int grid_gather;     // CTAs of the gather (8 warps each)
 };
+
+// ---------------------------------------------------------------------------
+// Multi-system launches (batches of independent systems).  A launch's blocks
+// are assigned to systems by a table of int4 {system, local block index,
+// local block count, 0}; every block works on one system and loads that
+// system's Dev into shared memory, so kernel bodies written for one system
+// (taking d, the local block index bx and the local grid size gx) run
+// unchanged.  Kernels whose work list is built on the device (the potentials)
+// instead walk a flattened list of {system, index in the system's list}.
+struct BatchArgs {
+    const Dev* devs;     // [nsys]
+    const int4* tab;     // block table of this launch
+};
+
+// block-wide copy of a parameter struct into shared memory (callers sync)
+template <typename S>
+__device__ __forceinline__ void copy_shared(S* dst, const S* src) {
+    static_assert(sizeof(S) % 8 == 0, "8-byte words");
+    const unsigned long long* a = reinterpret_cast<const unsigned long long*>(src);
+    unsigned long long* b = reinterpret_cast<unsigned long long*>(dst);
+    for (int k = threadIdx.x; k < (int)(sizeof(S) / 8); k += blockDim.x) b[k] = a[k];
+}
+
+__device__ __forceinline__ void load_dev(Dev* dst, const Dev* src) { copy_shared(dst, src); }
+
+// Opens a batched kernel: s_dev (the block's system), s_ent (its table entry).
+#define MIX_BATCH_BLOCK(ba)                                  \
+    __shared__ Dev s_dev;                                    \
+    __shared__ int4 s_ent;                                   \
+    if (threadIdx.x == 0) s_ent = (ba).tab[blockIdx.x];      \
+    __syncthreads();                                         \
+    load_dev(&s_dev, (ba).devs + s_ent.x);                   \
+    __syncthreads();
+
+// The same for kernels that only work on list rebuilds: the block returns
+// before loading anything when its system keeps its lists.
+#define MIX_BATCH_BLOCK_REBUILD(ba)                                       \
+    __shared__ Dev s_dev;                                                 \
+    __shared__ int4 s_ent;                                                \
+    __shared__ int s_go;                                                  \
+    if (threadIdx.x == 0) {                                               \
+        s_ent = (ba).tab[blockIdx.x];                                     \
+        s_go = (ba).devs[s_ent.x].status[SW_REBUILD];                     \
+    }                                                                     \
+    __syncthreads();                                                      \
+    if (s_go == 0) return;                                                \
+    load_dev(&s_dev, (ba).devs + s_ent.x);                                \
+    __syncthreads();
 
 template <typename T> struct Vec4;
 template <> struct Vec4<double> { using type = double4; };
@@ -184,6 +244,10 @@ struct SplTab {
     double rc, rc3;
     const T* c2;    // [16]
     const T* c3;    // [8][8][8]
+    // derived constants in T, formed on the host in float64 and rounded once
+    // (no float64 division per atom on the device)
+    T rc2, rc32;            // rc^2 (2-body), rc3^2
+    T invh2, invh3, invhc;  // 13/rc, 5/rc3, 5/(2 rc3)
 };
 
 // ---------------------------------------------------------------------------
@@ -220,11 +284,21 @@ __device__ __forceinline__ void set_status(int* st, int bits) { atomicOr(st + SW
 // float with a compensation term (Knuth's TwoSum at every step), so the float
 // path keeps double-like accuracy for the sum without float64 arithmetic per
 // lane (float64 runs at 1/62 of float on GB300).
-__device__ __forceinline__ double warp_sum_to_double(double v) {
+// The sum and its compensation stay in T through the shuffles; only lane 0's
+// result is meaningful, and callers convert it with lane0_double() inside a
+// lane-0 branch, so no warp-wide float64 instruction is issued (float64 is the
+// scarcest pipe on this part).
+struct WSum {
+    float s, c;
+};
+struct WSumD {
+    double s;
+};
+__device__ __forceinline__ WSumD warp_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
+    return {v};
 }
-__device__ __forceinline__ double warp_sum_to_double(float v) {
+__device__ __forceinline__ WSum warp_sum(float v) {
     float s = v, c = 0.f;
     for (int o = 16; o > 0; o >>= 1) {
         const float s2 = __shfl_down_sync(0xffffffffu, s, o);
@@ -235,8 +309,17 @@ __device__ __forceinline__ double warp_sum_to_double(float v) {
         s = t;
         c = __fadd_rn(__fadd_rn(c, c2), e);
     }
-    return (double)s + (double)c;
+    return {s, c};
 }
+__device__ __forceinline__ double lane0_double(WSumD w) { return w.s; }
+__device__ __forceinline__ double lane0_double(WSum w) { return (double)w.s + (double)w.c; }
+
+// Evaluation stamp in the w component of an incoming gradient row (the bits of
+// the integer epoch; a row counts only when its stamp is the current epoch).
+__device__ __forceinline__ float stamp_as(float, int e) { return __int_as_float(e); }
+__device__ __forceinline__ double stamp_as(double, int e) { return __longlong_as_double((long long)e); }
+__device__ __forceinline__ bool stamp_is(float w, int e) { return __float_as_int(w) == e; }
+__device__ __forceinline__ bool stamp_is(double w, int e) { return __double_as_longlong(w) == (long long)e; }
 
 // Pair vector for the potentials: the difference and minimum image in float64
 // (positions are absolute coordinates of up to hundreds of Angstrom), then

@@ -28,6 +28,58 @@ void launch_spline(const Dev& d, const void* tab, int precision, size_t smem, in
 // gather + blend + second half-kick (k_gather.cu)
 void launch_gather(const Dev& d, int precision, int integrate, double h, cudaStream_t s);
 
+// ---------------------------------------------------------------------------
+// multi-system step (batches of contexts sharing one stream)
+
+// Block-table classes: every batched launch uses the table of its granularity.
+enum BatchTabClass : int {
+    BT_ATOM = 0,   // 256 threads, a thread per atom (grid-stride)
+    BT_ONE,        // one block per system
+    BT_NB,         // 4 warps, a warp per atom (list build)
+    BT_REV,        // 256 threads, a thread per list slot (reverse map)
+    BT_WARP8,      // 8 warps, a warp per atom (buffer scan, gather)
+    BT_SCAN,       // SCAN_BLOCK atoms per block, the system's own block count
+    BT_GATHER,     // 8 warps of 32 atoms each (gather)
+    BT_COUNT
+};
+
+struct FlatArgs {
+    const Dev* devs;
+    int nsys;
+    int ngrp;
+    const int* egroup;   // [nsys] expensive group (systems sharing T, L, NP)
+    const int* elast;    // [nsys] 1 for the last system of its group
+    const int* ebase;    // [ngrp] start of each group in list_e
+    int2* list_e;        // {system, index in its expensive list}
+    int2* list_c;        // {system, index in its cheap list}
+    int* counts;         // [ngrp + 1] expensive totals per group, cheap total
+};
+
+struct BatchPlan {
+    BatchArgs ba[BT_COUNT];
+    int nblk[BT_COUNT];
+    const Regions* regions;   // [nsys]
+    int capp2;                // largest power-of-two list capacity (build scratch)
+    FlatArgs flat;
+};
+
+void launch_disp_batch(const BatchPlan& p, cudaStream_t s, int integrate, double dt, int force_rebuild);
+void launch_build_batch(const BatchPlan& p, cudaStream_t s);
+void launch_sets_batch(const BatchPlan& p, cudaStream_t s);
+cudaError_t ace_batch_configure(int precision, int L, int n, int cap, size_t* smem, int* grid);
+cudaError_t ace_batch_configure_f32(int L, int n, int cap, size_t* smem, int* grid);
+cudaError_t ace_batch_configure_f64(int L, int n, int cap, size_t* smem, int* grid);
+void launch_ace_batch(int precision, const Dev* devs, const void* tabs, const int2* list, const int* count, int n,
+                      int L, size_t smem, int grid, cudaStream_t s);
+void launch_ace_batch_f32(const Dev* devs, const void* tabs, const int2* list, const int* count, int n, int L,
+                          size_t smem, int grid, cudaStream_t s);
+void launch_ace_batch_f64(const Dev* devs, const void* tabs, const int2* list, const int* count, int n, int L,
+                          size_t smem, int grid, cudaStream_t s);
+cudaError_t spline_batch_configure(int precision, size_t* smem, int* grid);
+void launch_spline_batch(int precision, const Dev* devs, const void* tabs, const int2* list, const int* count,
+                         size_t smem, int grid, cudaStream_t s);
+void launch_gather_batch(const BatchPlan& p, int precision, int integrate, double dt, cudaStream_t s);
+
 int sm_count();
 
 // Raise (never lower) a kernel's dynamic shared-memory limit to `bytes`.  The

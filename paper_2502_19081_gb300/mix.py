@@ -44,7 +44,7 @@ EXPORTS = [
     "mix_fma_peak", "mix_tune", "mix_batch_create", "mix_batch_step", "mix_batch_sync", "mix_batch_tune",
     "mix_batch_destroy", "mix_batch_last_error", "mix_set_seeds", "mix_set_seed_rule", "mix_get_seeds",
     "mix_server_create", "mix_server_submit", "mix_server_tick", "mix_server_request", "mix_server_fetch",
-    "mix_server_destroy", "mix_server_last_error", "mix_admission_plan",
+    "mix_server_destroy", "mix_server_last_error", "mix_admission_plan", "mix_batch_set_fused", "mix_batch_info",
 ]
 
 MIX_PHASES = 6
@@ -189,6 +189,8 @@ def lib():
             L.mix_batch_sync.argtypes = [P]
             L.mix_batch_tune.argtypes = [P, ctypes.c_int, ip]
             L.mix_batch_destroy.argtypes = [P]
+            L.mix_batch_set_fused.argtypes = [P, ctypes.c_int]
+            L.mix_batch_info.argtypes = [P, ip, ip, i64p]
             L.mix_batch_last_error.restype = ctypes.c_char_p
             L.mix_batch_last_error.argtypes = [P]
             _lib = L
@@ -455,6 +457,19 @@ class Batch:
         out = ctypes.c_int()
         self._check(self.L.mix_batch_tune(self.h, int(reps), ctypes.byref(out)), "mix_batch_tune")
         return int(out.value)
+
+    def set_fused(self, on: bool = True):
+        """Fused step (one launch per kernel for all members) when the members
+        allow it (one precision, geometric regions); else one child graph per member."""
+        self._check(self.L.mix_batch_set_fused(self.h, 1 if on else 0), "mix_batch_set_fused")
+
+    def info(self) -> dict:
+        fused = ctypes.c_int()
+        groups = ctypes.c_int()
+        launches = ctypes.c_int64()
+        self._check(self.L.mix_batch_info(self.h, ctypes.byref(fused), ctypes.byref(groups), ctypes.byref(launches)),
+                    "mix_batch_info")
+        return {"fused": bool(fused.value), "groups": int(groups.value), "launches": int(launches.value)}
 
     def close(self):
         h = getattr(self, "h", None)

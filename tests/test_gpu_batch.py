@@ -29,7 +29,8 @@ def _replicas():
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-def test_batch_equals_members_alone(mx, prec):
+@pytest.mark.parametrize("fused", [True, False])
+def test_batch_equals_members_alone(mx, prec, fused):
     wls = _replicas()
     alone = []
     for wl in wls:
@@ -39,7 +40,9 @@ def test_batch_equals_members_alone(mx, prec):
         c.close()
     members = [mx.open_context(wl, precision=prec) for wl in wls]
     b = mx.Batch(members)
+    b.set_fused(fused)
     b.step(1.0, 8)
+    assert b.info()["fused"] == fused
     b.step(1.0, 12)
     b.sync()
     for c, (xa, va, fa, sa) in zip(members, alone):
@@ -92,3 +95,57 @@ def test_replica_forces_match_oracle(mx):
         x, _, F, _ = c.get_state()
         FB, _, _ = oracle.Model(wl).forces(x, oracle.MODE_METHOD)
         assert np.abs(F[:, :3] - FB[:, :3]).max() <= 1e-3
+
+
+def _mixed():
+    """Si and Fe cells: two groups of the expensive kernel, hot enough that
+    lists are rebuilt during the run."""
+    ace, spl = I.element_potentials("Si", np.random.default_rng(1), 5.0, 8, 3, 3)
+    out = [I.si_replica(70, 900, "vacancy", 1500.0, ace, spl), I.si_replica(71, 2000, "interstitial", 1200.0, ace, spl)]
+    for k, seed in enumerate((43, 44)):
+        wl = I.small_fe_box(seed, n_rad=5, l_max=4)
+        wl.system.v = I.maxwell_boltzmann(np.random.default_rng(seed), wl.system.n, wl.system.mass, 1500.0)
+        out.append(wl)
+    return out
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_fused_mixed_elements_with_rebuilds(mx, prec):
+    wls = _mixed()
+    alone = []
+    for wl in wls:
+        c = mx.open_context(wl, precision=prec)
+        c.step(1.0, 30)
+        alone.append((c.get_state(), c.stats()["rebuilds"]))
+        c.close()
+    members = [mx.open_context(wl, precision=prec) for wl in wls]
+    b = mx.Batch(members)
+    b.step(1.0, 11)
+    b.step(1.0, 19)
+    b.sync()
+    inf = b.info()
+    assert inf["fused"] and inf["groups"] == 2 and inf["launches"] > 0
+    for c, ((xa, va, fa, sa), ra) in zip(members, alone):
+        x, v, f, s = c.get_state()
+        assert s == sa == 30
+        assert c.stats()["rebuilds"] == ra
+        assert np.array_equal(x, xa) and np.array_equal(v, va) and np.array_equal(f, fa)
+    assert max(r for _, r in alone) > 2     # lists really were rebuilt along the way
+    b.close()
+
+
+def test_fused_batch_falls_back_for_seed_weights(mx):
+    wls = _mixed()[:2]
+    members = [mx.open_context(wl, precision=1) for wl in wls]
+    members[1].set_seeds([3, 4], 2.6, 3.5)
+    b = mx.Batch(members)
+    b.step(1.0, 5)
+    b.sync()
+    assert not b.info()["fused"]
+    a = mx.open_context(wls[1], precision=1)
+    a.set_seeds([3, 4], 2.6, 3.5)
+    a.step(1.0, 5)
+    xa, va, fa, _ = a.get_state()
+    x, v, f, _ = members[1].get_state()
+    assert np.array_equal(x, xa) and np.array_equal(f, fa)
+    b.close()
