@@ -30,6 +30,11 @@ __global__ void k_lambda(Dev d, Regions r) { lambda_body(d, r, blockIdx.x, gridD
 __device__ __forceinline__ void lambda_atom(const Dev& d, const Regions& r, int64_t i) {
     const double4 x = d.x[i];
     double best = 0.0;
+    // buffer-scan hints from the exact distances (triangle inequality, 1e-9 A
+    // margin): with every region farther than r_core + ramp + r_buffer_exp no
+    // neighbour closer than r_buffer_exp has lambda > 0 (bit 4); deeper than
+    // r_buffer_cheap inside some core no neighbour that close has lambda < 1 (bit 5)
+    bool far_e = true, deep_c = false;
     for (int k = 0; k < r.n; ++k) {
         const double* R = r.r[k];
         const double4 c = make_double4(R[1], R[2], R[3], 0.0);
@@ -43,6 +48,8 @@ __device__ __forceinline__ void lambda_atom(const Dev& d, const Regions& r, int6
         }
         const double dist = __dsqrt_rn(d2);
         const double rc = R[7], ramp = R[8];
+        if (!(dist >= rc + ramp + d.bufe + 1e-9)) far_e = false;
+        if (dist + d.bufc + 1e-9 <= rc) deep_c = true;
         double lr;
         if (dist < rc) lr = 1.0;
         else if (ramp > 0.0 && dist < __dadd_rn(rc, ramp)) lr = __dsub_rn(1.0, __ddiv_rn(__dsub_rn(dist, rc), ramp));
@@ -53,7 +60,7 @@ __device__ __forceinline__ void lambda_atom(const Dev& d, const Regions& r, int6
     double w = best;
     if (r.blend == MIX_BLEND_CUBIC) w = __dmul_rn(__dmul_rn(best, best), __dsub_rn(3.0, __dmul_rn(2.0, best)));
     d.wgt[i] = w;
-    d.flags[i] = (uint8_t)((best > 0.0 ? 1 : 0) | (best < 1.0 ? 2 : 0));
+    d.flags[i] = (uint8_t)((best > 0.0 ? 1 : 0) | (best < 1.0 ? 2 : 0) | (far_e ? 16 : 0) | (deep_c ? 32 : 0));
     d.esite_e[i] = 0.0;
     d.esite_c[i] = 0.0;
 }
@@ -177,8 +184,10 @@ constexpr int BUF_WARPS = 8;
 __device__ __forceinline__ void buffer_body(const Dev& d, int bx, int gx) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int64_t i = (int64_t)bx * BUF_WARPS + warp; i < d.n; i += (int64_t)gx * BUF_WARPS) {
-        const int f = d.flags[i] & 3;
-        const bool need_e = !(f & 1), need_c = !(f & 2);
+        const int fl = d.flags[i];
+        const int f = fl & 3;
+        // scan unless k_lambda's hints (bits 4, 5; geometric regions only) rule it out
+        const bool need_e = !(f & 1) && !(fl & 16), need_c = !(f & 2) && !(fl & 32);
         bool he = false, hc = false;
         if (need_e || need_c) {
             const double4 xi = d.x[i];

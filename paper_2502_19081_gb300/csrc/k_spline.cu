@@ -34,13 +34,16 @@ __device__ __forceinline__ void bspline4(T x, int qmax, int& q, T b[4], T db[4])
     db[3] = T(0.5) * u2;
 }
 
+// index of the pair p < q in a packed upper triangle
+__device__ __forceinline__ int tri3(int p, int q) { return p * NB3MAX - p * (p + 1) / 2 + (q - p - 1); }
+
 template <typename T>
 struct SplWarp {   // per-warp shared scratch
     int slot[NB3MAX];
     T v[NB3MAX][4];         // r_ij vector (x, y, z) and |r_ij|
     T g2[NB3MAX][4];        // 2-body part of dE_i/dr_ij of the 3-body neighbours
     T al[NB3MAX * T3S];     // a_jk
-    T cc[NB3MAX * T3S];     // c_jk (symmetric)
+    T cc[NB3MAX * (NB3MAX - 1) / 2];   // c_jk (symmetric: pairs p < q only)
 };
 
 // One evaluated atom (index a of the system's cheap list), by one warp; the
@@ -156,8 +159,7 @@ __device__ __forceinline__ void spline_atom(const Dev& d, const SplTab<T>& tab, 
             const T c = r3 > T(0) ? d3 * invhc / r3 : T(0);
             W.al[p * T3S + q] = d1 * invh3;
             W.al[q * T3S + p] = d2 * invh3;
-            W.cc[p * T3S + q] = c;
-            W.cc[q * T3S + p] = c;
+            W.cc[tri3(p, q)] = c;
         }
         __syncwarp();
         // 3-body slots: 2-body part plus the sum over the other 3-body neighbours
@@ -166,7 +168,7 @@ __device__ __forceinline__ void spline_atom(const Dev& d, const SplTab<T>& tab, 
             T sa = T(0), cx = T(0), cy = T(0), cz = T(0), cs = T(0);
             for (int q = 0; q < n3; ++q) {
                 if (q == p) continue;
-                const T c = W.cc[p * T3S + q];
+                const T c = W.cc[p < q ? tri3(p, q) : tri3(q, p)];
                 sa += W.al[p * T3S + q];
                 cs += c;
                 cx += c * W.v[q][0];

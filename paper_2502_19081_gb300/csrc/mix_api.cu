@@ -737,6 +737,8 @@ int mix_init(const mix_system* sys, const mix_ace* a, const mix_spline* sp, cons
     d.rc3 = sp->r_cut3;
     d.bufe2 = bufe * bufe;
     d.bufc2 = bufc * bufc;
+    d.bufe = bufe;
+    d.bufc = bufc;
     double extent = 0.0;
     for (int k = 0; k < 3; ++k) extent = std::max(extent, std::fabs(sys->box_lo[k]) + sys->box_len[k]);
     d.exact_lists = extent > 2000.0 ? 1 : 0;

@@ -99,6 +99,7 @@ struct Dev {
     double rcc, rcc2;    // cheap 2-body cutoff
     double rc3;          // cheap 3-body cutoff
     double bufe2, bufc2; // buffer radii squared
+    double bufe, bufc;   // buffer radii
     int exact_lists;     // 1: every neighbour candidate takes the float64 test
                          // (boxes beyond the float pre-filter's error bound)
     double4* x;
