@@ -375,7 +375,12 @@ def fe_screw(seed: int = 3, n_atoms: int = 256000, nrep_z: int = 26, sigma: floa
     dxy = dxy[near]
     order = np.lexsort((np.arange(pr.shape[0]), np.round(dxy, 9)))
     pr = pr[order[:n_atoms]]
-    theta = np.arctan2(pr[:, 1] - y0, pr[:, 0] - x0)
+    # sites on the cut (dy = 0 up to rounding, dx < 0) all take the +pi branch:
+    # the sign of the rounding noise must not pick the branch, or two sites of
+    # one column are displaced towards each other
+    dyc = pr[:, 1] - y0
+    dyc = np.where(np.abs(dyc) < 1e-9, 0.0, dyc)
+    theta = np.arctan2(dyc, pr[:, 0] - x0)
     pr[:, 2] = pr[:, 2] + b * theta / (2.0 * math.pi)
     pr = pr + rng.normal(0.0, sigma, pr.shape)
     rmax = float(np.max(np.hypot(pr[:, 0] - x0, pr[:, 1] - y0)))

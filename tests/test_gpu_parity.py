@@ -107,7 +107,7 @@ def test_forces_fp64_match_oracle(mx, name):
     assert np.all(ee[~me] == 0) and np.all(ec[~mc] == 0)
 
 
-@pytest.mark.parametrize("name", ["si_vacancy_215", "fe_box_685", "cluster_60"])
+@pytest.mark.parametrize("name", ["si_vacancy_215", "fe_box_685", "fe_box_l4", "cluster_60", "screw_3000"])
 def test_forces_fp32_within_gate(mx, name):
     wl = _wl(name)
     ctx = mx.open_context(wl, precision=mx.MIX_FP32)

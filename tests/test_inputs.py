@@ -23,6 +23,13 @@ def test_screw_cylinder_geometry():
     assert np.all(x[:, 2] >= 0) and np.all(x[:, 2] < w.system.box_len[2])
     assert np.all(x[:, :2] > w.system.box_lo[:2]) and np.all(x[:, :2] < w.system.box_lo[:2] + w.system.box_len[:2])
     assert r.max() < 33.0            # sqrt(N / (rho pi Lz)) = 30.6 A plus thermal noise
+    # no two sites closer than a bcc bond shortened by the core strain and noise
+    # (sites on the displacement cut must not be pushed onto their column neighbours)
+    d = x[:, None, :] - x[None, :, :]
+    d[..., 2] -= w.system.box_len[2] * np.rint(d[..., 2] / w.system.box_len[2])
+    r2 = np.einsum("ijk,ijk->ij", d, d)
+    np.fill_diagonal(r2, 1e9)
+    assert np.sqrt(r2.min()) > 1.5
 
 
 def test_replica_batch_statistics():
