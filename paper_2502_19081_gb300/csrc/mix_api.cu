@@ -168,6 +168,8 @@ struct mix_ctx {
     bool profiling;
     bool opt_graphs;
     cudaStream_t cap_stream;
+    cudaStream_t aux;          // second branch of an evaluation: the cheap potential
+    cudaEvent_t ev_fork, ev_join;
     cudaGraph_t graph;
     cudaGraphExec_t gexec;
     double graph_dt;
@@ -544,9 +546,15 @@ void enqueue_evaluation(mix_ctx* c, cudaStream_t s, int integrate, double dt, in
     if (prof) cudaEventRecordWithFlags(c->ev[3], s, ef);
     const void* at = c->precision == MIX_FP64 ? (const void*)&c->ace64 : (const void*)&c->ace32;
     const void* st = c->precision == MIX_FP64 ? (const void*)&c->spl64 : (const void*)&c->spl32;
+    // the two potentials write disjoint arrays: the cheap one runs on a second
+    // branch and fills the SMs the expensive kernel's last wave leaves idle
+    cudaEventRecord(c->ev_fork, s);
+    cudaStreamWaitEvent(c->aux, c->ev_fork, 0);
+    launch_spline(c->dev, st, c->precision, c->spl_smem, c->spl_grid, c->aux);
+    cudaEventRecord(c->ev_join, c->aux);
     launch_ace(c->dev, at, c->precision, c->L, c->ace_smem, c->ace_grid, s);
     if (prof) cudaEventRecordWithFlags(c->ev[4], s, ef);
-    launch_spline(c->dev, st, c->precision, c->spl_smem, c->spl_grid, s);
+    cudaStreamWaitEvent(s, c->ev_join, 0);
     if (prof) cudaEventRecordWithFlags(c->ev[5], s, ef);
     launch_gather(c->dev, c->precision, integrate, h, s);
     if (prof) cudaEventRecordWithFlags(c->ev[6], s, ef);
@@ -766,6 +774,14 @@ int mix_init(const mix_system* sys, const mix_ace* a, const mix_spline* sp, cons
     }
     e = cudaMallocHost((void**)&c->pinned, SW_COUNT * sizeof(int));
     if (e != cudaSuccess) {
+        delete c;
+        return MIX_ECUDA;
+    }
+    e = cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        cudaFreeHost(c->pinned);
         delete c;
         return MIX_ECUDA;
     }
@@ -1041,6 +1057,9 @@ int mix_destroy(mix_ctx* c) {
     else cudaDeviceSynchronize();
     drop_graph(c);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->aux) cudaStreamDestroy(c->aux);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->pinned) cudaFreeHost(c->pinned);
     if (c->profiling)
         for (int p = 0; p <= MIX_PHASES; ++p) cudaEventDestroy(c->ev[p]);
@@ -1264,6 +1283,8 @@ struct mix_batch {
     size_t spl_smem = 0;
     int spl_grid = 0;
     int64_t launches = 0;            // kernels launched by fused steps
+    cudaStream_t aux = nullptr;      // second branch (cheap potential) of the fused step
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace {
@@ -1470,6 +1491,12 @@ int fused_graph(mix_batch* b, int integrate, double dt, cudaGraph_t* graph, cuda
         cudaError_t e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
         if (e != cudaSuccess) return bfail(b, MIX_ECUDA, "capture stream");
     }
+    if (!b->aux) {
+        cudaError_t e = cudaStreamCreateWithFlags(&b->aux, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming);
+        if (e != cudaSuccess) return bfail(b, MIX_ECUDA, "second branch stream");
+    }
     cudaStream_t s = b->cap_stream;
     cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return bfail(b, MIX_ECUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e));
@@ -1477,13 +1504,18 @@ int fused_graph(mix_batch* b, int integrate, double dt, cudaGraph_t* graph, cuda
     launch_disp_batch(P, s, integrate, dt, 0);
     launch_build_batch(P, s);
     launch_sets_batch(P, s);
+    // cheap potential on a second branch, concurrent with the expensive groups
+    cudaEventRecord(b->ev_fork, s);
+    cudaStreamWaitEvent(b->aux, b->ev_fork, 0);
+    launch_spline_batch(b->precision, b->ddevs, b->dspl, P.flat.list_c, P.flat.counts + b->groups.size(), b->spl_smem,
+                        b->spl_grid, b->aux);
+    cudaEventRecord(b->ev_join, b->aux);
     for (size_t g = 0; g < b->groups.size(); ++g) {
         const mix_batch::Group& G = b->groups[g];
         launch_ace_batch(b->precision, b->ddevs, b->dace, P.flat.list_e + G.base, P.flat.counts + g, G.n, G.L, G.smem,
                          G.grid, s);
     }
-    launch_spline_batch(b->precision, b->ddevs, b->dspl, P.flat.list_c, P.flat.counts + b->groups.size(), b->spl_smem,
-                        b->spl_grid, s);
+    cudaStreamWaitEvent(s, b->ev_join, 0);
     launch_gather_batch(P, b->precision, integrate, dt, s);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(s, &g);
@@ -1659,6 +1691,9 @@ int mix_batch_destroy(mix_batch* b) {
     batch_drop(b);
     fused_free(b);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    if (b->aux) cudaStreamDestroy(b->aux);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->ev_join) cudaEventDestroy(b->ev_join);
     delete b;
     return MIX_OK;
 }
