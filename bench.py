@@ -323,6 +323,25 @@ def ours(args):
                                             flush)
     c2.close()
 
+    # the pure expensive potential on every atom (one region covering the box),
+    # same arithmetic, for the mixing speedup
+    from paper_2502_19081_gb300 import inputs as I
+    centre = tuple(float(v) for v in np.asarray(wl.system.box_lo) + 0.5 * np.asarray(wl.system.box_len))
+    everywhere = [I.Region(I.REGION_SPHERE, centre, (0.0, 0.0, 1.0), 1.0e4, 1.0)]
+    cx = mix.open_context(wl, precision=prec, regions=everywhere)
+    for _ in range(3):
+        cx.step(wl.dt, 1)
+    cx.sync()
+    cx.profile(True)
+    per_x = []
+    for _ in range(max(3, args.secondary_steps // 2)):
+        flush()
+        cx.step(wl.dt, 1)
+        per_x.append(float(np.sum(cx.get_profile()[1])))
+    cx.profile(False)
+    cx.close()
+    pure_ms = float(np.mean(per_x))
+
     if rank != 0:
         if world > 1:
             dist.barrier()
@@ -385,6 +404,10 @@ def ours(args):
                           "kernels_ms": {names[p]: float(tot2[p] / max(nev2, 1)) for p in range(len(names))}},
         "roofline": roof,
         "kernels": kern,
+        "mixing": {"pure_expensive_ms_per_step": pure_ms, "speedup": pure_ms / (total_max / args.steps),
+                   "s_ul": n * pe / (nstat["n_exp"] * pe + nstat["n_cheap"] * pc),
+                   "note": "speedup over the same step with the expensive potential on every atom; s_ul = the "
+                           "zero-overhead bound from algorithmic flops, N e / (|A_exp| e + |A_cheap| c)"},
         "fma_peak_tflops": {"fp64": peaks[mix.MIX_FP64] / 1e12, "fp32": peaks[mix.MIX_FP32] / 1e12},
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 3 * n * 32, "d2h_bytes_per_step": 3 * n * 32,
                 "steps": len(e2e_s), "entry": "mix_step_host (x, v, f in and out, pinned host memory)"},
