@@ -209,25 +209,37 @@ __global__ void __launch_bounds__(SPL_WARPS * 32) k_spline(Dev d, SplTab<T> tab)
 }
 
 // Many systems: a warp per entry {system, index} of the flattened cheap list;
-// the system's parameters and coefficient tables are read through L1.
+// the system's parameters are read through L1.  When every system has the same
+// coefficient tables (uniform != 0) the block stages them once in shared
+// memory, as the single-system kernel does; otherwise they are read through L1.
 template <typename T>
 __global__ void __launch_bounds__(SPL_WARPS * 32) kb_spline(const Dev* __restrict__ devs,
                                                            const SplTab<T>* __restrict__ tabs,
-                                                           const int2* __restrict__ list, const int* count_p) {
+                                                           const int2* __restrict__ list, const int* count_p,
+                                                           int uniform) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SplWarp<T>* ws = reinterpret_cast<SplWarp<T>*>(smem_raw);
+    T* c3s = reinterpret_cast<T*>(ws + SPL_WARPS);      // [512] (uniform tables only)
+    T* c2s = c3s + 512;                                  // [16]
     const int warp = threadIdx.x >> 5;
+    if (uniform) {
+        const T* c3 = tabs[0].c3;
+        const T* c2 = tabs[0].c2;
+        for (int k = threadIdx.x; k < 512; k += blockDim.x) c3s[k] = c3[k];
+        if (threadIdx.x < 16) c2s[threadIdx.x] = c2[threadIdx.x];
+        __syncthreads();
+    }
     const int count = *count_p;
     for (int g = blockIdx.x * SPL_WARPS + warp; g < count; g += gridDim.x * SPL_WARPS) {
         const int2 e = list[g];
         const SplTab<T>& tab = tabs[e.x];
-        spline_atom<T>(devs[e.x], tab, e.y, tab.c2, tab.c3, ws[warp]);
+        spline_atom<T>(devs[e.x], tab, e.y, uniform ? c2s : tab.c2, uniform ? c3s : tab.c3, ws[warp]);
     }
 }
 
 template <typename T>
 static cudaError_t spl_batch_cfg(size_t* smem, int* grid) {
-    const size_t bytes = SPL_WARPS * sizeof(SplWarp<T>);
+    const size_t bytes = SPL_WARPS * sizeof(SplWarp<T>) + (512 + 16) * sizeof(T);
     cudaError_t e = raise_smem_limit((const void*)kb_spline<T>, bytes);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -244,13 +256,13 @@ cudaError_t spline_batch_configure(int precision, size_t* smem, int* grid) {
 }
 
 void launch_spline_batch(int precision, const Dev* devs, const void* tabs, const int2* list, const int* count,
-                         size_t smem, int grid, cudaStream_t s) {
+                         int uniform, size_t smem, int grid, cudaStream_t s) {
     if (precision == MIX_FP64)
         kb_spline<double><<<grid, SPL_WARPS * 32, smem, s>>>(devs, static_cast<const SplTab<double>*>(tabs), list,
-                                                             count);
+                                                             count, uniform);
     else
         kb_spline<float><<<grid, SPL_WARPS * 32, smem, s>>>(devs, static_cast<const SplTab<float>*>(tabs), list,
-                                                            count);
+                                                            count, uniform);
 }
 
 template <typename T>

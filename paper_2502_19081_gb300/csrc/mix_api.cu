@@ -1282,6 +1282,7 @@ struct mix_batch {
     const void* dspl = nullptr;
     size_t spl_smem = 0;
     int spl_grid = 0;
+    int spl_uniform = 0;             // every member has the same cheap coefficient tables
     int64_t launches = 0;            // kernels launched by fused steps
     cudaStream_t aux = nullptr;      // second branch (cheap potential) of the fused step
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -1478,6 +1479,18 @@ int fused_build(mix_batch* b) {
         e = ace_batch_configure(b->precision, g.L, g.n, g.cap, &g.smem, &g.grid);
         if (e != cudaSuccess) return bfail(b, MIX_ECUDA, std::string("fused expensive kernel: ") + cudaGetErrorString(e));
     }
+    // identical cheap tables in every member: the fused kernel stages them once per block
+    {
+        const size_t tb = f64 ? sizeof(double) : sizeof(float);
+        const mix_ctx* c0 = b->m[0];
+        b->spl_uniform = 1;
+        for (int s = 1; s < ns && b->spl_uniform; ++s) {
+            const mix_ctx* c = b->m[s];
+            if (std::memcmp(c->arena.bytes.data() + c->o_sc2, c0->arena.bytes.data() + c0->o_sc2, 16 * tb) != 0 ||
+                std::memcmp(c->arena.bytes.data() + c->o_sc3, c0->arena.bytes.data() + c0->o_sc3, 512 * tb) != 0)
+                b->spl_uniform = 0;
+        }
+    }
     e = spline_batch_configure(b->precision, &b->spl_smem, &b->spl_grid);
     if (e != cudaSuccess) return bfail(b, MIX_ECUDA, std::string("fused cheap kernel: ") + cudaGetErrorString(e));
     return MIX_OK;
@@ -1507,8 +1520,8 @@ int fused_graph(mix_batch* b, int integrate, double dt, cudaGraph_t* graph, cuda
     // cheap potential on a second branch, concurrent with the expensive groups
     cudaEventRecord(b->ev_fork, s);
     cudaStreamWaitEvent(b->aux, b->ev_fork, 0);
-    launch_spline_batch(b->precision, b->ddevs, b->dspl, P.flat.list_c, P.flat.counts + b->groups.size(), b->spl_smem,
-                        b->spl_grid, b->aux);
+    launch_spline_batch(b->precision, b->ddevs, b->dspl, P.flat.list_c, P.flat.counts + b->groups.size(),
+                        b->spl_uniform, b->spl_smem, b->spl_grid, b->aux);
     cudaEventRecord(b->ev_join, b->aux);
     for (size_t g = 0; g < b->groups.size(); ++g) {
         const mix_batch::Group& G = b->groups[g];

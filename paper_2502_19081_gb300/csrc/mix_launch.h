@@ -77,7 +77,7 @@ void launch_ace_batch_f64(const Dev* devs, const void* tabs, const int2* list, c
                           size_t smem, int grid, cudaStream_t s);
 cudaError_t spline_batch_configure(int precision, size_t* smem, int* grid);
 void launch_spline_batch(int precision, const Dev* devs, const void* tabs, const int2* list, const int* count,
-                         size_t smem, int grid, cudaStream_t s);
+                         int uniform, size_t smem, int grid, cudaStream_t s);
 void launch_gather_batch(const BatchPlan& p, int precision, int integrate, double dt, cudaStream_t s);
 
 int sm_count();
