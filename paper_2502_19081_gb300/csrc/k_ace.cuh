@@ -655,12 +655,17 @@ __device__ __forceinline__ void ace_atom(const Dev& d, const AceTab<T>& tab, int
 
         // site energy (float64, fixed reduction order)
         const auto e = warp_sum(ep);   // fixed order; compensated for float
-        if (lane == 0) s_red[warp] = lane0_double(e);
-        __syncthreads();
-        if (tid == 0) {
-            double es = 0.0;
-            for (int w = 0; w < WN; ++w) es += s_red[w];
-            d.esite_e[i] = es;
+        if constexpr (sizeof(T) == 4) {
+            // float64 conversion and the sum over warps happen in the gather
+            if (lane == 0) d.epark_e[(int64_t)i * WN + warp] = make_float2(e.s, e.c);
+        } else {
+            if (lane == 0) s_red[warp] = lane0_double(e);
+            __syncthreads();
+            if (tid == 0) {
+                double es = 0.0;
+                for (int w = 0; w < WN; ++w) es += s_red[w];
+                d.esite_e[i] = es;
+            }
         }
         __syncthreads();
     }

@@ -112,6 +112,22 @@ __device__ __forceinline__ void gather_body(const Dev& d, int bx, int gx, int in
             F.w = 0.0;
             if (!(isfinite(F.x) && isfinite(F.y) && isfinite(F.z))) set_status(d.status, ST_NONFINITE);
             d.f[k] = F;
+            if constexpr (sizeof(T) == 4) {
+                // site energies of the float path (warp sums parked by the potentials)
+                const int fl = d.flags[k];
+                double ee = 0.0, ec = 0.0;
+                if (fl & 4) {
+                    const float2* pe = d.epark_e + k * ace_warps<T>();
+#pragma unroll
+                    for (int q = 0; q < ace_warps<T>(); ++q) ee += (double)pe[q].x + (double)pe[q].y;
+                }
+                if (fl & 8) {
+                    const float2 pc = d.epark_c[k];
+                    ec = (double)pc.x + (double)pc.y;
+                }
+                d.esite_e[k] = ee;
+                d.esite_c[k] = ec;
+            }
             if (integrate) {
                 double4 v = d.v[k];
                 v.x = __dadd_rn(v.x, __dmul_rn(h, F.x));

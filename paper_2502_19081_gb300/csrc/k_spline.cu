@@ -188,7 +188,11 @@ __device__ __forceinline__ void spline_atom(const Dev& d, const SplTab<T>& tab, 
         }
         __syncwarp();
         const auto epart = warp_sum(ep);   // fixed order; compensated for float
-        if (lane == 0) d.esite_c[i] = lane0_double(epart);
+        if constexpr (sizeof(T) == 4) {
+            if (lane == 0) d.epark_c[i] = make_float2(epart.s, epart.c);   // converted in the gather
+        } else {
+            if (lane == 0) d.esite_c[i] = lane0_double(epart);
+        }
         __syncwarp();
     }
 }

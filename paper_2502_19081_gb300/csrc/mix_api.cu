@@ -157,7 +157,7 @@ struct mix_ctx {
     size_t ws_bytes;
     size_t off_tab;
     size_t o_status, o_xb, o_xf, o_xr, o_cell3, o_cell_of, o_cell_count, o_cell_start, o_cell_fill, o_cell_atoms, o_nnb, o_nbr, o_rev,
-        o_lam, o_wgt, o_flags, o_act_e, o_act_c, o_pos_e, o_pos_c, o_blk_e, o_blk_c, o_ge, o_gc, o_gei, o_gci, o_ee, o_ec,
+        o_lam, o_wgt, o_flags, o_act_e, o_act_c, o_pos_e, o_pos_c, o_blk_e, o_blk_c, o_ge, o_gc, o_gei, o_gci, o_ee, o_ec, o_pe, o_pc,
         o_seed, o_core, o_zsum;
     size_t ace_smem, spl_smem;
     int ace_grid, spl_grid;
@@ -515,6 +515,8 @@ void layout(mix_ctx* c) {
     c->o_gci = take(N * cap * v4);
     c->o_ee = take(N * 8);
     c->o_ec = take(N * 8);
+    c->o_pe = take(N * 4 * sizeof(float2));
+    c->o_pc = take(N * sizeof(float2));
     c->o_seed = take(N);
     c->o_core = take(N);
     c->o_zsum = take(N * 4);
@@ -838,6 +840,8 @@ int mix_bind(mix_ctx* c, double* x, double* v, double* f, void* ws) {
     d.gc_in = w + c->o_gci;
     d.esite_e = reinterpret_cast<double*>(w + c->o_ee);
     d.esite_c = reinterpret_cast<double*>(w + c->o_ec);
+    d.epark_e = reinterpret_cast<float2*>(w + c->o_pe);
+    d.epark_c = reinterpret_cast<float2*>(w + c->o_pc);
     d.seed = reinterpret_cast<uint8_t*>(w + c->o_seed);
     d.core = reinterpret_cast<uint8_t*>(w + c->o_core);
     d.zsum = reinterpret_cast<int*>(w + c->o_zsum);

@@ -133,6 +133,11 @@ struct Dev {
     void* gc_in;         //   w = the evaluation (epoch) that wrote it; same for the cheap potential
     double* esite_e;
     double* esite_c;
+    // float path: the compensated (sum, correction) pairs of the site energies,
+    // per warp of the expensive kernel ([N][4]) and for the cheap one ([N]);
+    // the gather turns them into float64 site energies 32 atoms at a time
+    float2* epark_e;
+    float2* epark_c;
     uint8_t* seed;       // [N] seed atoms (seed-atom weights)
     uint8_t* core;       // [N] core atoms
     int* zsum;           // [N] coordination summed over the current averaging period
