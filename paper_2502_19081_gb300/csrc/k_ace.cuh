@@ -1,43 +1,47 @@
 // Expensive potential (templates): a linear atomic cluster expansion evaluated on the
 // compacted list of atoms in Lambda_exp plus its buffer (Sec. 4.5, Alg. 4).
 //
-// One CTA (4 warps) per evaluated atom, persistent over the list:
+// A CTA of ACE_GROUP warps takes groups of ACE_GROUP consecutive atoms of the
+// expensive list, and warp w owns atom w of its group through every step:
 //   1. neighbours inside the cutoff, compacted in slot order (FP64 pair
 //      vectors, rounded once to T);
-//   2. density A[lm][q] = sum_k R_q(r_k) Y_lm(u_k), neighbours in chunks:
-//      R (Chebyshev recurrence x (1 - (r/rc)^2)^3) and Y (associated-Legendre
-//      recurrence in z times Re/Im (x + iy)^m) go to shared memory, each thread
-//      keeps fixed outputs in registers;
+//   2. density A[lm][q] = sum_k R_q(r_k) Y_lm(u_k): the lanes evaluate R
+//      (Chebyshev recurrence x (1 - (r/rc)^2)^3) and Y (associated-Legendre
+//      recurrence in z times Re/Im (x + iy)^m) for 32 neighbours at a time into
+//      shared memory, then each lane accumulates fixed (lm, 4 q) outputs;
 //   3. nu <= 2 readout; omega = dE/dA initialised;
-//   4. nu = 3, the l-triples split over the warps (balanced on the host), each
-//      warp with its own omega copy, so the loop needs no block barrier:
-//        U[q1 q2][m3] = sum_q3 W[q1 q2 q3] A[l3 m3][q3]
-//        Z[q1 q2][m3] = sum_(m1 m2) G A[l1 m1][q1] A[l2 m2][q2]   (Gaunt-sparse)
-//        E += sum Z U;  omega3 += W^T Z;  omega1 += G A2 U;  omega2 += G A1 U;
-//      in the U/Z pass a lane owns one q1 and a block of qb consecutive q2
-//      (the W rows of that block sit in registers), so each Gaunt entry costs
-//      one packed table load, one scalar A1 load and one vector A2 load for qb
-//      accumulations; omega3 = W^T Z with a lane per output; where
-//      two l's coincide W is symmetrised on the host, the adjoints through the
-//      coinciding factors are equal, and one of them is computed and scaled
-//      (omega2 only for distinct l's, omega1 not when all three are equal);
-//   5. omega = sum of the warp copies (fixed order);
-//   6. pair gradients dE_i/dr_ij = u sum_lm sigma_lm Y_lm
+//   4. nu = 3, one l-triple (l1, l2, l3) after the other.  The triple's tables
+//      (W[q1 q2][q3], its transpose, the Gaunt entries in three orderings and
+//      their offsets) form one tile; the CTA streams the tiles from global
+//      memory into two shared-memory buffers with cp.async, fetching tile t+1
+//      while the warps work on tile t, so a tile crosses L2 once per group of
+//      atoms rather than once per atom.  Per warp:
+//        U[m3][q1][q2] = sum_q3 W[q1 q2][q3] A3[m3][q3]
+//        Z[m3][q1 q2]  = sum_(m1 m2) G A1[m1][q1] A2[m2][q2]     (Gaunt-sparse)
+//        E += sum Z U;  omega3 += W^T Z;  omega1 += G A2 U;  omega2 += G A1 U.
+//      In the U/Z pass a lane owns one q1 and a block of qb consecutive q2 (the
+//      W rows of that block sit in registers), so each Gaunt entry costs one
+//      packed entry load, one scalar A1 load and one vector A2 load for qb
+//      accumulations; omega3 = W^T Z with a lane per (2 q3) x (2 m3) block.
+//      Where two l's coincide W is symmetrised on the host, the adjoints
+//      through the coinciding factors are equal, and one of them is computed
+//      and scaled (omega2 only for distinct l's, omega1 not when all three are
+//      equal).  Each warp adds into its own atom's omega: no reduction across
+//      warps and no balancing of triples over warps;
+//   5. pair gradients dE_i/dr_ij = u sum_lm sigma_lm Y_lm
 //        + (grad_u p - u (u . grad_u p)) / r,  rho = omega R, sigma = omega R',
-//      R, R', Y recomputed per neighbour in registers, the lm sum split over
-//      pairs of warps; written per list slot, to the atom's own row and to the
-//      partner's incoming row (slot rev, stamped with the evaluation count).
+//      a lane per neighbour with R, R', Y recomputed in registers; written per
+//      list slot, to the atom's own row and to the partner's incoming row (slot
+//      rev, stamped with the evaluation count).
 // Per-atom arrays are stored transposed ([lm][q], q padded to NP = 4k with
 // zeros) so that the inner products run over 4-wide vector loads with no index
-// division.  Site energy partial sums are kept in T per thread and reduced in
-// float64 once per atom in a fixed order.
+// division.  The site energy is summed per lane in T and reduced once per atom
+// in a fixed order (compensated for float).
 #pragma once
 
 #include "mix_launch.h"
 
 namespace mixd {
-
-constexpr int ACE_CH = 64;               // neighbours per density chunk
 
 template <typename T> struct V4;
 template <> struct V4<float> {
@@ -60,28 +64,14 @@ __device__ __forceinline__ V4<double> ld4<double>(const double* p) {
     const double2 b = reinterpret_cast<const double2*>(p)[1];
     return {a.x, a.y, b.x, b.y};
 }
-template <typename T>
-__device__ __forceinline__ V4<T> ldg4(const T* p);
-template <>
-__device__ __forceinline__ V4<float> ldg4<float>(const float* p) {
-    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
-    return {v.x, v.y, v.z, v.w};
-}
-template <>
-__device__ __forceinline__ V4<double> ldg4<double>(const double* p) {
-    const double2 a = __ldg(reinterpret_cast<const double2*>(p));
-    const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
-    return {a.x, a.y, b.x, b.y};
-}
-
-// one Gaunt entry through the read-only path (one 8- or 16-byte load)
+// one Gaunt entry of a tile in shared memory (one 8- or 16-byte load)
 __device__ __forceinline__ void ld_gent(const GEnt<float>* p, int& pk, float& g) {
-    const int2 v = __ldg(reinterpret_cast<const int2*>(p));
+    const int2 v = *reinterpret_cast<const int2*>(p);
     pk = v.x;
     g = __int_as_float(v.y);
 }
 __device__ __forceinline__ void ld_gent(const GEnt<double>* p, int& pk, double& g) {
-    const int4 v = __ldg(reinterpret_cast<const int4*>(p));
+    const int4 v = *reinterpret_cast<const int4*>(p);
     pk = v.x;
     g = __hiloint2double(v.w, v.z);
 }
@@ -108,6 +98,15 @@ __device__ __forceinline__ void ld_blk(const T* p, T* out) {
     } else {
         out[0] = p[0];
     }
+}
+
+// s += a . b as one chain of four fused multiply-adds
+template <typename T>
+__device__ __forceinline__ void dot4_acc(T& s, const V4<T>& a, const V4<T>& b) {
+    s += a.x * b.x;
+    s += a.y * b.y;
+    s += a.z * b.z;
+    s += a.w * b.w;
 }
 
 // Pi[l][m] = d^m P_l / dz^m for 0 <= m <= l <= L (flattened l(l+1)/2 + m),
@@ -205,44 +204,99 @@ __device__ __forceinline__ void spline16(const T* __restrict__ c, T invh, T r, T
     dv = (c[q] * d0 + c[q + 1] * d1 + c[q + 2] * d2 + c[q + 3] * d3) * invh;
 }
 
-__host__ __device__ constexpr int ace_pad(int x) { return (x + 3) & ~3; }
+__host__ __device__ constexpr int ace_a16(int b) { return (b + 15) & ~15; }
 
-// shared-memory layout (element offsets), shared by host sizing and the kernel
-// The density chunk buffers (R, Y of up to ACE_CH neighbours) and the per-warp
-// nu = 3 scratch are never live together and share one region.
-struct AceSmem {
-    int o_u, o_At, o_om, o_gp, o_w, o_cR, o_cY, ws, total;
-    __host__ __device__ AceSmem(int cap, int n, int nq, int L, int NP, int W) {
-        const int nlm = (L + 1) * (L + 1);
-        const int D = 2 * L + 1;
-        o_u = 0;
-        o_At = ace_pad(4 * cap);
-        o_om = o_At + nlm * NP;
-        o_gp = o_om + nlm * NP;
-        o_w = o_gp + 2 * (16 * W) * 4;         // gradient partials: 2 halves x 16 W neighbours
-        o_cR = o_w;
-        o_cY = o_cR + ACE_CH * NP;
-        ws = D * n * NP + D * nq + nlm * NP;   // per warp: U, ZT, omega copy
-        const int chunk = ACE_CH * NP + ace_pad(ACE_CH * nlm);
-        const int wsall = W * ws;
-        total = o_w + (chunk > wsall ? chunk : wsall);
+// Shared memory (byte offsets, used by the host sizing and the kernels): two
+// tile buffers, then one region per warp.  In a warp region the density chunk
+// (R and Y of 32 neighbours) and the nu = 3 scratch of a triple (U, kept for
+// omega2, and the omega1 partial sums of the lane units) are never live
+// together and share one area.
+struct AceLay {
+    int tile;                            // bytes of one tile buffer
+    int o_w, wb;                         // first warp region, bytes per warp region
+    int o_u, o_at, o_om, o_scr, o_slot;  // offsets inside a warp region
+    int o_p1;                            // omega1 partials, inside the scratch area
+    int total;
+    __host__ __device__ AceLay(int tile_max, int cap, int n, int qb, int L, int NP, int ts, int warps) {
+        const int nlm = (L + 1) * (L + 1), D = 2 * L + 1;
+        tile = ace_a16(tile_max);
+        o_w = 2 * tile;
+        o_u = 0;                                  // [cap][4]: unit vector, r
+        o_at = o_u + ace_a16(4 * cap * ts);       // A[lm][q]
+        o_om = o_at + ace_a16(nlm * NP * ts);     // omega[lm][q]
+        o_scr = o_om + ace_a16(nlm * NP * ts);
+        o_p1 = ace_a16(D * n * NP * ts);          // after U[m3][q1][q2]; P1[m1][unit]
+        const int nu3 = o_p1 + D * n * (NP / qb) * ts;
+        const int chunk = (32 * NP + 32 * nlm) * ts;   // R[32][NP], Y[32][nlm]
+        o_slot = o_scr + ace_a16(nu3 > chunk ? nu3 : chunk);   // list slot per compacted neighbour
+        wb = o_slot + ace_a16(4 * cap);
+        total = o_w + warps * wb;
     }
 };
 
-// nu = 3, U and Z of one l-triple for this warp.  Lane units are (q1, block of
-// QB consecutive q2); the m3 loop is uniform over the warp so every Gaunt
-// entry and A3 row load is a broadcast.
-//   U[m3][q1][q2] = sum_q3 W[q1 q2][q3] A3[m3][q3]      (stored, q2 padded to NP)
-//   Z[m3][q1 n + q2] = sum_(m1 m2) G A1[m1][q1] A2[m2][q2]
-//   ep += sum U Z
-// Without U (all three l's equal: no adjoint needs U) only Z is formed and the
-// energy is taken in the omega3 pass as sum A3 (W^T Z), the same sum reordered.
-template <typename T, int NP, int QB, bool WITHU>
-__device__ __forceinline__ void nu3_uz(const T* __restrict__ W, const T* A1, const T* A2, const T* A3,
-                                       const int* g3o, const GEnt<T>* __restrict__ gent, int n, int nq, int d3,
-                                       int lane, T* U1, T* ZT, T& ep) {
+// asynchronous global -> shared copies (16 bytes per instruction; completion is
+// awaited per thread, then published to the CTA by a barrier)
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// the CTA copies tile t (a multiple of 16 bytes, 16-byte aligned) into buf
+__device__ __forceinline__ void tile_fetch(const unsigned char* tiles, const int* off, int t, unsigned char* buf) {
+    const int b0 = __ldg(off + t), nb = __ldg(off + t + 1) - b0;
+    for (int o = (int)threadIdx.x * 16; o < nb; o += (int)blockDim.x * 16) cp_async16(buf + o, tiles + b0 + o);
+    cp_async_commit();
+}
+
+// Reduce-scatter of 16 values over the warp: returns, in every lane, the sum
+// over all 32 lanes of entry (lane >> 1) & 15 (each sum is held by two lanes):
+// four halving exchanges (8 + 4 + 2 + 1 shuffles) and a last pairwise sum, in
+// a fixed order.
+template <typename T>
+__device__ __forceinline__ T warp_reduce_scatter16(T (&v)[16], int lane) {
+#pragma unroll
+    for (int h = 8; h >= 1; h >>= 1) {
+        const bool up = (lane & (2 * h)) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const T send = up ? v[i] : v[i + h];
+            const T keep = up ? v[i + h] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 2 * h);
+        }
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+// nu = 3 of one l-triple for this warp's atom, in one pass over lane units
+// (q1, block of QB consecutive q2).  A unit keeps the W rows of its block in
+// registers; for each m3 (uniform over the warp, so entry and A3 loads are
+// broadcasts) it forms
+//   U[m3][q1][q2] = sum_q3 W[q1 q2][q3] A3[m3][q3]           (registers)
+//   Z[m3][q1][q2] = sum_(m1 m2) G A1[m1][q1] A2[m2][q2]       (registers, Gaunt-sparse)
+// and from them, without storing Z:
+//   E      += sum U Z                                          (lane-local)
+//   omega3 += W^T Z: the unit's share sum_q2 W[q1 q2][q3] Z[m3][q1 q2] for all q3,
+//             summed over the warp by a reduce-scatter;
+//   omega1 += G A2 U: per Gaunt entry g sum_q2 A2[m2][q2] U[m3][q1][q2] from the
+//             A2 values already loaded for Z, summed over the entries of a run of
+//             equal m1 (the entries of one m3 are m1-major) in a register and
+//             added to the unit's partial P1[m1][unit] in shared memory; the
+//             partials of the units of one q1 are summed after the last m3;
+// and, for distinct l's only (omega2 needs it after the pass), stores U.
+// All three l's equal: U is not formed (no adjoint needs it) and the energy is
+// taken as sum A3 (W^T Z), the same sum reordered.
+template <typename T, int NP, int QB>
+__device__ __forceinline__ void nu3_units(const AceTileHdr& h, const T* W, const GEnt<T>* ge, const int* g3o,
+                                          const T* A1, const T* A2, const T* A3, int n, int lane, T* U1, T* P1,
+                                          T* o3, T mult3, T& ep) {
     constexpr int nqb = NP / QB;
     const int units = n * nqb;
+    const int d3 = 2 * h.l3 + 1;
+    const bool withu = h.mode != 3;
+    const bool keepu = h.mode == 0;
+    const int q3o = (lane >> 1) & 15;   // the omega3 entry this lane receives
     for (int u0 = 0; u0 < units; u0 += 32) {
         const int u = u0 + lane;
         const bool uv = u < units;
@@ -252,12 +306,11 @@ __device__ __forceinline__ void nu3_uz(const T* __restrict__ W, const T* A1, con
         T w[QB][NP];
 #pragma unroll
         for (int r = 0; r < QB; ++r) {
-            if (!WITHU) break;
             const bool ok = uv && q2 + r < n;
             const T* wr = W + (q1 * n + (ok ? q2 + r : 0)) * NP;
 #pragma unroll
             for (int p = 0; p < NP; p += 4) {
-                V4<T> v = ldg4<T>(wr + p);
+                V4<T> v = ld4<T>(wr + p);
                 if (!ok) v = V4<T>{T(0), T(0), T(0), T(0)};
                 w[r][p] = v.x;
                 w[r][p + 1] = v.y;
@@ -272,7 +325,7 @@ __device__ __forceinline__ void nu3_uz(const T* __restrict__ W, const T* A1, con
                 uo[r] = T(0);
                 z[r] = T(0);
             }
-            if (WITHU) {
+            if (withu) {
                 T a[NP];
 #pragma unroll
                 for (int p = 0; p < NP; p += 4) {
@@ -291,76 +344,188 @@ __device__ __forceinline__ void nu3_uz(const T* __restrict__ W, const T* A1, con
                 }
             }
             const int e1 = g3o[m3 + 1];
+            int cur = -1;
+            T c1 = T(0);
             for (int e = g3o[m3]; e < e1; ++e) {
                 int pk;
                 T g;
-                ld_gent(gent + e, pk, g);
-                const T ga = g * A1[(pk & 255) * NP + q1];
+                ld_gent(ge + e, pk, g);
+                const int m1 = pk & 255;
+                const T ga = g * A1[m1 * NP + q1];
                 T a2[QB];
                 ld_blk<T, QB>(A2 + (pk >> 8) * NP + q2, a2);
 #pragma unroll
                 for (int r = 0; r < QB; ++r) z[r] += ga * a2[r];
-            }
-            if (uv) {
-#pragma unroll
-                for (int r = 0; r < QB; ++r) {
-                    if (WITHU) U1[(m3 * n + q1) * NP + q2 + r] = uo[r];
-                    if (q2 + r < n) {
-                        ZT[m3 * nq + q1 * n + q2 + r] = z[r];
-                        if (WITHU) ep += uo[r] * z[r];
+                if (withu) {
+                    if (m1 != cur) {   // uniform over the warp
+                        if (cur >= 0 && uv) P1[cur * units + u] += c1;
+                        c1 = T(0);
+                        cur = m1;
                     }
+                    T dd = T(0);
+#pragma unroll
+                    for (int r = 0; r < QB; ++r) dd += a2[r] * uo[r];
+                    c1 += g * dd;
                 }
+            }
+            if (withu) {
+                if (cur >= 0 && uv) P1[cur * units + u] += c1;
+#pragma unroll
+                for (int r = 0; r < QB; ++r) ep += uo[r] * z[r];
+                if (keepu && uv) {
+#pragma unroll
+                    for (int r = 0; r < QB; ++r) U1[(m3 * n + q1) * NP + q2 + r] = uo[r];
+                }
+            }
+            // omega3 row m3
+            T pv[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                T s = T(0);
+                if (q < NP) {
+#pragma unroll
+                    for (int r = 0; r < QB; ++r) s += w[r][q < NP ? q : 0] * z[r];
+                }
+                pv[q] = s;
+            }
+            const T s3 = warp_reduce_scatter16<T>(pv, lane);
+            if ((lane & 1) == 0 && q3o < n) {
+                o3[m3 * NP + q3o] += mult3 * s3;
+                if (!withu) ep += A3[m3 * NP + q3o] * s3;
             }
         }
     }
 }
 
-// One evaluated atom (index a of the system's expensive list), by the whole CTA.
+// One l-triple for this warp's atom, from the tile in shared memory.
+template <typename T, int NP>
+__device__ __forceinline__ void nu3_tile(const unsigned char* tile, const AceTab<T>& tab, const T* At, T* om,
+                                         T* U1, T* P1, int lane, T& ep) {
+    constexpr int QM = sizeof(T) == 4 ? 4 : 2;     // largest q2 block of a lane unit
+    const AceTileHdr h = *reinterpret_cast<const AceTileHdr*>(tile);
+    const T* W = reinterpret_cast<const T*>(tile + sizeof(AceTileHdr));
+    const GEnt<T>* ge = reinterpret_cast<const GEnt<T>*>(tile + h.o_ge);
+    const int* g3o = reinterpret_cast<const int*>(tile + h.o_go);
+    const int n = tab.n;
+    const int d1 = 2 * h.l1 + 1, d2 = 2 * h.l2 + 1, d3 = 2 * h.l3 + 1;
+    const int* g1o = g3o + d3 + 1;
+    const int* g2o = g1o + d1 + 1;
+    // coinciding l's (W symmetrised on the host): scale instead of recompute
+    const T mult1 = h.mode == 1 ? T(2) : T(1);
+    const T mult3 = h.mode == 3 ? T(3) : (h.mode == 2 ? T(2) : T(1));
+    const T* A1 = At + h.l1 * h.l1 * NP;
+    const T* A2 = At + h.l2 * h.l2 * NP;
+    const T* A3 = At + h.l3 * h.l3 * NP;
+    T* o3 = om + h.l3 * h.l3 * NP;
+    const int qb = tab.qb;
+    if (qb == QM) nu3_units<T, NP, QM>(h, W, ge, g3o, A1, A2, A3, n, lane, U1, P1, o3, mult3, ep);
+    else nu3_units<T, NP, QM / 2>(h, W, ge, g3o, A1, A2, A3, n, lane, U1, P1, o3, mult3, ep);
+    __syncwarp();
+    // omega1 (equal to omega3 when all three l's coincide): sum the unit
+    // partials of each (m1, q1) and clear them for the next triple
+    if (h.mode != 3) {
+        const int nqb = NP / qb, units = n * nqb;
+        T* o1 = om + h.l1 * h.l1 * NP;
+        for (int o = lane; o < n * d1; o += 32) {
+            const int m1 = o / n, q1 = o - m1 * n;
+            T* pr = P1 + m1 * units + q1 * nqb;
+            T s = T(0);
+            for (int b = 0; b < nqb; ++b) {
+                s += pr[b];
+                pr[b] = T(0);
+            }
+            o1[m1 * NP + q1] += mult1 * s;
+        }
+    }
+    // omega2 += G A1 U, needed only when the three l's are distinct (otherwise
+    // it equals omega1 or omega3, already scaled in); a lane per (m2, 4 q2)
+    if (h.mode == 0) {
+        constexpr int NB4 = NP / 4;
+        T* o2 = om + h.l2 * h.l2 * NP;
+        for (int u = lane; u < d2 * NB4; u += 32) {
+            const int m2 = u / NB4, q2 = (u - m2 * NB4) * 4;
+            T c0 = T(0), c1 = T(0), c2 = T(0), c3 = T(0);
+            for (int e = g2o[m2]; e < g2o[m2 + 1]; ++e) {
+                int pk;
+                T gv;
+                ld_gent(ge + e, pk, gv);
+                const T* ar = A1 + (pk & 255) * NP;
+                const T* ur = U1 + (pk >> 8) * n * NP + q2;
+                T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+                for (int q1 = 0; q1 < n; ++q1) {
+                    const T av = ar[q1];
+                    const V4<T> u4 = ld4<T>(ur + q1 * NP);
+                    s0 += av * u4.x;
+                    s1 += av * u4.y;
+                    s2 += av * u4.z;
+                    s3 += av * u4.w;
+                }
+                c0 += gv * s0;
+                c1 += gv * s1;
+                c2 += gv * s2;
+                c3 += gv * s3;
+            }
+            T* orow = o2 + m2 * NP + q2;
+            orow[0] += c0;
+            if (q2 + 1 < n) orow[1] += c1;
+            if (q2 + 2 < n) orow[2] += c2;
+            if (q2 + 3 < n) orow[3] += c3;
+        }
+    }
+    __syncwarp();
+}
+
+// One group of atoms a0 .. a0 + ACE_GROUP - 1 of the system's expensive list
+// (those below nexp), warp w on atom a0 + w; every thread of the CTA calls it.
 template <typename T, int L, int NP>
-__device__ __forceinline__ void ace_atom(const Dev& d, const AceTab<T>& tab, int a, unsigned char* smem_raw,
-                                         int* s_slot, int* s_wcnt, double* s_red) {
+__device__ __forceinline__ void ace_group(const Dev& d, const AceTab<T>& tab, int a0, int nexp, unsigned char* smem) {
     constexpr int WN = ace_warps<T>();
-    constexpr int NT = WN * 32;
     constexpr int NLM = (L + 1) * (L + 1);
     constexpr int D = 2 * L + 1;
-    constexpr int NOUT = (NLM * NP + NT - 1) / NT;
-    constexpr int QM = sizeof(T) == 4 ? 4 : 2;     // largest q2 block of the U/Z pass
-    constexpr int PER = 16 * WN;                   // neighbours per gradient pass
+    constexpr int NQ4 = NP / 4;
+    constexpr int NU = NLM * NQ4;               // density units (lm, 4 q)
+    constexpr int NUL = (NU + 31) / 32;
     using V = typename Vec4<T>::type;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int n = tab.n, nq = tab.nq, cap = d.cap;
-    const AceSmem lay(cap, n, nq, L, NP, WN);
-    T* sm = reinterpret_cast<T*>(smem_raw);
-    T* s_u = sm + lay.o_u;
-    T* s_At = sm + lay.o_At;
-    T* s_om = sm + lay.o_om;
-    T* s_cR = sm + lay.o_cR;
-    T* s_cY = sm + lay.o_cY;
-    T* s_gp = sm + lay.o_gp;
-    T* U1 = sm + lay.o_w + warp * lay.ws;   // U[m3][q1][q2]
-    T* ZT = U1 + D * n * NP;                // Z[m3][q1 q2]
-    T* omw = ZT + D * nq;
+    const int n = tab.n, cap = d.cap, ntau = tab.ntau;
+    const AceLay lay(tab.tile_max, cap, n, tab.qb, L, NP, (int)sizeof(T), WN);
+    // the first tile lands while the warps run steps 1-3
+    if (ntau > 0) tile_fetch(tab.tiles, tab.tile_off, 0, smem);
 
+    unsigned char* wreg = smem + lay.o_w + warp * lay.wb;
+    T* su = reinterpret_cast<T*>(wreg + lay.o_u);
+    T* At = reinterpret_cast<T*>(wreg + lay.o_at);
+    T* om = reinterpret_cast<T*>(wreg + lay.o_om);
+    T* scr = reinterpret_cast<T*>(wreg + lay.o_scr);
+    int* slot = reinterpret_cast<int*>(wreg + lay.o_slot);
+    T* cR = scr;                 // density chunk
+    T* cY = scr + 32 * NP;
+    T* U1 = scr;                 // nu = 3
+    T* P1 = reinterpret_cast<T*>(wreg + lay.o_scr + lay.o_p1);
+
+    const int a = a0 + warp;
+    const bool has = a < nexp;
+    const int i = has ? d.act_e[a] : 0;
     V* GE = reinterpret_cast<V*>(d.ge);
     V* GIN = reinterpret_cast<V*>(d.ge_in);
     const int stamp = d.status[SW_EPOCH];
-    const T rc2 = (T)d.rce2;
     const T rc = (T)tab.rc;
     const T invrc = T(1) / rc;
     const T invh = T(13) / rc;
-    const unsigned lt = (1u << lane) - 1u;
-    {
-        const int i = d.act_e[a];
-        const PairFrame<T> pf(d, i);
-        const int m = d.nnb[i];
-        const int* row = d.nbr + (int64_t)i * cap;
-        const int* rvr = d.rev + (int64_t)i * cap;
-        V* grow = GE + (int64_t)i * cap;
+    const int* row = d.nbr + (int64_t)i * cap;
+    const int* rvr = d.rev + (int64_t)i * cap;
+    V* grow = GE + (int64_t)i * cap;
+    T ep = T(0);
+    int nb = 0;
 
+    if (has) {
         // 1. neighbours inside the cutoff, ordered compaction
-        int nb = 0;
-        for (int base = 0; base < m; base += NT) {
-            const int s = base + tid;
+        const PairFrame<T> pf(d, i);
+        const T rc2 = (T)d.rce2;
+        const int m = d.nnb[i];
+        const unsigned lt = (1u << lane) - 1u;
+        for (int b0 = 0; b0 < m; b0 += 32) {
+            const int s = b0 + lane;
             bool ok = false;
             T dv[3] = {T(0), T(0), T(0)}, r2 = T(0);
             if (s < m) {
@@ -375,299 +540,193 @@ __device__ __forceinline__ void ace_atom(const Dev& d, const AceTab<T>& tab, int
                 }
             }
             const unsigned bal = __ballot_sync(0xffffffffu, ok);
-            if (lane == 0) s_wcnt[warp] = __popc(bal);
-            __syncthreads();
-            int off = nb, tot = 0;
-#pragma unroll
-            for (int w = 0; w < WN; ++w) {
-                if (w < warp) off += s_wcnt[w];
-                tot += s_wcnt[w];
-            }
             if (ok) {
-                const int k = off + __popc(bal & lt);
+                const int k = nb + __popc(bal & lt);
                 const T r = sqrt(r2), ir = T(1) / r;
-                s_slot[k] = s;
-                s_u[4 * k + 0] = dv[0] * ir;
-                s_u[4 * k + 1] = dv[1] * ir;
-                s_u[4 * k + 2] = dv[2] * ir;
-                s_u[4 * k + 3] = r;
+                slot[k] = s;
+                su[4 * k + 0] = dv[0] * ir;
+                su[4 * k + 1] = dv[1] * ir;
+                su[4 * k + 2] = dv[2] * ir;
+                su[4 * k + 3] = r;
             }
-            nb += tot;
-            __syncthreads();
+            nb += __popc(bal);
         }
+        __syncwarp();
 
-        // 2. density, neighbours in chunks
-        T ep = T(0);
-        T acc[NOUT];
+        // 2. density, 32 neighbours at a time
+        T acc[NUL][4];
 #pragma unroll
-        for (int j = 0; j < NOUT; ++j) acc[j] = T(0);
-        for (int k0 = 0; k0 < nb; k0 += ACE_CH) {
-            const int kc = nb - k0 < ACE_CH ? nb - k0 : ACE_CH;
-            for (int kl = tid; kl < kc; kl += NT) {
-                const int k = k0 + kl;
-                const T r = s_u[4 * k + 3];
+        for (int j = 0; j < NUL; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = T(0);
+        for (int k0 = 0; k0 < nb; k0 += 32) {
+            const int kc = nb - k0 < 32 ? nb - k0 : 32;
+            if (lane < kc) {
+                const int k = k0 + lane;
+                const T r = su[4 * k + 3];
                 T R[NP], dR[NP];
                 radial<T, NP>(r, invrc, n, R, dR);
 #pragma unroll
-                for (int p = 0; p < NP; ++p) s_cR[kl * NP + p] = R[p];
-                ylm_eval<T, L>(s_u[4 * k], s_u[4 * k + 1], s_u[4 * k + 2], tab.ylmk, s_cY + kl * NLM);
+                for (int p = 0; p < NP; ++p) cR[lane * NP + p] = R[p];
+                ylm_eval<T, L>(su[4 * k], su[4 * k + 1], su[4 * k + 2], tab.ylmk, cY + lane * NLM);
                 if (tab.has_pair) {
-                    T v, dv;
-                    spline16<T>(tab.pair, invh, r, v, dv);
+                    T v, dvv;
+                    spline16<T>(tab.pair, invh, r, v, dvv);
                     ep += T(0.5) * v;
                 }
             }
-            __syncthreads();
+            __syncwarp();
 #pragma unroll
-            for (int j = 0; j < NOUT; ++j) {
-                const int o = tid + j * NT;
-                if (o < NLM * NP) {
-                    const int lm = o / NP, q = o - lm * NP;
-                    T s = acc[j];
-                    for (int kl = 0; kl < kc; ++kl) s += s_cR[kl * NP + q] * s_cY[kl * NLM + lm];
-                    acc[j] = s;
+            for (int j = 0; j < NUL; ++j) {
+                const int u = lane + 32 * j;
+                if (u < NU) {
+                    const int lm = u / NQ4, q4 = (u - lm * NQ4) * 4;
+                    for (int kl = 0; kl < kc; ++kl) {
+                        const T y = cY[kl * NLM + lm];
+                        const V4<T> r4 = ld4<T>(cR + kl * NP + q4);
+                        acc[j][0] += y * r4.x;
+                        acc[j][1] += y * r4.y;
+                        acc[j][2] += y * r4.z;
+                        acc[j][3] += y * r4.w;
+                    }
                 }
             }
-            __syncthreads();
+            __syncwarp();
         }
 #pragma unroll
-        for (int j = 0; j < NOUT; ++j) {
-            const int o = tid + j * NT;
-            if (o < NLM * NP) s_At[o] = acc[j];
+        for (int j = 0; j < NUL; ++j) {
+            const int u = lane + 32 * j;
+            if (u < NU) {
+                const int lm = u / NQ4, q4 = (u - lm * NQ4) * 4;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) At[lm * NP + q4 + c] = acc[j][c];
+            }
         }
-        // the density chunks are dead: zero this warp's scratch (its padding,
-        // q >= n and q1 q2 >= n*n, is read as zeros below and never written)
-        for (int k = lane; k < lay.ws; k += 32) U1[k] = T(0);
-        __syncthreads();
+        __syncwarp();
 
         // 3. nu = 1 and nu = 2; initialises omega
-#pragma unroll
-        for (int j = 0; j < NOUT; ++j) {
-            const int o = tid + j * NT;
-            if (o < NLM * NP) {
-                const int lm = o / NP, q = o - lm * NP;
-                T val = T(0);
-                if (q < n) {
-                    int l = 0;
-                    while ((l + 1) * (l + 1) <= lm) ++l;
-                    if (tab.nu >= 2) {
-                        const T* S2 = tab.S2 + ((int64_t)l * n + q) * n;
-                        const T* Ar = s_At + lm * NP;
-                        for (int q2 = 0; q2 < n; ++q2) val += S2[q2] * Ar[q2];
+        for (int o = lane; o < NLM * NP; o += 32) {
+            const int lm = o / NP, q = o - lm * NP;
+            T val = T(0);
+            if (q < n) {
+                int l = 0;
+                while ((l + 1) * (l + 1) <= lm) ++l;
+                if (tab.nu >= 2) {
+                    const T* S2 = tab.S2 + ((int64_t)l * n + q) * n;
+                    const T* Ar = At + lm * NP;
+                    T v2 = T(0);
+                    int q2 = 0;
+                    for (; q2 + 1 < n; q2 += 2) {
+                        val += __ldg(S2 + q2) * Ar[q2];
+                        v2 += __ldg(S2 + q2 + 1) * Ar[q2 + 1];
                     }
-                    const T av = s_At[o];
-                    ep += T(0.5) * av * val;
-                    if (lm == 0) {
-                        const T c = tab.c1[q];
-                        ep += c * av;
-                        val += c;
-                    }
+                    if (q2 < n) val += __ldg(S2 + q2) * Ar[q2];
+                    val += v2;
                 }
-                s_om[o] = val;
+                const T av = At[o];
+                ep += T(0.5) * av * val;
+                if (lm == 0) {
+                    const T c = __ldg(tab.c1 + q);
+                    ep += c * av;
+                    val += c;
+                }
             }
+            om[o] = val;
         }
+        // the omega1 partials start at zero (each triple clears what it used)
+        if (ntau > 0)
+            for (int o = lane; o < D * n * (NP / tab.qb); o += 32) P1[o] = T(0);
+        __syncwarp();
+    }
 
-        // 4. nu = 3: this warp's l-triples
-        for (int it = tab.wt_off[warp]; it < tab.wt_off[warp + 1]; ++it) {
-            const int t = tab.wt_list[it];
-            const int l1 = tab.tau[4 * t], l2 = tab.tau[4 * t + 1], l3 = tab.tau[4 * t + 2];
-            const int gb = tab.tau[4 * t + 3];
-            // coinciding l's (W symmetrised on the host): scale instead of recompute
-            const int mode = tab.tmode[t];
-            const T mult1 = mode == 1 ? T(2) : T(1);
-            const T mult3 = mode == 3 ? T(3) : (mode == 2 ? T(2) : T(1));
-            const int d1 = 2 * l1 + 1, d2 = 2 * l2 + 1, d3 = 2 * l3 + 1;
-            const T* A1 = s_At + l1 * l1 * NP;
-            const T* A2 = s_At + l2 * l2 * NP;
-            const T* A3 = s_At + l3 * l3 * NP;
-            const int* g3o = tab.goff + gb;
-            const int* g1o = g3o + d3 + 1;
-            const int* g2o = g1o + d1 + 1;
-            const T* W = tab.W3 + (int64_t)t * n * n * NP;
-            const T* WT = tab.WT3 + (int64_t)t * n * nq;
-            if (mode == 3) nu3_uz<T, NP, QM, false>(W, A1, A2, A3, g3o, tab.gent, n, nq, d3, lane, U1, ZT, ep);
-            else if (tab.qb == QM) nu3_uz<T, NP, QM, true>(W, A1, A2, A3, g3o, tab.gent, n, nq, d3, lane, U1, ZT, ep);
-            else nu3_uz<T, NP, QM / 2, true>(W, A1, A2, A3, g3o, tab.gent, n, nq, d3, lane, U1, ZT, ep);
-            __syncwarp();
-            // omega3 += W^T Z
-            for (int o = lane; o < n * d3; o += 32) {
-                const int q3 = o / d3, m3 = o - q3 * d3;
-                const T* wr = WT + q3 * nq;
-                const T* zr = ZT + m3 * nq;
-                T s = T(0);
-                for (int p = 0; p < nq; p += 4) {
-                    const V4<T> a4 = ldg4<T>(wr + p);
-                    const V4<T> b4 = ld4<T>(zr + p);
-                    s += a4.x * b4.x + a4.y * b4.y + a4.z * b4.z + a4.w * b4.w;
-                }
-                omw[(l3 * l3 + m3) * NP + q3] += mult3 * s;
-                if (mode == 3) ep += A3[m3 * NP + q3] * s;
-            }
-            __syncwarp();
-            // omega1 += G A2 U (equal to omega3 when all three l's coincide)
-            // (lanes in m1-major order: lanes sharing m1 share the Gaunt loop and its loads)
-            if (mode != 3) for (int o = lane; o < n * d1; o += 32) {
-                const int m1 = o / n, q1 = o - m1 * n;
-                T accv = T(0);
-                for (int e = g1o[m1]; e < g1o[m1 + 1]; ++e) {
-                    int pk;
-                    T gv;
-                    ld_gent(tab.gent + e, pk, gv);
-                    const T* ar = A2 + (pk & 255) * NP;
-                    const T* ur = U1 + ((pk >> 8) * n + q1) * NP;
-                    T s = T(0);
+    // 4. nu = 3, tile by tile (every thread takes part in the copies and barriers)
+    for (int t = 0; t < ntau; ++t) {
+        cp_async_wait_all();
+        __syncthreads();   // tile t visible; every warp is done with the other buffer
+        if (t + 1 < ntau) tile_fetch(tab.tiles, tab.tile_off, t + 1, smem + ((t + 1) & 1) * lay.tile);
+        if (has) nu3_tile<T, NP>(smem + (t & 1) * lay.tile, tab, At, om, U1, P1, lane, ep);
+    }
+    if (ntau > 0) __syncthreads();   // both buffers free for the next group's first tile
+
+    if (has) {
+        // 5. pair gradients, a lane per neighbour
+        const T* K = tab.ylmk;
+        for (int k = lane; k < nb; k += 32) {
+            const T x = su[4 * k], y = su[4 * k + 1], z = su[4 * k + 2], r = su[4 * k + 3];
+            T R[NP], dR[NP];
+            radial<T, NP>(r, invrc, n, R, dR);
+            T Pi[(L + 1) * (L + 2) / 2], C[L + 1], S[L + 1];
+            legendre_tables<T, L>(x, y, z, Pi, C, S);
+            T sy = T(0), Gx = T(0), Gy = T(0), Gz = T(0);
+#pragma unroll
+            for (int l = 0; l <= L; ++l) {
+                const int pl = l * (l + 1) / 2;
+#pragma unroll
+                for (int mm = -l; mm <= l; ++mm) {
+                    const int lm = l * l + l + mm;
+                    const T* orow = om + lm * NP;
+                    T rho = T(0), sig = T(0);
 #pragma unroll
                     for (int p = 0; p < NP; p += 4) {
-                        const V4<T> a4 = ld4<T>(ar + p);
-                        const V4<T> b4 = ld4<T>(ur + p);
-                        s += a4.x * b4.x + a4.y * b4.y + a4.z * b4.z + a4.w * b4.w;
+                        const V4<T> o4 = ld4<T>(orow + p);
+                        rho += o4.x * R[p] + o4.y * R[p + 1] + o4.z * R[p + 2] + o4.w * R[p + 3];
+                        sig += o4.x * dR[p] + o4.y * dR[p + 1] + o4.z * dR[p + 2] + o4.w * dR[p + 3];
                     }
-                    accv += gv * s;
-                }
-                omw[(l1 * l1 + m1) * NP + q1] += mult1 * accv;
-            }
-            __syncwarp();
-            // omega2 += G A1 U, needed only when the three l's are distinct
-            // (otherwise it equals omega1 or omega3, already scaled in)
-            if (mode == 0) for (int o = lane; o < n * d2; o += 32) {
-                const int m2 = o / n, q2 = o - m2 * n;
-                T accv = T(0);
-                for (int e = g2o[m2]; e < g2o[m2 + 1]; ++e) {
-                    int pk;
-                    T gv;
-                    ld_gent(tab.gent + e, pk, gv);
-                    const T* ar = A1 + (pk & 255) * NP;
-                    const T* ur = U1 + (pk >> 8) * n * NP + q2;
-                    T s = T(0);
-                    for (int q1 = 0; q1 < n; ++q1) s += ar[q1] * ur[q1 * NP];
-                    accv += gv * s;
-                }
-                omw[(l2 * l2 + m2) * NP + q2] += accv;
-            }
-            __syncwarp();
-        }
-        __syncthreads();
-
-        // 5. omega = nu<=2 part + the warp copies, in a fixed order
-        for (int o = tid; o < NLM * NP; o += NT) {
-            T s = s_om[o];
-#pragma unroll
-            for (int w = 0; w < WN; ++w) s += sm[lay.o_w + w * lay.ws + D * n * NP + D * nq + o];
-            s_om[o] = s;
-        }
-        __syncthreads();
-
-        // 6. pair gradients: warp pair (2s, 2s+1) takes neighbours k0 + 32 s .. k0 + 32 s + 31;
-        //    the two warps of a pair split the lm sum by parity
-        const int half = warp & 1, sub = warp >> 1;
-        for (int k0 = 0; k0 < nb; k0 += PER) {
-            const int kl = sub * 32 + lane;
-            const int k = k0 + kl;
-            T sy = T(0), Gx = T(0), Gy = T(0), Gz = T(0);
-            if (k < nb) {
-                const T x = s_u[4 * k], y = s_u[4 * k + 1], z = s_u[4 * k + 2], r = s_u[4 * k + 3];
-                T R[NP], dR[NP];
-                radial<T, NP>(r, invrc, n, R, dR);
-                T Pi[(L + 1) * (L + 2) / 2], C[L + 1], S[L + 1];
-                legendre_tables<T, L>(x, y, z, Pi, C, S);
-                const T* K = tab.ylmk;
-#pragma unroll
-                for (int l = 0; l <= L; ++l) {
-                    const int pl = l * (l + 1) / 2;
-#pragma unroll
-                    for (int mm = -l; mm <= l; ++mm) {
-                        const int lm = l * l + l + mm;
-                        if ((lm & 1) != half) continue;
-                        const T* orow = s_om + lm * NP;
-                        T rho = T(0), sig = T(0);
-#pragma unroll
-                        for (int p = 0; p < NP; p += 4) {
-                            const V4<T> o4 = ld4<T>(orow + p);
-                            rho += o4.x * R[p] + o4.y * R[p + 1] + o4.z * R[p + 2] + o4.w * R[p + 3];
-                            sig += o4.x * dR[p] + o4.y * dR[p + 1] + o4.z * dR[p + 2] + o4.w * dR[p + 3];
-                        }
-                        const int mu = mm < 0 ? -mm : mm;
-                        const T kk = K[lm];
-                        const T p = Pi[pl + mu];
-                        const T pz = (mu < l) ? Pi[pl + mu + 1] : T(0);
-                        T yv, gx, gy, gz;
-                        if (mm == 0) {
-                            yv = kk * p;
-                            gx = T(0);
-                            gy = T(0);
-                            gz = kk * pz;
-                        } else if (mm > 0) {
-                            // p_{l,m} = K Pi C_m
-                            yv = kk * p * C[mu];
-                            gx = kk * p * T(mu) * C[mu - 1];
-                            gy = -kk * p * T(mu) * S[mu - 1];
-                            gz = kk * pz * C[mu];
-                        } else {
-                            // p_{l,-m} = K Pi S_m
-                            yv = kk * p * S[mu];
-                            gx = kk * p * T(mu) * S[mu - 1];
-                            gy = kk * p * T(mu) * C[mu - 1];
-                            gz = kk * pz * S[mu];
-                        }
-                        sy += sig * yv;
-                        Gx += rho * gx;
-                        Gy += rho * gy;
-                        Gz += rho * gz;
+                    const int mu = mm < 0 ? -mm : mm;
+                    const T kk = __ldg(K + lm);
+                    const T p = Pi[pl + mu];
+                    const T pz = (mu < l) ? Pi[pl + mu + 1] : T(0);
+                    T yv, gx, gy, gz;
+                    if (mm == 0) {
+                        yv = kk * p;
+                        gx = T(0);
+                        gy = T(0);
+                        gz = kk * pz;
+                    } else if (mm > 0) {
+                        // p_{l,m} = K Pi C_m
+                        yv = kk * p * C[mu];
+                        gx = kk * p * T(mu) * C[mu - 1];
+                        gy = -kk * p * T(mu) * S[mu - 1];
+                        gz = kk * pz * C[mu];
+                    } else {
+                        // p_{l,-m} = K Pi S_m
+                        yv = kk * p * S[mu];
+                        gx = kk * p * T(mu) * S[mu - 1];
+                        gy = kk * p * T(mu) * C[mu - 1];
+                        gz = kk * pz * S[mu];
                     }
+                    sy += sig * yv;
+                    Gx += rho * gx;
+                    Gy += rho * gy;
+                    Gz += rho * gz;
                 }
             }
-            T* gp = s_gp + (half * PER + kl) * 4;
-            gp[0] = sy;
-            gp[1] = Gx;
-            gp[2] = Gy;
-            gp[3] = Gz;
-            __syncthreads();
-            if (tid < PER && k0 + tid < nb) {
-                const int kk = k0 + tid;
-                const T* g0 = s_gp + tid * 4;
-                const T* g1 = s_gp + (PER + tid) * 4;
-                const T x = s_u[4 * kk], y = s_u[4 * kk + 1], z = s_u[4 * kk + 2], r = s_u[4 * kk + 3];
-                const T syt = g0[0] + g1[0];
-                const T gxt = g0[1] + g1[1], gyt = g0[2] + g1[2], gzt = g0[3] + g1[3];
-                const T ug = x * gxt + y * gyt + z * gzt;
-                const T ir = T(1) / r;
-                T g[3] = {syt * x + (gxt - x * ug) * ir, syt * y + (gyt - y * ug) * ir, syt * z + (gzt - z * ug) * ir};
-                if (tab.has_pair) {
-                    T v, dv;
-                    spline16<T>(tab.pair, invh, r, v, dv);
-                    const T hp = T(0.5) * dv;
-                    g[0] += hp * x;
-                    g[1] += hp * y;
-                    g[2] += hp * z;
-                }
-                V gv;
-                gv.x = g[0];
-                gv.y = g[1];
-                gv.z = g[2];
-                gv.w = T(0);
-                const int slot = s_slot[kk];
-                grow[slot] = gv;
-                gv.w = stamp_as(T(0), stamp);
-                GIN[(int64_t)row[slot] * cap + rvr[slot]] = gv;
+            const T ug = x * Gx + y * Gy + z * Gz;
+            const T ir = T(1) / r;
+            T g[3] = {sy * x + (Gx - x * ug) * ir, sy * y + (Gy - y * ug) * ir, sy * z + (Gz - z * ug) * ir};
+            if (tab.has_pair) {
+                T v, dv;
+                spline16<T>(tab.pair, invh, r, v, dv);
+                const T hp = T(0.5) * dv;
+                g[0] += hp * x;
+                g[1] += hp * y;
+                g[2] += hp * z;
             }
-            __syncthreads();
+            V gv;
+            gv.x = g[0];
+            gv.y = g[1];
+            gv.z = g[2];
+            gv.w = T(0);
+            const int sl = slot[k];
+            grow[sl] = gv;
+            gv.w = stamp_as(T(0), stamp);
+            GIN[(int64_t)row[sl] * cap + rvr[sl]] = gv;
         }
 
-        // site energy (float64, fixed reduction order)
-        const auto e = warp_sum(ep);   // fixed order; compensated for float
-        if constexpr (sizeof(T) == 4) {
-            // float64 conversion and the sum over warps happen in the gather
-            if (lane == 0) d.epark_e[(int64_t)i * WN + warp] = make_float2(e.s, e.c);
-        } else {
-            if (lane == 0) s_red[warp] = lane0_double(e);
-            __syncthreads();
-            if (tid == 0) {
-                double es = 0.0;
-                for (int w = 0; w < WN; ++w) es += s_red[w];
-                d.esite_e[i] = es;
-            }
+        // site energy: fixed reduction order, compensated for float
+        const auto e = warp_sum(ep);
+        if (lane == 0) {
+            if constexpr (sizeof(T) == 4) d.epark_e[i] = make_float2(e.s, e.c);   // float64 in the gather
+            else d.esite_e[i] = lane0_double(e);
         }
-        __syncthreads();
     }
 }
 
@@ -675,16 +734,14 @@ template <typename T, int L, int NP>
 __global__ void __launch_bounds__(ace_warps<T>() * 32, ace_min_ctas<T>()) k_ace(Dev d, AceTab<T> tab) {
     constexpr int WN = ace_warps<T>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int s_slot[MAX_CAP];
-    __shared__ int s_wcnt[WN];
-    __shared__ double s_red[WN];
     const int count = d.status[SW_NEXP];
-    for (int a = blockIdx.x; a < count; a += gridDim.x) ace_atom<T, L, NP>(d, tab, a, smem_raw, s_slot, s_wcnt, s_red);
+    const int ng = (count + WN - 1) / WN;
+    for (int g = blockIdx.x; g < ng; g += gridDim.x) ace_group<T, L, NP>(d, tab, g * WN, count, smem_raw);
 }
 
-// Many systems: walks the flattened list {system, index in its expensive list}
-// of one group of systems sharing (T, L, NP); the CTA reloads the system's Dev
-// and tables into shared memory when the system changes.
+// Many systems: walks the flattened list {system, first atom of a group} of
+// one group of systems sharing (T, L, NP); the CTA reloads the system's Dev and
+// tables into shared memory when the system changes.
 template <typename T>
 struct AceBatch {
     const Dev* devs;
@@ -695,11 +752,7 @@ struct AceBatch {
 
 template <typename T, int L, int NP>
 __global__ void __launch_bounds__(ace_warps<T>() * 32, ace_min_ctas<T>()) kb_ace(AceBatch<T> b) {
-    constexpr int WN = ace_warps<T>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int s_slot[MAX_CAP];
-    __shared__ int s_wcnt[WN];
-    __shared__ double s_red[WN];
     __shared__ Dev s_dev;
     __shared__ AceTab<T> s_tab;
     const int count = *b.count;
@@ -713,19 +766,19 @@ __global__ void __launch_bounds__(ace_warps<T>() * 32, ace_min_ctas<T>()) kb_ace
             __syncthreads();
             cur = e.x;
         }
-        ace_atom<T, L, NP>(s_dev, s_tab, e.y, smem_raw, s_slot, s_wcnt, s_red);
+        ace_group<T, L, NP>(s_dev, s_tab, e.y, s_dev.status[SW_NEXP], smem_raw);
     }
 }
 
+// launch shape: the shared memory of the layout, and as many resident CTAs as fit
 template <typename T, int L, int NP>
-inline cudaError_t ace_cfg(int n, int cap, size_t* smem, int* grid) {
-    const int nq = (n * n + 3) & ~3;
-    const AceSmem lay(cap, n, nq, L, NP, ace_warps<T>());
-    const size_t bytes = (size_t)lay.total * sizeof(T);
-    cudaError_t e = raise_smem_limit((const void*)k_ace<T, L, NP>, bytes);
+inline cudaError_t ace_shape(const void* kern, int n, int cap, int tile_max, int qb, size_t* smem, int* grid) {
+    const AceLay lay(tile_max, cap, n, qb, L, NP, (int)sizeof(T), ace_warps<T>());
+    const size_t bytes = (size_t)lay.total;
+    cudaError_t e = raise_smem_limit(kern, bytes);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ace<T, L, NP>, ace_warps<T>() * 32, bytes);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, ace_warps<T>() * 32, bytes);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     *smem = bytes;
@@ -733,26 +786,32 @@ inline cudaError_t ace_cfg(int n, int cap, size_t* smem, int* grid) {
     return cudaSuccess;
 }
 
+template <typename T, int L, int NP>
+inline cudaError_t ace_cfg(bool batch, int n, int cap, int tile_max, int qb, size_t* smem, int* grid) {
+    const void* kern = batch ? (const void*)kb_ace<T, L, NP> : (const void*)k_ace<T, L, NP>;
+    return ace_shape<T, L, NP>(kern, n, cap, tile_max, qb, smem, grid);
+}
+
 template <typename T, int NP>
-inline cudaError_t ace_cfg_l(int L, int n, int cap, size_t* smem, int* grid) {
+inline cudaError_t ace_cfg_l(bool batch, int L, int n, int cap, int tile_max, int qb, size_t* smem, int* grid) {
     switch (L) {
-        case 0: return ace_cfg<T, 0, NP>(n, cap, smem, grid);
-        case 1: return ace_cfg<T, 1, NP>(n, cap, smem, grid);
-        case 2: return ace_cfg<T, 2, NP>(n, cap, smem, grid);
-        case 3: return ace_cfg<T, 3, NP>(n, cap, smem, grid);
-        case 4: return ace_cfg<T, 4, NP>(n, cap, smem, grid);
-        case 5: return ace_cfg<T, 5, NP>(n, cap, smem, grid);
-        case 6: return ace_cfg<T, 6, NP>(n, cap, smem, grid);
+        case 0: return ace_cfg<T, 0, NP>(batch, n, cap, tile_max, qb, smem, grid);
+        case 1: return ace_cfg<T, 1, NP>(batch, n, cap, tile_max, qb, smem, grid);
+        case 2: return ace_cfg<T, 2, NP>(batch, n, cap, tile_max, qb, smem, grid);
+        case 3: return ace_cfg<T, 3, NP>(batch, n, cap, tile_max, qb, smem, grid);
+        case 4: return ace_cfg<T, 4, NP>(batch, n, cap, tile_max, qb, smem, grid);
+        case 5: return ace_cfg<T, 5, NP>(batch, n, cap, tile_max, qb, smem, grid);
+        case 6: return ace_cfg<T, 6, NP>(batch, n, cap, tile_max, qb, smem, grid);
     }
     return cudaErrorInvalidValue;
 }
 
 template <typename T>
-inline cudaError_t ace_cfg_t(int L, int n, int cap, size_t* smem, int* grid) {
-    if (n <= 4) return ace_cfg_l<T, 4>(L, n, cap, smem, grid);
-    if (n <= 8) return ace_cfg_l<T, 8>(L, n, cap, smem, grid);
-    if (n <= 12) return ace_cfg_l<T, 12>(L, n, cap, smem, grid);
-    return ace_cfg_l<T, 16>(L, n, cap, smem, grid);
+inline cudaError_t ace_cfg_t(bool batch, int L, int n, int cap, int tile_max, int qb, size_t* smem, int* grid) {
+    if (n <= 4) return ace_cfg_l<T, 4>(batch, L, n, cap, tile_max, qb, smem, grid);
+    if (n <= 8) return ace_cfg_l<T, 8>(batch, L, n, cap, tile_max, qb, smem, grid);
+    if (n <= 12) return ace_cfg_l<T, 12>(batch, L, n, cap, tile_max, qb, smem, grid);
+    return ace_cfg_l<T, 16>(batch, L, n, cap, tile_max, qb, smem, grid);
 }
 
 template <typename T, int NP>
@@ -768,43 +827,12 @@ inline void ace_launch_l(const Dev& d, const AceTab<T>& tab, int L, size_t smem,
     }
 }
 
-// multi-system launches of one (T, L, NP) group
-template <typename T, int L, int NP>
-inline cudaError_t ace_batch_cfg(int n, int cap, size_t* smem, int* grid) {
-    const int nq = (n * n + 3) & ~3;
-    const AceSmem lay(cap, n, nq, L, NP, ace_warps<T>());
-    const size_t bytes = (size_t)lay.total * sizeof(T);
-    cudaError_t e = raise_smem_limit((const void*)kb_ace<T, L, NP>, bytes);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kb_ace<T, L, NP>, ace_warps<T>() * 32, bytes);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    *smem = bytes;
-    *grid = per_sm * sm_count();
-    return cudaSuccess;
-}
-
-template <typename T, int NP>
-inline cudaError_t ace_batch_cfg_l(int L, int n, int cap, size_t* smem, int* grid) {
-    switch (L) {
-        case 0: return ace_batch_cfg<T, 0, NP>(n, cap, smem, grid);
-        case 1: return ace_batch_cfg<T, 1, NP>(n, cap, smem, grid);
-        case 2: return ace_batch_cfg<T, 2, NP>(n, cap, smem, grid);
-        case 3: return ace_batch_cfg<T, 3, NP>(n, cap, smem, grid);
-        case 4: return ace_batch_cfg<T, 4, NP>(n, cap, smem, grid);
-        case 5: return ace_batch_cfg<T, 5, NP>(n, cap, smem, grid);
-        case 6: return ace_batch_cfg<T, 6, NP>(n, cap, smem, grid);
-    }
-    return cudaErrorInvalidValue;
-}
-
 template <typename T>
-inline cudaError_t ace_batch_cfg_t(int L, int n, int cap, size_t* smem, int* grid) {
-    if (n <= 4) return ace_batch_cfg_l<T, 4>(L, n, cap, smem, grid);
-    if (n <= 8) return ace_batch_cfg_l<T, 8>(L, n, cap, smem, grid);
-    if (n <= 12) return ace_batch_cfg_l<T, 12>(L, n, cap, smem, grid);
-    return ace_batch_cfg_l<T, 16>(L, n, cap, smem, grid);
+inline void ace_launch_t(const Dev& d, const AceTab<T>& tab, int L, size_t smem, int grid, cudaStream_t s) {
+    if (tab.np == 4) ace_launch_l<T, 4>(d, tab, L, smem, grid, s);
+    else if (tab.np == 8) ace_launch_l<T, 8>(d, tab, L, smem, grid, s);
+    else if (tab.np == 12) ace_launch_l<T, 12>(d, tab, L, smem, grid, s);
+    else ace_launch_l<T, 16>(d, tab, L, smem, grid, s);
 }
 
 template <typename T, int NP>
@@ -826,14 +854,6 @@ inline void ace_batch_launch_t(const AceBatch<T>& b, int n, int L, size_t smem, 
     else if (n <= 8) ace_batch_launch_l<T, 8>(b, L, smem, grid, s);
     else if (n <= 12) ace_batch_launch_l<T, 12>(b, L, smem, grid, s);
     else ace_batch_launch_l<T, 16>(b, L, smem, grid, s);
-}
-
-template <typename T>
-inline void ace_launch_t(const Dev& d, const AceTab<T>& tab, int L, size_t smem, int grid, cudaStream_t s) {
-    if (tab.np == 4) ace_launch_l<T, 4>(d, tab, L, smem, grid, s);
-    else if (tab.np == 8) ace_launch_l<T, 8>(d, tab, L, smem, grid, s);
-    else if (tab.np == 12) ace_launch_l<T, 12>(d, tab, L, smem, grid, s);
-    else ace_launch_l<T, 16>(d, tab, L, smem, grid, s);
 }
 
 }  // namespace mixd

@@ -4,16 +4,16 @@
 
 namespace mixd {
 
-cudaError_t ace_configure_f64(int L, int n, int cap, size_t* smem, int* grid) {
-    return ace_cfg_t<double>(L, n, cap, smem, grid);
+cudaError_t ace_configure_f64(int L, int n, int cap, int tile_max, int qb, size_t* smem, int* grid) {
+    return ace_cfg_t<double>(false, L, n, cap, tile_max, qb, smem, grid);
 }
 
 void launch_ace_f64(const Dev& d, const void* tab, int L, size_t smem, int grid, cudaStream_t s) {
     ace_launch_t<double>(d, *static_cast<const AceTab<double>*>(tab), L, smem, grid, s);
 }
 
-cudaError_t ace_batch_configure_f64(int L, int n, int cap, size_t* smem, int* grid) {
-    return ace_batch_cfg_t<double>(L, n, cap, smem, grid);
+cudaError_t ace_batch_configure_f64(int L, int n, int cap, int tile_max, int qb, size_t* smem, int* grid) {
+    return ace_cfg_t<double>(true, L, n, cap, tile_max, qb, smem, grid);
 }
 
 void launch_ace_batch_f64(const Dev* devs, const void* tabs, const int2* list, const int* count, int n, int L,
@@ -22,9 +22,10 @@ void launch_ace_batch_f64(const Dev* devs, const void* tabs, const int2* list, c
     ace_batch_launch_t<double>(b, n, L, smem, grid, s);
 }
 
-cudaError_t ace_configure(int precision, int L, int n, int cap, size_t* smem, int* grid) {
-    if (cap > MAX_CAP || n > 16) return cudaErrorInvalidValue;
-    return precision == MIX_FP64 ? ace_configure_f64(L, n, cap, smem, grid) : ace_configure_f32(L, n, cap, smem, grid);
+cudaError_t ace_configure(int precision, int L, int n, int cap, int tile_max, int qb, size_t* smem, int* grid) {
+    if (cap > MAX_CAP || n > 16 || qb < 1) return cudaErrorInvalidValue;
+    return precision == MIX_FP64 ? ace_configure_f64(L, n, cap, tile_max, qb, smem, grid)
+                                 : ace_configure_f32(L, n, cap, tile_max, qb, smem, grid);
 }
 
 void launch_ace(const Dev& d, const void* tab, int precision, int L, size_t smem, int grid, cudaStream_t s) {
@@ -36,10 +37,10 @@ void launch_ace(const Dev& d, const void* tab, int precision, int L, size_t smem
 
 namespace mixd {
 
-cudaError_t ace_batch_configure(int precision, int L, int n, int cap, size_t* smem, int* grid) {
-    if (cap > MAX_CAP || n > 16) return cudaErrorInvalidValue;
-    return precision == MIX_FP64 ? ace_batch_configure_f64(L, n, cap, smem, grid)
-                                 : ace_batch_configure_f32(L, n, cap, smem, grid);
+cudaError_t ace_batch_configure(int precision, int L, int n, int cap, int tile_max, int qb, size_t* smem, int* grid) {
+    if (cap > MAX_CAP || n > 16 || qb < 1) return cudaErrorInvalidValue;
+    return precision == MIX_FP64 ? ace_batch_configure_f64(L, n, cap, tile_max, qb, smem, grid)
+                                 : ace_batch_configure_f32(L, n, cap, tile_max, qb, smem, grid);
 }
 
 void launch_ace_batch(int precision, const Dev* devs, const void* tabs, const int2* list, const int* count, int n,

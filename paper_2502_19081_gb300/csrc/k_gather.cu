@@ -117,9 +117,8 @@ __device__ __forceinline__ void gather_body(const Dev& d, int bx, int gx, int in
                 const int fl = d.flags[k];
                 double ee = 0.0, ec = 0.0;
                 if (fl & 4) {
-                    const float2* pe = d.epark_e + k * ace_warps<T>();
-#pragma unroll
-                    for (int q = 0; q < ace_warps<T>(); ++q) ee += (double)pe[q].x + (double)pe[q].y;
+                    const float2 pe = d.epark_e[k];
+                    ee = (double)pe.x + (double)pe.y;
                 }
                 if (fl & 8) {
                     const float2 pc = d.epark_c[k];

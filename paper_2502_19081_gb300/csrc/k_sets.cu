@@ -347,10 +347,11 @@ __global__ void __launch_bounds__(SCAN_BLOCK) kb_scatter(BatchArgs ba) {
 }
 
 // Flattened lists of the evaluated atoms of every system: block s writes
-// {s, k} for k below its expensive (cheap) count at the sum of the counts of
-// the systems before it (within its expensive group; all systems for cheap).
-// The last system of a group writes the group's total; the last system the
-// cheap total.
+// {s, k} for k below its cheap count, and {s, ACE_GROUP k} for each group of
+// ACE_GROUP consecutive atoms of its expensive list (a CTA of the expensive
+// kernel takes one such group), at the sum of the counts of the systems before
+// it (within its expensive group; all systems for cheap).  The last system of
+// a group writes the group's total; the last system the cheap total.
 __global__ void kb_flatten(FlatArgs f) {
     __shared__ int red[2][32];
     const int s = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -358,7 +359,7 @@ __global__ void kb_flatten(FlatArgs f) {
     int oe = 0, oc = 0;
     for (int t = tid; t < s; t += blockDim.x) {
         const int* st = f.devs[t].status;
-        if (f.egroup[t] == g) oe += st[SW_NEXP];
+        if (f.egroup[t] == g) oe += (st[SW_NEXP] + ACE_GROUP - 1) / ACE_GROUP;
         oc += st[SW_NCHEAP];
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -377,10 +378,10 @@ __global__ void kb_flatten(FlatArgs f) {
         oc += red[1][w];
     }
     const int* st = f.devs[s].status;
-    const int ne = st[SW_NEXP], nc = st[SW_NCHEAP];
+    const int ne = (st[SW_NEXP] + ACE_GROUP - 1) / ACE_GROUP, nc = st[SW_NCHEAP];
     int2* le = f.list_e + f.ebase[g] + oe;
     int2* lc = f.list_c + oc;
-    for (int k = tid; k < ne; k += blockDim.x) le[k] = make_int2(s, k);
+    for (int k = tid; k < ne; k += blockDim.x) le[k] = make_int2(s, k * ACE_GROUP);
     for (int k = tid; k < nc; k += blockDim.x) lc[k] = make_int2(s, k);
     if (tid == 0) {
         if (f.elast[s]) f.counts[g] = oe + ne;

@@ -114,14 +114,56 @@ std::vector<T> conv(const std::vector<double>& v) {
     return std::vector<T>(v.begin(), v.end());
 }
 
+// The nu = 3 tables as one tile per l-triple (layout in AceTileHdr): W3 holds
+// the symmetrised coefficients [t][q1 q2][q3], tau the triples (l1, l2, l3,
+// first offset row), goff/gidx/gval the Gaunt entries in three orderings.
 template <typename T>
-std::vector<GEnt<T>> gaunt_entries(const std::vector<int>& idx, const std::vector<double>& val) {
-    std::vector<GEnt<T>> out(idx.size());
-    for (size_t k = 0; k < idx.size(); ++k) {
-        std::memset(&out[k], 0, sizeof(GEnt<T>));
-        out[k].pk = idx[k];
-        out[k].g = (T)val[k];
+std::vector<unsigned char> ace_tiles(int n, int np, const std::vector<int>& tau, const std::vector<int>& tmode,
+                                     const std::vector<int>& goff, const std::vector<int>& gidx,
+                                     const std::vector<double>& gval, const std::vector<double>& W3,
+                                     std::vector<int>& off, int& tile_max) {
+    const int ntau = (int)(tau.size() / 4);
+    std::vector<unsigned char> out;
+    off.assign(ntau + 1, 0);
+    tile_max = 0;
+    for (int t = 0; t < ntau; ++t) {
+        const int l1 = tau[4 * t], l2 = tau[4 * t + 1], l3 = tau[4 * t + 2], gb = tau[4 * t + 3];
+        const int rows = (2 * l3 + 2) + (2 * l1 + 2) + (2 * l2 + 2);
+        const int e0 = goff[gb], ne = goff[gb + rows - 1] - e0;
+        AceTileHdr h;
+        h.l1 = l1;
+        h.l2 = l2;
+        h.l3 = l3;
+        h.mode = tmode[t];
+        size_t o = sizeof(AceTileHdr) + (size_t)n * n * np * sizeof(T);
+        h.o_ge = (int)o;
+        o += (size_t)ne * sizeof(GEnt<T>);
+        h.o_go = (int)o;
+        o += (size_t)rows * sizeof(int);
+        o = (o + 15) & ~(size_t)15;
+        h.bytes = (int)o;
+        h.pad = 0;
+        std::vector<unsigned char> tile(o, 0);
+        std::memcpy(tile.data(), &h, sizeof h);
+        T* W = reinterpret_cast<T*>(tile.data() + sizeof(AceTileHdr));
+        for (int q12 = 0; q12 < n * n; ++q12)
+            for (int q3 = 0; q3 < n; ++q3) W[(size_t)q12 * np + q3] = (T)W3[((size_t)t * n * n + q12) * n + q3];
+        for (int k = 0; k < ne; ++k) {
+            GEnt<T> g;
+            std::memset(&g, 0, sizeof g);
+            g.pk = gidx[e0 + k];
+            g.g = (T)gval[e0 + k];
+            std::memcpy(tile.data() + h.o_ge + (size_t)k * sizeof g, &g, sizeof g);
+        }
+        for (int r = 0; r < rows; ++r) {
+            const int v = goff[gb + r] - e0;
+            std::memcpy(tile.data() + h.o_go + (size_t)r * sizeof(int), &v, sizeof v);
+        }
+        off[t] = (int)out.size();
+        out.insert(out.end(), tile.begin(), tile.end());
+        tile_max = std::max(tile_max, (int)o);
     }
+    off[ntau] = (int)out.size();
     return out;
 }
 
@@ -146,9 +188,8 @@ struct mix_ctx {
     int cap;
     // tables (offsets in the arena) and their element-type views
     Arena arena;
-    size_t o_c1, o_S2, o_W3, o_WT3, o_tau, o_goff, o_gent, o_ylmk, o_pair, o_sc2, o_sc3, o_wtoff, o_wtlist,
-        o_tmode;
-    int ntau, np, nq, qb;
+    size_t o_c1, o_S2, o_tiles, o_toff, o_ylmk, o_pair, o_sc2, o_sc3;
+    int ntau, np, nq, qb, tile_max;
     AceTab<double> ace64;
     AceTab<float> ace32;
     SplTab<double> spl64;
@@ -361,39 +402,6 @@ int build_tables(mix_ctx* c, const mix_ace* a, const mix_spline* sp) {
         if (tmode[t] == 0) f += 2.0 * nnz * nn * nn;
         c->nu3_flops += f;
     }
-    std::vector<double> W3p((size_t)c->ntau * n * n * np, 0.0), WT3((size_t)c->ntau * n * nq, 0.0);
-    for (int t = 0; t < c->ntau; ++t)
-        for (int q12 = 0; q12 < n * n; ++q12)
-            for (int q3 = 0; q3 < n; ++q3) {
-                const double w = W3[((size_t)t * n * n + q12) * n + q3];
-                W3p[((size_t)t * n * n + q12) * np + q3] = w;
-                WT3[((size_t)t * n + q3) * nq + q12] = w;
-            }
-    // l-triples to warps, longest first onto the least loaded warp
-    std::vector<std::pair<double, int>> cost;
-    for (int t = 0; t < c->ntau; ++t) {
-        const int l1 = tau[4 * t], l2 = tau[4 * t + 1], l3 = tau[4 * t + 2], gb = tau[4 * t + 3];
-        const double nnz = goff[gb + 2 * l3 + 1] - goff[gb];
-        const double cst = 4.0 * n * n * n * (2 * l3 + 1) + 6.0 * n * n * nnz + (double)n * n * (2 * l1 + 2 * l2 + 2);
-        cost.push_back({cst, t});
-    }
-    std::sort(cost.begin(), cost.end(), [](const std::pair<double, int>& x, const std::pair<double, int>& y) {
-        return x.first > y.first || (x.first == y.first && x.second < y.second);
-    });
-    const int warps = c->precision == MIX_FP64 ? ace_warps<double>() : ace_warps<float>();
-    std::vector<std::vector<int>> per(warps);
-    std::vector<double> load(warps, 0.0);
-    for (auto& ct : cost) {
-        int w = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-        per[w].push_back(ct.second);
-        load[w] += ct.first;
-    }
-    std::vector<int> wt_off(warps + 1, 0), wt_list;
-    for (int w = 0; w < warps; ++w) {
-        wt_off[w] = (int)wt_list.size();
-        for (int t : per[w]) wt_list.push_back(t);
-    }
-    wt_off[warps] = (int)wt_list.size();
     // q2 block of the U/Z pass: the largest block (4 float, 2 float64) or half
     // of it, whichever fills the warp's lanes better over n * np / qb units
     {
@@ -411,14 +419,13 @@ int build_tables(mix_ctx* c, const mix_ace* a, const mix_spline* sp) {
     if (a->pair) pair.assign(a->pair, a->pair + 16);
     std::vector<double> sc2(sp->c2, sp->c2 + 16), sc3(sp->c3, sp->c3 + 512);
 
+    std::vector<int> toff;
     Arena& A = c->arena;
     A.bytes.clear();
     if (c->precision == MIX_FP64) {
         c->o_c1 = A.put(c1);
         c->o_S2 = A.put(S2);
-        c->o_W3 = A.put(W3p);
-        c->o_WT3 = A.put(WT3);
-        c->o_gent = A.put(gaunt_entries<double>(gidx, gval));
+        c->o_tiles = A.put(ace_tiles<double>(n, np, tau, tmode, goff, gidx, gval, W3, toff, c->tile_max));
         c->o_ylmk = A.put(ylmk);
         c->o_pair = A.put(pair);
         c->o_sc2 = A.put(sc2);
@@ -426,19 +433,13 @@ int build_tables(mix_ctx* c, const mix_ace* a, const mix_spline* sp) {
     } else {
         c->o_c1 = A.put(conv<float>(c1));
         c->o_S2 = A.put(conv<float>(S2));
-        c->o_W3 = A.put(conv<float>(W3p));
-        c->o_WT3 = A.put(conv<float>(WT3));
-        c->o_gent = A.put(gaunt_entries<float>(gidx, gval));
+        c->o_tiles = A.put(ace_tiles<float>(n, np, tau, tmode, goff, gidx, gval, W3, toff, c->tile_max));
         c->o_ylmk = A.put(conv<float>(ylmk));
         c->o_pair = A.put(conv<float>(pair));
         c->o_sc2 = A.put(conv<float>(sc2));
         c->o_sc3 = A.put(conv<float>(sc3));
     }
-    c->o_tau = A.put(tau);
-    c->o_goff = A.put(goff);
-    c->o_wtoff = A.put(wt_off);
-    c->o_wtlist = A.put(wt_list);
-    c->o_tmode = A.put(tmode);
+    c->o_toff = A.put(toff);
     A.bytes.resize(align256(A.bytes.size()));
     return MIX_OK;
 }
@@ -455,14 +456,9 @@ void fill_tabs(mix_ctx* c, unsigned char* base, AceTab<T>& at, SplTab<T>& st) {
     at.rc = c->ace_rc;
     at.c1 = reinterpret_cast<const T*>(base + c->o_c1);
     at.S2 = reinterpret_cast<const T*>(base + c->o_S2);
-    at.W3 = reinterpret_cast<const T*>(base + c->o_W3);
-    at.WT3 = reinterpret_cast<const T*>(base + c->o_WT3);
-    at.wt_off = reinterpret_cast<const int*>(base + c->o_wtoff);
-    at.wt_list = reinterpret_cast<const int*>(base + c->o_wtlist);
-    at.tmode = reinterpret_cast<const int*>(base + c->o_tmode);
-    at.tau = reinterpret_cast<const int*>(base + c->o_tau);
-    at.goff = reinterpret_cast<const int*>(base + c->o_goff);
-    at.gent = reinterpret_cast<const GEnt<T>*>(base + c->o_gent);
+    at.tiles = base + c->o_tiles;
+    at.tile_off = reinterpret_cast<const int*>(base + c->o_toff);
+    at.tile_max = c->tile_max;
     at.qb = c->qb;
     at.ylmk = reinterpret_cast<const T*>(base + c->o_ylmk);
     at.pair = reinterpret_cast<const T*>(base + c->o_pair);
@@ -515,7 +511,7 @@ void layout(mix_ctx* c) {
     c->o_gci = take(N * cap * v4);
     c->o_ee = take(N * 8);
     c->o_ec = take(N * 8);
-    c->o_pe = take(N * 4 * sizeof(float2));
+    c->o_pe = take(N * sizeof(float2));
     c->o_pc = take(N * sizeof(float2));
     c->o_seed = take(N);
     c->o_core = take(N);
@@ -762,7 +758,7 @@ int mix_init(const mix_system* sys, const mix_ace* a, const mix_spline* sp, cons
         return st;
     }
     layout(c);
-    cudaError_t e = ace_configure(c->precision, c->L, c->n, c->cap, &c->ace_smem, &c->ace_grid);
+    cudaError_t e = ace_configure(c->precision, c->L, c->n, c->cap, c->tile_max, c->qb, &c->ace_smem, &c->ace_grid);
     if (e != cudaSuccess) {
         delete c;
         return MIX_ECUDA;
@@ -1276,7 +1272,7 @@ struct mix_batch {
     BatchPlan plan{};
     int precision = 0;
     struct Group {
-        int L, n, cap;
+        int L, n, cap, tile_max, qb;   // qb: the smallest unit block of the members
         size_t base, smem;
         int grid;
     };
@@ -1376,12 +1372,14 @@ int fused_build(mix_batch* b) {
         for (size_t k = 0; k < b->groups.size(); ++k)
             if (b->groups[k].L == c->L && npad(b->groups[k].n) == npad(c->n)) g = (int)k;
         if (g < 0) {
-            b->groups.push_back({c->L, c->n, c->cap, 0, 0, 0});
+            b->groups.push_back({c->L, c->n, c->cap, c->tile_max, c->qb, 0, 0, 0});
             gatoms.push_back(0);
             g = (int)b->groups.size() - 1;
         }
         b->groups[g].n = std::max(b->groups[g].n, c->n);
         b->groups[g].cap = std::max(b->groups[g].cap, c->cap);
+        b->groups[g].tile_max = std::max(b->groups[g].tile_max, c->tile_max);
+        b->groups[g].qb = std::min(b->groups[g].qb, c->qb);
         gatoms[g] += c->sys.n_atoms;
         egroup[s] = g;
     }
@@ -1480,7 +1478,7 @@ int fused_build(mix_batch* b) {
     F.counts = reinterpret_cast<int*>(base + o_cnt);
     // launch shapes of the potentials
     for (mix_batch::Group& g : b->groups) {
-        e = ace_batch_configure(b->precision, g.L, g.n, g.cap, &g.smem, &g.grid);
+        e = ace_batch_configure(b->precision, g.L, g.n, g.cap, g.tile_max, g.qb, &g.smem, &g.grid);
         if (e != cudaSuccess) return bfail(b, MIX_ECUDA, std::string("fused expensive kernel: ") + cudaGetErrorString(e));
     }
     // identical cheap tables in every member: the fused kernel stages them once per block

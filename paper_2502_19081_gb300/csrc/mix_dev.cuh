@@ -133,9 +133,9 @@ struct Dev {
     void* gc_in;         //   w = the evaluation (epoch) that wrote it; same for the cheap potential
     double* esite_e;
     double* esite_c;
-    // float path: the compensated (sum, correction) pairs of the site energies,
-    // per warp of the expensive kernel ([N][4]) and for the cheap one ([N]);
-    // the gather turns them into float64 site energies 32 atoms at a time
+    // float path: the compensated (sum, correction) pairs of the site energies
+    // of the two potentials ([N] each); the gather turns them into float64 site
+    // energies 32 atoms at a time
     float2* epark_e;
     float2* epark_c;
     uint8_t* seed;       // [N] seed atoms (seed-atom weights)
@@ -201,16 +201,20 @@ template <> struct Vec4<double> { using type = double4; };
 template <> struct Vec4<float> { using type = float4; };
 
 // Expensive-potential tables in the workspace (element type T).
-// Warps per CTA of the expensive kernel (both element types), and the CTAs per
-// SM the float kernel is compiled for: 5 x 4 warps (registers capped at 102 a
-// thread, shared memory ~43 KB a CTA) measured faster than 2 x 8 or 4 x 4.
+// Warps per CTA of the expensive kernel (both element types) = atoms per CTA
+// group (a warp per atom), and the CTAs per SM each kernel is compiled for.
+// Two atoms a CTA spread a small expensive set evenly over the SMs (1396
+// atoms: at most 10 a SM against 12 with groups of 4); the float kernel's
+// ~36 KB of shared memory a CTA (Fe, n = 10, lmax = 4, 128 neighbour slots)
+// leaves room for 6 CTAs, the float64 kernel's ~71 KB for 3.
+constexpr int ACE_GROUP = 2;
 template <typename T>
 __host__ __device__ constexpr int ace_warps() {
-    return 4;
+    return ACE_GROUP;
 }
 template <typename T>
 __host__ __device__ constexpr int ace_min_ctas() {
-    return sizeof(T) == 4 ? 5 : 1;
+    return sizeof(T) == 4 ? 6 : 2;
 }
 
 // One Gaunt coefficient with the packed m indices of its two other factors
@@ -221,25 +225,32 @@ struct __align__(sizeof(T) == 4 ? 8 : 16) GEnt {
     T g;
 };
 
+// Header of one l-triple tile of the nu = 3 tables.  A tile is one contiguous,
+// 16-byte aligned block (a multiple of 16 bytes) holding, at these byte offsets:
+//   W[q1 q2][q3]  (n*n rows of np, zero padded) right after the header,
+//   the Gaunt entries GEnt<T> in three orderings (by m3: m1 | m2 << 8 with m1
+//     ascending, by m1: m2 | m3 << 8, by m2: m1 | m3 << 8) at o_ge,
+//   their offset rows (per ordering 2l+2 ints: the first entry of each m, then
+//     the end; entry indices relative to o_ge) at o_go.
+// mode: 0 l's distinct, 1 l1 == l2, 2 l2 == l3, 3 all equal (W symmetrised over
+// the matching n indices).
+struct AceTileHdr {
+    int l1, l2, l3, mode;
+    int o_ge, o_go, bytes, pad;
+};
+
 template <typename T>
 struct AceTab {
     int n, L, nu, nlm, ntau;
     int np;             // n rounded up to a multiple of 4 (row length of padded tables)
     int nq;             // n*n rounded up to a multiple of 4
     int qb;             // q2 block per lane in the nu = 3 U/Z pass (divides np)
+    int tile_max;       // bytes of the largest nu = 3 tile
     double rc;
     const T* c1;        // [n]
     const T* S2;        // [L+1][n][n]  symmetric: W2 + W2^T, W2 upper-triangular c2
-    const T* W3;        // [ntau][n*n][np]  masked nu=3 coefficients W[q1 q2][q3], zero padded
-    const T* WT3;       // [ntau][n][nq]    the same, transposed: W[q3][q1 q2]
-    const int* wt_off;  // [warps + 1] ranges of wt_list handled by each warp
-    const int* wt_list; // [ntau] l-triple indices grouped by warp
-    const int* tmode;   // [ntau] 0: l's distinct, 1: l1 == l2, 2: l2 == l3, 3: all equal
-                        // (W3 symmetrised over the matching n indices)
-    const int* tau;     // [ntau][4]: l1, l2, l3, index of its first offset row
-    const int* goff;    // offset rows: for each tau, three orderings (by m3, m1, m2),
-                        // each 2l+2 entries (start index per m, then end)
-    const GEnt<T>* gent;  // [nnz] Gaunt coefficients in those orderings
+    const unsigned char* tiles;  // the ntau l-triple tiles, back to back
+    const int* tile_off;         // [ntau + 1] byte offset of each tile, then the end
     const T* ylmk;      // [nlm] normalisation of Y_lm times sqrt2 for m != 0
     const T* pair;      // [16] pair-term B-spline coefficients
     int has_pair;

@@ -14,10 +14,10 @@ void launch_sets(const Dev& d, const Regions& r, const SeedRule& sr, cudaStream_
 int sets_launches(const SeedRule& sr);   // kernels launch_sets enqueues
 
 // expensive potential (k_ace.cuh, k_ace_f32.cu, k_ace_f64.cu); returns cudaSuccess or the launch error
-cudaError_t ace_configure(int precision, int L, int n, int cap, size_t* smem, int* grid);
+cudaError_t ace_configure(int precision, int L, int n, int cap, int tile_max, int qb, size_t* smem, int* grid);
 void launch_ace(const Dev& d, const void* tab, int precision, int L, size_t smem, int grid, cudaStream_t s);
-cudaError_t ace_configure_f32(int L, int n, int cap, size_t* smem, int* grid);
-cudaError_t ace_configure_f64(int L, int n, int cap, size_t* smem, int* grid);
+cudaError_t ace_configure_f32(int L, int n, int cap, int tile_max, int qb, size_t* smem, int* grid);
+cudaError_t ace_configure_f64(int L, int n, int cap, int tile_max, int qb, size_t* smem, int* grid);
 void launch_ace_f32(const Dev& d, const void* tab, int L, size_t smem, int grid, cudaStream_t s);
 void launch_ace_f64(const Dev& d, const void* tab, int L, size_t smem, int grid, cudaStream_t s);
 
@@ -66,9 +66,9 @@ struct BatchPlan {
 void launch_disp_batch(const BatchPlan& p, cudaStream_t s, int integrate, double dt, int force_rebuild);
 void launch_build_batch(const BatchPlan& p, cudaStream_t s);
 void launch_sets_batch(const BatchPlan& p, cudaStream_t s);
-cudaError_t ace_batch_configure(int precision, int L, int n, int cap, size_t* smem, int* grid);
-cudaError_t ace_batch_configure_f32(int L, int n, int cap, size_t* smem, int* grid);
-cudaError_t ace_batch_configure_f64(int L, int n, int cap, size_t* smem, int* grid);
+cudaError_t ace_batch_configure(int precision, int L, int n, int cap, int tile_max, int qb, size_t* smem, int* grid);
+cudaError_t ace_batch_configure_f32(int L, int n, int cap, int tile_max, int qb, size_t* smem, int* grid);
+cudaError_t ace_batch_configure_f64(int L, int n, int cap, int tile_max, int qb, size_t* smem, int* grid);
 void launch_ace_batch(int precision, const Dev* devs, const void* tabs, const int2* list, const int* count, int n,
                       int L, size_t smem, int grid, cudaStream_t s);
 void launch_ace_batch_f32(const Dev* devs, const void* tabs, const int2* list, const int* count, int n, int L,
