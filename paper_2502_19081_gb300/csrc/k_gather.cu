@@ -23,28 +23,32 @@ using GSum = decltype(warp_sum(T(0)));
 
 // A warp gathers ga <= G_ATOMS atoms one after another (lanes over list slots, float
 // or float64 sums per potential and component, compensated for float) and parks
-// the six lane-0 sums per atom in shared memory; then lane t finishes atom t in
-// float64 (blend, non-finite check, second half-kick).  The float64 pipe of this
-// part runs at 1/64 of the float rate, so one float64 instruction should serve
-// many atoms, not one; ga trades that against the number of warps a small
-// system can keep busy.
+// the six lane-0 sums per atom in shared memory; then thread t of the block
+// finishes atom t of the block's chunk of G_WARPS * ga atoms in float64 (blend,
+// non-finite check, second half-kick).  The float64 pipe of this part runs at
+// 1/64 of the float rate and a warp-wide float64 instruction costs the same
+// with one active lane as with 32, so one float64 instruction should serve many
+// atoms: finishing per block rather than per warp keeps that true when ga is
+// small (ga trades gather latency against the warps a small system keeps busy).
 template <typename T>
 __device__ __forceinline__ void gather_body(const Dev& d, int bx, int gx, int integrate, double h, int ga,
                                             GSum<T>* park) {
     using V = typename Vec4<T>::type;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    GSum<T>* pk = park + warp * G_ATOMS * 6;
     const V* GE = reinterpret_cast<const V*>(d.ge);
     const V* GC = reinterpret_cast<const V*>(d.gc);
     const V* GEI = reinterpret_cast<const V*>(d.ge_in);
     const V* GCI = reinterpret_cast<const V*>(d.gc_in);
     const int cap = d.cap;
     const int stamp = d.status[SW_EPOCH];
-    const int64_t step = (int64_t)gx * G_WARPS * ga;
-    for (int64_t k0 = ((int64_t)bx * G_WARPS + warp) * ga; k0 < d.n; k0 += step) {
-        const int na = (int)(d.n - k0 < ga ? d.n - k0 : ga);
+    // the block takes chunks of G_WARPS * ga consecutive atoms, warp w atoms w*ga ..
+    const int64_t per_block = (int64_t)G_WARPS * ga;
+    for (int64_t b0 = (int64_t)bx * per_block; b0 < d.n; b0 += (int64_t)gx * per_block) {
+        const int nb = (int)(d.n - b0 < per_block ? d.n - b0 : per_block);
+        const int a0 = warp * ga;
+        const int na = nb - a0 >= ga ? ga : (nb - a0 > 0 ? nb - a0 : 0);
         for (int a = 0; a < na; ++a) {
-            const int64_t k = k0 + a;
+            const int64_t k = b0 + a0 + a;
             const int m = d.nnb[k];
             const int fk = d.flags[k];
             const bool own_e = (fk & 4) != 0, own_c = (fk & 8) != 0;
@@ -88,7 +92,7 @@ __device__ __forceinline__ void gather_body(const Dev& d, int bx, int gx, int in
             const GSum<T> r0 = warp_sum(tex), r1 = warp_sum(tey), r2 = warp_sum(tez);
             const GSum<T> r3 = warp_sum(tcx), r4 = warp_sum(tcy), r5 = warp_sum(tcz);
             if (lane == 0) {
-                GSum<T>* q = pk + a * 6;
+                GSum<T>* q = park + (a0 + a) * 6;
                 q[0] = r0;
                 q[1] = r1;
                 q[2] = r2;
@@ -97,10 +101,12 @@ __device__ __forceinline__ void gather_body(const Dev& d, int bx, int gx, int in
                 q[5] = r5;
             }
         }
-        __syncwarp();
-        if (lane < na) {
-            const int64_t k = k0 + lane;
-            const GSum<T>* q = pk + lane * 6;
+        __syncthreads();
+        // thread t finishes atom t of the chunk: one float64 instruction serves
+        // up to 32 atoms however the chunk was split over the warps
+        if ((int)threadIdx.x < nb) {
+            const int64_t k = b0 + threadIdx.x;
+            const GSum<T>* q = park + threadIdx.x * 6;
             const double ex = lane0_double(q[0]), ey = lane0_double(q[1]), ez = lane0_double(q[2]);
             const double cx = lane0_double(q[3]), cy = lane0_double(q[4]), cz = lane0_double(q[5]);
             const double w = d.wgt[k];
@@ -135,7 +141,7 @@ __device__ __forceinline__ void gather_body(const Dev& d, int bx, int gx, int in
                 d.v[k] = v;
             }
         }
-        __syncwarp();
+        __syncthreads();   // the park is reused by the next chunk
     }
 }
 
