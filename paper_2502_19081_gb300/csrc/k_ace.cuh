@@ -76,10 +76,19 @@ __device__ __forceinline__ void ld_gent(const GEnt<double>* p, int& pk, double& 
     g = __hiloint2double(v.w, v.z);
 }
 
-// QB consecutive values from shared memory (QB in {1, 2, 4}, aligned to QB)
+// QB consecutive values from shared memory (QB in {1, 2, 4}, aligned to QB;
+// QB = 6, float only, aligned to 2)
 template <typename T, int QB>
 __device__ __forceinline__ void ld_blk(const T* p, T* out) {
-    if constexpr (QB == 4) {
+    if constexpr (QB == 6) {
+        static_assert(sizeof(T) == 4, "6-wide blocks are float only");
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float2 v = reinterpret_cast<const float2*>(p)[k];
+            out[2 * k] = v.x;
+            out[2 * k + 1] = v.y;
+        }
+    } else if constexpr (QB == 4) {
         const V4<T> v = ld4<T>(p);
         out[0] = v.x;
         out[1] = v.y;
@@ -418,8 +427,18 @@ __device__ __forceinline__ void nu3_tile(const unsigned char* tile, const AceTab
     const T* A3 = At + h.l3 * h.l3 * NP;
     T* o3 = om + h.l3 * h.l3 * NP;
     const int qb = tab.qb;
-    if (qb == QM) nu3_units<T, NP, QM>(h, W, ge, g3o, A1, A2, A3, n, lane, U1, P1, o3, mult3, ep);
-    else nu3_units<T, NP, QM / 2>(h, W, ge, g3o, A1, A2, A3, n, lane, U1, P1, o3, mult3, ep);
+    bool done = false;
+    if constexpr (sizeof(T) == 4 && NP == 12) {
+        // n = 11 or 12: 6-wide blocks keep the units within one warp pass
+        if (qb == 6) {
+            nu3_units<T, NP, 6>(h, W, ge, g3o, A1, A2, A3, n, lane, U1, P1, o3, mult3, ep);
+            done = true;
+        }
+    }
+    if (!done) {
+        if (qb == QM) nu3_units<T, NP, QM>(h, W, ge, g3o, A1, A2, A3, n, lane, U1, P1, o3, mult3, ep);
+        else nu3_units<T, NP, QM / 2>(h, W, ge, g3o, A1, A2, A3, n, lane, U1, P1, o3, mult3, ep);
+    }
     __syncwarp();
     // omega1 (equal to omega3 when all three l's coincide): sum the unit
     // partials of each (m1, q1) and clear them for the next triple

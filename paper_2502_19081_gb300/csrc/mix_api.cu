@@ -402,15 +402,24 @@ int build_tables(mix_ctx* c, const mix_ace* a, const mix_spline* sp) {
         if (tmode[t] == 0) f += 2.0 * nnz * nn * nn;
         c->nu3_flops += f;
     }
-    // q2 block of the U/Z pass: the largest block (4 float, 2 float64) or half
-    // of it, whichever fills the warp's lanes better over n * np / qb units
+    // q2 block of a lane unit (q1, qb consecutive q2) in the nu = 3 pass: every
+    // pass of the warp over its units repeats the per-m3 work (a warp-wide
+    // reduction among it), so choose the block with the least estimated work,
+    // passes x (2 qb np multiply-adds + ~120 instructions of per-m3 overhead):
+    // 4 or 2 for float (6 as well where np = 12: n = 12 gives 24 units in one
+    // pass instead of 36 in two), 2 or 1 for float64
     {
-        const int qm = c->precision == MIX_FP64 ? 2 : 4;
-        auto eff = [&](int qb) {
+        std::vector<int> cand = c->precision == MIX_FP64 ? std::vector<int>{2, 1} : std::vector<int>{4, 2};
+        if (c->precision != MIX_FP64 && np == 12) cand.push_back(6);
+        double best = 0.0;
+        for (int qb : cand) {
             const int units = n * (np / qb);
-            return (double)units / (32.0 * ((units + 31) / 32));
-        };
-        c->qb = eff(qm / 2) > eff(qm) + 1e-12 ? qm / 2 : qm;
+            const double cost = (double)((units + 31) / 32) * (2.0 * qb * np + 120.0);
+            if (qb == cand[0] || cost < best - 1e-9) {
+                best = cost;
+                c->qb = qb;
+            }
+        }
     }
     std::vector<double> ylmk(nlm);
     for (int l = 0; l <= L; ++l)
