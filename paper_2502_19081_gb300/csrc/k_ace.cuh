@@ -410,7 +410,7 @@ __device__ __forceinline__ void nu3_units(const AceTileHdr& h, const T* W, const
 template <typename T, int NP>
 __device__ __forceinline__ void nu3_tile(const unsigned char* tile, const AceTab<T>& tab, const T* At, T* om,
                                          T* U1, T* P1, int lane, T& ep) {
-    constexpr int QM = sizeof(T) == 4 ? 4 : 2;     // largest q2 block of a lane unit
+    constexpr int QM = 4;     // largest power-of-two q2 block of a lane unit
     const AceTileHdr h = *reinterpret_cast<const AceTileHdr*>(tile);
     const T* W = reinterpret_cast<const T*>(tile + sizeof(AceTileHdr));
     const GEnt<T>* ge = reinterpret_cast<const GEnt<T>*>(tile + h.o_ge);

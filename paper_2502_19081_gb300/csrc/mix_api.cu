@@ -406,10 +406,10 @@ int build_tables(mix_ctx* c, const mix_ace* a, const mix_spline* sp) {
     // pass of the warp over its units repeats the per-m3 work (a warp-wide
     // reduction among it), so choose the block with the least estimated work,
     // passes x (2 qb np multiply-adds + ~120 instructions of per-m3 overhead):
-    // 4 or 2 for float (6 as well where np = 12: n = 12 gives 24 units in one
-    // pass instead of 36 in two), 2 or 1 for float64
+    // 4 or 2 (and for float 6 as well where np = 12: n = 12 gives 24 units in
+    // one pass instead of 36 in two)
     {
-        std::vector<int> cand = c->precision == MIX_FP64 ? std::vector<int>{2, 1} : std::vector<int>{4, 2};
+        std::vector<int> cand = {4, 2};
         if (c->precision != MIX_FP64 && np == 12) cand.push_back(6);
         double best = 0.0;
         for (int qb : cand) {
