@@ -101,12 +101,16 @@ __device__ __forceinline__ void gather_body(const Dev& d, int bx, int gx, int in
                 q[5] = r5;
             }
         }
-        __syncthreads();
         // thread t finishes atom t of the chunk: one float64 instruction serves
-        // up to 32 atoms however the chunk was split over the warps
-        if ((int)threadIdx.x < nb) {
-            const int64_t k = b0 + threadIdx.x;
-            const GSum<T>* q = park + threadIdx.x * 6;
+        // up to 32 atoms however the chunk was split over the warps (with a
+        // full warp's worth of atoms per warp, each warp finishes its own)
+        const bool own = ga == G_ATOMS;
+        if (own) __syncwarp();
+        else __syncthreads();
+        const int t = own ? a0 + lane : (int)threadIdx.x;
+        if (own ? lane < na : t < nb) {
+            const int64_t k = b0 + t;
+            const GSum<T>* q = park + t * 6;
             const double ex = lane0_double(q[0]), ey = lane0_double(q[1]), ez = lane0_double(q[2]);
             const double cx = lane0_double(q[3]), cy = lane0_double(q[4]), cz = lane0_double(q[5]);
             const double w = d.wgt[k];
@@ -141,7 +145,8 @@ __device__ __forceinline__ void gather_body(const Dev& d, int bx, int gx, int in
                 d.v[k] = v;
             }
         }
-        __syncthreads();   // the park is reused by the next chunk
+        if (own) __syncwarp();
+        else __syncthreads();   // the park is reused by the next chunk
     }
 }
 

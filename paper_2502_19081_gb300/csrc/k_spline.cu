@@ -1,11 +1,12 @@
 // Cheap potential: a 2+3-body cubic B-spline site energy evaluated on the
 // compacted list of atoms in Lambda_cheap plus its buffer (Sec. 4.5, Alg. 4):
 //   E_i = 1/2 sum_j V2(r_ij) + sum_{j<k; r_ij, r_ik < rc3} V3(r_ij, r_ik, r_jk).
-// One warp per evaluated atom.  Lanes own list slots for the 2-body part and
-// the final write; the 3-body pairs (j, k) are spread over the lanes, their
-// partial derivatives go to a per-warp table, and each lane then sums the
-// rows of its own 3-body neighbour in a fixed order (no atomics, so results
-// are bit-reproducible).
+// A group of LPA lanes per evaluated atom (a whole warp, or half a warp where
+// atoms have few neighbours: two atoms a warp).  Lanes own list slots for the
+// 2-body part and the final write; the 3-body pairs (j, k) are spread over the
+// lanes, their partial derivatives go to a per-group table, and each lane then
+// sums the rows of its own 3-body neighbour in a fixed order (no atomics, so
+// results are bit-reproducible).
 //   dV3 -> g_j += a_jk u_j + c_jk (r_j - r_k),  a_jk = dV3/d(first argument),
 //          c_jk = (dV3/dr_jk) / r_jk  (c3 symmetric in its first two indices).
 #include "mix_launch.h"
@@ -13,7 +14,13 @@
 namespace mixd {
 
 constexpr int SPL_WARPS = 4;
-constexpr int T3S = NB3MAX + 1;             // padded row stride of the pair tables
+
+// three-body neighbours an atom may have on chip: NB3MAX with a warp per atom,
+// fewer with half a warp (the per-group tables grow as the square)
+template <int LPA>
+__host__ __device__ constexpr int spl_nb() {
+    return LPA == 32 ? NB3MAX : 24;
+}
 
 __device__ __forceinline__ double tsqrt3(double x) { return sqrt(x); }
 __device__ __forceinline__ float tsqrt3(float x) { return sqrtf(x); }
@@ -34,31 +41,62 @@ __device__ __forceinline__ void bspline4(T x, int qmax, int& q, T b[4], T db[4])
     db[3] = T(0.5) * u2;
 }
 
-// index of the pair p < q in a packed upper triangle
-__device__ __forceinline__ int tri3(int p, int q) { return p * NB3MAX - p * (p + 1) / 2 + (q - p - 1); }
+// index of the pair p < q in a packed upper triangle of an NB x NB table
+template <int NB>
+__device__ __forceinline__ int tri3(int p, int q) { return p * NB - p * (p + 1) / 2 + (q - p - 1); }
 
-template <typename T>
-struct SplWarp {   // per-warp shared scratch
-    int slot[NB3MAX];
-    T v[NB3MAX][4];         // r_ij vector (x, y, z) and |r_ij|
-    T g2[NB3MAX][4];        // 2-body part of dE_i/dr_ij of the 3-body neighbours
-    T al[NB3MAX * T3S];     // a_jk
-    T cc[NB3MAX * (NB3MAX - 1) / 2];   // c_jk (symmetric: pairs p < q only)
+template <typename T, int NB>
+struct SplWarp {   // per-group shared scratch
+    static constexpr int S = NB + 1;   // padded row stride of the pair table
+    int slot[NB];
+    T v[NB][4];         // r_ij vector (x, y, z) and |r_ij|
+    T g2[NB][4];        // 2-body part of dE_i/dr_ij of the 3-body neighbours
+    T al[NB * S];       // a_jk
+    T cc[NB * (NB - 1) / 2];   // c_jk (symmetric: pairs p < q only)
 };
 
-// One evaluated atom (index a of the system's cheap list), by one warp; the
-// coefficient tables c2s, c3s may sit in shared or global memory.
-template <typename T>
+// Compensated sum over the LPA lanes of a group (fixed order; lane 0 of the
+// group holds the result).  For LPA = 32 this is warp_sum.
+template <int LPA>
+__device__ __forceinline__ WSum group_sum(float v, unsigned mask) {
+    float s = v, c = 0.f;
+#pragma unroll
+    for (int o = LPA / 2; o > 0; o >>= 1) {
+        const float s2 = __shfl_down_sync(mask, s, o, LPA);
+        const float c2 = __shfl_down_sync(mask, c, o, LPA);
+        const float t = __fadd_rn(s, s2);
+        const float bb = __fsub_rn(t, s);
+        const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bb)), __fsub_rn(s2, bb));
+        s = t;
+        c = __fadd_rn(__fadd_rn(c, c2), e);
+    }
+    return {s, c};
+}
+template <int LPA>
+__device__ __forceinline__ WSumD group_sum(double v, unsigned mask) {
+#pragma unroll
+    for (int o = LPA / 2; o > 0; o >>= 1) v += __shfl_down_sync(mask, v, o, LPA);
+    return {v};
+}
+
+// One evaluated atom (index a of the system's cheap list), by the group of
+// LPA lanes that owns W; the coefficient tables c2s, c3s may sit in shared or
+// global memory.
+template <typename T, int LPA>
 __device__ __forceinline__ void spline_atom(const Dev& d, const SplTab<T>& tab, int a, const T* c2s, const T* c3s,
-                                            SplWarp<T>& W) {
+                                            SplWarp<T, spl_nb<LPA>()>& W) {
+    constexpr int NB = spl_nb<LPA>();
+    constexpr int S = SplWarp<T, NB>::S;
     using V = typename Vec4<T>::type;
     const int lane = threadIdx.x & 31;
+    const int sub = lane & (LPA - 1);
+    const unsigned mask = LPA == 32 ? 0xffffffffu : (((1u << LPA) - 1u) << (lane & ~(LPA - 1)));
     V* GC = reinterpret_cast<V*>(d.gc);
     V* GIN = reinterpret_cast<V*>(d.gc_in);
     const int stamp = d.status[SW_EPOCH];
     const T rc2 = tab.rc2, rc32 = tab.rc32;
     const T invh2 = tab.invh2, invh3 = tab.invh3, invhc = tab.invhc;
-    const unsigned lt = (1u << lane) - 1u;
+    const unsigned lt = (1u << lane) - 1u;   // the ballots carry this group's lanes only
     const int cap = d.cap;
     {
         const int i = d.act_c[a];
@@ -70,9 +108,9 @@ __device__ __forceinline__ void spline_atom(const Dev& d, const SplTab<T>& tab, 
         T ep = T(0);
         int n3 = 0;
         // 2-body part; a slot without 3-body terms is final here (own row and the
-        // partner's incoming row); a 3-body slot waits in the warp's table
-        for (int c = 0; c * 32 < m; ++c) {
-            const int s = c * 32 + lane;
+        // partner's incoming row); a 3-body slot waits in the group's table
+        for (int c = 0; c * LPA < m; ++c) {
+            const int s = c * LPA + sub;
             bool is3 = false;
             T dv3[3] = {T(0), T(0), T(0)}, r = T(0), g2[3] = {T(0), T(0), T(0)};
             if (s < m) {
@@ -94,9 +132,9 @@ __device__ __forceinline__ void spline_atom(const Dev& d, const SplTab<T>& tab, 
                     is3 = r2 < rc32;
                 }
             }
-            const unsigned bal = __ballot_sync(0xffffffffu, is3);
+            const unsigned bal = __ballot_sync(mask, is3);
             const int p = is3 ? n3 + __popc(bal & lt) : -1;
-            if (is3 && p < NB3MAX) {
+            if (is3 && p < NB) {
                 W.slot[p] = s;
                 W.v[p][0] = dv3[0];
                 W.v[p][1] = dv3[1];
@@ -117,17 +155,17 @@ __device__ __forceinline__ void spline_atom(const Dev& d, const SplTab<T>& tab, 
             }
             n3 += __popc(bal);
         }
-        if (n3 > NB3MAX) {
-            if (lane == 0) {
+        if (n3 > NB) {
+            if (sub == 0) {
                 set_status(d.status, ST_NB3_OVERFLOW);
                 atomicMax(d.status + SW_NB3MAX, n3);
             }
-            n3 = NB3MAX;
+            n3 = NB;
         }
-        __syncwarp();
+        __syncwarp(mask);
         // 3-body pairs p < q, flattened over the lanes
         const int npair = n3 * (n3 - 1) / 2;
-        for (int t = lane; t < npair; t += 32) {
+        for (int t = sub; t < npair; t += LPA) {
             int p = 0, tt = t;
             while (tt >= n3 - 1 - p) {
                 tt -= n3 - 1 - p;
@@ -157,19 +195,18 @@ __device__ __forceinline__ void spline_atom(const Dev& d, const SplTab<T>& tab, 
             }
             ep += val;
             const T c = r3 > T(0) ? d3 * invhc / r3 : T(0);
-            W.al[p * T3S + q] = d1 * invh3;
-            W.al[q * T3S + p] = d2 * invh3;
-            W.cc[tri3(p, q)] = c;
+            W.al[p * S + q] = d1 * invh3;
+            W.al[q * S + p] = d2 * invh3;
+            W.cc[tri3<NB>(p, q)] = c;
         }
-        __syncwarp();
+        __syncwarp(mask);
         // 3-body slots: 2-body part plus the sum over the other 3-body neighbours
-        if (lane < n3) {
-            const int p = lane;
+        for (int p = sub; p < n3; p += LPA) {
             T sa = T(0), cx = T(0), cy = T(0), cz = T(0), cs = T(0);
             for (int q = 0; q < n3; ++q) {
                 if (q == p) continue;
-                const T c = W.cc[p < q ? tri3(p, q) : tri3(q, p)];
-                sa += W.al[p * T3S + q];
+                const T c = W.cc[p < q ? tri3<NB>(p, q) : tri3<NB>(q, p)];
+                sa += W.al[p * S + q];
                 cs += c;
                 cx += c * W.v[q][0];
                 cy += c * W.v[q][1];
@@ -186,46 +223,50 @@ __device__ __forceinline__ void spline_atom(const Dev& d, const SplTab<T>& tab, 
             gv.w = stamp_as(T(0), stamp);
             GIN[(int64_t)row[s] * cap + rvr[s]] = gv;
         }
-        __syncwarp();
-        const auto epart = warp_sum(ep);   // fixed order; compensated for float
+        __syncwarp(mask);
+        const auto epart = group_sum<LPA>(ep, mask);   // fixed order; compensated for float
         if constexpr (sizeof(T) == 4) {
-            if (lane == 0) d.epark_c[i] = make_float2(epart.s, epart.c);   // converted in the gather
+            if (sub == 0) d.epark_c[i] = make_float2(epart.s, epart.c);   // converted in the gather
         } else {
-            if (lane == 0) d.esite_c[i] = lane0_double(epart);
+            if (sub == 0) d.esite_c[i] = lane0_double(epart);
         }
-        __syncwarp();
+        __syncwarp(mask);
     }
 }
 
-template <typename T>
+template <typename T, int LPA>
 __global__ void __launch_bounds__(SPL_WARPS * 32) k_spline(Dev d, SplTab<T> tab) {
+    constexpr int G = 32 / LPA;   // atoms a warp works on at a time
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* c3s = reinterpret_cast<T*>(smem_raw);                 // [512]
     T* c2s = c3s + 512;                                       // [16]
-    SplWarp<T>* ws = reinterpret_cast<SplWarp<T>*>(c2s + 16);
-    const int warp = threadIdx.x >> 5;
+    SplWarp<T, spl_nb<LPA>()>* ws = reinterpret_cast<SplWarp<T, spl_nb<LPA>()>*>(c2s + 16);
+    const int warp = threadIdx.x >> 5, grp = (threadIdx.x & 31) / LPA;
     for (int k = threadIdx.x; k < 512; k += blockDim.x) c3s[k] = tab.c3[k];
     if (threadIdx.x < 16) c2s[threadIdx.x] = tab.c2[threadIdx.x];
     __syncthreads();
     const int count = d.status[SW_NCHEAP];
-    for (int a = blockIdx.x * SPL_WARPS + warp; a < count; a += gridDim.x * SPL_WARPS)
-        spline_atom<T>(d, tab, a, c2s, c3s, ws[warp]);
+    for (int a = (blockIdx.x * SPL_WARPS + warp) * G + grp; a < count; a += gridDim.x * SPL_WARPS * G)
+        spline_atom<T, LPA>(d, tab, a, c2s, c3s, ws[warp * G + grp]);
 }
 
-// Many systems: a warp per entry {system, index} of the flattened cheap list;
-// the system's parameters are read through L1.  When every system has the same
-// coefficient tables (uniform != 0) the block stages them once in shared
-// memory, as the single-system kernel does; otherwise they are read through L1.
-template <typename T>
+// Many systems: a lane group per entry {system, index} of the flattened cheap
+// list; the system's parameters are read through L1.  When every system has
+// the same coefficient tables (uniform != 0) the block stages them once in
+// shared memory, as the single-system kernel does; otherwise they are read
+// through L1.
+template <typename T, int LPA>
 __global__ void __launch_bounds__(SPL_WARPS * 32) kb_spline(const Dev* __restrict__ devs,
                                                            const SplTab<T>* __restrict__ tabs,
                                                            const int2* __restrict__ list, const int* count_p,
                                                            int uniform) {
+    constexpr int G = 32 / LPA;
+    using SW = SplWarp<T, spl_nb<LPA>()>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    SplWarp<T>* ws = reinterpret_cast<SplWarp<T>*>(smem_raw);
-    T* c3s = reinterpret_cast<T*>(ws + SPL_WARPS);      // [512] (uniform tables only)
+    SW* ws = reinterpret_cast<SW*>(smem_raw);
+    T* c3s = reinterpret_cast<T*>(ws + SPL_WARPS * G);   // [512] (uniform tables only)
     T* c2s = c3s + 512;                                  // [16]
-    const int warp = threadIdx.x >> 5;
+    const int warp = threadIdx.x >> 5, grp = (threadIdx.x & 31) / LPA;
     if (uniform) {
         const T* c3 = tabs[0].c3;
         const T* c2 = tabs[0].c2;
@@ -234,20 +275,25 @@ __global__ void __launch_bounds__(SPL_WARPS * 32) kb_spline(const Dev* __restric
         __syncthreads();
     }
     const int count = *count_p;
-    for (int g = blockIdx.x * SPL_WARPS + warp; g < count; g += gridDim.x * SPL_WARPS) {
+    for (int g = (blockIdx.x * SPL_WARPS + warp) * G + grp; g < count; g += gridDim.x * SPL_WARPS * G) {
         const int2 e = list[g];
         const SplTab<T>& tab = tabs[e.x];
-        spline_atom<T>(devs[e.x], tab, e.y, uniform ? c2s : tab.c2, uniform ? c3s : tab.c3, ws[warp]);
+        spline_atom<T, LPA>(devs[e.x], tab, e.y, uniform ? c2s : tab.c2, uniform ? c3s : tab.c3, ws[warp * G + grp]);
     }
 }
 
-template <typename T>
-static cudaError_t spl_batch_cfg(size_t* smem, int* grid) {
-    const size_t bytes = SPL_WARPS * sizeof(SplWarp<T>) + (512 + 16) * sizeof(T);
-    cudaError_t e = raise_smem_limit((const void*)kb_spline<T>, bytes);
+template <typename T, int LPA>
+static size_t spl_bytes() {
+    return SPL_WARPS * (32 / LPA) * sizeof(SplWarp<T, spl_nb<LPA>()>) + (512 + 16) * sizeof(T);
+}
+
+template <typename T, int LPA>
+static cudaError_t spl_shape(const void* kern, size_t* smem, int* grid) {
+    const size_t bytes = spl_bytes<T, LPA>();
+    cudaError_t e = raise_smem_limit(kern, bytes);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kb_spline<T>, SPL_WARPS * 32, bytes);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SPL_WARPS * 32, bytes);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     *smem = bytes;
@@ -255,44 +301,47 @@ static cudaError_t spl_batch_cfg(size_t* smem, int* grid) {
     return cudaSuccess;
 }
 
-cudaError_t spline_batch_configure(int precision, size_t* smem, int* grid) {
-    return precision == MIX_FP64 ? spl_batch_cfg<double>(smem, grid) : spl_batch_cfg<float>(smem, grid);
-}
+int spline_nb3(int lpa) { return lpa == 16 ? spl_nb<16>() : spl_nb<32>(); }
 
-void launch_spline_batch(int precision, const Dev* devs, const void* tabs, const int2* list, const int* count,
-                         int uniform, size_t smem, int grid, cudaStream_t s) {
+cudaError_t spline_batch_configure(int precision, int lpa, size_t* smem, int* grid) {
     if (precision == MIX_FP64)
-        kb_spline<double><<<grid, SPL_WARPS * 32, smem, s>>>(devs, static_cast<const SplTab<double>*>(tabs), list,
-                                                             count, uniform);
-    else
-        kb_spline<float><<<grid, SPL_WARPS * 32, smem, s>>>(devs, static_cast<const SplTab<float>*>(tabs), list,
-                                                            count, uniform);
+        return lpa == 16 ? spl_shape<double, 16>((const void*)kb_spline<double, 16>, smem, grid)
+                         : spl_shape<double, 32>((const void*)kb_spline<double, 32>, smem, grid);
+    return lpa == 16 ? spl_shape<float, 16>((const void*)kb_spline<float, 16>, smem, grid)
+                     : spl_shape<float, 32>((const void*)kb_spline<float, 32>, smem, grid);
 }
 
-template <typename T>
-static cudaError_t spl_cfg(int cap, size_t* smem, int* grid) {
-    (void)cap;
-    const size_t bytes = (512 + 16) * sizeof(T) + SPL_WARPS * sizeof(SplWarp<T>);
-    cudaError_t e = raise_smem_limit((const void*)k_spline<T>, bytes);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spline<T>, SPL_WARPS * 32, bytes);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    *smem = bytes;
-    *grid = per_sm * sm_count();
-    return cudaSuccess;
+void launch_spline_batch(int precision, int lpa, const Dev* devs, const void* tabs, const int2* list,
+                         const int* count, int uniform, size_t smem, int grid, cudaStream_t s) {
+    if (precision == MIX_FP64) {
+        const auto* t = static_cast<const SplTab<double>*>(tabs);
+        if (lpa == 16) kb_spline<double, 16><<<grid, SPL_WARPS * 32, smem, s>>>(devs, t, list, count, uniform);
+        else kb_spline<double, 32><<<grid, SPL_WARPS * 32, smem, s>>>(devs, t, list, count, uniform);
+    } else {
+        const auto* t = static_cast<const SplTab<float>*>(tabs);
+        if (lpa == 16) kb_spline<float, 16><<<grid, SPL_WARPS * 32, smem, s>>>(devs, t, list, count, uniform);
+        else kb_spline<float, 32><<<grid, SPL_WARPS * 32, smem, s>>>(devs, t, list, count, uniform);
+    }
 }
 
-cudaError_t spline_configure(int precision, int cap, size_t* smem, int* grid) {
-    return precision == MIX_FP64 ? spl_cfg<double>(cap, smem, grid) : spl_cfg<float>(cap, smem, grid);
-}
-
-void launch_spline(const Dev& d, const void* tab, int precision, size_t smem, int grid, cudaStream_t s) {
+cudaError_t spline_configure(int precision, int lpa, size_t* smem, int* grid) {
     if (precision == MIX_FP64)
-        k_spline<double><<<grid, SPL_WARPS * 32, smem, s>>>(d, *static_cast<const SplTab<double>*>(tab));
-    else
-        k_spline<float><<<grid, SPL_WARPS * 32, smem, s>>>(d, *static_cast<const SplTab<float>*>(tab));
+        return lpa == 16 ? spl_shape<double, 16>((const void*)k_spline<double, 16>, smem, grid)
+                         : spl_shape<double, 32>((const void*)k_spline<double, 32>, smem, grid);
+    return lpa == 16 ? spl_shape<float, 16>((const void*)k_spline<float, 16>, smem, grid)
+                     : spl_shape<float, 32>((const void*)k_spline<float, 32>, smem, grid);
+}
+
+void launch_spline(const Dev& d, const void* tab, int precision, int lpa, size_t smem, int grid, cudaStream_t s) {
+    if (precision == MIX_FP64) {
+        const auto& t = *static_cast<const SplTab<double>*>(tab);
+        if (lpa == 16) k_spline<double, 16><<<grid, SPL_WARPS * 32, smem, s>>>(d, t);
+        else k_spline<double, 32><<<grid, SPL_WARPS * 32, smem, s>>>(d, t);
+    } else {
+        const auto& t = *static_cast<const SplTab<float>*>(tab);
+        if (lpa == 16) k_spline<float, 16><<<grid, SPL_WARPS * 32, smem, s>>>(d, t);
+        else k_spline<float, 32><<<grid, SPL_WARPS * 32, smem, s>>>(d, t);
+    }
 }
 
 }  // namespace mixd

@@ -202,6 +202,7 @@ struct mix_ctx {
         o_seed, o_core, o_zsum;
     size_t ace_smem, spl_smem;
     int ace_grid, spl_grid;
+    int spl_lpa;                      // lanes per atom of the cheap kernel (32 or 16)
     int ace_grid_max, spl_grid_max;   // resident CTAs at full occupancy
     int64_t gaunt_nnz, tau_d3_sum, basis_size;
     double nu3_flops;
@@ -557,7 +558,7 @@ void enqueue_evaluation(mix_ctx* c, cudaStream_t s, int integrate, double dt, in
     // branch and fills the SMs the expensive kernel's last wave leaves idle
     cudaEventRecord(c->ev_fork, s);
     cudaStreamWaitEvent(c->aux, c->ev_fork, 0);
-    launch_spline(c->dev, st, c->precision, c->spl_smem, c->spl_grid, c->aux);
+    launch_spline(c->dev, st, c->precision, c->spl_lpa, c->spl_smem, c->spl_grid, c->aux);
     cudaEventRecord(c->ev_join, c->aux);
     launch_ace(c->dev, at, c->precision, c->L, c->ace_smem, c->ace_grid, s);
     if (prof) cudaEventRecordWithFlags(c->ev[4], s, ef);
@@ -641,7 +642,8 @@ int read_status(mix_ctx* c) {
     if (st & ST_NBR_OVERFLOW)
         return fail(c, MIX_EOVERFLOW, "neighbour list overflow: %d neighbours, capacity %d", c->pinned[SW_MAXNB], c->cap);
     if (st & ST_NB3_OVERFLOW)
-        return fail(c, MIX_EOVERFLOW, "three-body neighbours %d exceed %d", c->pinned[SW_NB3MAX], NB3MAX);
+        return fail(c, MIX_EOVERFLOW, "three-body neighbours %d exceed %d", c->pinned[SW_NB3MAX],
+                    spline_nb3(c->spl_lpa));
     if (st & ST_NONFINITE) return fail(c, MIX_ENUMERIC, "non-finite position or force");
     if (st & ST_OUT_OF_BOX) return fail(c, MIX_EBOX, "an atom left the box in a non-periodic dimension");
     if (st & ST_REV_MISSING) return fail(c, MIX_EINVAL, "asymmetric neighbour list");
@@ -772,7 +774,17 @@ int mix_init(const mix_system* sys, const mix_ace* a, const mix_spline* sp, cons
         delete c;
         return MIX_ECUDA;
     }
-    e = spline_configure(c->precision, c->cap, &c->spl_smem, &c->spl_grid);
+    // Half a warp per cheap atom where atoms have few neighbours: a periodic bulk
+    // whose mean count inside the 3-body cutoff is at most 8 (a third of the 24
+    // such neighbours a half-warp group holds on chip; Si about 5, bcc Fe 12).
+    {
+        bool bulk = vol > 0;
+        for (int k = 0; k < 3; ++k) bulk = bulk && sys->periodic[k];
+        const double rho = vol > 0 ? (double)sys->n_atoms / vol : 0.0;
+        const double n3 = rho * 4.0 / 3.0 * M_PI * sp->r_cut3 * sp->r_cut3 * sp->r_cut3;
+        c->spl_lpa = bulk && n3 <= 8.0 ? 16 : 32;
+    }
+    e = spline_configure(c->precision, c->spl_lpa, &c->spl_smem, &c->spl_grid);
     c->ace_grid_max = c->ace_grid;
     c->spl_grid_max = c->spl_grid;
     if (e != cudaSuccess) {
@@ -1292,6 +1304,7 @@ struct mix_batch {
     size_t spl_smem = 0;
     int spl_grid = 0;
     int spl_uniform = 0;             // every member has the same cheap coefficient tables
+    int spl_lpa = 32;                // lanes per atom of the fused cheap kernel
     int64_t launches = 0;            // kernels launched by fused steps
     cudaStream_t aux = nullptr;      // second branch (cheap potential) of the fused step
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -1502,7 +1515,11 @@ int fused_build(mix_batch* b) {
                 b->spl_uniform = 0;
         }
     }
-    e = spline_batch_configure(b->precision, &b->spl_smem, &b->spl_grid);
+    // half a warp per cheap atom only when every member runs that way alone
+    b->spl_lpa = 16;
+    for (int s = 0; s < ns; ++s)
+        if (b->m[s]->spl_lpa != 16) b->spl_lpa = 32;
+    e = spline_batch_configure(b->precision, b->spl_lpa, &b->spl_smem, &b->spl_grid);
     if (e != cudaSuccess) return bfail(b, MIX_ECUDA, std::string("fused cheap kernel: ") + cudaGetErrorString(e));
     return MIX_OK;
 }
@@ -1531,7 +1548,7 @@ int fused_graph(mix_batch* b, int integrate, double dt, cudaGraph_t* graph, cuda
     // cheap potential on a second branch, concurrent with the expensive groups
     cudaEventRecord(b->ev_fork, s);
     cudaStreamWaitEvent(b->aux, b->ev_fork, 0);
-    launch_spline_batch(b->precision, b->ddevs, b->dspl, P.flat.list_c, P.flat.counts + b->groups.size(),
+    launch_spline_batch(b->precision, b->spl_lpa, b->ddevs, b->dspl, P.flat.list_c, P.flat.counts + b->groups.size(),
                         b->spl_uniform, b->spl_smem, b->spl_grid, b->aux);
     cudaEventRecord(b->ev_join, b->aux);
     for (size_t g = 0; g < b->groups.size(); ++g) {

@@ -22,8 +22,11 @@ void launch_ace_f32(const Dev& d, const void* tab, int L, size_t smem, int grid,
 void launch_ace_f64(const Dev& d, const void* tab, int L, size_t smem, int grid, cudaStream_t s);
 
 // cheap potential (k_spline.cu)
-cudaError_t spline_configure(int precision, int cap, size_t* smem, int* grid);
-void launch_spline(const Dev& d, const void* tab, int precision, size_t smem, int grid, cudaStream_t s);
+// lpa: lanes per evaluated atom (32, or 16 for atoms with few neighbours);
+// spline_nb3(lpa): three-body neighbours an atom may have on chip with lpa lanes
+cudaError_t spline_configure(int precision, int lpa, size_t* smem, int* grid);
+int spline_nb3(int lpa);
+void launch_spline(const Dev& d, const void* tab, int precision, int lpa, size_t smem, int grid, cudaStream_t s);
 
 // gather + blend + second half-kick (k_gather.cu)
 void launch_gather(const Dev& d, int precision, int integrate, double h, cudaStream_t s);
@@ -75,9 +78,9 @@ void launch_ace_batch_f32(const Dev* devs, const void* tabs, const int2* list, c
                           size_t smem, int grid, cudaStream_t s);
 void launch_ace_batch_f64(const Dev* devs, const void* tabs, const int2* list, const int* count, int n, int L,
                           size_t smem, int grid, cudaStream_t s);
-cudaError_t spline_batch_configure(int precision, size_t* smem, int* grid);
-void launch_spline_batch(int precision, const Dev* devs, const void* tabs, const int2* list, const int* count,
-                         int uniform, size_t smem, int grid, cudaStream_t s);
+cudaError_t spline_batch_configure(int precision, int lpa, size_t* smem, int* grid);
+void launch_spline_batch(int precision, int lpa, const Dev* devs, const void* tabs, const int2* list,
+                         const int* count, int uniform, size_t smem, int grid, cudaStream_t s);
 void launch_gather_batch(const BatchPlan& p, int precision, int integrate, double dt, cudaStream_t s);
 
 int sm_count();
