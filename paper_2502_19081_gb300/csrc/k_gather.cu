@@ -88,9 +88,19 @@ __device__ __forceinline__ void gather_body(const Dev& d, int bx, int gx, int in
                     }
                 }
             }
-            // lanes combined in a fixed order
-            const GSum<T> r0 = warp_sum(tex), r1 = warp_sum(tey), r2 = warp_sum(tez);
-            const GSum<T> r3 = warp_sum(tcx), r4 = warp_sum(tcy), r5 = warp_sum(tcz);
+            // lanes combined in a fixed order (only for the potentials the atom uses:
+            // the flags are uniform over the warp)
+            GSum<T> r0{}, r1{}, r2{}, r3{}, r4{}, r5{};
+            if (use_e) {
+                r0 = warp_sum(tex);
+                r1 = warp_sum(tey);
+                r2 = warp_sum(tez);
+            }
+            if (use_c) {
+                r3 = warp_sum(tcx);
+                r4 = warp_sum(tcy);
+                r5 = warp_sum(tcz);
+            }
             if (lane == 0) {
                 GSum<T>* q = park + (a0 + a) * 6;
                 q[0] = r0;

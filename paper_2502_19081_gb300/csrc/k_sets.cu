@@ -35,8 +35,23 @@ __device__ __forceinline__ void lambda_atom(const Dev& d, const Regions& r, int6
     // neighbour closer than r_buffer_exp has lambda > 0 (bit 4); deeper than
     // r_buffer_cheap inside some core no neighbour that close has lambda < 1 (bit 5)
     bool far_e = true, deep_c = false;
+    float4 xs = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (r.screen) xs = d.xf[i];
     for (int k = 0; k < r.n; ++k) {
         const double* R = r.r[k];
+        if (r.screen) {
+            // float screen: clearly beyond the ramp and the expensive buffer of
+            // this region, which then contributes nothing (see Regions)
+            float v[3] = {xs.x - r.cf[k][0], xs.y - r.cf[k][1], xs.z - r.cf[k][2]};
+            for (int t = 0; t < 3; ++t)
+                if (d.box.per[t]) v[t] -= r.Lf[t] * rintf(v[t] * r.iLf[t]);
+            float d2f = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+            if ((int)R[0] == MIX_REGION_CYLINDER) {
+                const float tt = v[0] * r.cf[k][3] + v[1] * r.cf[k][4] + v[2] * r.cf[k][5];
+                d2f -= tt * tt;
+            }
+            if (d2f > r.far2[k]) continue;
+        }
         const double4 c = make_double4(R[1], R[2], R[3], 0.0);
         double v[3];
         delta_rn(d.box, c, x, v);
@@ -193,16 +208,41 @@ __device__ __forceinline__ void buffer_body(const Dev& d, int bx, int gx) {
             const double4 xi = d.x[i];
             const int m = d.nnb[i];
             const int* row = d.nbr + i * (int64_t)d.cap;
+            // float screen from the cell-relative float positions the potentials
+            // use; float64 only within 1e-3 A^2 of a buffer radius
+            const bool screen = d.xr != nullptr && !d.exact_lists;
+            float4 xri = make_float4(0.f, 0.f, 0.f, 0.f);
+            int ci = 0;
+            if (screen) {
+                xri = d.xr[i];
+                ci = d.cell3[i];
+            }
             for (int s = lane; s < m; s += 32) {
                 const int j = row[s];
                 const int fj = d.flags[j] & 3;
                 const bool cand_e = need_e && (fj & 1), cand_c = need_c && (fj & 2);
                 if (cand_e || cand_c) {
-                    double dd[3];
-                    delta_rn(d.box, xi, d.x[j], dd);
-                    const double r2 = norm2_rn(dd);
-                    he = he || (cand_e && r2 < d.bufe2);
-                    hc = hc || (cand_c && r2 < d.bufc2);
+                    bool ie = false, ic = false, exact = !screen;
+                    if (screen) {
+                        const float r2f = pair_r2_float(d, xri, ci, j);
+                        if (cand_e) {
+                            if (r2f < d.bufe2_lo) ie = true;
+                            else if (r2f <= d.bufe2_hi) exact = true;
+                        }
+                        if (cand_c) {
+                            if (r2f < d.bufc2_lo) ic = true;
+                            else if (r2f <= d.bufc2_hi) exact = true;
+                        }
+                    }
+                    if (exact) {
+                        double dd[3];
+                        delta_rn(d.box, xi, d.x[j], dd);
+                        const double r2 = norm2_rn(dd);
+                        ie = cand_e && r2 < d.bufe2;
+                        ic = cand_c && r2 < d.bufc2;
+                    }
+                    he = he || ie;
+                    hc = hc || ic;
                 }
             }
             he = __any_sync(0xffffffffu, he);

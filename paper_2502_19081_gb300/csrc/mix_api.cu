@@ -756,6 +756,10 @@ int mix_init(const mix_system* sys, const mix_ace* a, const mix_spline* sp, cons
     d.bufc2 = bufc * bufc;
     d.bufe = bufe;
     d.bufc = bufc;
+    d.bufe2_lo = (float)(d.bufe2 - 1e-3);
+    d.bufe2_hi = (float)(d.bufe2 + 1e-3);
+    d.bufc2_lo = (float)(d.bufc2 - 1e-3);
+    d.bufc2_hi = (float)(d.bufc2 + 1e-3);
     double extent = 0.0;
     for (int k = 0; k < 3; ++k) extent = std::max(extent, std::fabs(sys->box_lo[k]) + sys->box_len[k]);
     d.exact_lists = extent > 2000.0 ? 1 : 0;
@@ -909,6 +913,17 @@ int mix_set_regions(mix_ctx* c, const mix_region* r, int n) {
         q[6] = nrm > 0 ? az / nrm : az;
         q[7] = r[k].r_core;
         q[8] = r[k].ramp;
+        for (int t = 0; t < 3; ++t) {
+            R.cf[k][t] = (float)q[1 + t];
+            R.cf[k][3 + t] = (float)q[4 + t];
+        }
+        const double far = r[k].r_core + r[k].ramp + c->dev.bufe + std::sqrt(c->dev.half_skin2) + 0.01;
+        R.far2[k] = (float)(far * far);
+    }
+    R.screen = c->dev.exact_lists ? 0 : 1;
+    for (int t = 0; t < 3; ++t) {
+        R.Lf[t] = (float)c->dev.box.L[t];
+        R.iLf[t] = (float)c->dev.box.invL[t];
     }
     c->regions = R;
     c->seedrule.mode = 0;

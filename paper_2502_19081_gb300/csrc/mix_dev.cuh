@@ -66,6 +66,15 @@ struct Regions {
     int n;
     int blend;
     double r[MIX_MAX_REGIONS][9];   // kind, centre[3], axis[3] (unit), r_core, ramp
+    // float screen of the weights (when screen != 0): an atom whose float
+    // position of the last list build lies farther than sqrt(far2[k]) from region
+    // k (from its axis for a cylinder) gets lambda 0 from it and leaves the
+    // buffer hints alone; far2 = (r_core + ramp + r_buffer_exp + skin/2 + 0.01)^2
+    // covers the drift since the build (< skin/2) and the float rounding (< 1e-3 A)
+    int screen;
+    float cf[MIX_MAX_REGIONS][6];   // centre[3], axis[3]
+    float far2[MIX_MAX_REGIONS];
+    float Lf[3], iLf[3];            // box lengths and inverses
 };
 
 // Weights from seed atoms instead of geometric regions (Alg. 1-2).
@@ -100,6 +109,10 @@ struct Dev {
     double rc3;          // cheap 3-body cutoff
     double bufe2, bufc2; // buffer radii squared
     double bufe, bufc;   // buffer radii
+    // float screen of the buffer test: a float squared distance below lo is
+    // inside, above hi outside (1e-3 A^2 either side of the radius, against a
+    // float error below 1e-4 A^2); in between the float64 test decides
+    float bufe2_lo, bufe2_hi, bufc2_lo, bufc2_hi;
     int exact_lists;     // 1: every neighbour candidate takes the float64 test
                          // (boxes beyond the float pre-filter's error bound)
     double4* x;
@@ -373,6 +386,7 @@ struct PairFrame<float> {
     float4 xri;
     int ci;
     __device__ __forceinline__ PairFrame(const Dev& d, int i) : xri(d.xr[i]), ci(d.cell3[i]) {}
+    __device__ __forceinline__ PairFrame(float4 x, int c) : xri(x), ci(c) {}
     __device__ __forceinline__ void vec(const Dev& d, int j, float v[3], float& r2) const {
         const float4 xrj = d.xr[j];
         const int cj = d.cell3[j];
@@ -389,5 +403,12 @@ struct PairFrame<float> {
         r2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
     }
 };
+
+// squared length of the float pair vector to atom j from the frame (xri, ci)
+__device__ __forceinline__ float pair_r2_float(const Dev& d, float4 xri, int ci, int j) {
+    float v[3], r2;
+    PairFrame<float>(xri, ci).vec(d, j, v, r2);
+    return r2;
+}
 
 }  // namespace mixd
