@@ -1,8 +1,8 @@
 // Cheap potential: a 2+3-body cubic B-spline site energy evaluated on the
 // compacted list of atoms in Lambda_cheap plus its buffer (Sec. 4.5, Alg. 4):
 //   E_i = 1/2 sum_j V2(r_ij) + sum_{j<k; r_ij, r_ik < rc3} V3(r_ij, r_ik, r_jk).
-// A group of LPA lanes per evaluated atom (a whole warp, or half a warp where
-// atoms have few neighbours: two atoms a warp).  Lanes own list slots for the
+// A group of LPA lanes per evaluated atom (a whole warp, or half or a quarter
+// of a warp where atoms have few neighbours: two or four atoms a warp).  Lanes own list slots for the
 // 2-body part and the final write; the 3-body pairs (j, k) are spread over the
 // lanes, their partial derivatives go to a per-group table, and each lane then
 // sums the rows of its own 3-body neighbour in a fixed order (no atomics, so
@@ -16,10 +16,10 @@ namespace mixd {
 constexpr int SPL_WARPS = 4;
 
 // three-body neighbours an atom may have on chip: NB3MAX with a warp per atom,
-// fewer with half a warp (the per-group tables grow as the square)
+// fewer with half or a quarter of a warp (the per-group tables grow as the square)
 template <int LPA>
 __host__ __device__ constexpr int spl_nb() {
-    return LPA == 32 ? NB3MAX : 24;
+    return LPA == 32 ? NB3MAX : (LPA == 16 ? 24 : 16);
 }
 
 __device__ __forceinline__ double tsqrt3(double x) { return sqrt(x); }
@@ -301,47 +301,58 @@ static cudaError_t spl_shape(const void* kern, size_t* smem, int* grid) {
     return cudaSuccess;
 }
 
-int spline_nb3(int lpa) { return lpa == 16 ? spl_nb<16>() : spl_nb<32>(); }
+int spline_nb3(int lpa) { return lpa == 8 ? spl_nb<8>() : (lpa == 16 ? spl_nb<16>() : spl_nb<32>()); }
+
+template <typename T>
+static cudaError_t spl_batch_cfg(int lpa, size_t* smem, int* grid) {
+    if (lpa == 8) return spl_shape<T, 8>((const void*)kb_spline<T, 8>, smem, grid);
+    if (lpa == 16) return spl_shape<T, 16>((const void*)kb_spline<T, 16>, smem, grid);
+    return spl_shape<T, 32>((const void*)kb_spline<T, 32>, smem, grid);
+}
 
 cudaError_t spline_batch_configure(int precision, int lpa, size_t* smem, int* grid) {
-    if (precision == MIX_FP64)
-        return lpa == 16 ? spl_shape<double, 16>((const void*)kb_spline<double, 16>, smem, grid)
-                         : spl_shape<double, 32>((const void*)kb_spline<double, 32>, smem, grid);
-    return lpa == 16 ? spl_shape<float, 16>((const void*)kb_spline<float, 16>, smem, grid)
-                     : spl_shape<float, 32>((const void*)kb_spline<float, 32>, smem, grid);
+    return precision == MIX_FP64 ? spl_batch_cfg<double>(lpa, smem, grid) : spl_batch_cfg<float>(lpa, smem, grid);
+}
+
+template <typename T>
+static void spl_batch_launch(int lpa, const Dev* devs, const SplTab<T>* t, const int2* list, const int* count,
+                             int uniform, size_t smem, int grid, cudaStream_t s) {
+    if (lpa == 8) kb_spline<T, 8><<<grid, SPL_WARPS * 32, smem, s>>>(devs, t, list, count, uniform);
+    else if (lpa == 16) kb_spline<T, 16><<<grid, SPL_WARPS * 32, smem, s>>>(devs, t, list, count, uniform);
+    else kb_spline<T, 32><<<grid, SPL_WARPS * 32, smem, s>>>(devs, t, list, count, uniform);
 }
 
 void launch_spline_batch(int precision, int lpa, const Dev* devs, const void* tabs, const int2* list,
                          const int* count, int uniform, size_t smem, int grid, cudaStream_t s) {
-    if (precision == MIX_FP64) {
-        const auto* t = static_cast<const SplTab<double>*>(tabs);
-        if (lpa == 16) kb_spline<double, 16><<<grid, SPL_WARPS * 32, smem, s>>>(devs, t, list, count, uniform);
-        else kb_spline<double, 32><<<grid, SPL_WARPS * 32, smem, s>>>(devs, t, list, count, uniform);
-    } else {
-        const auto* t = static_cast<const SplTab<float>*>(tabs);
-        if (lpa == 16) kb_spline<float, 16><<<grid, SPL_WARPS * 32, smem, s>>>(devs, t, list, count, uniform);
-        else kb_spline<float, 32><<<grid, SPL_WARPS * 32, smem, s>>>(devs, t, list, count, uniform);
-    }
+    if (precision == MIX_FP64)
+        spl_batch_launch<double>(lpa, devs, static_cast<const SplTab<double>*>(tabs), list, count, uniform, smem,
+                                 grid, s);
+    else
+        spl_batch_launch<float>(lpa, devs, static_cast<const SplTab<float>*>(tabs), list, count, uniform, smem,
+                                grid, s);
+}
+
+template <typename T>
+static cudaError_t spl_cfg(int lpa, size_t* smem, int* grid) {
+    if (lpa == 8) return spl_shape<T, 8>((const void*)k_spline<T, 8>, smem, grid);
+    if (lpa == 16) return spl_shape<T, 16>((const void*)k_spline<T, 16>, smem, grid);
+    return spl_shape<T, 32>((const void*)k_spline<T, 32>, smem, grid);
 }
 
 cudaError_t spline_configure(int precision, int lpa, size_t* smem, int* grid) {
-    if (precision == MIX_FP64)
-        return lpa == 16 ? spl_shape<double, 16>((const void*)k_spline<double, 16>, smem, grid)
-                         : spl_shape<double, 32>((const void*)k_spline<double, 32>, smem, grid);
-    return lpa == 16 ? spl_shape<float, 16>((const void*)k_spline<float, 16>, smem, grid)
-                     : spl_shape<float, 32>((const void*)k_spline<float, 32>, smem, grid);
+    return precision == MIX_FP64 ? spl_cfg<double>(lpa, smem, grid) : spl_cfg<float>(lpa, smem, grid);
+}
+
+template <typename T>
+static void spl_launch(const Dev& d, const SplTab<T>& t, int lpa, size_t smem, int grid, cudaStream_t s) {
+    if (lpa == 8) k_spline<T, 8><<<grid, SPL_WARPS * 32, smem, s>>>(d, t);
+    else if (lpa == 16) k_spline<T, 16><<<grid, SPL_WARPS * 32, smem, s>>>(d, t);
+    else k_spline<T, 32><<<grid, SPL_WARPS * 32, smem, s>>>(d, t);
 }
 
 void launch_spline(const Dev& d, const void* tab, int precision, int lpa, size_t smem, int grid, cudaStream_t s) {
-    if (precision == MIX_FP64) {
-        const auto& t = *static_cast<const SplTab<double>*>(tab);
-        if (lpa == 16) k_spline<double, 16><<<grid, SPL_WARPS * 32, smem, s>>>(d, t);
-        else k_spline<double, 32><<<grid, SPL_WARPS * 32, smem, s>>>(d, t);
-    } else {
-        const auto& t = *static_cast<const SplTab<float>*>(tab);
-        if (lpa == 16) k_spline<float, 16><<<grid, SPL_WARPS * 32, smem, s>>>(d, t);
-        else k_spline<float, 32><<<grid, SPL_WARPS * 32, smem, s>>>(d, t);
-    }
+    if (precision == MIX_FP64) spl_launch<double>(d, *static_cast<const SplTab<double>*>(tab), lpa, smem, grid, s);
+    else spl_launch<float>(d, *static_cast<const SplTab<float>*>(tab), lpa, smem, grid, s);
 }
 
 }  // namespace mixd

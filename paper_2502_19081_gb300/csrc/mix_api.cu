@@ -778,15 +778,16 @@ int mix_init(const mix_system* sys, const mix_ace* a, const mix_spline* sp, cons
         delete c;
         return MIX_ECUDA;
     }
-    // Half a warp per cheap atom where atoms have few neighbours: a periodic bulk
-    // whose mean count inside the 3-body cutoff is at most 8 (a third of the 24
-    // such neighbours a half-warp group holds on chip; Si about 5, bcc Fe 12).
+    // Fewer lanes per cheap atom where atoms have few neighbours: in a periodic
+    // bulk whose mean count inside the 3-body cutoff is at most a third of what
+    // the group holds on chip, a quarter warp (16 slots) up to 5.3 or half a warp
+    // (24 slots) up to 8; a warp (32 slots) otherwise.  Si has about 5, bcc Fe 12.
     {
         bool bulk = vol > 0;
         for (int k = 0; k < 3; ++k) bulk = bulk && sys->periodic[k];
         const double rho = vol > 0 ? (double)sys->n_atoms / vol : 0.0;
         const double n3 = rho * 4.0 / 3.0 * M_PI * sp->r_cut3 * sp->r_cut3 * sp->r_cut3;
-        c->spl_lpa = bulk && n3 <= 8.0 ? 16 : 32;
+        c->spl_lpa = !bulk ? 32 : (n3 * 3.0 <= spline_nb3(8) ? 8 : (n3 * 3.0 <= spline_nb3(16) ? 16 : 32));
     }
     e = spline_configure(c->precision, c->spl_lpa, &c->spl_smem, &c->spl_grid);
     c->ace_grid_max = c->ace_grid;
@@ -1530,10 +1531,9 @@ int fused_build(mix_batch* b) {
                 b->spl_uniform = 0;
         }
     }
-    // half a warp per cheap atom only when every member runs that way alone
-    b->spl_lpa = 16;
-    for (int s = 0; s < ns; ++s)
-        if (b->m[s]->spl_lpa != 16) b->spl_lpa = 32;
+    // the widest lane group any member needs alone
+    b->spl_lpa = 8;
+    for (int s = 0; s < ns; ++s) b->spl_lpa = std::max(b->spl_lpa, b->m[s]->spl_lpa);
     e = spline_batch_configure(b->precision, b->spl_lpa, &b->spl_smem, &b->spl_grid);
     if (e != cudaSuccess) return bfail(b, MIX_ECUDA, std::string("fused cheap kernel: ") + cudaGetErrorString(e));
     return MIX_OK;
