@@ -30,11 +30,16 @@ using GSum = decltype(warp_sum(T(0)));
 // with one active lane as with 32, so one float64 instruction should serve many
 // atoms: finishing per block rather than per warp keeps that true when ga is
 // small (ga trades gather latency against the warps a small system keeps busy).
-template <typename T>
+// LPA lanes gather one atom (a warp, or a quarter warp where lists are short:
+// four atoms of the warp's share at a time).
+template <typename T, int LPA>
 __device__ __forceinline__ void gather_body(const Dev& d, int bx, int gx, int integrate, double h, int ga,
                                             GSum<T>* park) {
     using V = typename Vec4<T>::type;
+    constexpr int G = 32 / LPA;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int sub = lane & (LPA - 1), grp = lane / LPA;
+    const unsigned mask = LPA == 32 ? 0xffffffffu : (((1u << LPA) - 1u) << (lane & ~(LPA - 1)));
     const V* GE = reinterpret_cast<const V*>(d.ge);
     const V* GC = reinterpret_cast<const V*>(d.gc);
     const V* GEI = reinterpret_cast<const V*>(d.ge_in);
@@ -47,7 +52,7 @@ __device__ __forceinline__ void gather_body(const Dev& d, int bx, int gx, int in
         const int nb = (int)(d.n - b0 < per_block ? d.n - b0 : per_block);
         const int a0 = warp * ga;
         const int na = nb - a0 >= ga ? ga : (nb - a0 > 0 ? nb - a0 : 0);
-        for (int a = 0; a < na; ++a) {
+        for (int a = grp; a < na; a += G) {
             const int64_t k = b0 + a0 + a;
             const int m = d.nnb[k];
             const int fk = d.flags[k];
@@ -58,7 +63,7 @@ __device__ __forceinline__ void gather_body(const Dev& d, int bx, int gx, int in
             // own row: dE_k/dr_kj; incoming row: dE_j/dr_jk, present when j was
             // evaluated in this evaluation (its stamp is current)
             T tex = T(0), tey = T(0), tez = T(0), tcx = T(0), tcy = T(0), tcz = T(0);
-            for (int s = lane; s < m; s += 32) {
+            for (int s = sub; s < m; s += LPA) {
                 if (use_e) {
                     if (own_e) {
                         const V g = GE[base + s];
@@ -89,19 +94,19 @@ __device__ __forceinline__ void gather_body(const Dev& d, int bx, int gx, int in
                 }
             }
             // lanes combined in a fixed order (only for the potentials the atom uses:
-            // the flags are uniform over the warp)
+            // the flags are uniform over the group)
             GSum<T> r0{}, r1{}, r2{}, r3{}, r4{}, r5{};
             if (use_e) {
-                r0 = warp_sum(tex);
-                r1 = warp_sum(tey);
-                r2 = warp_sum(tez);
+                r0 = group_sum<LPA>(tex, mask);
+                r1 = group_sum<LPA>(tey, mask);
+                r2 = group_sum<LPA>(tez, mask);
             }
             if (use_c) {
-                r3 = warp_sum(tcx);
-                r4 = warp_sum(tcy);
-                r5 = warp_sum(tcz);
+                r3 = group_sum<LPA>(tcx, mask);
+                r4 = group_sum<LPA>(tcy, mask);
+                r5 = group_sum<LPA>(tcz, mask);
             }
-            if (lane == 0) {
+            if (sub == 0) {
                 GSum<T>* q = park + (a0 + a) * 6;
                 q[0] = r0;
                 q[1] = r1;
@@ -160,17 +165,24 @@ __device__ __forceinline__ void gather_body(const Dev& d, int bx, int gx, int in
     }
 }
 
-template <typename T>
+template <typename T, int LPA>
 __global__ void __launch_bounds__(G_WARPS * 32) k_gather(Dev d, int integrate, double h, int ga) {
     __shared__ GSum<T> park[G_WARPS * G_ATOMS * 6];
-    gather_body<T>(d, blockIdx.x, gridDim.x, integrate, h, ga, park);
+    gather_body<T, LPA>(d, blockIdx.x, gridDim.x, integrate, h, ga, park);
 }
 
+// lanes per gathered atom: a quarter warp for lists of at most 64 slots
+__host__ __device__ inline int gather_lpa(int cap) { return cap <= 64 ? 8 : 32; }
+
+// Each block belongs to one system and gathers with that system's own lane
+// groups, so a system's forces are bit for bit those it gets alone.
 template <typename T>
 __global__ void __launch_bounds__(G_WARPS * 32) kb_gather(BatchArgs ba, int integrate, double dt) {
     __shared__ GSum<T> park[G_WARPS * G_ATOMS * 6];
     MIX_BATCH_BLOCK(ba)
-    gather_body<T>(s_dev, s_ent.y, s_ent.z, integrate, half_kick(dt, s_dev.mass), G_ATOMS, park);
+    const double h = half_kick(dt, s_dev.mass);
+    if (gather_lpa(s_dev.cap) == 8) gather_body<T, 8>(s_dev, s_ent.y, s_ent.z, integrate, h, G_ATOMS, park);
+    else gather_body<T, 32>(s_dev, s_ent.y, s_ent.z, integrate, h, G_ATOMS, park);
 }
 
 void launch_gather_batch(const BatchPlan& p, int precision, int integrate, double dt, cudaStream_t s) {
@@ -181,18 +193,24 @@ void launch_gather_batch(const BatchPlan& p, int precision, int integrate, doubl
 }
 
 void launch_gather(const Dev& d, int precision, int integrate, double h, cudaStream_t s) {
-    // atoms per warp: enough warps for about half occupancy, at most G_ATOMS
+    const int lpa = gather_lpa(d.cap);
+    // atoms per warp: enough warps for about half occupancy, at most G_ATOMS, and
+    // with quarter-warp groups at least one atom per group
     const int64_t warps_wanted = (int64_t)sm_count() * 32;
     int ga = (int)((d.n + warps_wanted - 1) / warps_wanted);
-    ga = ga < 1 ? 1 : (ga > G_ATOMS ? G_ATOMS : ga);
+    ga = ga < 32 / lpa ? 32 / lpa : (ga > G_ATOMS ? G_ATOMS : ga);
     const int64_t per_block = (int64_t)G_WARPS * ga;
     int64_t want = (d.n + per_block - 1) / per_block;
     int64_t lim = d.grid_gather > 0 ? d.grid_gather : (int64_t)sm_count() * 8;
     const int grid = (int)(want < lim ? want : lim);
-    if (precision == MIX_FP64)
-        k_gather<double><<<grid > 0 ? grid : 1, G_WARPS * 32, 0, s>>>(d, integrate, h, ga);
-    else
-        k_gather<float><<<grid > 0 ? grid : 1, G_WARPS * 32, 0, s>>>(d, integrate, h, ga);
+    const int gr = grid > 0 ? grid : 1;
+    if (precision == MIX_FP64) {
+        if (lpa == 8) k_gather<double, 8><<<gr, G_WARPS * 32, 0, s>>>(d, integrate, h, ga);
+        else k_gather<double, 32><<<gr, G_WARPS * 32, 0, s>>>(d, integrate, h, ga);
+    } else {
+        if (lpa == 8) k_gather<float, 8><<<gr, G_WARPS * 32, 0, s>>>(d, integrate, h, ga);
+        else k_gather<float, 32><<<gr, G_WARPS * 32, 0, s>>>(d, integrate, h, ga);
+    }
 }
 
 }  // namespace mixd

@@ -341,6 +341,30 @@ __device__ __forceinline__ WSum warp_sum(float v) {
     }
     return {s, c};
 }
+// Compensated sum over the LPA lanes of a group (fixed order; lane 0 of the
+// group holds the result).  For LPA = 32 this is warp_sum.
+template <int LPA>
+__device__ __forceinline__ WSum group_sum(float v, unsigned mask) {
+    float s = v, c = 0.f;
+#pragma unroll
+    for (int o = LPA / 2; o > 0; o >>= 1) {
+        const float s2 = __shfl_down_sync(mask, s, o, LPA);
+        const float c2 = __shfl_down_sync(mask, c, o, LPA);
+        const float t = __fadd_rn(s, s2);
+        const float bb = __fsub_rn(t, s);
+        const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bb)), __fsub_rn(s2, bb));
+        s = t;
+        c = __fadd_rn(__fadd_rn(c, c2), e);
+    }
+    return {s, c};
+}
+template <int LPA>
+__device__ __forceinline__ WSumD group_sum(double v, unsigned mask) {
+#pragma unroll
+    for (int o = LPA / 2; o > 0; o >>= 1) v += __shfl_down_sync(mask, v, o, LPA);
+    return {v};
+}
+
 __device__ __forceinline__ double lane0_double(WSumD w) { return w.s; }
 __device__ __forceinline__ double lane0_double(WSum w) { return (double)w.s + (double)w.c; }
 
