@@ -641,9 +641,32 @@ int read_status(mix_ctx* c) {
     const int st = c->pinned[SW_STATUS];
     if (st & ST_NBR_OVERFLOW)
         return fail(c, MIX_EOVERFLOW, "neighbour list overflow: %d neighbours, capacity %d", c->pinned[SW_MAXNB], c->cap);
-    if (st & ST_NB3_OVERFLOW)
-        return fail(c, MIX_EOVERFLOW, "three-body neighbours %d exceed %d", c->pinned[SW_NB3MAX],
-                    spline_nb3(c->spl_lpa));
+    if (st & ST_NB3_OVERFLOW) {
+        const int seen = c->pinned[SW_NB3MAX], lim = spline_nb3(c->spl_lpa), lpa = c->spl_lpa;
+        if (lpa < 32 && seen <= spline_nb3(32)) {
+            // the cheap kernel's narrow lane groups were chosen from the mean
+            // density and this system has denser spots: widen them to a warp for
+            // the evaluations that follow (this one is incomplete), clear the flag
+            // and make any batch holding the context re-plan
+            size_t smem = 0;
+            int grid = 0;
+            if (spline_configure(c->precision, 32, &smem, &grid) == cudaSuccess) {
+                c->spl_lpa = 32;
+                c->spl_smem = smem;
+                c->spl_grid = c->spl_grid_max = grid;
+                drop_graph(c);
+                c->regions_version++;
+                int w[2] = {st & ~ST_NB3_OVERFLOW, 0};
+                cudaMemcpy(c->dev.status + SW_STATUS, &w[0], sizeof(int), cudaMemcpyHostToDevice);
+                cudaMemcpy(c->dev.status + SW_NB3MAX, &w[1], sizeof(int), cudaMemcpyHostToDevice);
+                return fail(c, MIX_EOVERFLOW,
+                            "three-body neighbours %d exceeded the %d of %d-lane groups; the context now "
+                            "evaluates the cheap potential with a warp per atom: repeat the evaluation",
+                            seen, lim, lpa);
+            }
+        }
+        return fail(c, MIX_EOVERFLOW, "three-body neighbours %d exceed %d", seen, lim);
+    }
     if (st & ST_NONFINITE) return fail(c, MIX_ENUMERIC, "non-finite position or force");
     if (st & ST_OUT_OF_BOX) return fail(c, MIX_EBOX, "an atom left the box in a non-periodic dimension");
     if (st & ST_REV_MISSING) return fail(c, MIX_EINVAL, "asymmetric neighbour list");

@@ -9,6 +9,8 @@
   edge cases (empty system, capacity overflow, atom leaving the box), and the
   256,000-atom screw cylinder on sampled atoms.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -209,6 +211,30 @@ def test_deterministic_and_resumable(mx):
     d = xc[:, :3] - xa[:, :3]
     d -= wl.system.box_len * np.rint(d / wl.system.box_len)
     assert np.abs(d).max() < 1e-12 and _max_abs(vc, va) < 1e-12 and _max_abs(fc, fa) < 1e-10
+
+
+def test_three_body_overflow_widens_the_cheap_lane_groups(mx):
+    """A Si bulk whose mean three-body count puts the cheap potential on
+    quarter-warp lane groups (16 on-chip three-body slots), with a dense spot of
+    18 atoms 0.9 A apart in the vacancy: the first evaluation reports the
+    overflow and widens the groups to a warp; the repeat matches the oracle."""
+    wl = I.si_vacancy(ncell=5)
+    s = wl.system
+    g = np.array([[i, j, k] for i in range(3) for j in range(3) for k in range(2)], float) * 0.9
+    extra = s.box_len / 2 + 0.3 + g - g.mean(axis=0)
+    x = np.concatenate([s.x, np.column_stack([extra, np.zeros(len(extra))])])
+    wl.system = dataclasses.replace(s, x=x, v=np.zeros_like(x))
+    ctx = mx.Context(wl)
+    with pytest.raises(mx.MixError) as e:
+        ctx.forces()
+        ctx.sync()
+    assert e.value.code == mx.MIX_EOVERFLOW and "warp per atom" in str(e.value)
+    ctx.forces()
+    ctx.sync()
+    x1, _, F, _ = ctx.get_state()
+    FB, _, _ = oracle.Model(wl).forces(x1, oracle.MODE_METHOD)
+    assert _max_abs(F[:, :3], FB[:, :3]) < 1e-9 * max(1.0, float(np.abs(FB[:, :3]).max()))
+    ctx.close()
 
 
 def test_host_buffer_entry_point_matches_device_path(mx):
