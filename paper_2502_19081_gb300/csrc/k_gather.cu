@@ -30,8 +30,8 @@ using GSum = decltype(warp_sum(T(0)));
 // with one active lane as with 32, so one float64 instruction should serve many
 // atoms: finishing per block rather than per warp keeps that true when ga is
 // small (ga trades gather latency against the warps a small system keeps busy).
-// LPA lanes gather one atom (a warp, or a quarter warp where lists are short:
-// four atoms of the warp's share at a time).
+// LPA lanes gather one atom (a warp, or half or a quarter of a warp where lists
+// are short: two or four atoms of the warp's share at a time).
 template <typename T, int LPA>
 __device__ __forceinline__ void gather_body(const Dev& d, int bx, int gx, int integrate, double h, int ga,
                                             GSum<T>* park) {
@@ -171,8 +171,9 @@ __global__ void __launch_bounds__(G_WARPS * 32) k_gather(Dev d, int integrate, d
     gather_body<T, LPA>(d, blockIdx.x, gridDim.x, integrate, h, ga, park);
 }
 
-// lanes per gathered atom: a quarter warp for lists of at most 64 slots
-__host__ __device__ inline int gather_lpa(int cap) { return cap <= 64 ? 8 : 32; }
+// lanes per gathered atom (the system's d.gat_lpa: a quarter warp for mean list
+// lengths up to 40, half a warp up to 80, else a warp; 32 when unset)
+__host__ __device__ inline int gather_lpa(const Dev& d) { return d.gat_lpa == 8 || d.gat_lpa == 16 ? d.gat_lpa : 32; }
 
 // Each block belongs to one system and gathers with that system's own lane
 // groups, so a system's forces are bit for bit those it gets alone.
@@ -181,7 +182,9 @@ __global__ void __launch_bounds__(G_WARPS * 32) kb_gather(BatchArgs ba, int inte
     __shared__ GSum<T> park[G_WARPS * G_ATOMS * 6];
     MIX_BATCH_BLOCK(ba)
     const double h = half_kick(dt, s_dev.mass);
-    if (gather_lpa(s_dev.cap) == 8) gather_body<T, 8>(s_dev, s_ent.y, s_ent.z, integrate, h, G_ATOMS, park);
+    const int lpa = gather_lpa(s_dev);
+    if (lpa == 8) gather_body<T, 8>(s_dev, s_ent.y, s_ent.z, integrate, h, G_ATOMS, park);
+    else if (lpa == 16) gather_body<T, 16>(s_dev, s_ent.y, s_ent.z, integrate, h, G_ATOMS, park);
     else gather_body<T, 32>(s_dev, s_ent.y, s_ent.z, integrate, h, G_ATOMS, park);
 }
 
@@ -193,7 +196,7 @@ void launch_gather_batch(const BatchPlan& p, int precision, int integrate, doubl
 }
 
 void launch_gather(const Dev& d, int precision, int integrate, double h, cudaStream_t s) {
-    const int lpa = gather_lpa(d.cap);
+    const int lpa = gather_lpa(d);
     // atoms per warp: enough warps for about half occupancy, at most G_ATOMS, and
     // with quarter-warp groups at least one atom per group
     const int64_t warps_wanted = (int64_t)sm_count() * 32;
@@ -206,9 +209,11 @@ void launch_gather(const Dev& d, int precision, int integrate, double h, cudaStr
     const int gr = grid > 0 ? grid : 1;
     if (precision == MIX_FP64) {
         if (lpa == 8) k_gather<double, 8><<<gr, G_WARPS * 32, 0, s>>>(d, integrate, h, ga);
+        else if (lpa == 16) k_gather<double, 16><<<gr, G_WARPS * 32, 0, s>>>(d, integrate, h, ga);
         else k_gather<double, 32><<<gr, G_WARPS * 32, 0, s>>>(d, integrate, h, ga);
     } else {
         if (lpa == 8) k_gather<float, 8><<<gr, G_WARPS * 32, 0, s>>>(d, integrate, h, ga);
+        else if (lpa == 16) k_gather<float, 16><<<gr, G_WARPS * 32, 0, s>>>(d, integrate, h, ga);
         else k_gather<float, 32><<<gr, G_WARPS * 32, 0, s>>>(d, integrate, h, ga);
     }
 }

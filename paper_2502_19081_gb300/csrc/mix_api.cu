@@ -756,11 +756,14 @@ int mix_init(const mix_system* sys, const mix_ace* a, const mix_spline* sp, cons
     const int64_t ncell = (int64_t)d.cells.nc[0] * d.cells.nc[1] * d.cells.nc[2];
     if (ncell > (1 << 26)) return bad("too many cells");
     d.cells.ncell = (int)ncell;
+    const double rho_mean = vol > 0 ? (double)sys->n_atoms / vol : 0.0;
+    const double expect = rho_mean * 4.0 / 3.0 * M_PI * c->rlist * c->rlist * c->rlist;
+    // gather lane groups from the mean list length (not the capacity, so that the
+    // order of every sum, and with it every result, is independent of it)
+    d.gat_lpa = expect <= 40.0 ? 8 : (expect <= 80.0 ? 16 : 32);
     if (opt->nbr_cap > 0) {
         c->cap = opt->nbr_cap;
     } else {
-        const double rho = vol > 0 ? (double)sys->n_atoms / vol : 0.0;
-        const double expect = rho * 4.0 / 3.0 * M_PI * c->rlist * c->rlist * c->rlist;
         int cap = (int)std::ceil(1.4 * expect + 16.0);
         cap = std::max(cap, 64);
         c->cap = ((cap + 31) / 32) * 32;

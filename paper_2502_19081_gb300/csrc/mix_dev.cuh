@@ -113,6 +113,7 @@ struct Dev {
     // inside, above hi outside (1e-3 A^2 either side of the radius, against a
     // float error below 1e-4 A^2); in between the float64 test decides
     float bufe2_lo, bufe2_hi, bufc2_lo, bufc2_hi;
+    int gat_lpa;         // lanes per atom of the gather (8, 16, 32), from the mean list length
     int exact_lists;     // 1: every neighbour candidate takes the float64 test
                          // (boxes beyond the float pre-filter's error bound)
     double4* x;
