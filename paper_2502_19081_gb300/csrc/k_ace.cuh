@@ -11,23 +11,21 @@
 //      shared memory, then each lane accumulates fixed (lm, 4 q) outputs;
 //   3. nu <= 2 readout; omega = dE/dA initialised;
 //   4. nu = 3, one l-triple (l1, l2, l3) after the other.  The triple's tables
-//      (W[q1 q2][q3], its transpose, the Gaunt entries in three orderings and
-//      their offsets) form one tile; the CTA streams the tiles from global
-//      memory into two shared-memory buffers with cp.async, fetching tile t+1
-//      while the warps work on tile t, so a tile crosses L2 once per group of
-//      atoms rather than once per atom.  Per warp:
+//      (W[q1 q2][q3], the Gaunt entries in three orderings and their offsets)
+//      form one tile; the CTA streams the tiles from global memory into two
+//      shared-memory buffers with cp.async, fetching tile t+1 while the warps
+//      work on tile t, so a tile crosses L2 once per group of atoms rather
+//      than once per atom.  Per warp, one pass over lane units (q1, block of qb
+//      consecutive q2; the W rows of the block sit in registers) does all of
 //        U[m3][q1][q2] = sum_q3 W[q1 q2][q3] A3[m3][q3]
 //        Z[m3][q1 q2]  = sum_(m1 m2) G A1[m1][q1] A2[m2][q2]     (Gaunt-sparse)
-//        E += sum Z U;  omega3 += W^T Z;  omega1 += G A2 U;  omega2 += G A1 U.
-//      In the U/Z pass a lane owns one q1 and a block of qb consecutive q2 (the
-//      W rows of that block sit in registers), so each Gaunt entry costs one
-//      packed entry load, one scalar A1 load and one vector A2 load for qb
-//      accumulations; omega3 = W^T Z with a lane per (2 q3) x (2 m3) block.
-//      Where two l's coincide W is symmetrised on the host, the adjoints
-//      through the coinciding factors are equal, and one of them is computed
-//      and scaled (omega2 only for distinct l's, omega1 not when all three are
-//      equal).  Each warp adds into its own atom's omega: no reduction across
-//      warps and no balancing of triples over warps;
+//        E += sum Z U;  omega3 += W^T Z;  omega1 += G A2 U
+//      with U and Z in registers (see nu3_units); omega2 += G A1 U, needed
+//      for distinct l's only, reads U from shared memory afterwards.  Where two
+//      l's coincide W is symmetrised on the host, the adjoints through the
+//      coinciding factors are equal, and one of them is computed and scaled.
+//      Each warp adds into its own atom's omega: no reduction across warps
+//      and no balancing of triples over warps;
 //   5. pair gradients dE_i/dr_ij = u sum_lm sigma_lm Y_lm
 //        + (grad_u p - u (u . grad_u p)) / r,  rho = omega R, sigma = omega R',
 //      a lane per neighbour with R, R', Y recomputed in registers; written per
