@@ -195,28 +195,43 @@ __global__ void __launch_bounds__(SEED_WARPS * 32) k_blend(Dev d, SeedRule sr) {
 
 constexpr int BUF_WARPS = 8;
 
-// One warp per atom: buffer membership through the neighbour list.
-__device__ __forceinline__ void buffer_body(const Dev& d, int bx, int gx) {
+// Buffer membership through the neighbour list.  A warp takes apw <= 32
+// consecutive atoms: each lane tests its atom's flags (and the hints k_lambda
+// left), then the whole warp scans, one after another, the lists of the atoms
+// that need it.  In a large system most atoms need no scan and then cost a
+// lane rather than a warp (apw = 32); a small one keeps a warp per atom (apw =
+// 1) so that its few scans run side by side.
+__device__ __forceinline__ void buffer_body(const Dev& d, int bx, int gx, int apw) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int64_t i = (int64_t)bx * BUF_WARPS + warp; i < d.n; i += (int64_t)gx * BUF_WARPS) {
-        const int fl = d.flags[i];
+    // float screen from the cell-relative float positions the potentials use;
+    // float64 only within 1e-3 A^2 of a buffer radius
+    const bool screen = d.xr != nullptr && !d.exact_lists;
+    for (int64_t base = ((int64_t)bx * BUF_WARPS + warp) * apw; base < d.n;
+         base += (int64_t)gx * BUF_WARPS * apw) {
+        const int64_t im = base + lane;
+        const bool valid = lane < apw && im < d.n;
+        const int fl = valid ? (int)d.flags[im] : 0;
         const int f = fl & 3;
         // scan unless k_lambda's hints (bits 4, 5; geometric regions only) rule it out
-        const bool need_e = !(f & 1) && !(fl & 16), need_c = !(f & 2) && !(fl & 32);
-        bool he = false, hc = false;
-        if (need_e || need_c) {
+        const bool my_ne = valid && !(f & 1) && !(fl & 16), my_nc = valid && !(f & 2) && !(fl & 32);
+        unsigned todo = __ballot_sync(0xffffffffu, my_ne || my_nc);
+        bool my_he = false, my_hc = false;
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int64_t i = base + src;
+            const bool need_e = __shfl_sync(0xffffffffu, my_ne, src);
+            const bool need_c = __shfl_sync(0xffffffffu, my_nc, src);
             const double4 xi = d.x[i];
             const int m = d.nnb[i];
             const int* row = d.nbr + i * (int64_t)d.cap;
-            // float screen from the cell-relative float positions the potentials
-            // use; float64 only within 1e-3 A^2 of a buffer radius
-            const bool screen = d.xr != nullptr && !d.exact_lists;
             float4 xri = make_float4(0.f, 0.f, 0.f, 0.f);
             int ci = 0;
             if (screen) {
                 xri = d.xr[i];
                 ci = d.cell3[i];
             }
+            bool he = false, hc = false;
             for (int s = lane; s < m; s += 32) {
                 const int j = row[s];
                 const int fj = d.flags[j] & 3;
@@ -247,15 +262,21 @@ __device__ __forceinline__ void buffer_body(const Dev& d, int bx, int gx) {
             }
             he = __any_sync(0xffffffffu, he);
             hc = __any_sync(0xffffffffu, hc);
+            if (lane == src) {
+                my_he = he;
+                my_hc = hc;
+            }
         }
-        if (lane == 0) {
-            const int ae = (f & 1) || he ? 4 : 0;
-            const int ac = (f & 2) || hc ? 8 : 0;
-            d.flags[i] = (uint8_t)(f | ae | ac);
+        if (valid) {
+            const int ae = (f & 1) || my_he ? 4 : 0;
+            const int ac = (f & 2) || my_hc ? 8 : 0;
+            d.flags[im] = (uint8_t)(f | ae | ac);
         }
     }
 }
-__global__ void __launch_bounds__(BUF_WARPS * 32) k_buffer(Dev d) { buffer_body(d, blockIdx.x, gridDim.x); }
+__global__ void __launch_bounds__(BUF_WARPS * 32) k_buffer(Dev d, int apw) {
+    buffer_body(d, blockIdx.x, gridDim.x, apw);
+}
 
 // Per-block counts of the two evaluated sets (and of the diagnostic sets).
 __device__ __forceinline__ void count_body(const Dev& d, int bx) {
@@ -375,7 +396,7 @@ __global__ void kb_lambda(BatchArgs ba, const Regions* __restrict__ regions) {
 }
 __global__ void __launch_bounds__(BUF_WARPS * 32) kb_buffer(BatchArgs ba) {
     MIX_BATCH_BLOCK(ba)
-    buffer_body(s_dev, s_ent.y, s_ent.z);
+    buffer_body(s_dev, s_ent.y, s_ent.z, 32);
 }
 __global__ void __launch_bounds__(SCAN_BLOCK) kb_count(BatchArgs ba) {
     MIX_BATCH_BLOCK(ba)
@@ -443,10 +464,16 @@ void launch_sets(const Dev& d, const Regions& r, const SeedRule& sr, cudaStream_
         k_core<<<gs > 0 ? gs : 1, SEED_WARPS * 32, 0, s>>>(d, sr);
         k_blend<<<gs > 0 ? gs : 1, SEED_WARPS * 32, 0, s>>>(d, sr);
     }
-    int64_t want = (d.n + BUF_WARPS - 1) / BUF_WARPS;
+    // atoms per warp: one up to 512 atoms per SM (a 256,000-atom system gets 3,
+    // which keeps its shell of scanning atoms spread over many warps), up to 32
+    // beyond
+    const int64_t warps_full = (int64_t)sm_count() * 512;
+    int64_t apw = (d.n + warps_full - 1) / warps_full;
+    apw = apw < 1 ? 1 : (apw > 32 ? 32 : apw);
+    int64_t want = (d.n + BUF_WARPS * apw - 1) / (BUF_WARPS * apw);
     int64_t lim = d.grid_buffer > 0 ? d.grid_buffer : (int64_t)sm_count() * 8;
     const int gb = (int)(want < lim ? want : lim);
-    k_buffer<<<gb > 0 ? gb : 1, BUF_WARPS * 32, 0, s>>>(d);
+    k_buffer<<<gb > 0 ? gb : 1, BUF_WARPS * 32, 0, s>>>(d, (int)apw);
     k_count<<<d.nblk, SCAN_BLOCK, 0, s>>>(d);
     k_scatter<<<d.nblk, SCAN_BLOCK, 0, s>>>(d);
 }
