@@ -189,7 +189,7 @@ struct mix_ctx {
     // tables (offsets in the arena) and their element-type views
     Arena arena;
     size_t o_c1, o_S2, o_tiles, o_toff, o_ylmk, o_pair, o_sc2, o_sc3;
-    int ntau, np, nq, qb, tile_max;
+    int ntau, np, qb, tile_max;
     AceTab<double> ace64;
     AceTab<float> ace32;
     SplTab<double> spl64;
@@ -363,11 +363,10 @@ int build_tables(mix_ctx* c, const mix_ace* a, const mix_spline* sp) {
                : (l1 == l2 || l2 == l3) ? nn * nn * (nn + 1) / 2 : nn * nn * nn;
     }
     c->basis_size = n + (a->nu_max >= 2 ? (int64_t)L1 * n * (n + 1) / 2 : 0) + nb3;
-    // padded layouts of the nu = 3 coefficients: W[q1 q2][q3] rows of np, and its
-    // transpose W[q3][q1 q2] rows of nq (zeros in the padding)
-    const int np = (n + 3) & ~3, nq = (n * n + 3) & ~3;
+    // padded layout of the nu = 3 coefficients: W[q1 q2][q3] rows of np (zeros
+    // in the padding)
+    const int np = (n + 3) & ~3;
     c->np = np;
-    c->nq = nq;
     // Where two l's of a triple coincide the Gaunt factor is symmetric in the
     // matching (l, m) pairs, so the energy only sees the part of W symmetric in
     // the matching n indices.  Symmetrising W there leaves E unchanged and makes
@@ -462,7 +461,6 @@ void fill_tabs(mix_ctx* c, unsigned char* base, AceTab<T>& at, SplTab<T>& st) {
     at.nlm = (c->L + 1) * (c->L + 1);
     at.ntau = c->ntau;
     at.np = c->np;
-    at.nq = c->nq;
     at.rc = c->ace_rc;
     at.c1 = reinterpret_cast<const T*>(base + c->o_c1);
     at.S2 = reinterpret_cast<const T*>(base + c->o_S2);

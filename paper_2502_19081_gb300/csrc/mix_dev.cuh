@@ -257,7 +257,6 @@ template <typename T>
 struct AceTab {
     int n, L, nu, nlm, ntau;
     int np;             // n rounded up to a multiple of 4 (row length of padded tables)
-    int nq;             // n*n rounded up to a multiple of 4
     int qb;             // q2 block per lane in the nu = 3 U/Z pass (divides np)
     int tile_max;       // bytes of the largest nu = 3 tile
     double rc;
