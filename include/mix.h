@@ -17,6 +17,12 @@
  *    detected by kernels (capacity overflow, non-finite values, an atom leaving
  *    a non-periodic box) surface at the next synchronising call: mix_sync(),
  *    the mix_get_* exports, mix_get_state() and the *_host entry points.
+ *  - MIX_EOVERFLOW has two causes.  A neighbour row longer than the context's
+ *    capacity is fatal for the context until it is re-created with a larger
+ *    one.  A three-body neighbour count above what the cheap kernel's narrow
+ *    lane groups hold (chosen at mix_init from the mean density) makes the
+ *    context switch to a warp per atom for later evaluations; the forces of
+ *    the failing evaluation are incomplete and the caller repeats it.
  *  - Ownership: positions, velocities, forces and the workspace are caller-owned
  *    device buffers that the library borrows from mix_bind() until the next
  *    mix_bind() or mix_destroy(); it never frees them.  Host arrays passed to

@@ -202,7 +202,7 @@ struct mix_ctx {
         o_seed, o_core, o_zsum;
     size_t ace_smem, spl_smem;
     int ace_grid, spl_grid;
-    int spl_lpa;                      // lanes per atom of the cheap kernel (32 or 16)
+    int spl_lpa;                      // lanes per atom of the cheap kernel (32, 16 or 8)
     int ace_grid_max, spl_grid_max;   // resident CTAs at full occupancy
     int64_t gaunt_nnz, tau_d3_sum, basis_size;
     double nu3_flops;

@@ -22,7 +22,7 @@ void launch_ace_f32(const Dev& d, const void* tab, int L, size_t smem, int grid,
 void launch_ace_f64(const Dev& d, const void* tab, int L, size_t smem, int grid, cudaStream_t s);
 
 // cheap potential (k_spline.cu)
-// lpa: lanes per evaluated atom (32, or 16 for atoms with few neighbours);
+// lpa: lanes per evaluated atom (32, or 16 or 8 for atoms with few neighbours);
 // spline_nb3(lpa): three-body neighbours an atom may have on chip with lpa lanes
 cudaError_t spline_configure(int precision, int lpa, size_t* smem, int* grid);
 int spline_nb3(int lpa);

@@ -602,19 +602,26 @@ class Server:
 
 def open_context(workload, precision: int = MIX_FP64, retries: int = 2, **kw) -> Context:
     """Create a context and evaluate forces once; if the neighbour capacity
-    overflows, recreate it with room for the observed maximum."""
+    overflows, recreate it with room for the observed maximum.  A three-body
+    overflow of the cheap kernel's narrow lane groups (the neighbour rows fit)
+    has already widened them inside the context: the evaluation is repeated on
+    the same context."""
     cap = kw.pop("nbr_cap", 0)
     for _ in range(retries + 1):
         ctx = Context(workload, precision=precision, nbr_cap=cap, **kw)
-        try:
-            ctx.forces()
-            ctx.sync()
-            return ctx
-        except MixError as e:
-            if e.code != MIX_EOVERFLOW:
-                raise
-            st = ctx.stats(check=False)
-            need = max(int(st["max_neighbours"]), ctx.cap + 1)
-            ctx.close()
-            cap = min(256, ((int(need * 1.25) + 31) // 32) * 32)
+        for _ in range(2):
+            try:
+                ctx.forces()
+                ctx.sync()
+                return ctx
+            except MixError as e:
+                if e.code != MIX_EOVERFLOW:
+                    raise
+                st = ctx.stats(check=False)
+                if int(st["max_neighbours"]) <= ctx.cap:
+                    continue
+                break
+        need = max(int(st["max_neighbours"]), ctx.cap + 1)
+        ctx.close()
+        cap = min(256, ((int(need * 1.25) + 31) // 32) * 32)
     raise MixError(MIX_EOVERFLOW, "neighbour capacity could not be sized")

@@ -234,7 +234,15 @@ def test_three_body_overflow_widens_the_cheap_lane_groups(mx):
     x1, _, F, _ = ctx.get_state()
     FB, _, _ = oracle.Model(wl).forces(x1, oracle.MODE_METHOD)
     assert _max_abs(F[:, :3], FB[:, :3]) < 1e-9 * max(1.0, float(np.abs(FB[:, :3]).max()))
+    cap0 = ctx.cap
     ctx.close()
+    # open_context repeats the evaluation on the widened context instead of
+    # growing the neighbour capacity
+    b = mx.open_context(wl)
+    _, _, Fb, _ = b.get_state()
+    assert b.cap == cap0
+    assert _max_abs(Fb[:, :3], FB[:, :3]) < 1e-9 * max(1.0, float(np.abs(FB[:, :3]).max()))
+    b.close()
 
 
 def test_host_buffer_entry_point_matches_device_path(mx):
