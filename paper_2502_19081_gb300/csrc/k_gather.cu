@@ -37,6 +37,7 @@ __device__ __forceinline__ void gather_body(const Dev& d, int bx, int gx, int in
                                             GSum<T>* park) {
     using V = typename Vec4<T>::type;
     constexpr int G = 32 / LPA;
+    constexpr int GU = 2;   // slots a lane loads before summing them
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int sub = lane & (LPA - 1), grp = lane / LPA;
     const unsigned mask = LPA == 32 ? 0xffffffffu : (((1u << LPA) - 1u) << (lane & ~(LPA - 1)));
@@ -52,44 +53,69 @@ __device__ __forceinline__ void gather_body(const Dev& d, int bx, int gx, int in
         const int nb = (int)(d.n - b0 < per_block ? d.n - b0 : per_block);
         const int a0 = warp * ga;
         const int na = nb - a0 >= ga ? ga : (nb - a0 > 0 ? nb - a0 : 0);
+        // the next atom's list length and flags are loaded ahead
+        int mn = 0, fn = 0;
+        if (grp < na) {
+            mn = d.nnb[b0 + a0 + grp];
+            fn = d.flags[b0 + a0 + grp];
+        }
         for (int a = grp; a < na; a += G) {
             const int64_t k = b0 + a0 + a;
-            const int m = d.nnb[k];
-            const int fk = d.flags[k];
+            const int m = mn, fk = fn;
+            if (a + G < na) {
+                mn = d.nnb[k + G];
+                fn = d.flags[k + G];
+            }
             const bool own_e = (fk & 4) != 0, own_c = (fk & 8) != 0;
             // w > 0 iff lambda > 0 and w < 1 iff lambda < 1 (flags bits 0, 1)
             const bool use_e = (fk & 1) != 0, use_c = (fk & 2) != 0;
             const int64_t base = k * cap;
             // own row: dE_k/dr_kj; incoming row: dE_j/dr_jk, present when j was
-            // evaluated in this evaluation (its stamp is current)
+            // evaluated in this evaluation (its stamp is current).  A lane loads
+            // GU of its slots before it sums them (in slot order).
             T tex = T(0), tey = T(0), tez = T(0), tcx = T(0), tcy = T(0), tcz = T(0);
-            for (int s = sub; s < m; s += LPA) {
-                if (use_e) {
-                    if (own_e) {
-                        const V g = GE[base + s];
-                        tex += g.x;
-                        tey += g.y;
-                        tez += g.z;
-                    }
-                    const V g = GEI[base + s];
-                    if (stamp_is(g.w, stamp)) {
-                        tex -= g.x;
-                        tey -= g.y;
-                        tez -= g.z;
+            for (int s0 = sub; s0 < m; s0 += GU * LPA) {
+                if (use_e) {   // few atoms: slot by slot
+#pragma unroll 1
+                    for (int s = s0; s < m && s < s0 + GU * LPA; s += LPA) {
+                        if (own_e) {
+                            const V g = GE[base + s];
+                            tex += g.x;
+                            tey += g.y;
+                            tez += g.z;
+                        }
+                        const V g = GEI[base + s];
+                        if (stamp_is(g.w, stamp)) {
+                            tex -= g.x;
+                            tey -= g.y;
+                            tez -= g.z;
+                        }
                     }
                 }
                 if (use_c) {
-                    if (own_c) {
-                        const V g = GC[base + s];
-                        tcx += g.x;
-                        tcy += g.y;
-                        tcz += g.z;
+                    V go[GU], gi[GU];
+#pragma unroll
+                    for (int u = 0; u < GU; ++u) {
+                        const int s = s0 + u * LPA;
+                        if (s < m) {
+                            if (own_c) go[u] = GC[base + s];
+                            gi[u] = GCI[base + s];
+                        }
                     }
-                    const V g = GCI[base + s];
-                    if (stamp_is(g.w, stamp)) {
-                        tcx -= g.x;
-                        tcy -= g.y;
-                        tcz -= g.z;
+#pragma unroll
+                    for (int u = 0; u < GU; ++u) {
+                        if (s0 + u * LPA < m) {
+                            if (own_c) {
+                                tcx += go[u].x;
+                                tcy += go[u].y;
+                                tcz += go[u].z;
+                            }
+                            if (stamp_is(gi[u].w, stamp)) {
+                                tcx -= gi[u].x;
+                                tcy -= gi[u].y;
+                                tcz -= gi[u].z;
+                            }
+                        }
                     }
                 }
             }
@@ -166,7 +192,7 @@ __device__ __forceinline__ void gather_body(const Dev& d, int bx, int gx, int in
 }
 
 template <typename T, int LPA>
-__global__ void __launch_bounds__(G_WARPS * 32) k_gather(Dev d, int integrate, double h, int ga) {
+__global__ void __launch_bounds__(G_WARPS * 32, sizeof(T) == 4 ? 4 : 2) k_gather(Dev d, int integrate, double h, int ga) {
     __shared__ GSum<T> park[G_WARPS * G_ATOMS * 6];
     gather_body<T, LPA>(d, blockIdx.x, gridDim.x, integrate, h, ga, park);
 }

@@ -408,7 +408,7 @@ __global__ void __launch_bounds__(SCAN_BLOCK) kb_scatter(BatchArgs ba) {
 }
 
 // Flattened lists of the evaluated atoms of every system: block s writes
-// {s, k} for k below its cheap count, and {s, ACE_GROUP k} for each group of
+// {s, i} for each atom i of its cheap list, and {s, ACE_GROUP k} for each group of
 // ACE_GROUP consecutive atoms of its expensive list (a CTA of the expensive
 // kernel takes one such group), at the sum of the counts of the systems before
 // it (within its expensive group; all systems for cheap).  The last system of
@@ -443,7 +443,8 @@ __global__ void kb_flatten(FlatArgs f) {
     int2* le = f.list_e + f.ebase[g] + oe;
     int2* lc = f.list_c + oc;
     for (int k = tid; k < ne; k += blockDim.x) le[k] = make_int2(s, k * ACE_GROUP);
-    for (int k = tid; k < nc; k += blockDim.x) lc[k] = make_int2(s, k);
+    const int* act_c = f.devs[s].act_c;
+    for (int k = tid; k < nc; k += blockDim.x) lc[k] = make_int2(s, act_c[k]);
     if (tid == 0) {
         if (f.elast[s]) f.counts[g] = oe + ne;
         if (s == f.nsys - 1) f.counts[f.ngrp] = oc + nc;

@@ -3,12 +3,16 @@
 //   E_i = 1/2 sum_j V2(r_ij) + sum_{j<k; r_ij, r_ik < rc3} V3(r_ij, r_ik, r_jk).
 // A group of LPA lanes per evaluated atom (a whole warp, or half or a quarter
 // of a warp where atoms have few neighbours: two or four atoms a warp).  Lanes own list slots for the
-// 2-body part and the final write; the 3-body pairs (j, k) are spread over the
-// lanes, their partial derivatives go to a per-group table, and each lane then
-// sums the rows of its own 3-body neighbour in a fixed order (no atomics, so
-// results are bit-reproducible).
-//   dV3 -> g_j += a_jk u_j + c_jk (r_j - r_k),  a_jk = dV3/d(first argument),
-//          c_jk = (dV3/dr_jk) / r_jk  (c3 symmetric in its first two indices).
+// 2-body part and the final write; the 3-body pairs (p, q), p < q, numbered
+// t = q (q - 1) / 2 + p (so the pairs of the first n3 neighbours are t <
+// n3 (n3 - 1) / 2 whatever n3 is), are spread over the lanes, their partial
+// derivatives go to per-group tables, and each lane then sums the pairs of its
+// own 3-body neighbour in a fixed order (no atomics, so results are
+// bit-reproducible).
+//   dV3 -> g_p += a_p u_p + c_pq (r_p - r_q),  a_p = dV3/d r_p,
+//          c_pq = (dV3/dr_pq) / r_pq  (c3 symmetric in its first two indices).
+// Coefficients are read as windows: the four control points of one interval
+// are one aligned vector (one shared-memory load).
 #include "mix_launch.h"
 
 namespace mixd {
@@ -22,8 +26,8 @@ __host__ __device__ constexpr int spl_nb() {
     return LPA == 32 ? NB3MAX : (LPA == 16 ? 24 : 16);
 }
 
-__device__ __forceinline__ double tsqrt3(double x) { return sqrt(x); }
-__device__ __forceinline__ float tsqrt3(float x) { return sqrtf(x); }
+__device__ __forceinline__ double trsqrt(double x) { return rsqrt(x); }
+__device__ __forceinline__ float trsqrt(float x) { return rsqrtf(x); }
 
 template <typename T>
 __device__ __forceinline__ void bspline4(T x, int qmax, int& q, T b[4], T db[4]) {
@@ -41,28 +45,41 @@ __device__ __forceinline__ void bspline4(T x, int qmax, int& q, T b[4], T db[4])
     db[3] = T(0.5) * u2;
 }
 
-// index of the pair p < q in a packed upper triangle of an NB x NB table
-template <int NB>
-__device__ __forceinline__ int tri3(int p, int q) { return p * NB - p * (p + 1) / 2 + (q - p - 1); }
-
 template <typename T, int NB>
 struct SplWarp {   // per-group shared scratch
-    static constexpr int S = NB + 1;   // padded row stride of the pair table
+    static constexpr int NP = NB * (NB - 1) / 2;
+    typename Vec4<T>::type v[NB];   // r_ij (x, y, z) and |r_ij| of the 3-body neighbours
+    T hp[NB];           // (dV2/dr) / (2 r): the slot's 2-body gradient is hp r_ij
+    T ir[NB];           // 1 / |r_ij|
     int slot[NB];
-    T v[NB][4];         // r_ij vector (x, y, z) and |r_ij|
-    T g2[NB][4];        // 2-body part of dE_i/dr_ij of the 3-body neighbours
-    T al[NB * S];       // a_jk
-    T cc[NB * (NB - 1) / 2];   // c_jk (symmetric: pairs p < q only)
+    T a1[NP];           // pair t = (p, q): dV3/dr_p
+    T a2[NP];           //                  dV3/dr_q
+    T cc[NP];           //                  (dV3/dr_pq) / r_pq
 };
 
-// One evaluated atom (index a of the system's cheap list), by the group of
-// LPA lanes that owns W; the coefficient tables c2s, c3s may sit in shared or
+// shared bytes of the pair-number table tq[t] = q of pair t (the block's groups share it)
+template <int NB>
+__host__ __device__ constexpr int spl_tq_bytes() {
+    return (NB * (NB - 1) / 2 + 15) / 16 * 16;
+}
+
+template <int NB>
+__device__ __forceinline__ void spl_fill_tq(unsigned char* tq) {
+    for (int t = threadIdx.x; t < NB * (NB - 1) / 2; t += blockDim.x) {
+        int q = 1;
+        while (q * (q + 1) / 2 <= t) ++q;
+        tq[t] = (unsigned char)q;
+    }
+}
+
+// One evaluated atom i (an entry of the system's cheap list), by the group of
+// LPA lanes that owns W; the coefficient windows c2w, c3w may sit in shared or
 // global memory.
 template <typename T, int LPA>
-__device__ __forceinline__ void spline_atom(const Dev& d, const SplTab<T>& tab, int a, const T* c2s, const T* c3s,
-                                            SplWarp<T, spl_nb<LPA>()>& W) {
+__device__ __forceinline__ void spline_atom(const Dev& d, const SplTab<T>& tab, int i,
+                                            const typename Vec4<T>::type* c2w, const typename Vec4<T>::type* c3w,
+                                            const unsigned char* tq, SplWarp<T, spl_nb<LPA>()>& W) {
     constexpr int NB = spl_nb<LPA>();
-    constexpr int S = SplWarp<T, NB>::S;
     using V = typename Vec4<T>::type;
     const int lane = threadIdx.x & 31;
     const int sub = lane & (LPA - 1);
@@ -75,7 +92,7 @@ __device__ __forceinline__ void spline_atom(const Dev& d, const SplTab<T>& tab, 
     const unsigned lt = (1u << lane) - 1u;   // the ballots carry this group's lanes only
     const int cap = d.cap;
     {
-        const int i = d.act_c[a];
+        using Pt = typename PairFrame<T>::Pt;
         const PairFrame<T> pf(d, i);
         const int m = d.nnb[i];
         const int* row = d.nbr + (int64_t)i * cap;
@@ -84,50 +101,65 @@ __device__ __forceinline__ void spline_atom(const Dev& d, const SplTab<T>& tab, 
         T ep = T(0);
         int n3 = 0;
         // 2-body part; a slot without 3-body terms is final here (own row and the
-        // partner's incoming row); a 3-body slot waits in the group's table
+        // partner's incoming row); a 3-body slot waits in the group's table.
+        // The next chunk's partner, reverse slot and position are loaded before
+        // this chunk is evaluated, so their latency overlaps its arithmetic.
+        int jn = 0, rn = 0;
+        Pt ptn{};
+        if (sub < m) {
+            jn = row[sub];
+            rn = rvr[sub];
+            ptn = PairFrame<T>::load(d, jn);
+        }
         for (int c = 0; c * LPA < m; ++c) {
             const int s = c * LPA + sub;
+            const int j = jn, rj = rn;
+            const Pt pt = ptn;
+            if (s + LPA < m) {
+                jn = row[s + LPA];
+                rn = rvr[s + LPA];
+                ptn = PairFrame<T>::load(d, jn);
+            }
             bool is3 = false;
-            T dv3[3] = {T(0), T(0), T(0)}, r = T(0), g2[3] = {T(0), T(0), T(0)};
+            T dv3[3] = {T(0), T(0), T(0)}, r = T(0), hp = T(0), ri = T(0);
             if (s < m) {
                 T r2;
-                pf.vec(d, row[s], dv3, r2);
+                pf.vec(d, pt, dv3, r2);
                 if (r2 < rc2) {
-                    r = sqrt(r2);
-                    T v, dv;
+                    ri = trsqrt(r2);
+                    r = r2 * ri;
                     int q;
                     T b[4], db[4];
-                    bspline4<T>(r * invh2, 12, q, b, db);
-                    v = c2s[q] * b[0] + c2s[q + 1] * b[1] + c2s[q + 2] * b[2] + c2s[q + 3] * b[3];
-                    dv = (c2s[q] * db[0] + c2s[q + 1] * db[1] + c2s[q + 2] * db[2] + c2s[q + 3] * db[3]) * invh2;
+                    bspline4<T>(r * invh2, SPL_W2 - 1, q, b, db);
+                    const V w = c2w[q];
+                    const T v = w.x * b[0] + w.y * b[1] + w.z * b[2] + w.w * b[3];
+                    const T dv = (w.x * db[0] + w.y * db[1] + w.z * db[2] + w.w * db[3]) * invh2;
                     ep += T(0.5) * v;
-                    const T hp = T(0.5) * dv / r;
-                    g2[0] = hp * dv3[0];
-                    g2[1] = hp * dv3[1];
-                    g2[2] = hp * dv3[2];
+                    hp = T(0.5) * dv * ri;
                     is3 = r2 < rc32;
                 }
             }
             const unsigned bal = __ballot_sync(mask, is3);
             const int p = is3 ? n3 + __popc(bal & lt) : -1;
             if (is3 && p < NB) {
+                V u;
+                u.x = dv3[0];
+                u.y = dv3[1];
+                u.z = dv3[2];
+                u.w = r;
+                W.v[p] = u;
+                W.hp[p] = hp;
+                W.ir[p] = ri;
                 W.slot[p] = s;
-                W.v[p][0] = dv3[0];
-                W.v[p][1] = dv3[1];
-                W.v[p][2] = dv3[2];
-                W.v[p][3] = r;
-                W.g2[p][0] = g2[0];
-                W.g2[p][1] = g2[1];
-                W.g2[p][2] = g2[2];
             } else if (s < m) {
                 V gv;
-                gv.x = g2[0];
-                gv.y = g2[1];
-                gv.z = g2[2];
+                gv.x = hp * dv3[0];
+                gv.y = hp * dv3[1];
+                gv.z = hp * dv3[2];
                 gv.w = T(0);
                 grow[s] = gv;
                 gv.w = stamp_as(T(0), stamp);
-                GIN[(int64_t)row[s] * cap + rvr[s]] = gv;   // the partner's incoming row
+                GIN[(int64_t)j * cap + rj] = gv;   // the partner's incoming row
             }
             n3 += __popc(bal);
         }
@@ -139,60 +171,76 @@ __device__ __forceinline__ void spline_atom(const Dev& d, const SplTab<T>& tab, 
             n3 = NB;
         }
         __syncwarp(mask);
-        // 3-body pairs p < q, flattened over the lanes
+        // 3-body pairs t = q (q - 1) / 2 + p, p < q < n3, over the lanes
         const int npair = n3 * (n3 - 1) / 2;
         for (int t = sub; t < npair; t += LPA) {
-            int p = 0, tt = t;
-            while (tt >= n3 - 1 - p) {
-                tt -= n3 - 1 - p;
-                ++p;
-            }
-            const int q = p + 1 + tt;
-            const T wx = W.v[q][0] - W.v[p][0], wy = W.v[q][1] - W.v[p][1], wz = W.v[q][2] - W.v[p][2];
-            const T r3 = tsqrt3(wx * wx + wy * wy + wz * wz);
+            const int q = tq[t], p = t - q * (q - 1) / 2;
+            const V vp = W.v[p], vq = W.v[q];
+            const T wx = vq.x - vp.x, wy = vq.y - vp.y, wz = vq.z - vp.z;
+            const T w2 = wx * wx + wy * wy + wz * wz;
+            const T ri3 = w2 > T(0) ? trsqrt(w2) : T(0);
+            const T r3 = w2 * ri3;
             int qa, qb, qc;
             T ba[4], dba[4], bb[4], dbb[4], bc[4], dbc[4];
-            bspline4<T>(W.v[p][3] * invh3, 4, qa, ba, dba);
-            bspline4<T>(W.v[q][3] * invh3, 4, qb, bb, dbb);
-            bspline4<T>(r3 * invhc, 4, qc, bc, dbc);
+            bspline4<T>(vp.w * invh3, SPL_W3 - 1, qa, ba, dba);
+            bspline4<T>(vq.w * invh3, SPL_W3 - 1, qb, bb, dbb);
+            bspline4<T>(r3 * invhc, SPL_W3 - 1, qc, bc, dbc);
+            // contract the third argument, then the second, then the first
             T val = T(0), d1 = T(0), d2 = T(0), d3 = T(0);
 #pragma unroll
             for (int x = 0; x < 4; ++x) {
+                const V* cr = c3w + ((qa + x) * 8 + qb) * SPL_W3 + qc;
+                T s0 = T(0), s1 = T(0), s3 = T(0);
 #pragma unroll
                 for (int y = 0; y < 4; ++y) {
-                    const T* cr = c3s + ((qa + x) * 8 + (qb + y)) * 8 + qc;
-                    const T t0 = cr[0] * bc[0] + cr[1] * bc[1] + cr[2] * bc[2] + cr[3] * bc[3];
-                    const T t1 = cr[0] * dbc[0] + cr[1] * dbc[1] + cr[2] * dbc[2] + cr[3] * dbc[3];
-                    val += t0 * ba[x] * bb[y];
-                    d1 += t0 * dba[x] * bb[y];
-                    d2 += t0 * ba[x] * dbb[y];
-                    d3 += t1 * ba[x] * bb[y];
+                    const V w = cr[y * SPL_W3];
+                    const T t0 = w.x * bc[0] + w.y * bc[1] + w.z * bc[2] + w.w * bc[3];
+                    const T t1 = w.x * dbc[0] + w.y * dbc[1] + w.z * dbc[2] + w.w * dbc[3];
+                    s0 += t0 * bb[y];
+                    s1 += t0 * dbb[y];
+                    s3 += t1 * bb[y];
                 }
+                val += s0 * ba[x];
+                d1 += s0 * dba[x];
+                d2 += s1 * ba[x];
+                d3 += s3 * ba[x];
             }
             ep += val;
-            const T c = r3 > T(0) ? d3 * invhc / r3 : T(0);
-            W.al[p * S + q] = d1 * invh3;
-            W.al[q * S + p] = d2 * invh3;
-            W.cc[tri3<NB>(p, q)] = c;
+            W.a1[t] = d1 * invh3;
+            W.a2[t] = d2 * invh3;
+            W.cc[t] = d3 * invhc * ri3;
         }
         __syncwarp(mask);
         // 3-body slots: 2-body part plus the sum over the other 3-body neighbours
+        // (q ascending: first the pairs (q, p), then the pairs (p, q))
         for (int p = sub; p < n3; p += LPA) {
             T sa = T(0), cx = T(0), cy = T(0), cz = T(0), cs = T(0);
-            for (int q = 0; q < n3; ++q) {
-                if (q == p) continue;
-                const T c = W.cc[p < q ? tri3<NB>(p, q) : tri3<NB>(q, p)];
-                sa += W.al[p * S + q];
+            const int tp = p * (p - 1) / 2;
+            for (int q = 0; q < p; ++q) {
+                const T c = W.cc[tp + q];
+                const V vq = W.v[q];
+                sa += W.a2[tp + q];
                 cs += c;
-                cx += c * W.v[q][0];
-                cy += c * W.v[q][1];
-                cz += c * W.v[q][2];
+                cx += c * vq.x;
+                cy += c * vq.y;
+                cz += c * vq.z;
             }
-            const T ir = T(1) / W.v[p][3];
+            for (int q = p + 1; q < n3; ++q) {
+                const int t = q * (q - 1) / 2 + p;
+                const T c = W.cc[t];
+                const V vq = W.v[q];
+                sa += W.a1[t];
+                cs += c;
+                cx += c * vq.x;
+                cy += c * vq.y;
+                cz += c * vq.z;
+            }
+            const V vp = W.v[p];
+            const T k = W.hp[p] + sa * W.ir[p] + cs;
             V gv;
-            gv.x = W.g2[p][0] + (sa * W.v[p][0] * ir + cs * W.v[p][0] - cx);
-            gv.y = W.g2[p][1] + (sa * W.v[p][1] * ir + cs * W.v[p][1] - cy);
-            gv.z = W.g2[p][2] + (sa * W.v[p][2] * ir + cs * W.v[p][2] - cz);
+            gv.x = k * vp.x - cx;
+            gv.y = k * vp.y - cy;
+            gv.z = k * vp.z - cz;
             gv.w = T(0);
             const int s = W.slot[p];
             grow[s] = gv;
@@ -210,57 +258,88 @@ __device__ __forceinline__ void spline_atom(const Dev& d, const SplTab<T>& tab, 
     }
 }
 
-template <typename T, int LPA>
-__global__ void __launch_bounds__(SPL_WARPS * 32) k_spline(Dev d, SplTab<T> tab) {
-    constexpr int G = 32 / LPA;   // atoms a warp works on at a time
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* c3s = reinterpret_cast<T*>(smem_raw);                 // [512]
-    T* c2s = c3s + 512;                                       // [16]
-    SplWarp<T, spl_nb<LPA>()>* ws = reinterpret_cast<SplWarp<T, spl_nb<LPA>()>*>(c2s + 16);
-    const int warp = threadIdx.x >> 5, grp = (threadIdx.x & 31) / LPA;
-    for (int k = threadIdx.x; k < 512; k += blockDim.x) c3s[k] = tab.c3[k];
-    if (threadIdx.x < 16) c2s[threadIdx.x] = tab.c2[threadIdx.x];
-    __syncthreads();
-    const int count = d.status[SW_NCHEAP];
-    for (int a = (blockIdx.x * SPL_WARPS + warp) * G + grp; a < count; a += gridDim.x * SPL_WARPS * G)
-        spline_atom<T, LPA>(d, tab, a, c2s, c3s, ws[warp * G + grp]);
+// window counts of the two coefficient tables (4-vectors)
+constexpr int SPL_NW = 64 * SPL_W3 + SPL_W2;
+
+template <typename T>
+__device__ __forceinline__ void spl_stage(typename Vec4<T>::type* dst, const T* c3w, const T* c2w) {
+    using V = typename Vec4<T>::type;
+    const V* s3 = reinterpret_cast<const V*>(c3w);
+    const V* s2 = reinterpret_cast<const V*>(c2w);
+    for (int k = threadIdx.x; k < SPL_NW; k += blockDim.x) dst[k] = k < 64 * SPL_W3 ? s3[k] : s2[k - 64 * SPL_W3];
 }
 
-// Many systems: a lane group per entry {system, index} of the flattened cheap
+template <typename T, int LPA>
+__global__ void __launch_bounds__(SPL_WARPS * 32, sizeof(T) == 4 ? 6 : 1) k_spline(Dev d, SplTab<T> tab) {
+    constexpr int G = 32 / LPA;   // atoms a warp works on at a time
+    constexpr int NB = spl_nb<LPA>();
+    using V = typename Vec4<T>::type;
+    using SW = SplWarp<T, NB>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V* c3s = reinterpret_cast<V*>(smem_raw);   // [64 * SPL_W3] then [SPL_W2]
+    V* c2s = c3s + 64 * SPL_W3;
+    SW* ws = reinterpret_cast<SW*>(c3s + SPL_NW);
+    unsigned char* tq = reinterpret_cast<unsigned char*>(ws + SPL_WARPS * G);
+    const int warp = threadIdx.x >> 5, grp = (threadIdx.x & 31) / LPA;
+    spl_stage<T>(c3s, tab.c3w, tab.c2w);
+    spl_fill_tq<NB>(tq);
+    __syncthreads();
+    const int count = d.status[SW_NCHEAP];
+    const int stride = gridDim.x * SPL_WARPS * G;
+    int a = (blockIdx.x * SPL_WARPS + warp) * G + grp;
+    int i = a < count ? d.act_c[a] : 0;
+    while (a < count) {   // the next atom's index is loaded ahead
+        const int an = a + stride;
+        const int in = an < count ? d.act_c[an] : 0;
+        spline_atom<T, LPA>(d, tab, i, c2s, c3s, tq, ws[warp * G + grp]);
+        a = an;
+        i = in;
+    }
+}
+
+// Many systems: a lane group per entry {system, atom} of the flattened cheap
 // list; the system's parameters are read through L1.  When every system has
 // the same coefficient tables (uniform != 0) the block stages them once in
 // shared memory, as the single-system kernel does; otherwise they are read
 // through L1.
 template <typename T, int LPA>
-__global__ void __launch_bounds__(SPL_WARPS * 32) kb_spline(const Dev* __restrict__ devs,
+__global__ void __launch_bounds__(SPL_WARPS * 32, sizeof(T) == 4 ? 6 : 1) kb_spline(const Dev* __restrict__ devs,
                                                            const SplTab<T>* __restrict__ tabs,
                                                            const int2* __restrict__ list, const int* count_p,
                                                            int uniform) {
     constexpr int G = 32 / LPA;
-    using SW = SplWarp<T, spl_nb<LPA>()>;
+    constexpr int NB = spl_nb<LPA>();
+    using V = typename Vec4<T>::type;
+    using SW = SplWarp<T, NB>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    SW* ws = reinterpret_cast<SW*>(smem_raw);
-    T* c3s = reinterpret_cast<T*>(ws + SPL_WARPS * G);   // [512] (uniform tables only)
-    T* c2s = c3s + 512;                                  // [16]
+    V* c3s = reinterpret_cast<V*>(smem_raw);   // uniform tables only
+    V* c2s = c3s + 64 * SPL_W3;
+    SW* ws = reinterpret_cast<SW*>(c3s + SPL_NW);
+    unsigned char* tq = reinterpret_cast<unsigned char*>(ws + SPL_WARPS * G);
     const int warp = threadIdx.x >> 5, grp = (threadIdx.x & 31) / LPA;
-    if (uniform) {
-        const T* c3 = tabs[0].c3;
-        const T* c2 = tabs[0].c2;
-        for (int k = threadIdx.x; k < 512; k += blockDim.x) c3s[k] = c3[k];
-        if (threadIdx.x < 16) c2s[threadIdx.x] = c2[threadIdx.x];
-        __syncthreads();
-    }
+    if (uniform) spl_stage<T>(c3s, tabs[0].c3w, tabs[0].c2w);
+    spl_fill_tq<NB>(tq);
+    __syncthreads();
     const int count = *count_p;
-    for (int g = (blockIdx.x * SPL_WARPS + warp) * G + grp; g < count; g += gridDim.x * SPL_WARPS * G) {
-        const int2 e = list[g];
+    const int stride = gridDim.x * SPL_WARPS * G;
+    int g = (blockIdx.x * SPL_WARPS + warp) * G + grp;
+    int2 e = g < count ? list[g] : make_int2(0, 0);
+    while (g < count) {   // the next entry is loaded ahead
+        const int gn = g + stride;
+        const int2 en = gn < count ? list[gn] : make_int2(0, 0);
         const SplTab<T>& tab = tabs[e.x];
-        spline_atom<T, LPA>(devs[e.x], tab, e.y, uniform ? c2s : tab.c2, uniform ? c3s : tab.c3, ws[warp * G + grp]);
+        spline_atom<T, LPA>(devs[e.x], tab, e.y, uniform ? c2s : reinterpret_cast<const V*>(tab.c2w),
+                            uniform ? c3s : reinterpret_cast<const V*>(tab.c3w), tq, ws[warp * G + grp]);
+        g = gn;
+        e = en;
     }
 }
 
 template <typename T, int LPA>
 static size_t spl_bytes() {
-    return SPL_WARPS * (32 / LPA) * sizeof(SplWarp<T, spl_nb<LPA>()>) + (512 + 16) * sizeof(T);
+    constexpr int NB = spl_nb<LPA>();
+    return SPL_NW * sizeof(typename Vec4<T>::type) + SPL_WARPS * (32 / LPA) * sizeof(SplWarp<T, NB>) +
+           spl_tq_bytes<NB>();
 }
 
 template <typename T, int LPA>

@@ -426,7 +426,14 @@ int build_tables(mix_ctx* c, const mix_ace* a, const mix_spline* sp) {
         for (int m = -l; m <= l; ++m) ylmk[l * l + l + m] = ylm_norm(l, m);
     std::vector<double> pair(16, 0.0);
     if (a->pair) pair.assign(a->pair, a->pair + 16);
-    std::vector<double> sc2(sp->c2, sp->c2 + 16), sc3(sp->c3, sp->c3 + 512);
+    // cheap-potential coefficient windows (the kernel reads each interval's four
+    // control points as one aligned vector)
+    std::vector<double> sc2(SPL_W2 * 4), sc3(64 * SPL_W3 * 4);
+    for (int q = 0; q < SPL_W2; ++q)
+        for (int k = 0; k < 4; ++k) sc2[q * 4 + k] = sp->c2[q + k];
+    for (int ab = 0; ab < 64; ++ab)
+        for (int z = 0; z < SPL_W3; ++z)
+            for (int k = 0; k < 4; ++k) sc3[(ab * SPL_W3 + z) * 4 + k] = sp->c3[ab * 8 + z + k];
 
     std::vector<int> toff;
     Arena& A = c->arena;
@@ -473,8 +480,8 @@ void fill_tabs(mix_ctx* c, unsigned char* base, AceTab<T>& at, SplTab<T>& st) {
     at.has_pair = c->has_pair ? 1 : 0;
     st.rc = c->spl_rc;
     st.rc3 = c->spl_rc3;
-    st.c2 = reinterpret_cast<const T*>(base + c->o_sc2);
-    st.c3 = reinterpret_cast<const T*>(base + c->o_sc3);
+    st.c2w = reinterpret_cast<const T*>(base + c->o_sc2);
+    st.c3w = reinterpret_cast<const T*>(base + c->o_sc3);
     st.rc2 = (T)(c->dev.rcc2);
     st.rc32 = (T)(c->spl_rc3 * c->spl_rc3);
     st.invh2 = (T)(13.0 / c->spl_rc);
@@ -1550,8 +1557,10 @@ int fused_build(mix_batch* b) {
         b->spl_uniform = 1;
         for (int s = 1; s < ns && b->spl_uniform; ++s) {
             const mix_ctx* c = b->m[s];
-            if (std::memcmp(c->arena.bytes.data() + c->o_sc2, c0->arena.bytes.data() + c0->o_sc2, 16 * tb) != 0 ||
-                std::memcmp(c->arena.bytes.data() + c->o_sc3, c0->arena.bytes.data() + c0->o_sc3, 512 * tb) != 0)
+            if (std::memcmp(c->arena.bytes.data() + c->o_sc2, c0->arena.bytes.data() + c0->o_sc2,
+                            SPL_W2 * 4 * tb) != 0 ||
+                std::memcmp(c->arena.bytes.data() + c->o_sc3, c0->arena.bytes.data() + c0->o_sc3,
+                            64 * SPL_W3 * 4 * tb) != 0)
                 b->spl_uniform = 0;
         }
     }

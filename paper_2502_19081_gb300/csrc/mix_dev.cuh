@@ -269,11 +269,17 @@ struct AceTab {
     int has_pair;
 };
 
+constexpr int SPL_W2 = 13;   // pair-term intervals on [0, rc]
+constexpr int SPL_W3 = 5;    // three-body intervals along each argument
+
 template <typename T>
 struct SplTab {
     double rc, rc3;
-    const T* c2;    // [16]
-    const T* c3;    // [8][8][8]
+    // coefficient windows, one aligned 4-vector each (the four control points
+    // one cubic B-spline interval reads): c2w[q] = c2[q..q+3] for q < SPL_W2,
+    // c3w[(a * 8 + b) * SPL_W3 + z] = c3[a][b][z..z+3] for z < SPL_W3
+    const T* c2w;   // [SPL_W2][4]
+    const T* c3w;   // [64][SPL_W3][4]
     // derived constants in T, formed on the host in float64 and rounded once
     // (no float64 division per atom on the device)
     T rc2, rc32;            // rc^2 (2-body), rc3^2
@@ -396,24 +402,40 @@ __device__ __forceinline__ void pair_vec(const Box& b, const double4& xi, const 
 template <typename T>
 struct PairFrame;
 
+// Pt: what vec() reads of the partner atom, loadable ahead of its use
 template <>
 struct PairFrame<double> {
+    struct Pt {
+        double4 x;
+    };
     double4 xi;
     __device__ __forceinline__ PairFrame(const Dev& d, int i) : xi(d.x[i]) {}
+    static __device__ __forceinline__ Pt load(const Dev& d, int j) { return Pt{d.x[j]}; }
+    __device__ __forceinline__ void vec(const Dev& d, const Pt& p, double v[3], double& r2) const {
+        pair_vec<double>(d.box, xi, p.x, v, r2);
+    }
     __device__ __forceinline__ void vec(const Dev& d, int j, double v[3], double& r2) const {
-        pair_vec<double>(d.box, xi, d.x[j], v, r2);
+        vec(d, load(d, j), v, r2);
     }
 };
 
 template <>
 struct PairFrame<float> {
+    struct Pt {
+        float4 x;
+        int c;
+    };
     float4 xri;
     int ci;
     __device__ __forceinline__ PairFrame(const Dev& d, int i) : xri(d.xr[i]), ci(d.cell3[i]) {}
     __device__ __forceinline__ PairFrame(float4 x, int c) : xri(x), ci(c) {}
+    static __device__ __forceinline__ Pt load(const Dev& d, int j) { return Pt{d.xr[j], d.cell3[j]}; }
     __device__ __forceinline__ void vec(const Dev& d, int j, float v[3], float& r2) const {
-        const float4 xrj = d.xr[j];
-        const int cj = d.cell3[j];
+        vec(d, load(d, j), v, r2);
+    }
+    __device__ __forceinline__ void vec(const Dev& d, const Pt& p, float v[3], float& r2) const {
+        const float4 xrj = p.x;
+        const int cj = p.c;
         const float a[3] = {xrj.x - xri.x, xrj.y - xri.y, xrj.z - xri.z};
 #pragma unroll
         for (int k = 0; k < 3; ++k) {

@@ -54,7 +54,7 @@ struct FlatArgs {
     const int* elast;    // [nsys] 1 for the last system of its group
     const int* ebase;    // [ngrp] start of each group in list_e
     int2* list_e;        // {system, index in its expensive list}
-    int2* list_c;        // {system, index in its cheap list}
+    int2* list_c;        // {system, atom} for each entry of the systems' cheap lists
     int* counts;         // [ngrp + 1] expensive totals per group, cheap total
 };
 
