@@ -155,21 +155,33 @@ __global__ void k_cell_fill(Dev d) { cell_fill_body(d, blockIdx.x, gridDim.x); }
 
 constexpr int NB_WARPS = 4;
 
-// One warp per atom: scan the 27-cell stencil (as up to 18 contiguous runs of
-// cells), keep r2 < rlist2 with a ballot compaction into shared memory, sort
-// the row ascending with a warp bitonic network, write it out.
+// One warp per atom: the 27-cell stencil is up to 18 contiguous runs of cells
+// (9 rows (dz, dy), one or two runs along x each); lane r < 18 finds run r, a
+// warp prefix sum numbers all candidates of all runs, and the lanes take 32
+// consecutive candidates at a time across run boundaries (in run order, so the
+// compacted row is the same as a run-by-run scan) with the next 32 loaded
+// ahead.  Candidates with r2 < rlist2 are compacted into shared memory with a
+// ballot; each lane then ranks its entries among the row (atom indices are
+// distinct) and writes them to their sorted places.
 __device__ __forceinline__ int pow2_cap(int cap) {
     int c = 32;
     while (c < cap) c <<= 1;
     return c;
 }
 
+constexpr int NB_RUNS = 18;
+
 __device__ __forceinline__ void neigh_build_body(const Dev& d, int bx, int gx, int capp2, int* sbuf) {
     if (d.status[SW_REBUILD] == 0) return;
+    __shared__ int s_runx[NB_WARPS][NB_RUNS];   // cell_atoms index of a run's first candidate, less its number
+    __shared__ int s_runi[NB_WARPS][NB_RUNS];   // candidates in runs 0..r
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int* buf = sbuf + warp * capp2;
+    int* runx = s_runx[warp];
+    int* runi = s_runi[warp];
     const unsigned lt = (1u << lane) - 1u;
     const int ncx = d.cells.nc[0], ncy = d.cells.nc[1], ncz = d.cells.nc[2];
+    const int cap = d.cap;
     // float pre-filter: the float distance is within 2e-5 relative of the
     // float64 one for boxes up to a few thousand Angstrom, so only candidates
     // inside a +-2e-4 band around the threshold need the exact float64 test
@@ -181,86 +193,100 @@ __device__ __forceinline__ void neigh_build_body(const Dev& d, int bx, int gx, i
         const float4 xif = d.xf[i];
         const int c = d.cell_of[i];
         const int cx = c % ncx, cy = (c / ncx) % ncy, cz = c / (ncx * ncy);
-        int cnt = 0;
-        for (int dz = -1; dz <= 1; ++dz) {
-            int qz = cz + dz;
+        int len = 0, t0 = 0;
+        if (lane < NB_RUNS) {
+            const int rr = lane >> 1, run = lane & 1;
+            int qz = cz + rr / 3 - 1, qy = cy + rr % 3 - 1;
+            bool in = true;
             if (d.box.per[2]) qz = (qz + ncz) % ncz;
-            else if (qz < 0 || qz >= ncz) continue;
-            for (int dy = -1; dy <= 1; ++dy) {
-                int qy = cy + dy;
-                if (d.box.per[1]) qy = (qy + ncy) % ncy;
-                else if (qy < 0 || qy >= ncy) continue;
+            else in = qz >= 0 && qz < ncz;
+            if (d.box.per[1]) qy = (qy + ncy) % ncy;
+            else in = in && qy >= 0 && qy < ncy;
+            // runs of cells along x: [a0, b0] and optionally [a1, b1]
+            int a0, b0, a1 = 1, b1 = 0;
+            if (d.box.per[0]) {
+                if (cx == 0) { a0 = 0; b0 = 1; a1 = ncx - 1; b1 = ncx - 1; }
+                else if (cx == ncx - 1) { a0 = ncx - 2; b0 = ncx - 1; a1 = 0; b1 = 0; }
+                else { a0 = cx - 1; b0 = cx + 1; }
+            } else {
+                a0 = cx > 0 ? cx - 1 : 0;
+                b0 = cx < ncx - 1 ? cx + 1 : ncx - 1;
+            }
+            const int ra = run == 0 ? a0 : a1, rb = run == 0 ? b0 : b1;
+            if (in && ra <= rb) {
                 const int row = (qz * ncy + qy) * ncx;
-                // runs of cells along x: [a0, b0] and optionally [a1, b1]
-                int a0, b0, a1 = 1, b1 = 0;
-                if (d.box.per[0]) {
-                    if (cx == 0) { a0 = 0; b0 = 1; a1 = ncx - 1; b1 = ncx - 1; }
-                    else if (cx == ncx - 1) { a0 = ncx - 2; b0 = ncx - 1; a1 = 0; b1 = 0; }
-                    else { a0 = cx - 1; b0 = cx + 1; }
-                } else {
-                    a0 = cx > 0 ? cx - 1 : 0;
-                    b0 = cx < ncx - 1 ? cx + 1 : ncx - 1;
-                }
-                for (int run = 0; run < 2; ++run) {
-                    const int ra = run == 0 ? a0 : a1, rb = run == 0 ? b0 : b1;
-                    if (ra > rb) continue;
-                    const int t0 = d.cell_start[row + ra], t1 = d.cell_start[row + rb + 1];
-                    for (int tb = t0; tb < t1; tb += 32) {
-                        const int t = tb + lane;
-                        bool ok = false;
-                        int j = -1;
-                        if (t < t1) {
-                            j = d.cell_atoms[t];
-                            if (j != (int)i) {
-                                const float4 xjf = d.xf[j];
-                                float df[3] = {xjf.x - xif.x, xjf.y - xif.y, xjf.z - xif.z};
+                t0 = d.cell_start[row + ra];
+                len = d.cell_start[row + rb + 1] - t0;
+            }
+        }
+        int inc = len;
 #pragma unroll
-                                for (int k = 0; k < 3; ++k)
-                                    if (d.box.per[k]) df[k] -= Lf[k] * rintf(df[k] * iLf[k]);
-                                const float r2f = df[0] * df[0] + df[1] * df[1] + df[2] * df[2];
-                                if (r2f < lo2 && !d.exact_lists) {
-                                    ok = true;
-                                } else if (r2f <= hi2 || d.exact_lists) {
-                                    double dd[3];
-                                    delta_rn(d.box, xi, d.x[j], dd);
-                                    ok = norm2_rn(dd) < d.rlist2;
-                                }
-                            }
-                        }
-                        const unsigned m = __ballot_sync(0xffffffffu, ok);
-                        if (ok) {
-                            const int p = cnt + __popc(m & lt);
-                            if (p < capp2) buf[p] = j;
-                        }
-                        cnt += __popc(m);
-                    }
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += v;
+        }
+        const int total = __shfl_sync(0xffffffffu, inc, 31);
+        if (lane < NB_RUNS) {
+            runi[lane] = inc;
+            runx[lane] = t0 - (inc - len);
+        }
+        __syncwarp();
+        int r = 0;   // run of this lane's candidate (non-decreasing in the candidate number)
+        int jn = -1;
+        if (lane < total) {
+            while (lane >= runi[r]) ++r;
+            jn = d.cell_atoms[runx[r] + lane];
+        }
+        int cnt = 0;
+        for (int u = lane; u - lane < total; u += 32) {
+            const int j = jn;
+            if (u + 32 < total) {
+                while (u + 32 >= runi[r]) ++r;
+                jn = d.cell_atoms[runx[r] + u + 32];
+            }
+            bool ok = false;
+            if (u < total && j != (int)i) {
+                const float4 xjf = d.xf[j];
+                float df[3] = {xjf.x - xif.x, xjf.y - xif.y, xjf.z - xif.z};
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+                    if (d.box.per[k]) df[k] -= Lf[k] * rintf(df[k] * iLf[k]);
+                const float r2f = df[0] * df[0] + df[1] * df[1] + df[2] * df[2];
+                if (r2f < lo2 && !d.exact_lists) {
+                    ok = true;
+                } else if (r2f <= hi2 || d.exact_lists) {
+                    double dd[3];
+                    delta_rn(d.box, xi, d.x[j], dd);
+                    ok = norm2_rn(dd) < d.rlist2;
                 }
             }
+            const unsigned m = __ballot_sync(0xffffffffu, ok);
+            if (ok) {
+                const int p = cnt + __popc(m & lt);
+                if (p < capp2) buf[p] = j;
+            }
+            cnt += __popc(m);
         }
         if (lane == 0) {
             atomicMax(d.status + SW_MAXNB, cnt);
-            if (cnt > d.cap) set_status(d.status, ST_NBR_OVERFLOW);
+            if (cnt > cap) set_status(d.status, ST_NBR_OVERFLOW);
         }
-        const int mlen = cnt < d.cap ? cnt : d.cap;
-        for (int p = mlen + lane; p < capp2; p += 32) buf[p] = INT_MAX;
+        const int mlen = cnt < cap ? cnt : cap;
+        // pad to whole 4-vectors with INT_MAX (ranks unaffected): m4 <= capp2
+        const int m4 = (mlen + 3) & ~3;
+        if (mlen + lane < m4) buf[mlen + lane] = INT_MAX;
         __syncwarp();
-        for (int k = 2; k <= capp2; k <<= 1) {
-            for (int j = k >> 1; j > 0; j >>= 1) {
-                for (int t = lane; t < (capp2 >> 1); t += 32) {
-                    const int a = (t / j) * 2 * j + (t % j);
-                    const int b = a + j;
-                    const bool up = (a & k) == 0;
-                    const int va = buf[a], vb = buf[b];
-                    if ((va > vb) == up) {
-                        buf[a] = vb;
-                        buf[b] = va;
-                    }
-                }
-                __syncwarp();
+        int* row = d.nbr + i * (int64_t)cap;
+        const int4* b4 = reinterpret_cast<const int4*>(buf);
+        for (int p = lane; p < mlen; p += 32) {
+            const int v = buf[p];
+            int rank = 0;
+            for (int q = 0; q < (m4 >> 2); ++q) {
+                const int4 w = b4[q];
+                rank += (w.x < v) + (w.y < v) + (w.z < v) + (w.w < v);
             }
+            row[rank] = v;
         }
-        int* row = d.nbr + i * (int64_t)d.cap;
-        for (int p = lane; p < mlen; p += 32) row[p] = buf[p];
         if (lane == 0) {
             d.nnb[i] = mlen;
             d.xb[i] = xi;
@@ -270,7 +296,7 @@ __device__ __forceinline__ void neigh_build_body(const Dev& d, int bx, int gx, i
 }
 
 __global__ void __launch_bounds__(NB_WARPS * 32) k_neigh_build(Dev d, int capp2) {
-    extern __shared__ int sbuf[];
+    extern __shared__ __align__(16) int sbuf[];
     neigh_build_body(d, blockIdx.x, gridDim.x, capp2, sbuf);
 }
 
@@ -327,7 +353,7 @@ __global__ void kb_cell_fill(BatchArgs ba) {
     cell_fill_body(s_dev, s_ent.y, s_ent.z);
 }
 __global__ void __launch_bounds__(NB_WARPS * 32) kb_neigh_build(BatchArgs ba) {
-    extern __shared__ int sbuf[];
+    extern __shared__ __align__(16) int sbuf[];
     MIX_BATCH_BLOCK_REBUILD(ba)
     neigh_build_body(s_dev, s_ent.y, s_ent.z, pow2_cap(s_dev.cap), sbuf);
 }
