@@ -444,7 +444,15 @@ __global__ void kb_flatten(FlatArgs f) {
     int2* lc = f.list_c + oc;
     for (int k = tid; k < ne; k += blockDim.x) le[k] = make_int2(s, k * ACE_GROUP);
     const int* act_c = f.devs[s].act_c;
-    for (int k = tid; k < nc; k += blockDim.x) lc[k] = make_int2(s, act_c[k]);
+    for (int k0 = tid; k0 < nc; k0 += 4 * blockDim.x) {   // four reads in flight a thread
+        int v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (k0 + u * (int)blockDim.x < nc) v[u] = act_c[k0 + u * blockDim.x];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (k0 + u * (int)blockDim.x < nc) lc[k0 + u * blockDim.x] = make_int2(s, v[u]);
+    }
     if (tid == 0) {
         if (f.elast[s]) f.counts[g] = oe + ne;
         if (s == f.nsys - 1) f.counts[f.ngrp] = oc + nc;
@@ -488,7 +496,7 @@ void launch_sets_batch(const BatchPlan& p, cudaStream_t s) {
     kb_buffer<<<p.nblk[BT_WARP8], BUF_WARPS * 32, 0, s>>>(p.ba[BT_WARP8]);
     kb_count<<<p.nblk[BT_SCAN], SCAN_BLOCK, 0, s>>>(p.ba[BT_SCAN]);
     kb_scatter<<<p.nblk[BT_SCAN], SCAN_BLOCK, 0, s>>>(p.ba[BT_SCAN]);
-    kb_flatten<<<p.flat.nsys, 256, 0, s>>>(p.flat);
+    kb_flatten<<<p.flat.nsys, 1024, 0, s>>>(p.flat);
 }
 
 }  // namespace mixd

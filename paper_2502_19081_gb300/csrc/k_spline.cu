@@ -94,6 +94,7 @@ __device__ __forceinline__ void spline_atom(const Dev& d, const SplTab<T>& tab, 
     {
         using Pt = typename PairFrame<T>::Pt;
         const PairFrame<T> pf(d, i);
+        const typename PairFrame<T>::Geo geo = PairFrame<T>::geo(d);   // once per atom, in registers
         const int m = d.nnb[i];
         const int* row = d.nbr + (int64_t)i * cap;
         const int* rvr = d.rev + (int64_t)i * cap;
@@ -124,7 +125,7 @@ __device__ __forceinline__ void spline_atom(const Dev& d, const SplTab<T>& tab, 
             T dv3[3] = {T(0), T(0), T(0)}, r = T(0), hp = T(0), ri = T(0);
             if (s < m) {
                 T r2;
-                pf.vec(d, pt, dv3, r2);
+                pf.vec(geo, pt, dv3, r2);
                 if (r2 < rc2) {
                     ri = trsqrt(r2);
                     r = r2 * ri;

@@ -402,15 +402,23 @@ __device__ __forceinline__ void pair_vec(const Box& b, const double4& xi, const 
 template <typename T>
 struct PairFrame;
 
-// Pt: what vec() reads of the partner atom, loadable ahead of its use
+// Pt: what vec() reads of the partner atom, loadable ahead of its use; Geo:
+// what it reads of the system's box and cells, loadable once into registers
 template <>
 struct PairFrame<double> {
     struct Pt {
         double4 x;
     };
+    struct Geo {
+        const Box* b;
+    };
     double4 xi;
     __device__ __forceinline__ PairFrame(const Dev& d, int i) : xi(d.x[i]) {}
     static __device__ __forceinline__ Pt load(const Dev& d, int j) { return Pt{d.x[j]}; }
+    static __device__ __forceinline__ Geo geo(const Dev& d) { return Geo{&d.box}; }
+    __device__ __forceinline__ void vec(const Geo& g, const Pt& p, double v[3], double& r2) const {
+        pair_vec<double>(*g.b, xi, p.x, v, r2);
+    }
     __device__ __forceinline__ void vec(const Dev& d, const Pt& p, double v[3], double& r2) const {
         pair_vec<double>(d.box, xi, p.x, v, r2);
     }
@@ -429,22 +437,39 @@ struct PairFrame<float> {
     int ci;
     __device__ __forceinline__ PairFrame(const Dev& d, int i) : xri(d.xr[i]), ci(d.cell3[i]) {}
     __device__ __forceinline__ PairFrame(float4 x, int c) : xri(x), ci(c) {}
+    struct Geo {
+        int per[3], nc[3];
+        float hf[3];
+    };
     static __device__ __forceinline__ Pt load(const Dev& d, int j) { return Pt{d.xr[j], d.cell3[j]}; }
+    static __device__ __forceinline__ Geo geo(const Dev& d) {
+        Geo g;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            g.per[k] = d.box.per[k];
+            g.nc[k] = d.cells.nc[k];
+            g.hf[k] = d.cells.hf[k];
+        }
+        return g;
+    }
     __device__ __forceinline__ void vec(const Dev& d, int j, float v[3], float& r2) const {
         vec(d, load(d, j), v, r2);
     }
     __device__ __forceinline__ void vec(const Dev& d, const Pt& p, float v[3], float& r2) const {
+        vec(geo(d), p, v, r2);
+    }
+    __device__ __forceinline__ void vec(const Geo& g, const Pt& p, float v[3], float& r2) const {
         const float4 xrj = p.x;
         const int cj = p.c;
         const float a[3] = {xrj.x - xri.x, xrj.y - xri.y, xrj.z - xri.z};
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             int dc = ((cj >> (10 * k)) & 1023) - ((ci >> (10 * k)) & 1023);
-            if (d.box.per[k]) {
-                if (dc > 1) dc -= d.cells.nc[k];
-                else if (dc < -1) dc += d.cells.nc[k];
+            if (g.per[k]) {
+                if (dc > 1) dc -= g.nc[k];
+                else if (dc < -1) dc += g.nc[k];
             }
-            v[k] = a[k] + (float)dc * d.cells.hf[k];
+            v[k] = a[k] + (float)dc * g.hf[k];
         }
         r2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
     }
