@@ -300,37 +300,38 @@ __global__ void __launch_bounds__(NB_WARPS * 32) k_neigh_build(Dev d, int capp2)
     neigh_build_body(d, blockIdx.x, gridDim.x, capp2, sbuf);
 }
 
-// rev[i][s] = position of i in the row of j = nbr[i][s] (binary search).
-__device__ __forceinline__ void neigh_rev_slot(const Dev& d, int64_t idx) {
-    const int64_t i = idx / d.cap;
-    const int s = (int)(idx - i * d.cap);
-    if (s >= d.nnb[i]) return;
-    const int j = d.nbr[idx];
-    const int* row = d.nbr + (int64_t)j * d.cap;
-    int lo = 0, hi = d.nnb[j] - 1, pos = -1;
-    while (lo <= hi) {
-        const int mid = (lo + hi) >> 1;
-        const int v = row[mid];
-        if (v == (int)i) {
-            pos = mid;
-            break;
-        }
-        if (v < (int)i) lo = mid + 1;
-        else hi = mid - 1;
-    }
-    if (pos < 0) {
-        set_status(d.status, ST_REV_MISSING);
-        pos = 0;
-    }
-    d.rev[idx] = pos;
-}
-
+// rev[i][s] = position of i in the row of j = nbr[i][s] (binary search in the
+// sorted row).  A warp per atom, lanes over its row's slots.
 __device__ __forceinline__ void neigh_rev_body(const Dev& d, int bx, int gx) {
     if (d.status[SW_REBUILD] == 0) return;
-    const int64_t tot = d.n * (int64_t)d.cap;
-    for (int64_t idx = bx * (int64_t)blockDim.x + threadIdx.x; idx < tot; idx += (int64_t)gx * blockDim.x)
-        neigh_rev_slot(d, idx);
+    const int lane = threadIdx.x & 31, wpb = (int)(blockDim.x >> 5);
+    const int cap = d.cap;
+    for (int64_t i = (int64_t)bx * wpb + (threadIdx.x >> 5); i < d.n; i += (int64_t)gx * wpb) {
+        const int m = d.nnb[i];
+        const int* ri = d.nbr + i * cap;
+        for (int s = lane; s < m; s += 32) {
+            const int j = ri[s];
+            const int* row = d.nbr + (int64_t)j * cap;
+            int lo = 0, hi = d.nnb[j] - 1, pos = -1;
+            while (lo <= hi) {
+                const int mid = (lo + hi) >> 1;
+                const int v = row[mid];
+                if (v == (int)i) {
+                    pos = mid;
+                    break;
+                }
+                if (v < (int)i) lo = mid + 1;
+                else hi = mid - 1;
+            }
+            if (pos < 0) {
+                set_status(d.status, ST_REV_MISSING);
+                pos = 0;
+            }
+            d.rev[i * cap + s] = pos;
+        }
+    }
 }
+
 __global__ void k_neigh_rev(Dev d) { neigh_rev_body(d, blockIdx.x, gridDim.x); }
 
 // ---------------------------------------------------------------------------
@@ -400,8 +401,7 @@ void launch_build(const Dev& d, cudaStream_t s) {
     int64_t lim = d.grid_build > 0 ? d.grid_build : (int64_t)sm_count() * 16;
     int grid = (int)(want < lim ? want : lim);
     k_neigh_build<<<grid > 0 ? grid : 1, NB_WARPS * 32, NB_WARPS * capp2 * sizeof(int), s>>>(d, capp2);
-    const int64_t tot = d.n * (int64_t)d.cap;
-    const int nr = (int)((tot + 255) / 256);
+    const int nr = (int)((d.n + 7) / 8);   // a warp per atom
     k_neigh_rev<<<nr > 0 ? nr : 1, 256, 0, s>>>(d);
 }
 

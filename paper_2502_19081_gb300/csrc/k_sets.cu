@@ -28,7 +28,8 @@ __device__ __forceinline__ void lambda_body(const Dev& d, const Regions& r, int 
 __global__ void k_lambda(Dev d, Regions r) { lambda_body(d, r, blockIdx.x, gridDim.x); }
 
 __device__ __forceinline__ void lambda_atom(const Dev& d, const Regions& r, int64_t i) {
-    const double4 x = d.x[i];
+    double4 x = make_double4(0.0, 0.0, 0.0, 0.0);   // read once some region is not screened out
+    bool have_x = false;
     double best = 0.0;
     // buffer-scan hints from the exact distances (triangle inequality, 1e-9 A
     // margin): with every region farther than r_core + ramp + r_buffer_exp no
@@ -51,6 +52,10 @@ __device__ __forceinline__ void lambda_atom(const Dev& d, const Regions& r, int6
                 d2f -= tt * tt;
             }
             if (d2f > r.far2[k]) continue;
+        }
+        if (!have_x) {
+            x = d.x[i];
+            have_x = true;
         }
         const double4 c = make_double4(R[1], R[2], R[3], 0.0);
         double v[3];
@@ -392,7 +397,10 @@ __global__ void __launch_bounds__(SCAN_BLOCK) k_scatter(Dev d) { scatter_body(d,
 
 __global__ void kb_lambda(BatchArgs ba, const Regions* __restrict__ regions) {
     MIX_BATCH_BLOCK(ba)
-    lambda_body(s_dev, regions[s_ent.x], s_ent.y, s_ent.z);
+    __shared__ Regions s_reg;   // the system's regions, read per atom
+    copy_shared(&s_reg, regions + s_ent.x);
+    __syncthreads();
+    lambda_body(s_dev, s_reg, s_ent.y, s_ent.z);
 }
 __global__ void __launch_bounds__(BUF_WARPS * 32) kb_buffer(BatchArgs ba) {
     MIX_BATCH_BLOCK(ba)

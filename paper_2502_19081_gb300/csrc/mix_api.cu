@@ -1475,7 +1475,7 @@ int fused_build(mix_batch* b) {
         const Dev& d = devs[s];
         const int64_t n = d.n;
         auto blocks = [](int64_t units, int64_t per) { return (int)std::max<int64_t>(1, (units + per - 1) / per); };
-        const int gx[BT_COUNT] = {blocks(n, 1024), 1, blocks(n, 32), blocks(n * (int64_t)d.cap, 2048),
+        const int gx[BT_COUNT] = {blocks(n, 1024), 1, blocks(n, 32), blocks(n, 64),
                                   blocks(n, 256), std::max(1, d.nblk), blocks(n, 256)};
         for (int k = 0; k < BT_COUNT; ++k)
             for (int bx = 0; bx < gx[k]; ++bx) tabs[k].push_back(make_int4(s, bx, gx[k], 0));

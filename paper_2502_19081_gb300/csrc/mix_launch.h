@@ -39,7 +39,7 @@ enum BatchTabClass : int {
     BT_ATOM = 0,   // 256 threads, a thread per atom (grid-stride)
     BT_ONE,        // one block per system
     BT_NB,         // 4 warps, a warp per atom (list build)
-    BT_REV,        // 256 threads, a thread per list slot (reverse map)
+    BT_REV,        // 8 warps, a warp per atom (reverse map)
     BT_WARP8,      // 8 warps of 32 atoms each (buffer scan)
     BT_SCAN,       // SCAN_BLOCK atoms per block, the system's own block count
     BT_GATHER,     // 8 warps of 32 atoms each (gather)
