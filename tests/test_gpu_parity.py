@@ -260,6 +260,32 @@ def test_host_buffer_entry_point_matches_device_path(mx):
     assert np.abs(d).max() < 1e-12 and _max_abs(vh, va) < 1e-12 and _max_abs(fh, fa) < 1e-10
 
 
+def test_host_entry_point_with_page_locked_buffers(mx):
+    """Page-locked host buffers (with and without forces in and out) give the
+    device path's trajectory."""
+    torch = pytest.importorskip("torch")
+    wl = I.small_fe_box(17, r_core=4.0, ramp=3.0)
+    a = mx.open_context(wl)
+    x0, v0, f0, _ = a.get_state()
+    a.step(1.0, 5)
+    xa, va, fa, _ = a.get_state()
+    b = mx.open_context(wl)
+    hx, hv, hf = (torch.from_numpy(np.ascontiguousarray(t)).pin_memory() for t in (x0, v0, f0))
+    xh, vh, fh = hx.numpy(), hv.numpy(), hf.numpy()
+    for _ in range(5):
+        b.step_host(xh, vh, fh, 1.0, 1)
+    d = xh[:, :3] - xa[:, :3]
+    d -= wl.system.box_len * np.rint(d / wl.system.box_len)
+    assert np.abs(d).max() < 1e-12 and _max_abs(vh, va) < 1e-12 and _max_abs(fh, fa) < 1e-10
+    # and the same buffers without forces in or out
+    c = mx.open_context(wl)
+    hx2, hv2 = (torch.from_numpy(np.ascontiguousarray(t)).pin_memory() for t in (x0, v0))
+    c.step_host(hx2.numpy(), hv2.numpy(), None, 1.0, 5)
+    d = hx2.numpy()[:, :3] - xa[:, :3]
+    d -= wl.system.box_len * np.rint(d / wl.system.box_len)
+    assert np.abs(d).max() < 1e-12 and _max_abs(hv2.numpy(), va) < 1e-12
+
+
 def test_empty_system(mx):
     wl = I.cluster_workload(18, n=4)
     wl.system = I.System(x=np.zeros((0, 4)), v=np.zeros((0, 4)), mass=wl.system.mass,
