@@ -231,22 +231,32 @@ __device__ __forceinline__ void neigh_build_body(const Dev& d, int bx, int gx, i
             runx[lane] = t0 - (inc - len);
         }
         __syncwarp();
-        int r = 0;   // run of this lane's candidate (non-decreasing in the candidate number)
-        int jn = -1;
+        // the atom two passes ahead and the position one pass ahead are loaded
+        // before this pass is tested (r: run of the furthest candidate loaded)
+        int r = 0;
+        int jn = -1, jnn = -1;
+        float4 xn = make_float4(0.f, 0.f, 0.f, 0.f);
         if (lane < total) {
             while (lane >= runi[r]) ++r;
             jn = d.cell_atoms[runx[r] + lane];
+            xn = d.xf[jn];
+        }
+        if (lane + 32 < total) {
+            while (lane + 32 >= runi[r]) ++r;
+            jnn = d.cell_atoms[runx[r] + lane + 32];
         }
         int cnt = 0;
         for (int u = lane; u - lane < total; u += 32) {
             const int j = jn;
-            if (u + 32 < total) {
-                while (u + 32 >= runi[r]) ++r;
-                jn = d.cell_atoms[runx[r] + u + 32];
+            const float4 xjf = xn;
+            jn = jnn;
+            if (u + 32 < total) xn = d.xf[jnn];
+            if (u + 64 < total) {
+                while (u + 64 >= runi[r]) ++r;
+                jnn = d.cell_atoms[runx[r] + u + 64];
             }
             bool ok = false;
             if (u < total && j != (int)i) {
-                const float4 xjf = d.xf[j];
                 float df[3] = {xjf.x - xif.x, xjf.y - xif.y, xjf.z - xif.z};
 #pragma unroll
                 for (int k = 0; k < 3; ++k)
