@@ -197,9 +197,6 @@ __global__ void __launch_bounds__(G_WARPS * 32, sizeof(T) == 4 ? 4 : 2) k_gather
     gather_body<T, LPA>(d, blockIdx.x, gridDim.x, integrate, h, ga, park);
 }
 
-// lanes per gathered atom (the system's d.gat_lpa: a quarter warp for mean list
-// lengths up to 40, half a warp up to 80, else a warp; 32 when unset)
-__host__ __device__ inline int gather_lpa(const Dev& d) { return d.gat_lpa == 8 || d.gat_lpa == 16 ? d.gat_lpa : 32; }
 
 // Each block belongs to one system and gathers with that system's own lane
 // groups, so a system's forces are bit for bit those it gets alone.

@@ -202,12 +202,17 @@ constexpr int BUF_WARPS = 8;
 
 // Buffer membership through the neighbour list.  A warp takes apw <= 32
 // consecutive atoms: each lane tests its atom's flags (and the hints k_lambda
-// left), then the whole warp scans, one after another, the lists of the atoms
-// that need it.  In a large system most atoms need no scan and then cost a
-// lane rather than a warp (apw = 32); a small one keeps a warp per atom (apw =
-// 1) so that its few scans run side by side.
+// left), then groups of LPA lanes scan the lists of the atoms that need it,
+// 32 / LPA atoms at a time (the flags are ORs over a row, so the result does
+// not depend on LPA).  In a large system most atoms need no scan and then cost
+// a lane rather than a warp (apw = 32); a small one keeps a warp per atom (apw
+// = 1, LPA = 32) so that its few scans run side by side.
+template <int LPA>
 __device__ __forceinline__ void buffer_body(const Dev& d, int bx, int gx, int apw) {
+    constexpr int G = 32 / LPA;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int grp = lane / LPA, sub = lane & (LPA - 1);
+    const unsigned gmask = LPA == 32 ? 0xffffffffu : (((1u << LPA) - 1u) << (grp * LPA));
     // float screen from the cell-relative float positions the potentials use;
     // float64 only within 1e-3 A^2 of a buffer radius
     const bool screen = d.xr != nullptr && !d.exact_lists;
@@ -222,54 +227,67 @@ __device__ __forceinline__ void buffer_body(const Dev& d, int bx, int gx, int ap
         unsigned todo = __ballot_sync(0xffffffffu, my_ne || my_nc);
         bool my_he = false, my_hc = false;
         while (todo) {
-            const int src = __ffs(todo) - 1;
-            todo &= todo - 1;
-            const int64_t i = base + src;
-            const bool need_e = __shfl_sync(0xffffffffu, my_ne, src);
-            const bool need_c = __shfl_sync(0xffffffffu, my_nc, src);
-            const double4 xi = d.x[i];
-            const int m = d.nnb[i];
-            const int* row = d.nbr + i * (int64_t)d.cap;
-            float4 xri = make_float4(0.f, 0.f, 0.f, 0.f);
-            int ci = 0;
-            if (screen) {
-                xri = d.xr[i];
-                ci = d.cell3[i];
-            }
+            // group g takes the (g + 1)-th atom still to scan
+            unsigned t = todo;
+            for (int k = 0; k < grp; ++k) t &= t - 1;
+            const int src = t ? __ffs(t) - 1 : -1;
+#pragma unroll
+            for (int k = 0; k < G; ++k) todo &= todo - 1;
+            const int sl = src < 0 ? 0 : src;
+            const bool need_e = __shfl_sync(0xffffffffu, my_ne, sl) && src >= 0;
+            const bool need_c = __shfl_sync(0xffffffffu, my_nc, sl) && src >= 0;
             bool he = false, hc = false;
-            for (int s = lane; s < m; s += 32) {
-                const int j = row[s];
-                const int fj = d.flags[j] & 3;
-                const bool cand_e = need_e && (fj & 1), cand_c = need_c && (fj & 2);
-                if (cand_e || cand_c) {
-                    bool ie = false, ic = false, exact = !screen;
-                    if (screen) {
-                        const float r2f = pair_r2_float(d, xri, ci, j);
-                        if (cand_e) {
-                            if (r2f < d.bufe2_lo) ie = true;
-                            else if (r2f <= d.bufe2_hi) exact = true;
+            if (src >= 0) {
+                const int64_t i = base + src;
+                const int m = d.nnb[i];
+                const int* row = d.nbr + i * (int64_t)d.cap;
+                float4 xri = make_float4(0.f, 0.f, 0.f, 0.f);
+                int ci = 0;
+                if (screen) {
+                    xri = d.xr[i];
+                    ci = d.cell3[i];
+                }
+                for (int s = sub; s < m; s += LPA) {
+                    const int j = row[s];
+                    const int fj = d.flags[j] & 3;
+                    const bool cand_e = need_e && (fj & 1), cand_c = need_c && (fj & 2);
+                    if (cand_e || cand_c) {
+                        bool ie = false, ic = false, exact = !screen;
+                        if (screen) {
+                            const float r2f = pair_r2_float(d, xri, ci, j);
+                            if (cand_e) {
+                                if (r2f < d.bufe2_lo) ie = true;
+                                else if (r2f <= d.bufe2_hi) exact = true;
+                            }
+                            if (cand_c) {
+                                if (r2f < d.bufc2_lo) ic = true;
+                                else if (r2f <= d.bufc2_hi) exact = true;
+                            }
                         }
-                        if (cand_c) {
-                            if (r2f < d.bufc2_lo) ic = true;
-                            else if (r2f <= d.bufc2_hi) exact = true;
+                        if (exact) {
+                            double dd[3];
+                            delta_rn(d.box, d.x[i], d.x[j], dd);
+                            const double r2 = norm2_rn(dd);
+                            ie = cand_e && r2 < d.bufe2;
+                            ic = cand_c && r2 < d.bufc2;
                         }
+                        he = he || ie;
+                        hc = hc || ic;
                     }
-                    if (exact) {
-                        double dd[3];
-                        delta_rn(d.box, xi, d.x[j], dd);
-                        const double r2 = norm2_rn(dd);
-                        ie = cand_e && r2 < d.bufe2;
-                        ic = cand_c && r2 < d.bufc2;
-                    }
-                    he = he || ie;
-                    hc = hc || ic;
                 }
             }
-            he = __any_sync(0xffffffffu, he);
-            hc = __any_sync(0xffffffffu, hc);
-            if (lane == src) {
-                my_he = he;
-                my_hc = hc;
+            he = (__ballot_sync(0xffffffffu, he) & gmask) != 0;
+            hc = (__ballot_sync(0xffffffffu, hc) & gmask) != 0;
+            // hand each group's result to its atom's lane
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                const int sg = __shfl_sync(0xffffffffu, src, g * LPA);
+                const bool eg = __shfl_sync(0xffffffffu, he, g * LPA);
+                const bool cg = __shfl_sync(0xffffffffu, hc, g * LPA);
+                if (lane == sg) {
+                    my_he = eg;
+                    my_hc = cg;
+                }
             }
         }
         if (valid) {
@@ -279,8 +297,17 @@ __device__ __forceinline__ void buffer_body(const Dev& d, int bx, int gx, int ap
         }
     }
 }
+
+// one atom a warp (apw = 1) takes the whole warp; else the system's lane groups
+__device__ __forceinline__ void buffer_dispatch(const Dev& d, int bx, int gx, int apw) {
+    const int lpa = apw == 1 ? 32 : gather_lpa(d);
+    if (lpa == 8) buffer_body<8>(d, bx, gx, apw);
+    else if (lpa == 16) buffer_body<16>(d, bx, gx, apw);
+    else buffer_body<32>(d, bx, gx, apw);
+}
+
 __global__ void __launch_bounds__(BUF_WARPS * 32) k_buffer(Dev d, int apw) {
-    buffer_body(d, blockIdx.x, gridDim.x, apw);
+    buffer_dispatch(d, blockIdx.x, gridDim.x, apw);
 }
 
 // Per-block counts of the two evaluated sets (and of the diagnostic sets).
@@ -404,7 +431,7 @@ __global__ void kb_lambda(BatchArgs ba, const Regions* __restrict__ regions) {
 }
 __global__ void __launch_bounds__(BUF_WARPS * 32) kb_buffer(BatchArgs ba) {
     MIX_BATCH_BLOCK(ba)
-    buffer_body(s_dev, s_ent.y, s_ent.z, 32);
+    buffer_dispatch(s_dev, s_ent.y, s_ent.z, 32);
 }
 __global__ void __launch_bounds__(SCAN_BLOCK) kb_count(BatchArgs ba) {
     MIX_BATCH_BLOCK(ba)

@@ -402,6 +402,11 @@ __device__ __forceinline__ void pair_vec(const Box& b, const double4& xi, const 
 template <typename T>
 struct PairFrame;
 
+// lanes per atom of the kernels that walk one list row with a lane group (the
+// gather, the buffer scan): the system's d.gat_lpa, a quarter warp for mean
+// list lengths up to 40, half a warp up to 80, else a warp; 32 when unset
+__host__ __device__ inline int gather_lpa(const Dev& d) { return d.gat_lpa == 8 || d.gat_lpa == 16 ? d.gat_lpa : 32; }
+
 // Pt: what vec() reads of the partner atom, loadable ahead of its use; Geo:
 // what it reads of the system's box and cells, loadable once into registers
 template <>
