@@ -37,7 +37,7 @@ __device__ __forceinline__ void gather_body(const Dev& d, int bx, int gx, int in
                                             GSum<T>* park) {
     using V = typename Vec4<T>::type;
     constexpr int G = 32 / LPA;
-    constexpr int GU = 2;   // slots a lane loads before summing them
+    constexpr int GU = LPA == 8 ? 4 : 2;   // slots a lane loads before summing them
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int sub = lane & (LPA - 1), grp = lane / LPA;
     const unsigned mask = LPA == 32 ? 0xffffffffu : (((1u << LPA) - 1u) << (lane & ~(LPA - 1)));
