@@ -171,6 +171,9 @@ __device__ __forceinline__ int pow2_cap(int cap) {
 
 constexpr int NB_RUNS = 18;
 
+// AHEAD2: also load the float positions a pass ahead (the batched kernel; the
+// single-context one, on longer candidate runs, measured faster without)
+template <bool AHEAD2>
 __device__ __forceinline__ void neigh_build_body(const Dev& d, int bx, int gx, int capp2, int* sbuf) {
     if (d.status[SW_REBUILD] == 0) return;
     __shared__ int s_runx[NB_WARPS][NB_RUNS];   // cell_atoms index of a run's first candidate, less its number
@@ -231,32 +234,40 @@ __device__ __forceinline__ void neigh_build_body(const Dev& d, int bx, int gx, i
             runx[lane] = t0 - (inc - len);
         }
         __syncwarp();
-        // the atom two passes ahead and the position one pass ahead are loaded
-        // before this pass is tested (r: run of the furthest candidate loaded)
+        // AHEAD2: the atom two passes ahead and the position one pass ahead are
+        // loaded before this pass is tested; else the atom one pass ahead
+        // (r: run of the furthest candidate loaded)
         int r = 0;
         int jn = -1, jnn = -1;
         float4 xn = make_float4(0.f, 0.f, 0.f, 0.f);
         if (lane < total) {
             while (lane >= runi[r]) ++r;
             jn = d.cell_atoms[runx[r] + lane];
-            xn = d.xf[jn];
+            if (AHEAD2) xn = d.xf[jn];
         }
-        if (lane + 32 < total) {
+        if (AHEAD2 && lane + 32 < total) {
             while (lane + 32 >= runi[r]) ++r;
             jnn = d.cell_atoms[runx[r] + lane + 32];
         }
         int cnt = 0;
         for (int u = lane; u - lane < total; u += 32) {
             const int j = jn;
-            const float4 xjf = xn;
-            jn = jnn;
-            if (u + 32 < total) xn = d.xf[jnn];
-            if (u + 64 < total) {
-                while (u + 64 >= runi[r]) ++r;
-                jnn = d.cell_atoms[runx[r] + u + 64];
+            float4 xjf;
+            if (AHEAD2) {
+                xjf = xn;
+                jn = jnn;
+                if (u + 32 < total) xn = d.xf[jnn];
+                if (u + 64 < total) {
+                    while (u + 64 >= runi[r]) ++r;
+                    jnn = d.cell_atoms[runx[r] + u + 64];
+                }
+            } else if (u + 32 < total) {
+                while (u + 32 >= runi[r]) ++r;
+                jn = d.cell_atoms[runx[r] + u + 32];
             }
             bool ok = false;
             if (u < total && j != (int)i) {
+                if (!AHEAD2) xjf = d.xf[j];
                 float df[3] = {xjf.x - xif.x, xjf.y - xif.y, xjf.z - xif.z};
 #pragma unroll
                 for (int k = 0; k < 3; ++k)
@@ -307,7 +318,7 @@ __device__ __forceinline__ void neigh_build_body(const Dev& d, int bx, int gx, i
 
 __global__ void __launch_bounds__(NB_WARPS * 32) k_neigh_build(Dev d, int capp2) {
     extern __shared__ __align__(16) int sbuf[];
-    neigh_build_body(d, blockIdx.x, gridDim.x, capp2, sbuf);
+    neigh_build_body<false>(d, blockIdx.x, gridDim.x, capp2, sbuf);
 }
 
 // rev[i][s] = position of i in the row of j = nbr[i][s] (binary search in the
@@ -366,7 +377,7 @@ __global__ void kb_cell_fill(BatchArgs ba) {
 __global__ void __launch_bounds__(NB_WARPS * 32) kb_neigh_build(BatchArgs ba) {
     extern __shared__ __align__(16) int sbuf[];
     MIX_BATCH_BLOCK_REBUILD(ba)
-    neigh_build_body(s_dev, s_ent.y, s_ent.z, pow2_cap(s_dev.cap), sbuf);
+    neigh_build_body<true>(s_dev, s_ent.y, s_ent.z, pow2_cap(s_dev.cap), sbuf);
 }
 __global__ void kb_neigh_rev(BatchArgs ba) {
     MIX_BATCH_BLOCK_REBUILD(ba)
