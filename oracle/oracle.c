@@ -91,8 +91,16 @@ static int cells_init(const obox* b, double rlist, ocells* c) {
     return OR_OK;
 }
 
+/* Cell index along d.  In a periodic dimension the coordinate is first folded
+ * into [0, L) as x - L floor(x / L): between list rebuilds an atom may sit up
+ * to half a skin outside a periodic face, and its cell must be the one its
+ * image lies in (clamping it into the edge cell would leave partners more than
+ * h - rlist beyond the face outside the 27-cell stencil).  Pair vectors stay
+ * minimum images of the raw positions (box_delta). */
 static int cell_coord(const obox* b, const ocells* c, const double* x, int d) {
-    double s = (x[d] - b->lo[d]) * c->invh[d];
+    double t = x[d] - b->lo[d];
+    if (b->per[d]) t = t - b->L[d] * floor(t * b->invL[d]);
+    double s = t * c->invh[d];
     int q = (int)floor(s);
     if (q < 0) q = 0;
     if (q > c->nc[d] - 1) q = c->nc[d] - 1;

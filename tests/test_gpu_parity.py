@@ -190,6 +190,31 @@ def test_checkpoints_along_a_trajectory(mx):
     assert st["rebuilds"] >= 1 and st["n_exp"] > 1000
 
 
+def test_mid_interval_checkpoint_outside_periodic_faces(mx):
+    """Between list rebuilds positions are folded only at the last rebuild, so
+    atoms sit up to half a skin outside the periodic faces.  Si 12x12x12 with
+    a vacancy (L = 65.172 A: the oracle's 13 cells at rc = 5 A are 0.013 A
+    wider than rc) at 1500 K: at checkpoints with atoms outside the box the
+    oracle re-evaluates sets and forces on the GPU's own bits."""
+    wl = I.si_vacancy(ncell=12, sigma=0.1)
+    rng = np.random.default_rng(3)
+    s = wl.system
+    wl.system = dataclasses.replace(s, v=I.maxwell_boltzmann(rng, s.n, s.mass, 1500.0))
+    ctx = mx.open_context(wl)
+    om = oracle.Model(wl)
+    seen = 0
+    for _ in range(3):
+        ctx.step(wl.dt, 7)
+        x, _, F, _ = ctx.get_state()
+        out = np.any((x[:, :3] < 0) | (x[:, :3] >= s.box_len), axis=1)
+        seen += int(out.sum() > 0)
+        fl, _, _ = ctx.sets()
+        assert np.array_equal(fl, om.sets(x))
+        FB, _, _ = om.forces(x, oracle.MODE_METHOD)
+        assert _max_abs(F[:, :3], FB[:, :3]) < TOL64
+    assert seen >= 1
+
+
 def test_deterministic_and_resumable(mx):
     wl = I.small_fe_box(16, r_core=4.0, ramp=3.0, sigma=0.15)
     a = mx.open_context(wl)

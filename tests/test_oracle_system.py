@@ -52,6 +52,98 @@ def test_neighbour_cells_equal_brute_force(orc):
                 assert np.array_equal(a[1][i, :a[0][i]], b[1][i, :b[0][i]])
 
 
+def _outside_face_pairs(L, rl, rng):
+    """Pairs of atoms whose minimum-image distance is just below rl, one atom of
+    each pair 0.01-0.15 A outside a low or a high periodic face, its partner
+    across that face; plus scattered atoms, some outside two faces at once."""
+    pts = []
+    for d in range(3):
+        for side in (0, 1):
+            for delta in (0.01, 0.05, 0.10, 0.15):
+                for r in (rl - 0.10, rl - 0.03, rl - 0.005):
+                    a = rng.uniform(0.3 * L, 0.7 * L, 3)
+                    b = a + rng.normal(0.0, 0.01, 3)
+                    if side == 0:
+                        a[d] = -delta            # below the low face
+                        b[d] = L - delta - r     # to its left, across the face
+                    else:
+                        a[d] = L + delta         # above the high face
+                        b[d] = delta + r         # to its right, across the face
+                    pts += [a, b]
+    for _ in range(120):
+        a = rng.uniform(0.0, L, 3)
+        for d in rng.choice(3, size=int(rng.integers(1, 3)), replace=False):
+            a[d] = -rng.uniform(0.01, 0.15) if rng.random() < 0.5 else L + rng.uniform(0.01, 0.15)
+        pts.append(a)
+    x = np.zeros((len(pts), 4))
+    x[:, :3] = np.array(pts)
+    return x
+
+
+def test_neighbour_cells_outside_periodic_faces(orc):
+    """Positions up to skin/2 outside a periodic face (the state between list
+    rebuilds) in a box whose cell width exceeds the list radius by only
+    0.013 A (Si 12x12x12, L = 65.172 A, 13 cells at r = 5.0): the cell-list
+    result still equals the O(N^2) enumeration, and the cell ids are those of
+    the folded coordinates."""
+    L = 12 * 5.431
+    box = np.array([L, L, L])
+    rng = np.random.default_rng(11)
+    x = _outside_face_pairs(L, 5.0, rng)
+    outside = np.any((x[:, :3] < 0) | (x[:, :3] >= L), axis=1)
+    assert outside.sum() > 150
+    for rl in (5.0, 5.0 - 1e-3, 4.9):
+        a = orc.neighbours(x, np.zeros(3), box, (1, 1, 1), rl, cap=64)
+        b = orc.neighbours(x, np.zeros(3), box, (1, 1, 1), rl, cap=64, brute=True)
+        assert b[0].sum() >= 144                     # every planted pair is a neighbour pair
+        assert np.array_equal(a[0], b[0])
+        for i in range(x.shape[0]):
+            assert np.array_equal(a[1][i, :a[0][i]], b[1][i, :b[0][i]])
+    nc, cid = orc.cells(x, np.zeros(3), box, (1, 1, 1), 5.0)
+    assert list(nc) == [13, 13, 13]
+    y = orc.wrap(x, box, (1, 1, 1))
+    _, cy = orc.cells(y, np.zeros(3), box, (1, 1, 1), 5.0)
+    assert np.array_equal(cid, cy)
+
+
+def test_forces_and_sets_unchanged_by_periodic_images(orc):
+    """Moving the atoms within 0.15 A of a face to their images just outside
+    the opposite face (the state between list rebuilds) changes no set and no
+    force beyond rounding, since every distance is a minimum image.  Si
+    12x12x12 with a vacancy and 0.25 A displacements (so that pairs fall in
+    the band a cell list with clamped rather than folded coordinates misses):
+    13 cells at rc = 5.0 A, 0.013 A wider than rc."""
+    wl = I.si_vacancy(ncell=12, sigma=0.25)
+    s = wl.system
+    assert abs(s.box_len[0] - 12 * 5.431) < 1e-9
+    x0 = orc.wrap(s.x, s.box_len, s.periodic)
+    shift = np.zeros_like(x0)
+    for d in range(3):
+        shift[x0[:, d] < 0.15, d] = s.box_len[d]
+        shift[x0[:, d] > s.box_len[d] - 0.15, d] = -s.box_len[d]
+    x1 = x0 + shift
+    moved = np.any(shift != 0, axis=1)
+    assert moved.sum() > 100
+    assert np.any(x1[:, :3] >= s.box_len) and np.any(x1[:, :3] < 0)
+    # pairs across a face at distances in (h - 0.15, rc): the band at stake
+    nnb, nbr = orc.neighbours(x0, s.box_lo, s.box_len, s.periodic, 5.0, cap=64, brute=True)
+    h = s.box_len[0] / 13
+    band = 0
+    for i in np.flatnonzero(moved):
+        for j in nbr[i, :nnb[i]]:
+            d = x0[j, :3] - x0[i, :3]
+            if np.any(np.abs(d) > 0.5 * s.box_len[0]):
+                d = d - s.box_len * np.rint(d / s.box_len)
+                band += int(np.sqrt(d @ d) > h - 0.15)
+    assert band > 10
+    om = orc.Model(wl)
+    assert np.array_equal(om.sets(x0), om.sets(x1))
+    for mode in (orc.MODE_METHOD, orc.MODE_PURE_CHEAP):
+        F0, _, _ = om.forces(x0, mode)
+        F1, _, _ = om.forces(x1, mode)
+        assert float(np.abs(F0[:, :3] - F1[:, :3]).max()) < 1e-10
+
+
 def test_cells_in_range_and_rejects_small_boxes(orc):
     s = I.si_vacancy().system
     nc, cid = orc.cells(s.x, s.box_lo, s.box_len, s.periodic, 5.3)
