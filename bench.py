@@ -5,8 +5,10 @@ on GB300, in atom-steps/s.
 A step is one velocity-Verlet step of the whole hot path: skin test and (when
 needed) cell/neighbour-list rebuild, blend weights, evaluated sets with their
 buffers, expensive potential on its set, cheap potential on its set, atomics-free
-gather + blend, second half-kick.  Workload: bcc Fe 20x20x10 + <110> dumbbell
-(8001 atoms), seeded synthetic positions and potentials.
+gather + blend, second half-kick.  Default workload: the 256,000-atom bcc Fe
+screw-dislocation cylinder (the largest single-GPU configuration), with the
+8,001-atom Fe dumbbell reported beside it; seeded synthetic positions and
+potentials.
 
 Timing: W untimed warm-up steps, then K steps; before every timed step a 512 MB
 buffer is written to flush L2 (129 MB), outside the timed interval; each step is
@@ -15,7 +17,7 @@ its kernel groups.  Multi-GPU (torchrun): independent replicas, one per rank,
 no collective on the data path; value = atoms x steps x ranks / max rank time.
 
 --impl reference times the FP64 CPU oracle (the program the GPU path is checked
-against) on the host cores, on the same workload.
+against) on the host cores, on the same workload, for a bounded time.
 """
 from __future__ import annotations
 
@@ -45,11 +47,13 @@ def parse():
     p.add_argument("--steps", type=int, default=50)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="fe_dumbbell_8001")
+    p.add_argument("--workload", default="fe_screw_256000")
     p.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     p.add_argument("--secondary-steps", type=int, default=20)
     p.add_argument("--e2e-steps", type=int, default=20)
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--no-secondary", action="store_true")
+    p.add_argument("--ref-seconds", type=float, default=90.0)
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--serve-seconds", type=float, default=60.0)
     p.add_argument("--serve-rate", type=float, default=20.0)
@@ -193,12 +197,13 @@ class Clocks:
 # GPU arm
 
 
-def run_precision(mix, torch, wl, precision, steps, warmup, flush):
-    ctx = mix.open_context(wl, precision=precision)
+def run_precision(mix, torch, wl, precision, steps, warmup, flush, regions=None):
+    ctx = mix.open_context(wl, precision=precision, regions=regions)
     for _ in range(warmup):
         ctx.step(wl.dt, 1)
     ctx.sync()
     launches0 = ctx.info()["launches"]
+    rebuilds0 = ctx.stats()["rebuilds"]
     ctx.profile(True)
     per_step = []
     for _ in range(steps):
@@ -210,29 +215,97 @@ def run_precision(mix, torch, wl, precision, steps, warmup, flush):
     ctx.profile(False)
     ctx.sync()
     launches = ctx.info()["launches"] - launches0
-    return ctx, np.array(per_step), tot, nev, launches
+    rebuilds = ctx.stats()["rebuilds"] - rebuilds0
+    return ctx, np.array(per_step), tot, nev, launches, rebuilds
 
 
-def cpu_baseline(wl, seconds: float):
-    """The oracle as it stands (C, OpenMP over sites), on this host's cores, on
-    consecutive mixed velocity-Verlet steps of the same workload."""
+def host_cores() -> int:
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+
+
+def oracle_leg(wl, x0, seconds: float):
+    """The oracle as it stands (C, OpenMP over sites) on this host's cores: its
+    forces and site energies at x0 (the GPU contexts' first positions), then
+    consecutive mixed velocity-Verlet steps for about `seconds` (at least one)."""
     import oracle
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    cores = host_cores()
     oracle.set_threads(cores)
     m = oracle.Model(wl)
-    x, v = wl.system.x, wl.system.v
-    F, _, _ = m.forces(x, oracle.MODE_METHOD)
+    t0 = time.perf_counter()
+    F, Ee, Ec = m.forces(x0, oracle.MODE_METHOD)
+    t_force = time.perf_counter() - t0
+    x, v, Fs = x0, np.array(wl.system.v, dtype=np.float64), F
     done = 0
     t0 = time.perf_counter()
     while True:
-        x, v, F, _ = m.md(x, v, F, wl.dt, 1, oracle.MODE_METHOD)
+        x, v, Fs, _ = m.md(x, v, Fs, wl.dt, 1, oracle.MODE_METHOD)
         done += 1
         el = time.perf_counter() - t0
         if el >= seconds or done >= 50:
             break
-    return {"value": wl.system.n * done / el, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{done} mixed velocity-Verlet steps of {wl.name} ({wl.system.n} atoms), FP64, "
-                      f"OpenMP over sites, {el:.1f} s"}
+    base = {"value": wl.system.n * done / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{done} mixed velocity-Verlet step(s) of {wl.name} ({wl.system.n} atoms), FP64, "
+                      f"OpenMP over sites on {cores} threads, {el:.1f} s (after one {t_force:.1f} s force "
+                      f"evaluation at the starting positions, not timed)"}
+    return base, F, Ee, Ec
+
+
+def oracle_single_thread(names, seconds: float = 4.0):
+    """Single-thread oracle throughput on the small workloads (one core)."""
+    import oracle
+    from paper_2502_19081_gb300 import inputs as I
+    out = {}
+    oracle.set_threads(1)
+    try:
+        for name in names:
+            wl = I.workload(name)
+            m = oracle.Model(wl)
+            x, v = wl.system.x, wl.system.v
+            F, _, _ = m.forces(x, oracle.MODE_METHOD)
+            done = 0
+            t0 = time.perf_counter()
+            while True:
+                x, v, F, _ = m.md(x, v, F, wl.dt, 1, oracle.MODE_METHOD)
+                done += 1
+                el = time.perf_counter() - t0
+                if el >= seconds or done >= 200:
+                    break
+            out[name] = {"value": wl.system.n * done / el, "unit": UNIT, "cores": 1, "steps": done}
+    finally:
+        oracle.set_threads(host_cores())
+    return out
+
+
+def errors_against(ctx_F, ctx_E, F_ref, E_ref, flags):
+    """max |dF| over atoms, max |dE_i| over each potential's evaluated sites and
+    the error of each potential's total energy over its evaluated set."""
+    dF = float(np.abs(ctx_F[:, :3] - F_ref[:, :3]).max()) if len(F_ref) else 0.0
+    out = {"force_max_abs_eV_per_A": dF}
+    for k, (e, er, bit) in enumerate(zip(ctx_E, E_ref, (4, 8))):
+        sel = (flags & bit) > 0
+        name = "exp" if k == 0 else "cheap"
+        out[f"site_energy_{name}_max_abs_eV"] = float(np.abs(e[sel] - er[sel]).max()) if sel.any() else 0.0
+        out[f"energy_{name}_total_abs_eV"] = float(abs(np.sum(e[sel]) - np.sum(er[sel])))
+    return out
+
+
+def phase_bytes(name: str, n: int, nst: dict, rebuild_frac: float) -> float:
+    """Algorithmic DRAM bytes per step of a memory-bound phase (atom-major
+    float64 rows of 32 B, int32 lists): disp reads x, v, f and writes x, v;
+    lists (rebuild steps only) read x and write cell ids, nnb and the sorted
+    rows and reverse slots; sets read x and the list and write weights and
+    flags; gather reads both potentials' own and incoming slot rows (16 B a
+    slot in float) and writes f, v."""
+    nb = nst["nnb_list"]
+    if name == "disp":
+        return n * 96.0
+    if name == "lists":
+        return rebuild_frac * n * (32.0 + 4.0 + 4.0 + 8.0 * nb)
+    if name == "sets":
+        return n * (32.0 + 4.0 * nb + 9.0 + 4.0)
+    if name == "gather":
+        return nst["n_exp"] * 2 * 16.0 * nst["nnb_exp_rc"] + nst["n_cheap"] * 2 * 16.0 * nst["nnb_cheap_rc"] + n * 72.0
+    return 0.0
 
 
 def profiled_traffic(profile: str, sources) -> "int | None":
@@ -256,6 +329,125 @@ def profiled_traffic(profile: str, sources) -> "int | None":
     return int(vals["traffic_bytes_per_launch"])
 
 
+def gpu_leg(mix, torch, wl, prec, args, flush, peaks, hbm, oracle_seconds, e2e=True, timed_steps=None,
+            secondary_steps=None):
+    """Everything the line reports for one workload on the GPU (and, unless
+    --no-cpu, the oracle beside it)."""
+    steps = args.steps if timed_steps is None else timed_steps
+    sec = args.secondary_steps if secondary_steps is None else secondary_steps
+    names = mix.PHASE_NAMES
+    # FP64 path at the starting positions: reference bits for the other precisions
+    c64 = mix.open_context(wl, precision=mix.MIX_FP64)
+    x0, _, F64, _ = c64.get_state()
+    E64 = c64.site_energies()
+    flags, _, _ = c64.sets()
+    nst = neighbour_stats(c64, wl)
+    nnb, _, _ = c64.neighbours()
+    nst["nnb_list"] = float(np.mean(nnb)) if len(nnb) else 0.0
+    info = c64.info()
+    c64.close()
+    firsts = {mix.MIX_FP64: (F64, E64)}
+    for p in {prec, mix.MIX_FP32}:
+        if p in firsts:
+            continue
+        cp = mix.open_context(wl, precision=p)
+        _, _, Fp, _ = cp.get_state()
+        firsts[p] = (Fp, cp.site_energies())
+        cp.close()
+
+    ctx, per, tot, nev, launches, rebuilds = run_precision(mix, torch, wl, prec, steps, args.warmup, flush)
+    total_ms = float(per.sum())
+    e2e_blk = None
+    if e2e:
+        n = wl.system.n
+        hx = torch.empty((n, 4), dtype=torch.float64, pin_memory=True)
+        hv = torch.empty_like(hx, pin_memory=True)
+        hf = torch.empty_like(hx, pin_memory=True)
+        xs, vs, fs, _ = ctx.get_state()
+        hx.numpy()[:] = xs
+        hv.numpy()[:] = vs
+        hf.numpy()[:] = fs
+        e2e_s = []
+        for _ in range(max(1, args.e2e_steps)):
+            flush()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx.step_host(hx.numpy(), hv.numpy(), hf.numpy(), wl.dt, 1)
+            e2e_s.append(time.perf_counter() - t0)
+        e2e_blk = {"value": n / float(np.mean(e2e_s)), "unit": UNIT, "h2d_bytes_per_step": 3 * n * 32,
+                   "d2h_bytes_per_step": 3 * n * 32, "steps": len(e2e_s),
+                   "entry": "mix_step_host (x, v, f in and out, pinned host memory)"}
+    ctx.close()
+
+    # the FP64 path (or FP32 when FP64 is the headline), shorter
+    other = mix.MIX_FP64 if prec != mix.MIX_FP64 else mix.MIX_FP32
+    c2, per2, tot2, nev2, _, _ = run_precision(mix, torch, wl, other, sec, 3, flush)
+    c2.close()
+
+    # pure potentials on every atom, same arithmetic: the measured speed ratio
+    # S_C/E and the zero-overhead bound (paper SI, load balancing)
+    centre = tuple(float(v) for v in np.asarray(wl.system.box_lo) + 0.5 * np.asarray(wl.system.box_len))
+    from paper_2502_19081_gb300 import inputs as I
+    everywhere = [I.Region(I.REGION_SPHERE, centre, (0.0, 0.0, 1.0), 1.0e4, 1.0)]
+    pure = {}
+    for key, regs in (("exp", everywhere), ("cheap", [])):
+        cx, perx, _, _, _, _ = run_precision(mix, torch, wl, prec, max(3, sec // 2), 3, flush, regions=regs)
+        cx.close()
+        pure[key] = float(np.mean(perx))
+
+    n = wl.system.n
+    ms_step = total_ms / steps
+    phase_ms = tot / max(nev, 1)
+    pe = exp_flops_per_atom(wl, info, nst["nnb_exp_rc"])
+    pc = cheap_flops_per_atom(nst["nnb_cheap_rc"], nst["n3_cheap"])
+    rf = rebuilds / max(steps, 1)
+    kern = {}
+    for p, nm in enumerate(names):
+        kb = {"ms": float(phase_ms[p]), "share": float(phase_ms[p] / phase_ms.sum())}
+        if nm == "exp":
+            kb["algorithmic_flops"] = pe * nst["n_exp"]
+            kb["tflops"] = kb["algorithmic_flops"] / (phase_ms[p] * 1e-3) / 1e12 if phase_ms[p] > 0 else 0.0
+        elif nm == "cheap":
+            # the cheap kernel runs on a second stream beside the expensive one:
+            # its phase time is only the part not hidden behind it; its own
+            # throughput comes from the pure-cheap step below
+            kb["algorithmic_flops"] = pc * nst["n_cheap"]
+            kb["note"] = "concurrent with exp on a second stream; ms = the part after exp ends"
+        else:
+            kb["algorithmic_bytes"] = phase_bytes(nm, n, nst, rf)
+            kb["gbs"] = kb["algorithmic_bytes"] / (phase_ms[p] * 1e-3) / 1e9 if phase_ms[p] > 0 else 0.0
+            kb["hbm_frac"] = kb["gbs"] / hbm
+        kern[nm] = kb
+    kern["cheap"]["pure_cheap_step_tflops"] = pc * n / (pure["cheap"] * 1e-3) / 1e12
+    s_ce = pure["exp"] / pure["cheap"]
+    s_ul = n * s_ce / (nst["n_exp"] * s_ce + nst["n_cheap"])
+    speedup = pure["exp"] / ms_step
+    blk = {
+        "value": n * steps / (total_ms * 1e-3), "ms_per_step": ms_step,
+        "p50_ms": float(np.percentile(per, 50)), "p99_ms": float(np.percentile(per, 99)),
+        "per_step_ms": per, "total_ms": total_ms, "phase_ms": phase_ms, "launches": int(launches),
+        "kernels": kern, "nstat": nst, "info": info, "pe": pe, "pc": pc, "rebuilds": int(rebuilds),
+        "other": {"precision": other, "value": n * len(per2) / (per2.sum() * 1e-3),
+                  "ms_per_step": float(per2.mean()), "p50_ms": float(np.percentile(per2, 50)),
+                  "p99_ms": float(np.percentile(per2, 99)),
+                  "kernels_ms": {names[p]: float(tot2[p] / max(nev2, 1)) for p in range(len(names))}},
+        "mixing": {"pure_expensive_ms_per_step": pure["exp"], "pure_cheap_ms_per_step": pure["cheap"],
+                   "s_ce_measured": s_ce, "speedup": speedup, "s_ul": s_ul, "speedup_over_s_ul": speedup / s_ul,
+                   "note": "speedup = pure-expensive step / mixed step, same arithmetic; s_ul = N S / (N_E S + N_C) "
+                           "with S = S_C/E the measured ratio of the pure-expensive to the pure-cheap step time "
+                           "(paper SI, load balancing); N_E, N_C = evaluated set sizes"},
+        "e2e": e2e_blk, "x0": x0, "flags": flags, "firsts": firsts,
+    }
+    blk["errors_vs_gpu_fp64"] = {mix.PREC_NAMES[p]: errors_against(F, E, F64, E64, flags)
+                                 for p, (F, E) in firsts.items() if p != mix.MIX_FP64}
+    if not args.no_cpu:
+        cpu, Fo, Eeo, Eco = oracle_leg(wl, x0, oracle_seconds)
+        blk["cpu_baseline"] = cpu
+        blk["errors_vs_oracle"] = {mix.PREC_NAMES[p]: errors_against(F, E, Fo, (Eeo, Eco), flags)
+                                   for p, (F, E) in firsts.items()}
+    return blk
+
+
 def ours(args):
     import torch
     import torch.distributed as dist
@@ -268,79 +460,25 @@ def ours(args):
     torch.cuda.set_device(local)
     B.build()
     wl = make_workload(args.workload, rank)
-    prec = mix.MIX_FP32 if args.precision == "fp32" else mix.MIX_FP64
-    other = mix.MIX_FP64 if prec == mix.MIX_FP32 else mix.MIX_FP32
+    prec = {"fp32": mix.MIX_FP32, "fp64": mix.MIX_FP64}[args.precision]
     flush_buf = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
     def flush():
         flush_buf.zero_()
 
     peaks = {p: mix.fma_peak(p) for p in (mix.MIX_FP64, mix.MIX_FP32)}
-
-    # accuracy of the headline precision against the FP64 path at the same positions
-    c64 = mix.open_context(wl, precision=mix.MIX_FP64)
-    x0, _, F64, _ = c64.get_state()
-    nstat = neighbour_stats(c64, wl)
-    info = c64.info()
-    c64.close()
-    cp = mix.open_context(wl, precision=prec)
-    _, _, Fp, _ = cp.get_state()
-    cp.close()
-    ferr = float(np.abs(Fp[:, :3] - F64[:, :3]).max())
+    peaks_file = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    hbm = json.load(open(peaks_file))["hbm_gbs"] if os.path.exists(peaks_file) else 6800.0
 
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     clocks = Clocks(local)
     clocks.start()
-    ctx, per, tot, nev, launches = run_precision(mix, torch, wl, prec, args.steps, args.warmup, flush)
+    main = gpu_leg(mix, torch, wl, prec, args, flush, peaks, hbm, args.cpu_seconds if rank == 0 else 0.0)
     clk = clocks.stop()
-    total_ms = float(per.sum())
-    total_max = max_over_ranks(total_ms, device="cuda")
+    total_max = max_over_ranks(main["total_ms"], device="cuda")
     value = job_throughput(wl.system.n, args.steps, world, total_max)
-
-    # end to end through the host-buffer entry point (pinned host arrays)
-    n = wl.system.n
-    hx = torch.empty((n, 4), dtype=torch.float64, pin_memory=True)
-    hv = torch.empty_like(hx, pin_memory=True)
-    hf = torch.empty_like(hx, pin_memory=True)
-    xs, vs, fs, _ = ctx.get_state()
-    hx.numpy()[:] = xs
-    hv.numpy()[:] = vs
-    hf.numpy()[:] = fs
-    e2e_s = []
-    for _ in range(max(1, args.e2e_steps)):
-        flush()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        ctx.step_host(hx.numpy(), hv.numpy(), hf.numpy(), wl.dt, 1)
-        e2e_s.append(time.perf_counter() - t0)
-    e2e_val = n / float(np.mean(e2e_s))
-    ctx.close()
-
-    # the other precision, shorter
-    c2, per2, tot2, nev2, _ = run_precision(mix, torch, wl, other, args.secondary_steps, max(3, args.warmup // 2),
-                                            flush)
-    c2.close()
-
-    # the pure expensive potential on every atom (one region covering the box),
-    # same arithmetic, for the mixing speedup
-    from paper_2502_19081_gb300 import inputs as I
-    centre = tuple(float(v) for v in np.asarray(wl.system.box_lo) + 0.5 * np.asarray(wl.system.box_len))
-    everywhere = [I.Region(I.REGION_SPHERE, centre, (0.0, 0.0, 1.0), 1.0e4, 1.0)]
-    cx = mix.open_context(wl, precision=prec, regions=everywhere)
-    for _ in range(3):
-        cx.step(wl.dt, 1)
-    cx.sync()
-    cx.profile(True)
-    per_x = []
-    for _ in range(max(3, args.secondary_steps // 2)):
-        flush()
-        cx.step(wl.dt, 1)
-        per_x.append(float(np.sum(cx.get_profile()[1])))
-    cx.profile(False)
-    cx.close()
-    pure_ms = float(np.mean(per_x))
 
     if rank != 0:
         if world > 1:
@@ -348,34 +486,32 @@ def ours(args):
             dist.destroy_process_group()
         return
 
-    phase_ms = tot / max(nev, 1)
-    dom = int(np.argmax(phase_ms))
     names = mix.PHASE_NAMES
-    pe = exp_flops_per_atom(wl, info, nstat["nnb_exp_rc"])
-    pc = cheap_flops_per_atom(nstat["nnb_cheap_rc"], nstat["n3_cheap"])
+    phase_ms = main["phase_ms"]
+    dom = int(np.argmax(phase_ms))
     peak = peaks[prec]
+    kern = main["kernels"]
     if names[dom] in ("exp", "cheap"):
-        fl = pe * nstat["n_exp"] if names[dom] == "exp" else pc * nstat["n_cheap"]
+        fl = kern[names[dom]]["algorithmic_flops"]
         ach = fl / (phase_ms[dom] * 1e-3)
         roof = {"kernel": "k_ace" if names[dom] == "exp" else "k_spline", "bound": "alu",
                 "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": (profiled_traffic("k_ace_fe_dumbbell_8001.md", ("k_ace.cuh", "k_ace_f32.cu"))
-                            if names[dom] == "exp" and prec == mix.MIX_FP32 and wl.name == "fe_dumbbell_8001"
-                            else None),
+                "traffic": (profiled_traffic(f"k_ace_{wl.name}.md", ("k_ace.cuh", "k_ace_f32.cu"))
+                            if names[dom] == "exp" and prec == mix.MIX_FP32 else None),
                 "algorithmic_flops_per_launch": fl,
-                "peak_source": f"measured FMA microbenchmark ({'fp32' if prec == mix.MIX_FP32 else 'fp64'}), "
-                               "mix_fma_peak"}
+                "peak_source": f"measured FMA microbenchmark ({mix.PREC_NAMES[prec]}), mix_fma_peak"}
     else:
-        peaks_file = os.path.join(ROOT, "MEASURED_PEAKS.json")
-        hbm = json.load(open(peaks_file))["hbm_gbs"] if os.path.exists(peaks_file) else 6800.0
-        byts = n * 400.0
+        byts = kern[names[dom]]["algorithmic_bytes"]
         ach = byts / (phase_ms[dom] * 1e-3) / 1e9
         roof = {"kernel": names[dom], "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": ach / hbm, "traffic": None}
-    kern = {names[p]: {"ms": float(phase_ms[p]), "share": float(phase_ms[p] / phase_ms.sum())}
-            for p in range(len(names))}
-    pname = "f32" if prec == mix.MIX_FP32 else "f64"
-    oname = "f64" if prec == mix.MIX_FP32 else "f32"
+                "frac": ach / hbm, "traffic": None, "algorithmic_bytes_per_launch": byts,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    n = wl.system.n
+    pname = mix.PREC_NAMES[prec]
+    other = main["other"]
+    nst = main["nstat"]
+    errs = main.get("errors_vs_oracle", main["errors_vs_gpu_fp64"])
+    ferr = errs[pname]["force_max_abs_eV_per_A"] if pname in errs else 0.0
     out = {
         "metric": METRIC,
         "value": value,
@@ -384,8 +520,8 @@ def ours(args):
         "steps": args.steps,
         "warmup": args.warmup,
         "ms_per_step": total_max / args.steps,
-        "p50_ms": float(np.percentile(per, 50)),
-        "p99_ms": float(np.percentile(per, 99)),
+        "p50_ms": main["p50_ms"],
+        "p99_ms": main["p99_ms"],
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
@@ -394,28 +530,41 @@ def ours(args):
         "config": {"workload": wl.name, "n_atoms": n, "potential_arithmetic": pname, "integration": "f64",
                    "expensive": f"linear ACE n={wl.ace.n_rad} lmax={wl.ace.l_max} body order {wl.ace.nu_max + 1}",
                    "cheap": "2+3-body cubic B-spline", "l2": "flushed before every timed step (512 MB write)",
-                   "parallelism": f"replicas x{world}", "evaluated_exp": nstat["n_exp"],
-                   "evaluated_cheap": nstat["n_cheap"]},
-        "force_err_vs_fp64_eV_per_A": ferr,
+                   "parallelism": f"replicas x{world}", "evaluated_exp": nst["n_exp"],
+                   "evaluated_cheap": nst["n_cheap"]},
+        "force_err_vs_oracle_eV_per_A": ferr,
         "gate_eV_per_A": GATE,
         "within_gate": bool(ferr <= GATE),
-        oname + "_path": {"value": wl.system.n * len(per2) / (per2.sum() * 1e-3), "ms_per_step": float(per2.mean()),
-                          "p50_ms": float(np.percentile(per2, 50)), "p99_ms": float(np.percentile(per2, 99)),
-                          "kernels_ms": {names[p]: float(tot2[p] / max(nev2, 1)) for p in range(len(names))}},
+        "errors": errs,
+        "errors_reference": "oracle (FP64 CPU) at the starting positions" if "errors_vs_oracle" in main
+                            else "GPU FP64 path at the starting positions",
+        mix.PREC_NAMES[other["precision"]] + "_path": {k: v for k, v in other.items() if k != "precision"},
         "roofline": roof,
         "kernels": kern,
-        "mixing": {"pure_expensive_ms_per_step": pure_ms, "speedup": pure_ms / (total_max / args.steps),
-                   "s_ul": n * pe / (nstat["n_exp"] * pe + nstat["n_cheap"] * pc),
-                   "note": "speedup over the same step with the expensive potential on every atom; s_ul = the "
-                           "zero-overhead bound from algorithmic flops, N e / (|A_exp| e + |A_cheap| c)"},
+        "mixing": main["mixing"],
         "fma_peak_tflops": {"fp64": peaks[mix.MIX_FP64] / 1e12, "fp32": peaks[mix.MIX_FP32] / 1e12},
-        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 3 * n * 32, "d2h_bytes_per_step": 3 * n * 32,
-                "steps": len(e2e_s), "entry": "mix_step_host (x, v, f in and out, pinned host memory)"},
-        "gpu_launches": int(launches),
+        "e2e": main["e2e"],
+        "gpu_launches": main["launches"],
+        "rebuilds_in_timed_steps": main["rebuilds"],
         "clocks": clk,
     }
+    if "cpu_baseline" in main:
+        out["cpu_baseline"] = main["cpu_baseline"]
+    # the 8,001-atom Fe dumbbell beside it: the configuration the paper's ~11x
+    # mixing speedup at ~8,000 atoms is comparable with
+    if args.workload != "fe_dumbbell_8001" and not args.no_secondary:
+        wl2 = make_workload("fe_dumbbell_8001", 0)
+        sec = gpu_leg(mix, torch, wl2, mix.MIX_FP32, args, flush, peaks, hbm, 8.0, e2e=True,
+                      timed_steps=max(10, args.steps), secondary_steps=args.secondary_steps)
+        e2 = sec.get("errors_vs_oracle", sec["errors_vs_gpu_fp64"])
+        out["fe_dumbbell_8001"] = {
+            "value": sec["value"], "ms_per_step": sec["ms_per_step"], "p50_ms": sec["p50_ms"],
+            "p99_ms": sec["p99_ms"], "dtype": "f32", "errors": e2, "f64_path": sec["other"],
+            "mixing": sec["mixing"], "kernels": sec["kernels"], "e2e": sec["e2e"],
+            "cpu_baseline": sec.get("cpu_baseline"),
+            "evaluated_exp": sec["nstat"]["n_exp"], "evaluated_cheap": sec["nstat"]["n_cheap"]}
     if not args.no_cpu:
-        out["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
+        out["oracle_single_thread"] = oracle_single_thread(["si_vacancy_215", "fe_dumbbell_8001"])
     print(json.dumps(out), flush=True)
     if world > 1:
         dist.barrier()
@@ -580,34 +729,42 @@ def serve_bench(args):
 
 
 def reference(args):
-    """The oracle arm: FP64 C oracle on the host cores, same workload and metric."""
+    """The oracle arm: FP64 C oracle on the host cores, same workload and
+    metric.  One oracle step of the 256,000-atom cylinder takes seconds, so
+    the arm times at most K steps within --ref-seconds (at least one) after
+    one untimed force evaluation (its warm-up), and says so in the line."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
     import oracle
     oracle.build()
     wl = make_workload(args.workload, 0)
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    cores = host_cores()
     oracle.set_threads(cores)
     m = oracle.Model(wl)
     x, v = wl.system.x, wl.system.v
     F, _, _ = m.forces(x, oracle.MODE_METHOD)
-    for _ in range(args.warmup):
-        x, v, F, _ = m.md(x, v, F, wl.dt, 1, oracle.MODE_METHOD)
     per = []
-    for _ in range(args.steps):
+    t_all = time.perf_counter()
+    while len(per) < args.steps:
         t0 = time.perf_counter()
         x, v, F, _ = m.md(x, v, F, wl.dt, 1, oracle.MODE_METHOD)
         per.append(time.perf_counter() - t0)
+        if time.perf_counter() - t_all >= args.ref_seconds:
+            break
     per = np.array(per)
     value = wl.system.n * len(per) / per.sum()
+    sample = (f"{len(per)} of the {args.steps} requested mixed velocity-Verlet steps of {wl.name} "
+              f"({wl.system.n} atoms), FP64, OpenMP over sites on {cores} threads, bounded at "
+              f"{args.ref_seconds:.0f} s; warm-up: one untimed force evaluation")
     out = {
         "impl": "reference",
         "metric": METRIC,
         "value": value,
         "unit": UNIT,
         "n_gpus": world,
-        "steps": args.steps,
+        "steps": len(per),
+        "steps_requested": args.steps,
         "warmup": args.warmup,
         "ms_per_step": float(per.mean() * 1e3),
         "p50_ms": float(np.percentile(per, 50) * 1e3),
@@ -619,8 +776,7 @@ def reference(args):
         "data": "synthetic",
         "config": {"workload": wl.name, "n_atoms": wl.system.n, "potential_arithmetic": "f64",
                    "integration": "f64", "parallelism": "host cores"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"{len(per)} mixed velocity-Verlet steps of {wl.name}"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out), flush=True)

@@ -32,6 +32,7 @@ MIX_EBOX = -8
 
 MIX_FP64 = 0
 MIX_FP32 = 1
+PREC_NAMES = {MIX_FP64: "f64", MIX_FP32: "f32"}
 MIX_BLEND_LINEAR = 0
 MIX_BLEND_CUBIC = 1
 
