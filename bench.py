@@ -48,7 +48,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="fe_screw_256000")
-    p.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    p.add_argument("--precision", default="auto", choices=["auto", "fp32", "fp64", "bf16", "bf16x3"])
     p.add_argument("--secondary-steps", type=int, default=20)
     p.add_argument("--e2e-steps", type=int, default=20)
     p.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -330,12 +330,16 @@ def profiled_traffic(profile: str, sources) -> "int | None":
 
 
 def gpu_leg(mix, torch, wl, prec, args, flush, peaks, hbm, oracle_seconds, e2e=True, timed_steps=None,
-            secondary_steps=None):
+            secondary_steps=None, candidates=None):
     """Everything the line reports for one workload on the GPU (and, unless
-    --no-cpu, the oracle beside it)."""
+    --no-cpu, the oracle beside it).  prec None: the first of `candidates`
+    whose force error against the FP64 path at the starting positions is
+    within the gate (else FP32) is the headline precision; every candidate
+    and the FP64 path are timed beside it."""
     steps = args.steps if timed_steps is None else timed_steps
     sec = args.secondary_steps if secondary_steps is None else secondary_steps
     names = mix.PHASE_NAMES
+    candidates = list(candidates or [])
     # FP64 path at the starting positions: reference bits for the other precisions
     c64 = mix.open_context(wl, precision=mix.MIX_FP64)
     x0, _, F64, _ = c64.get_state()
@@ -347,15 +351,22 @@ def gpu_leg(mix, torch, wl, prec, args, flush, peaks, hbm, oracle_seconds, e2e=T
     info = c64.info()
     c64.close()
     firsts = {mix.MIX_FP64: (F64, E64)}
-    for p in {prec, mix.MIX_FP32}:
+    for p in [mix.MIX_FP32] + candidates + ([prec] if prec is not None else []):
         if p in firsts:
             continue
         cp = mix.open_context(wl, precision=p)
         _, _, Fp, _ = cp.get_state()
         firsts[p] = (Fp, cp.site_energies())
         cp.close()
+    if prec is None:
+        prec = mix.MIX_FP32
+        for p in candidates:
+            if float(np.abs(firsts[p][0][:, :3] - F64[:, :3]).max()) <= GATE:
+                prec = p
+                break
 
     ctx, per, tot, nev, launches, rebuilds = run_precision(mix, torch, wl, prec, steps, args.warmup, flush)
+    hinfo = ctx.info()
     total_ms = float(per.sum())
     e2e_blk = None
     if e2e:
@@ -383,6 +394,16 @@ def gpu_leg(mix, torch, wl, prec, args, flush, peaks, hbm, oracle_seconds, e2e=T
     other = mix.MIX_FP64 if prec != mix.MIX_FP64 else mix.MIX_FP32
     c2, per2, tot2, nev2, _, _ = run_precision(mix, torch, wl, other, sec, 3, flush)
     c2.close()
+    # the other reduced precisions, as long as the FP64 path's run
+    others = {}
+    for p in firsts:
+        if p in (prec, other):
+            continue
+        cq, perq, totq, nevq, _, _ = run_precision(mix, torch, wl, p, sec, 3, flush)
+        cq.close()
+        others[p] = {"value": wl.system.n * len(perq) / (perq.sum() * 1e-3), "ms_per_step": float(perq.mean()),
+                     "p50_ms": float(np.percentile(perq, 50)), "p99_ms": float(np.percentile(perq, 99)),
+                     "kernels_ms": {names[k]: float(totq[k] / max(nevq, 1)) for k in range(len(names))}}
 
     # pure potentials on every atom, same arithmetic: the measured speed ratio
     # S_C/E and the zero-overhead bound (paper SI, load balancing)
@@ -426,7 +447,7 @@ def gpu_leg(mix, torch, wl, prec, args, flush, peaks, hbm, oracle_seconds, e2e=T
         "value": n * steps / (total_ms * 1e-3), "ms_per_step": ms_step,
         "p50_ms": float(np.percentile(per, 50)), "p99_ms": float(np.percentile(per, 99)),
         "per_step_ms": per, "total_ms": total_ms, "phase_ms": phase_ms, "launches": int(launches),
-        "kernels": kern, "nstat": nst, "info": info, "pe": pe, "pc": pc, "rebuilds": int(rebuilds),
+        "kernels": kern, "nstat": nst, "info": info, "hinfo": hinfo, "pe": pe, "pc": pc, "rebuilds": int(rebuilds),
         "other": {"precision": other, "value": n * len(per2) / (per2.sum() * 1e-3),
                   "ms_per_step": float(per2.mean()), "p50_ms": float(np.percentile(per2, 50)),
                   "p99_ms": float(np.percentile(per2, 99)),
@@ -436,7 +457,7 @@ def gpu_leg(mix, torch, wl, prec, args, flush, peaks, hbm, oracle_seconds, e2e=T
                    "note": "speedup = pure-expensive step / mixed step, same arithmetic; s_ul = N S / (N_E S + N_C) "
                            "with S = S_C/E the measured ratio of the pure-expensive to the pure-cheap step time "
                            "(paper SI, load balancing); N_E, N_C = evaluated set sizes"},
-        "e2e": e2e_blk, "x0": x0, "flags": flags, "firsts": firsts,
+        "e2e": e2e_blk, "x0": x0, "flags": flags, "firsts": firsts, "prec": prec, "others": others,
     }
     blk["errors_vs_gpu_fp64"] = {mix.PREC_NAMES[p]: errors_against(F, E, F64, E64, flags)
                                  for p, (F, E) in firsts.items() if p != mix.MIX_FP64}
@@ -460,7 +481,14 @@ def ours(args):
     torch.cuda.set_device(local)
     B.build()
     wl = make_workload(args.workload, rank)
-    prec = {"fp32": mix.MIX_FP32, "fp64": mix.MIX_FP64}[args.precision]
+    pmap = {"fp32": mix.MIX_FP32, "fp64": mix.MIX_FP64, "bf16": mix.MIX_BF16, "bf16x3": mix.MIX_BF16_SPLIT}
+    # auto: the 256,000-atom cylinder's readout runs on the tensor cores in bf16,
+    # the hi/lo split when plain bf16 misses the force gate; FP32 elsewhere
+    prec = pmap.get(args.precision)
+    cands = [mix.MIX_BF16, mix.MIX_BF16_SPLIT] if args.precision == "auto" and args.workload == "fe_screw_256000" \
+        else []
+    if args.precision == "auto" and not cands:
+        prec = mix.MIX_FP32
     flush_buf = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
     def flush():
@@ -475,7 +503,9 @@ def ours(args):
     torch.cuda.synchronize()
     clocks = Clocks(local)
     clocks.start()
-    main = gpu_leg(mix, torch, wl, prec, args, flush, peaks, hbm, args.cpu_seconds if rank == 0 else 0.0)
+    main = gpu_leg(mix, torch, wl, prec, args, flush, peaks, hbm, args.cpu_seconds if rank == 0 else 0.0,
+                   candidates=cands)
+    prec = main["prec"]
     clk = clocks.stop()
     total_max = max_over_ranks(main["total_ms"], device="cuda")
     value = job_throughput(wl.system.n, args.steps, world, total_max)
@@ -489,17 +519,28 @@ def ours(args):
     names = mix.PHASE_NAMES
     phase_ms = main["phase_ms"]
     dom = int(np.argmax(phase_ms))
-    peak = peaks[prec]
+    peak = peaks[mix.MIX_FP64 if prec == mix.MIX_FP64 else mix.MIX_FP32]
     kern = main["kernels"]
     if names[dom] in ("exp", "cheap"):
         fl = kern[names[dom]]["algorithmic_flops"]
         ach = fl / (phase_ms[dom] * 1e-3)
         roof = {"kernel": "k_ace" if names[dom] == "exp" else "k_spline", "bound": "alu",
                 "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": (profiled_traffic(f"k_ace_{wl.name}.md", ("k_ace.cuh", "k_ace_f32.cu"))
-                            if names[dom] == "exp" and prec == mix.MIX_FP32 else None),
+                "traffic": (profiled_traffic(f"k_ace_{mix.PREC_NAMES[prec]}_{wl.name}.md",
+                                             ("k_ace.cuh", "k_ace_f32.cu", "k_ace_tc.cuh", "tc.cuh"))
+                            if names[dom] == "exp" and prec != mix.MIX_FP64 else None),
                 "algorithmic_flops_per_launch": fl,
-                "peak_source": f"measured FMA microbenchmark ({mix.PREC_NAMES[prec]}), mix_fma_peak"}
+                "peak_source": "measured FMA microbenchmark "
+                               f"({'fp64' if prec == mix.MIX_FP64 else 'fp32'}), mix_fma_peak (of measured)"}
+        if names[dom] == "exp" and prec in (mix.MIX_BF16, mix.MIX_BF16_SPLIT):
+            # the part of the kernel on the tensor cores: V = Z W per l-triple,
+            # 2 d3 n^2 n flops per atom (three products with the split)
+            tfl = main["hinfo"]["tc_flops_per_atom"] * main["nstat"]["n_exp"]
+            tpk = json.load(open(peaks_file))["bf16_tflops"] * 1e12 if os.path.exists(peaks_file) else 1.9e15
+            roof["tensor_part"] = {"flops_per_launch": tfl, "achieved": tfl / (phase_ms[dom] * 1e-3) / 1e12,
+                                   "peak": tpk / 1e12, "unit": "TFLOP/s",
+                                   "frac": tfl / (phase_ms[dom] * 1e-3) / tpk,
+                                   "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, of measured)"}
     else:
         byts = kern[names[dom]]["algorithmic_bytes"]
         ach = byts / (phase_ms[dom] * 1e-3) / 1e9
@@ -539,6 +580,9 @@ def ours(args):
         "errors_reference": "oracle (FP64 CPU) at the starting positions" if "errors_vs_oracle" in main
                             else "GPU FP64 path at the starting positions",
         mix.PREC_NAMES[other["precision"]] + "_path": {k: v for k, v in other.items() if k != "precision"},
+        "precisions": {mix.PREC_NAMES[p]: dict(v, force_err_eV_per_A=errs.get(mix.PREC_NAMES[p], {}).get(
+            "force_max_abs_eV_per_A"), within_gate=bool(errs.get(mix.PREC_NAMES[p], {}).get(
+                "force_max_abs_eV_per_A", 1.0) <= GATE)) for p, v in main["others"].items()},
         "roofline": roof,
         "kernels": kern,
         "mixing": main["mixing"],

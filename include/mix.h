@@ -55,9 +55,20 @@ extern "C" {
 #define MIX_EBOX (-8)       /* an atom left the box in a non-periodic dimension */
 
 /* arithmetic of the potential evaluations (integration, lambda and force
- * accumulation are always float64) */
+ * accumulation are always float64).  The bf16 modes are the float path with
+ * the dense contraction of the nu = 3 product basis with the readout
+ * coefficients (linear ACE readout, Sec. 2.1, Table 1), V = Z W with Z the
+ * Gaunt-coupled product of two densities and W the coefficients, on the tensor
+ * cores: bf16 operands, float accumulation; the site energy E = sum A3 V and
+ * the adjoint omega3 = V follow from it, and each atom's energy is summed with
+ * a compensation term.  MIX_BF16_SPLIT splits both operands into bf16 hi and
+ * lo parts (x = hi + lo) and accumulates Zhi Whi + Zlo Whi + Zhi Wlo, about
+ * 16 significant bits per product: the fallback when plain bf16 exceeds an
+ * accuracy target.  A potential without nu = 3 terms runs the float path. */
 #define MIX_FP64 0
 #define MIX_FP32 1
+#define MIX_BF16 2
+#define MIX_BF16_SPLIT 3
 
 /* region shapes (Sec. 4.4: core radius and blend width around a defect) */
 #define MIX_REGION_SPHERE 0    /* distance to a centre point */
@@ -128,7 +139,7 @@ typedef struct {
 } mix_spline;
 
 typedef struct {
-    int precision;          /* MIX_FP64 or MIX_FP32 */
+    int precision;          /* MIX_FP64, MIX_FP32, MIX_BF16 or MIX_BF16_SPLIT */
     double skin;            /* neighbour-list skin, Angstrom (> 0); lists rebuild
                                when an atom moved more than skin / 2 */
     int blend;              /* MIX_BLEND_* */
@@ -162,7 +173,13 @@ typedef struct {
     int status_bits;        /* raw device status word */
 } mix_stats;
 
-/* Create a context on the current CUDA device.  `cuda_stream` is a cudaStream_t
+/* Create a context on the current CUDA device: one force-mixing simulation
+ * (Sec. 4, Alg. 4) of a system with an expensive and a cheap potential
+ * (Sec. 2.1: a linear atomic cluster expansion and a 2+3-body spline of the
+ * UF3 family), each evaluated on its own set plus a one-cutoff buffer (Sec.
+ * 4.5); the regions that weight them are set by mix_set_regions (Sec. 4.4) or
+ * mix_set_seeds (Alg. 1-2).  The potentials' coefficients are copied (host
+ * arrays may be freed after the call).  `cuda_stream` is a cudaStream_t
  * (NULL = legacy default stream).  Errors: MIX_EINVAL for unsupported sizes or
  * a box too small for the cutoff; MIX_ECUDA. */
 int mix_init(const mix_system* sys, const mix_ace* expensive, const mix_spline* cheap,
@@ -290,6 +307,9 @@ typedef struct {
     int gather_grid;        /* CTAs of the gather kernel */
     int build_grid;         /* CTAs of the neighbour-list kernel */
     int buffer_grid;        /* CTAs of the buffer-scan kernel */
+    int exp_tensor_cores;   /* 1: the nu = 3 readout runs on the tensor cores (bf16 modes) */
+    double tc_flops_per_atom;  /* algorithmic flops of that readout, V = Z W: sum over
+                                  l-triples of 2 (2 l3 + 1) n^3 per evaluated atom */
 } mix_info;
 
 int mix_get_info(const mix_ctx* ctx, mix_info* info);
@@ -309,6 +329,17 @@ int mix_get_profile(mix_ctx* ctx, double* total_ms /*[MIX_PHASES] nullable*/, do
  * CUDA events on `cuda_stream`.  Used as the arithmetic roofline.  Allocates
  * and frees a small device buffer (one value per block) for its result sink. */
 int mix_fma_peak(int precision, void* cuda_stream, double* flops_per_s);
+
+/* Check of the tensor-core building block of the bf16 readout (no counterpart
+ * in the paper; used by the tests): D = A B^T with A [128][k] and B [n][k] bf16
+ * (raw 16-bit patterns, row-major) and D [128][n] float32, all caller-owned
+ * device memory, formed by one CTA with the shared-memory operand layout,
+ * tcgen05.mma instructions and TMEM read-back of the readout kernel.
+ * 16 <= n <= 256 and 16 <= k <= 160, both multiples of 16 (else MIX_EINVAL).
+ * *status_dev (device int, caller-cleared) gets bit 0 set, and D is NaN, if the
+ * bounded wait for the MMAs gave up.  Asynchronous on cuda_stream. */
+int mix_tc_selftest(const void* a_dev, const void* b_dev, int n, int k, float* d_dev, int* status_dev,
+                    void* cuda_stream);
 
 /* ------------------------------------------------------------------------ */
 /* Launch-shape autotuning and batches of trajectories.  The paper has no      */
@@ -468,7 +499,9 @@ int mix_admission_plan(const size_t* need, const int64_t* atoms, int n_queued, s
 /* [N][cap] int32.  The box follows mix_system's rules.  Limits: N <=         */
 /* MIX_NOALLOC_MAX_ATOMS, cells <= MIX_NOALLOC_MAX_CELLS, 1 <= cap <= 256;     */
 /* anything larger returns MIX_EINVAL before touching the GPU.  A row longer  */
-/* than cap returns MIX_EOVERFLOW (rows are then truncated).                  */
+/* than cap returns MIX_EOVERFLOW (rows are then truncated).  A non-finite    */
+/* coordinate returns MIX_ENUMERIC, one outside a non-periodic dimension of   */
+/* the box MIX_EBOX (the lists are then meaningless).                         */
 /*                                                                            */
 /* The call enqueues its work on cuda_stream and waits for it.  The first     */
 /* call on a device looks up the array's device address (cudaGetSymbolAddress */

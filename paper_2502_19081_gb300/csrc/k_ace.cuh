@@ -38,6 +38,7 @@
 #pragma once
 
 #include "mix_launch.h"
+#include "tc.cuh"
 
 namespace mixd {
 
@@ -219,15 +220,16 @@ __host__ __device__ constexpr int ace_a16(int b) { return (b + 15) & ~15; }
 // omega2, and the omega1 partial sums of the lane units) are never live
 // together and share one area.
 struct AceLay {
-    int tile;                            // bytes of one tile buffer
+    int tile;                            // bytes of one tile buffer (nbuf buffers)
     int o_w, wb;                         // first warp region, bytes per warp region
     int o_u, o_at, o_om, o_scr, o_slot;  // offsets inside a warp region
     int o_p1;                            // omega1 partials, inside the scratch area
     int total;
-    __host__ __device__ AceLay(int tile_max, int cap, int n, int qb, int L, int NP, int ts, int warps) {
+    __host__ __device__ AceLay(int tile_max, int cap, int n, int qb, int L, int NP, int ts, int warps,
+                               int nbuf = 2) {
         const int nlm = (L + 1) * (L + 1), D = 2 * L + 1;
         tile = ace_a16(tile_max);
-        o_w = 2 * tile;
+        o_w = nbuf * tile;
         o_u = 0;                                  // [cap][4]: unit vector, r
         o_at = o_u + ace_a16(4 * cap * ts);       // A[lm][q]
         o_om = o_at + ace_a16(nlm * NP * ts);     // omega[lm][q]
@@ -294,10 +296,17 @@ __device__ __forceinline__ T warp_reduce_scatter16(T (&v)[16], int lane) {
 // and, for distinct l's only (omega2 needs it after the pass), stores U.
 // All three l's equal: U is not formed (no adjoint needs it) and the energy is
 // taken as sum A3 (W^T Z), the same sum reordered.
-template <typename T, int NP, int QB>
+//
+// TCM != 0 (float only; the tensor-core readout): omega3 and the energy are
+// not formed here.  Z goes, rounded to bf16 (TCM == 2: also its remainder, the
+// lo part), into this atom's rows of the MMA operand tile (row m3, column
+// q1 n + q2 of the K-major layout of tc.cuh), from which the tensor cores form
+// V = Z W (omega3 = mult3 V, E = sum A3 V) after the pass.
+template <typename T, int NP, int QB, int TCM = 0>
 __device__ __forceinline__ void nu3_units(const AceTileHdr& h, const T* W, const GEnt<T>* ge, const int* g3o,
                                           const T* A1, const T* A2, const T* A3, int n, int lane, T* U1, T* P1,
-                                          T* o3, T mult3, T& ep) {
+                                          T* o3, T mult3, T& ep, unsigned char* zhi = nullptr,
+                                          unsigned char* zlo = nullptr, int zsbo = 0) {
     constexpr int nqb = NP / QB;
     const int units = n * nqb;
     const int d3 = 2 * h.l3 + 1;
@@ -377,13 +386,30 @@ __device__ __forceinline__ void nu3_units(const AceTileHdr& h, const T* W, const
             }
             if (withu) {
                 if (cur >= 0 && uv) P1[cur * units + u] += c1;
+                if constexpr (TCM == 0) {
 #pragma unroll
-                for (int r = 0; r < QB; ++r) ep += uo[r] * z[r];
+                    for (int r = 0; r < QB; ++r) ep += uo[r] * z[r];
+                }
                 if (keepu && uv) {
 #pragma unroll
                     for (int r = 0; r < QB; ++r) U1[(m3 * n + q1) * NP + q2 + r] = uo[r];
                 }
             }
+            if constexpr (TCM != 0) {
+                if (uv) {
+#pragma unroll
+                    for (int r = 0; r < QB; ++r) {
+                        if (q2 + r < n) {
+                            const int o = tc_off(m3, q1 * n + q2 + r, TC_LBO_A, zsbo);
+                            const __nv_bfloat16 hi = __float2bfloat16_rn((float)z[r]);
+                            *reinterpret_cast<__nv_bfloat16*>(zhi + o) = hi;
+                            if constexpr (TCM == 2)
+                                *reinterpret_cast<__nv_bfloat16*>(zlo + o) =
+                                    __float2bfloat16_rn((float)z[r] - __bfloat162float(hi));
+                        }
+                    }
+                }
+            } else {
             // omega3 row m3
             T pv[16];
 #pragma unroll
@@ -400,14 +426,18 @@ __device__ __forceinline__ void nu3_units(const AceTileHdr& h, const T* W, const
                 o3[m3 * NP + q3o] += mult3 * s3;
                 if (!withu) ep += A3[m3 * NP + q3o] * s3;
             }
+            }
         }
     }
 }
 
 // One l-triple for this warp's atom, from the tile in shared memory.
-template <typename T, int NP>
+// PART 1: the unit pass; PART 2: omega1 from the unit partials and omega2;
+// PART 3: both.
+template <typename T, int NP, int TCM = 0, int PART = 3>
 __device__ __forceinline__ void nu3_tile(const unsigned char* tile, const AceTab<T>& tab, const T* At, T* om,
-                                         T* U1, T* P1, int lane, T& ep) {
+                                         T* U1, T* P1, int lane, T& ep, unsigned char* zhi = nullptr,
+                                         unsigned char* zlo = nullptr, int zsbo = 0) {
     constexpr int QM = 4;     // largest power-of-two q2 block of a lane unit
     const AceTileHdr h = *reinterpret_cast<const AceTileHdr*>(tile);
     const T* W = reinterpret_cast<const T*>(tile + sizeof(AceTileHdr));
@@ -425,19 +455,25 @@ __device__ __forceinline__ void nu3_tile(const unsigned char* tile, const AceTab
     const T* A3 = At + h.l3 * h.l3 * NP;
     T* o3 = om + h.l3 * h.l3 * NP;
     const int qb = tab.qb;
+    if constexpr ((PART & 1) != 0) {
     bool done = false;
     if constexpr (sizeof(T) == 4 && NP == 12) {
         // n = 11 or 12: 6-wide blocks keep the units within one warp pass
         if (qb == 6) {
-            nu3_units<T, NP, 6>(h, W, ge, g3o, A1, A2, A3, n, lane, U1, P1, o3, mult3, ep);
+            nu3_units<T, NP, 6, TCM>(h, W, ge, g3o, A1, A2, A3, n, lane, U1, P1, o3, mult3, ep, zhi, zlo, zsbo);
             done = true;
         }
     }
     if (!done) {
-        if (qb == QM) nu3_units<T, NP, QM>(h, W, ge, g3o, A1, A2, A3, n, lane, U1, P1, o3, mult3, ep);
-        else nu3_units<T, NP, QM / 2>(h, W, ge, g3o, A1, A2, A3, n, lane, U1, P1, o3, mult3, ep);
+        if (qb == QM)
+            nu3_units<T, NP, QM, TCM>(h, W, ge, g3o, A1, A2, A3, n, lane, U1, P1, o3, mult3, ep, zhi, zlo, zsbo);
+        else
+            nu3_units<T, NP, QM / 2, TCM>(h, W, ge, g3o, A1, A2, A3, n, lane, U1, P1, o3, mult3, ep, zhi, zlo,
+                                          zsbo);
     }
     __syncwarp();
+    }
+    if constexpr ((PART & 2) == 0) return;
     // omega1 (equal to omega3 when all three l's coincide): sum the unit
     // partials of each (m1, q1) and clear them for the next triple
     if (h.mode != 3) {
@@ -492,11 +528,30 @@ __device__ __forceinline__ void nu3_tile(const unsigned char* tile, const AceTab
     __syncwarp();
 }
 
-// One group of atoms a0 .. a0 + ACE_GROUP - 1 of the system's expensive list
-// (those below nexp), warp w on atom a0 + w; every thread of the CTA calls it.
-template <typename T, int L, int NP>
-__device__ __forceinline__ void ace_group(const Dev& d, const AceTab<T>& tab, int a0, int nexp, unsigned char* smem) {
-    constexpr int WN = ace_warps<T>();
+// State of the tensor-core readout of one thread (TCM != 0).
+struct TcState {
+    unsigned char* zhi;   // A operand: Z rows of the CTA's atoms (bf16)
+    unsigned char* zlo;   // their remainders (hi/lo split) or null
+    uint32_t tmem;        // accumulator V (128 lanes x 16 columns f32)
+    uint32_t bar;         // mbarrier the MMAs of a triple arrive on
+    uint32_t phase;       // parity of its next completion
+    int kp, sbo;          // K (n^2 padded to 16), A row-group stride in bytes
+    int nbuf;             // tile buffers: 2 (the next tile streams in during this one) or 1
+    int abort;            // a completion wait ran out: no further waits
+};
+
+// polls of an mbarrier before a readout MMA is declared lost (status bit
+// ST_TC_TIMEOUT, reported as MIX_ETIMEOUT)
+constexpr int TC_WAIT_POLLS = 1 << 20;
+
+// One group of atoms a0 .. a0 + WN - 1 of the system's expensive list (those
+// below nexp), warp w on atom a0 + w; every thread of the CTA calls it.
+// TCM != 0 (float only): the nu = 3 readout V = Z W runs on the tensor cores
+// for the CTA's TC_ACE_WARPS atoms at once (16 rows (atom, m3) per atom).
+template <typename T, int L, int NP, int TCM = 0>
+__device__ __forceinline__ void ace_group(const Dev& d, const AceTab<T>& tab, int a0, int nexp, unsigned char* smem,
+                                          TcState* tc = nullptr) {
+    constexpr int WN = TCM != 0 ? TC_ACE_WARPS : ace_warps<T>();
     constexpr int NLM = (L + 1) * (L + 1);
     constexpr int D = 2 * L + 1;
     constexpr int NQ4 = NP / 4;
@@ -505,7 +560,7 @@ __device__ __forceinline__ void ace_group(const Dev& d, const AceTab<T>& tab, in
     using V = typename Vec4<T>::type;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int n = tab.n, cap = d.cap, ntau = tab.ntau;
-    const AceLay lay(tab.tile_max, cap, n, tab.qb, L, NP, (int)sizeof(T), WN);
+    const AceLay lay(tab.tile_max, cap, n, tab.qb, L, NP, (int)sizeof(T), WN, TCM != 0 ? tc->nbuf : 2);
     // the first tile lands while the warps run steps 1-3
     if (ntau > 0) tile_fetch(tab.tiles, tab.tile_off, 0, smem);
 
@@ -655,11 +710,82 @@ __device__ __forceinline__ void ace_group(const Dev& d, const AceTab<T>& tab, in
     }
 
     // 4. nu = 3, tile by tile (every thread takes part in the copies and barriers)
-    for (int t = 0; t < ntau; ++t) {
-        cp_async_wait_all();
-        __syncthreads();   // tile t visible; every warp is done with the other buffer
-        if (t + 1 < ntau) tile_fetch(tab.tiles, tab.tile_off, t + 1, smem + ((t + 1) & 1) * lay.tile);
-        if (has) nu3_tile<T, NP>(smem + (t & 1) * lay.tile, tab, At, om, U1, P1, lane, ep);
+    if constexpr (TCM == 0) {
+        for (int t = 0; t < ntau; ++t) {
+            cp_async_wait_all();
+            __syncthreads();   // tile t visible; every warp is done with the other buffer
+            if (t + 1 < ntau) tile_fetch(tab.tiles, tab.tile_off, t + 1, smem + ((t + 1) & 1) * lay.tile);
+            if (has) nu3_tile<T, NP>(smem + (t & 1) * lay.tile, tab, At, om, U1, P1, lane, ep);
+        }
+    } else {
+        // Per triple: the warps write Z rows (and form U, omega1, omega2 as in
+        // the CUDA-core pass); one thread issues V = Z W over K = kp (one MMA
+        // per 16 columns, three with the hi/lo split: Zhi Whi + Zlo Whi +
+        // Zhi Wlo); the warps take omega1 and omega2 meanwhile, then wait for
+        // the MMAs and read their own rows of V: omega3 += mult3 V,
+        // E += sum A3 V (lane-local, summed with the atom's other terms).
+        const int slot_w = 2 * (warp & 3) + (warp >> 2);   // this warp's 16 rows of the MMA tile
+        unsigned char* zh = tc->zhi + 2 * slot_w * tc->sbo;
+        unsigned char* zl = TCM == 2 ? tc->zlo + 2 * slot_w * tc->sbo : nullptr;
+        const bool own = (lane >> 4) == (warp >> 2);      // TMEM lane 32 (warp % 4) + lane is this atom's row
+        const int m3r = lane & 15;
+        const uint32_t idesc = tc_idesc_bf16(128, 16);
+        const int kp = tc->kp, sbo_b = (kp / 8) * TC_LBO_B;
+        for (int t = 0; t < ntau; ++t) {
+            unsigned char* tile = smem + (tc->nbuf == 2 ? (t & 1) : 0) * lay.tile;
+            if (tc->nbuf == 1 && t > 0) {
+                __syncthreads();   // every warp is done with tile t - 1
+                tile_fetch(tab.tiles, tab.tile_off, t, tile);
+            }
+            cp_async_wait_all();
+            fence_async_smem();    // the coefficient operand this thread copied, visible to the tensor cores
+            __syncthreads();       // tile t visible; every warp is done with the other buffer and with V of t - 1
+            if (tc->nbuf == 2 && t + 1 < ntau)
+                tile_fetch(tab.tiles, tab.tile_off, t + 1, smem + ((t + 1) & 1) * lay.tile);
+            const AceTileHdr h = *reinterpret_cast<const AceTileHdr*>(tile);
+            if (has) nu3_tile<T, NP, TCM, 1>(tile, tab, At, om, U1, P1, lane, ep, zh, zl, tc->sbo);
+            fence_async_smem();    // this thread's Z rows, visible to the tensor cores
+            __syncthreads();
+            if (tid == 0 && !tc->abort) {
+                tc_fence_after();
+                const unsigned char* wb = tile + h.o_wb;
+                for (int s = 0; s < kp / 16; ++s) {
+                    const uint64_t ah = tc_desc(smem_u32(tc->zhi + s * 2 * TC_LBO_A), TC_LBO_A, tc->sbo);
+                    const uint64_t bh = tc_desc(smem_u32(wb + s * 2 * TC_LBO_B), TC_LBO_B, sbo_b);
+                    tc_mma_bf16(tc->tmem, ah, bh, idesc, s > 0 ? 1u : 0u);
+                    if constexpr (TCM == 2) {
+                        const uint64_t al = tc_desc(smem_u32(tc->zlo + s * 2 * TC_LBO_A), TC_LBO_A, tc->sbo);
+                        const uint64_t bl = tc_desc(smem_u32(wb + 2 * sbo_b + s * 2 * TC_LBO_B), TC_LBO_B, sbo_b);
+                        tc_mma_bf16(tc->tmem, al, bh, idesc, 1u);
+                        tc_mma_bf16(tc->tmem, ah, bl, idesc, 1u);
+                    }
+                }
+                tc_commit(tc->bar);
+            }
+            if (has) nu3_tile<T, NP, TCM, 2>(tile, tab, At, om, U1, P1, lane, ep, zh, zl, tc->sbo);
+            if (!tc->abort && !mbar_wait(tc->bar, tc->phase, TC_WAIT_POLLS)) {
+                tc->abort = 1;
+                set_status(d.status, ST_TC_TIMEOUT);
+            }
+            tc->phase ^= 1u;
+            tc_fence_after();
+            float v[16];
+            tmem_ld16(tc->tmem + ((uint32_t)(32 * (warp & 3)) << 16), v);
+            if (has && own && m3r < 2 * h.l3 + 1 && !tc->abort) {
+                const T mult3 = h.mode == 3 ? T(3) : (h.mode == 2 ? T(2) : T(1));
+                T* o3 = om + (h.l3 * h.l3 + m3r) * NP;
+                const T* a3 = At + (h.l3 * h.l3 + m3r) * NP;
+#pragma unroll
+                for (int q = 0; q < NP; ++q) {
+                    if (q < n) {
+                        o3[q] += mult3 * (T)v[q];
+                        ep += a3[q] * (T)v[q];
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+        }
     }
     if (ntau > 0) __syncthreads();   // both buffers free for the next group's first tile
 

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "mix_launch.h"
+#include "tc.cuh"
 
 using namespace mixd;
 
@@ -114,14 +115,32 @@ std::vector<T> conv(const std::vector<double>& v) {
     return std::vector<T>(v.begin(), v.end());
 }
 
+// bf16 bit pattern of a float, rounded to nearest (ties to even)
+uint16_t bf16_bits(float f) {
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+double bf16_value(uint16_t b) {
+    const uint32_t u = (uint32_t)b << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return (double)f;
+}
+
 // The nu = 3 tables as one tile per l-triple (layout in AceTileHdr): W3 holds
 // the symmetrised coefficients [t][q1 q2][q3], tau the triples (l1, l2, l3,
 // first offset row), goff/gidx/gval the Gaunt entries in three orderings.
+// tcm (tensor-core readout): 1 appends W as the bf16 B operand, 2 also its
+// bf16 remainders; tiles are then 128-byte multiples.
 template <typename T>
 std::vector<unsigned char> ace_tiles(int n, int np, const std::vector<int>& tau, const std::vector<int>& tmode,
                                      const std::vector<int>& goff, const std::vector<int>& gidx,
                                      const std::vector<double>& gval, const std::vector<double>& W3,
-                                     std::vector<int>& off, int& tile_max) {
+                                     std::vector<int>& off, int& tile_max, int tcm = 0) {
+    const int kp = (n * n + 15) & ~15;
+    const int sbo_b = (kp / 8) * TC_LBO_B;   // 8 rows of B; two such groups hold the 16 q3 rows
     const int ntau = (int)(tau.size() / 4);
     std::vector<unsigned char> out;
     off.assign(ntau + 1, 0);
@@ -141,8 +160,14 @@ std::vector<unsigned char> ace_tiles(int n, int np, const std::vector<int>& tau,
         h.o_go = (int)o;
         o += (size_t)rows * sizeof(int);
         o = (o + 15) & ~(size_t)15;
+        h.o_wb = 0;
+        if (tcm) {
+            o = (o + 127) & ~(size_t)127;
+            h.o_wb = (int)o;
+            o += (size_t)(tcm == 2 ? 2 : 1) * 2 * sbo_b;
+            o = (o + 127) & ~(size_t)127;
+        }
         h.bytes = (int)o;
-        h.pad = 0;
         std::vector<unsigned char> tile(o, 0);
         std::memcpy(tile.data(), &h, sizeof h);
         T* W = reinterpret_cast<T*>(tile.data() + sizeof(AceTileHdr));
@@ -158,6 +183,20 @@ std::vector<unsigned char> ace_tiles(int n, int np, const std::vector<int>& tau,
         for (int r = 0; r < rows; ++r) {
             const int v = goff[gb + r] - e0;
             std::memcpy(tile.data() + h.o_go + (size_t)r * sizeof(int), &v, sizeof v);
+        }
+        if (tcm) {
+            // B[q3][k] = W[k][q3], k = q1 n + q2 (zero padding stays zero)
+            for (int k = 0; k < n * n; ++k)
+                for (int q3 = 0; q3 < n; ++q3) {
+                    const double w = W3[((size_t)t * n * n + k) * n + q3];
+                    const uint16_t hi = bf16_bits((float)w);
+                    const size_t at = (size_t)h.o_wb + (size_t)tc_off(q3, k, TC_LBO_B, sbo_b);
+                    std::memcpy(tile.data() + at, &hi, 2);
+                    if (tcm == 2) {
+                        const uint16_t lo = bf16_bits((float)(w - bf16_value(hi)));
+                        std::memcpy(tile.data() + at + 2 * sbo_b, &lo, 2);
+                    }
+                }
         }
         off[t] = (int)out.size();
         out.insert(out.end(), tile.begin(), tile.end());
@@ -202,6 +241,8 @@ struct mix_ctx {
         o_seed, o_core, o_zsum;
     size_t ace_smem, spl_smem;
     int ace_grid, spl_grid;
+    int ace_tcm;                      // 0: CUDA-core nu = 3; 1, 2: tensor-core readout (bf16, bf16 hi/lo)
+    int ace_nbuf;                     // tile buffers of the tensor-core kernel
     int spl_lpa;                      // lanes per atom of the cheap kernel (32, 16 or 8)
     int ace_grid_max, spl_grid_max;   // resident CTAs at full occupancy
     int64_t gaunt_nnz, tau_d3_sum, basis_size;
@@ -449,7 +490,8 @@ int build_tables(mix_ctx* c, const mix_ace* a, const mix_spline* sp) {
     } else {
         c->o_c1 = A.put(conv<float>(c1));
         c->o_S2 = A.put(conv<float>(S2));
-        c->o_tiles = A.put(ace_tiles<float>(n, np, tau, tmode, goff, gidx, gval, W3, toff, c->tile_max));
+        c->ace_tcm = c->ntau == 0 ? 0 : (c->precision == MIX_BF16 ? 1 : (c->precision == MIX_BF16_SPLIT ? 2 : 0));
+        c->o_tiles = A.put(ace_tiles<float>(n, np, tau, tmode, goff, gidx, gval, W3, toff, c->tile_max, c->ace_tcm));
         c->o_ylmk = A.put(conv<float>(ylmk));
         c->o_pair = A.put(conv<float>(pair));
         c->o_sc2 = A.put(conv<float>(sc2));
@@ -565,7 +607,8 @@ void enqueue_evaluation(mix_ctx* c, cudaStream_t s, int integrate, double dt, in
     cudaStreamWaitEvent(c->aux, c->ev_fork, 0);
     launch_spline(c->dev, st, c->precision, c->spl_lpa, c->spl_smem, c->spl_grid, c->aux);
     cudaEventRecord(c->ev_join, c->aux);
-    launch_ace(c->dev, at, c->precision, c->L, c->ace_smem, c->ace_grid, s);
+    if (c->ace_tcm) launch_ace_tc(c->dev, at, c->ace_tcm, c->L, c->ace_smem, c->ace_grid, c->ace_nbuf, s);
+    else launch_ace(c->dev, at, c->precision, c->L, c->ace_smem, c->ace_grid, s);
     if (prof) cudaEventRecordWithFlags(c->ev[4], s, ef);
     cudaStreamWaitEvent(s, c->ev_join, 0);
     if (prof) cudaEventRecordWithFlags(c->ev[5], s, ef);
@@ -675,6 +718,7 @@ int read_status(mix_ctx* c) {
     if (st & ST_NONFINITE) return fail(c, MIX_ENUMERIC, "non-finite position or force");
     if (st & ST_OUT_OF_BOX) return fail(c, MIX_EBOX, "an atom left the box in a non-periodic dimension");
     if (st & ST_REV_MISSING) return fail(c, MIX_EINVAL, "asymmetric neighbour list");
+    if (st & ST_TC_TIMEOUT) return fail(c, MIX_ETIMEOUT, "a wait for the tensor-core readout gave up");
     return MIX_OK;
 }
 
@@ -712,7 +756,9 @@ int mix_init(const mix_system* sys, const mix_ace* a, const mix_spline* sp, cons
         for (int q = 0; q < 8; ++q)
             for (int r = 0; r < 8; ++r)
                 if (sp->c3[(p * 8 + q) * 8 + r] != sp->c3[(q * 8 + p) * 8 + r]) return bad("c3 not symmetric");
-    if (opt->precision != MIX_FP64 && opt->precision != MIX_FP32) return bad("precision");
+    if (opt->precision != MIX_FP64 && opt->precision != MIX_FP32 && opt->precision != MIX_BF16 &&
+        opt->precision != MIX_BF16_SPLIT)
+        return bad("precision");
     if (!(opt->skin > 0)) return bad("skin");
     if (opt->blend != MIX_BLEND_LINEAR && opt->blend != MIX_BLEND_CUBIC) return bad("blend");
     c->sys = *sys;
@@ -744,6 +790,8 @@ int mix_init(const mix_system* sys, const mix_ace* a, const mix_spline* sp, cons
         d.box.L[k] = sys->box_len[k];
         d.box.invL[k] = 1.0 / sys->box_len[k];
         d.box.per[k] = sys->periodic[k] ? 1 : 0;
+        // checked as a double before it becomes an int (at most 1023 cells a dimension)
+        if (!(sys->box_len[k] / c->rlist < 1024.0)) return bad("more than 1023 cells along one dimension");
         int ncd = (int)std::floor(sys->box_len[k] / c->rlist);
         if (d.box.per[k]) {
             if (sys->box_lo[k] != 0.0) return bad("periodic box_lo must be 0");
@@ -804,10 +852,14 @@ int mix_init(const mix_system* sys, const mix_ace* a, const mix_spline* sp, cons
         return st;
     }
     layout(c);
-    cudaError_t e = ace_configure(c->precision, c->L, c->n, c->cap, c->tile_max, c->qb, &c->ace_smem, &c->ace_grid);
+    cudaError_t e = c->ace_tcm
+                        ? ace_tc_configure(c->ace_tcm, c->L, c->n, c->cap, c->tile_max, c->qb, &c->ace_smem,
+                                           &c->ace_grid, &c->ace_nbuf)
+                        : ace_configure(c->precision, c->L, c->n, c->cap, c->tile_max, c->qb, &c->ace_smem,
+                                        &c->ace_grid);
     if (e != cudaSuccess) {
         delete c;
-        return MIX_ECUDA;
+        return e == cudaErrorInvalidValue ? MIX_EINVAL : MIX_ECUDA;
     }
     // Fewer lanes per cheap atom where atoms have few neighbours: in a periodic
     // bulk whose mean count inside the 3-body cutoff is at most a third of what
@@ -1146,7 +1198,7 @@ int mix_get_info(const mix_ctx* c, mix_info* info) {
     info->workspace_bytes = c->ws_bytes;
     info->exp_smem_bytes = c->ace_smem;
     info->exp_grid = c->ace_grid;
-    info->exp_threads = 32 * (c->precision == MIX_FP64 ? ace_warps<double>() : ace_warps<float>());
+    info->exp_threads = 32 * (c->ace_tcm ? TC_ACE_WARPS : (c->precision == MIX_FP64 ? ace_warps<double>() : ace_warps<float>()));
     info->cheap_smem_bytes = c->spl_smem;
     info->cheap_grid = c->spl_grid;
     info->launches_per_evaluation = evals_launches(c);
@@ -1154,6 +1206,8 @@ int mix_get_info(const mix_ctx* c, mix_info* info) {
     info->gather_grid = c->dev.grid_gather;
     info->build_grid = c->dev.grid_build;
     info->buffer_grid = c->dev.grid_buffer;
+    info->exp_tensor_cores = c->ace_tcm ? 1 : 0;
+    info->tc_flops_per_atom = c->ace_tcm ? 2.0 * (double)c->tau_d3_sum * c->n * c->n * c->n : 0.0;
     return MIX_OK;
 }
 
@@ -1192,6 +1246,15 @@ int mix_get_profile(mix_ctx* c, double* total_ms, double* last_ms, int64_t* eval
 int mix_fma_peak(int precision, void* stream, double* flops) {
     if (!flops || (precision != MIX_FP64 && precision != MIX_FP32)) return MIX_EINVAL;
     return fma_peak(precision, (cudaStream_t)stream, flops);
+}
+
+int mix_tc_selftest(const void* a_dev, const void* b_dev, int n, int k, float* d_dev, int* status_dev,
+                    void* stream) {
+    if (!a_dev || !b_dev || !d_dev || !status_dev) return MIX_EINVAL;
+    if (n < 16 || n > 256 || n % 16 || k < 16 || k > 160 || k % 16) return MIX_EINVAL;
+    const cudaError_t e = tc_selftest(static_cast<const uint16_t*>(a_dev), static_cast<const uint16_t*>(b_dev), n,
+                                      k, d_dev, status_dev, (cudaStream_t)stream);
+    return e == cudaSuccess ? MIX_OK : MIX_ECUDA;
 }
 
 const char* mix_strerror(int code) {
@@ -1408,7 +1471,7 @@ int batch_graph(mix_batch* b, int integrate, double dt, cudaGraph_t* graph, cuda
 bool fused_eligible(const mix_batch* b) {
     if (!b->want_fused || b->m.empty()) return false;
     for (const mix_ctx* c : b->m)
-        if (!c->bound || c->precision != b->m[0]->precision || c->seedrule.mode != 0) return false;
+        if (!c->bound || c->precision != b->m[0]->precision || c->seedrule.mode != 0 || c->ace_tcm) return false;
     return true;
 }
 

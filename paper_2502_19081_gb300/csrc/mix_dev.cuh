@@ -17,6 +17,7 @@ enum StatusBits : int {
     ST_NB3_OVERFLOW = 4,     // more than NB3MAX three-body neighbours
     ST_NONFINITE = 8,        // non-finite position or force
     ST_OUT_OF_BOX = 16,      // atom outside a non-periodic dimension
+    ST_TC_TIMEOUT = 32,      // a bounded wait for tensor-core MMAs gave up
 };
 enum StatusWord : int {
     SW_STATUS = 0,
@@ -230,6 +231,9 @@ template <typename T>
 __host__ __device__ constexpr int ace_min_ctas() {
     return sizeof(T) == 4 ? 6 : 2;
 }
+// The tensor-core readout (float, bf16 operands) takes groups of 8 atoms, a
+// warp each: 8 x 16 rows (atom, m3) fill the M = 128 rows of one MMA tile.
+constexpr int TC_ACE_WARPS = 8;
 
 // One Gaunt coefficient with the packed m indices of its two other factors
 // (ma | mb << 8, 0-based), loaded as one 8- or 16-byte word.
@@ -247,10 +251,14 @@ struct __align__(sizeof(T) == 4 ? 8 : 16) GEnt {
 //   their offset rows (per ordering 2l+2 ints: the first entry of each m, then
 //     the end; entry indices relative to o_ge) at o_go.
 // mode: 0 l's distinct, 1 l1 == l2, 2 l2 == l3, 3 all equal (W symmetrised over
-// the matching n indices).
+// the matching n indices).  Tiles of the tensor-core readout (bf16 modes) also
+// hold, at o_wb (128-byte aligned; 0 otherwise), W as the MMA's B operand: 16
+// rows (q3, zero beyond n) by kp columns (q1 n + q2, zero beyond n^2) of bf16
+// in the K-major core-matrix layout (tc.cuh, K stride TC_LBO_B), followed for
+// the hi/lo split by the same layout of the remainders W - bf16(W).
 struct AceTileHdr {
     int l1, l2, l3, mode;
-    int o_ge, o_go, bytes, pad;
+    int o_ge, o_go, bytes, o_wb;
 };
 
 template <typename T>

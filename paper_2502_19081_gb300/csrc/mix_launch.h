@@ -21,6 +21,17 @@ cudaError_t ace_configure_f64(int L, int n, int cap, int tile_max, int qb, size_
 void launch_ace_f32(const Dev& d, const void* tab, int L, size_t smem, int grid, cudaStream_t s);
 void launch_ace_f64(const Dev& d, const void* tab, int L, size_t smem, int grid, cudaStream_t s);
 
+// expensive potential with the tensor-core readout (k_ace_tc.cu; float tables
+// with the bf16 operand sections): tcm 1 bf16, 2 bf16 hi/lo.  *nbuf: tile
+// buffers that fit shared memory (2, else 1); cudaErrorInvalidValue when even
+// one does not fit
+cudaError_t ace_tc_configure(int tcm, int L, int n, int cap, int tile_max, int qb, size_t* smem, int* grid,
+                             int* nbuf);
+void launch_ace_tc(const Dev& d, const void* tab, int tcm, int L, size_t smem, int grid, int nbuf, cudaStream_t s);
+
+// tensor-core building block check (k_tc.cu)
+cudaError_t tc_selftest(const uint16_t* a, const uint16_t* b, int n, int k, float* d, int* status, cudaStream_t s);
+
 // cheap potential (k_spline.cu)
 // lpa: lanes per evaluated atom (32, or 16 or 8 for atoms with few neighbours);
 // spline_nb3(lpa): three-body neighbours an atom may have on chip with lpa lanes

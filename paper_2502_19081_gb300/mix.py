@@ -32,7 +32,9 @@ MIX_EBOX = -8
 
 MIX_FP64 = 0
 MIX_FP32 = 1
-PREC_NAMES = {MIX_FP64: "f64", MIX_FP32: "f32"}
+MIX_BF16 = 2          # float path, nu = 3 readout on the tensor cores (bf16 operands, float accumulation)
+MIX_BF16_SPLIT = 3    # the same with hi/lo bf16 operand splits (three MMAs per product)
+PREC_NAMES = {MIX_FP64: "f64", MIX_FP32: "f32", MIX_BF16: "bf16", MIX_BF16_SPLIT: "bf16x3"}
 MIX_BLEND_LINEAR = 0
 MIX_BLEND_CUBIC = 1
 
@@ -46,6 +48,7 @@ EXPORTS = [
     "mix_batch_destroy", "mix_batch_last_error", "mix_set_seeds", "mix_set_seed_rule", "mix_get_seeds",
     "mix_server_create", "mix_server_submit", "mix_server_tick", "mix_server_request", "mix_server_fetch",
     "mix_server_destroy", "mix_server_last_error", "mix_admission_plan", "mix_batch_set_fused", "mix_batch_info",
+    "mix_tc_selftest",
 ]
 
 MIX_PHASES = 6
@@ -100,7 +103,8 @@ class mix_info(ctypes.Structure):
                 ("exp_grid", ctypes.c_int), ("exp_threads", ctypes.c_int), ("cheap_smem_bytes", ctypes.c_size_t),
                 ("cheap_grid", ctypes.c_int), ("launches_per_evaluation", ctypes.c_int),
                 ("launches", ctypes.c_int64), ("gather_grid", ctypes.c_int), ("build_grid", ctypes.c_int),
-                ("buffer_grid", ctypes.c_int)]
+                ("buffer_grid", ctypes.c_int), ("exp_tensor_cores", ctypes.c_int),
+                ("tc_flops_per_atom", ctypes.c_double)]
 
 
 class mix_server_options(ctypes.Structure):
@@ -182,6 +186,7 @@ def lib():
             L.mix_profile.argtypes = [P, ctypes.c_int]
             L.mix_get_profile.argtypes = [P, dp, dp, i64p]
             L.mix_fma_peak.argtypes = [ctypes.c_int, P, dp]
+            L.mix_tc_selftest.argtypes = [P, P, ctypes.c_int, ctypes.c_int, P, P, P]
             L.mix_neighbours_noalloc.argtypes = [ctypes.c_int64, P, dp, dp, ip, ctypes.c_double, ctypes.c_int,
                                                  P, P, P, P]
             L.mix_tune.argtypes = [P, ctypes.c_int]
@@ -496,16 +501,45 @@ def fma_peak(precision: int, stream=None) -> float:
     return float(out.value)
 
 
+def tc_selftest(a, b, d, status, stream=None) -> None:
+    """mix_tc_selftest on torch device tensors: a [128, k] and b [n, k] bfloat16,
+    d [128, n] float32 (written: a @ b.T on the tensor cores), status [1] int32
+    (bit 0 set if the wait for the MMAs gave up).  Asynchronous on `stream`."""
+    import torch
+    for t, dt, shp in ((a, torch.bfloat16, None), (b, torch.bfloat16, None), (d, torch.float32, None),
+                       (status, torch.int32, (1,))):
+        if t.dtype != dt or not t.is_cuda or not t.is_contiguous():
+            raise ValueError("tc_selftest: a, b bfloat16, d float32, status int32, contiguous CUDA tensors")
+    n, k = int(b.shape[0]), int(b.shape[1])
+    if tuple(a.shape) != (128, k) or tuple(d.shape) != (128, n) or status.numel() < 1:
+        raise ValueError("tc_selftest: shapes a [128, k], b [n, k], d [128, n]")
+    s = stream if stream is not None else torch.cuda.current_stream(a.device)
+    st = lib().mix_tc_selftest(ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(b.data_ptr()), n, k,
+                               ctypes.c_void_p(d.data_ptr()), ctypes.c_void_p(status.data_ptr()),
+                               ctypes.c_void_p(s.cuda_stream))
+    if st != MIX_OK:
+        raise MixError(st, "mix_tc_selftest: " + lib().mix_strerror(st).decode())
+
+
 def neighbours_noalloc(x, box_lo, box_len, periodic, r_list: float, cap: int, nnb, nbr, rev, stream=None) -> int:
     """mix_neighbours_noalloc on torch device tensors: x [N, 4] float64 (read),
     nnb [N], nbr [N, cap], rev [N, cap] int32 (written).  For callers that may
     not allocate device memory; returns the status code."""
     import torch
-    s = stream if stream is not None else torch.cuda.current_stream()
+    n = int(x.shape[0])
+    dev = x.device
+    if x.dtype != torch.float64 or x.dim() != 2 or x.shape[1] != 4:
+        raise ValueError("neighbours_noalloc: x must be a [N, 4] float64 tensor")
+    for t, name in ((x, "x"), (nnb, "nnb"), (nbr, "nbr"), (rev, "rev")):
+        if not t.is_cuda or t.device != dev or not t.is_contiguous():
+            raise ValueError(f"neighbours_noalloc: {name} must be a contiguous tensor on {dev}")
+    for t, need, name in ((nnb, n, "nnb"), (nbr, n * int(cap), "nbr"), (rev, n * int(cap), "rev")):
+        if t.dtype != torch.int32 or t.numel() < need:
+            raise ValueError(f"neighbours_noalloc: {name} must be int32 with at least {need} entries")
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
     lo = _f64(box_lo)
     ln = _f64(box_len)
     per = np.ascontiguousarray(periodic, dtype=np.int32)
-    n = int(x.shape[0])
     return int(lib().mix_neighbours_noalloc(n, ctypes.c_void_p(x.data_ptr()), _dp(lo), _dp(ln), _ip(per),
                                             float(r_list), int(cap), ctypes.c_void_p(nnb.data_ptr()),
                                             ctypes.c_void_p(nbr.data_ptr()), ctypes.c_void_p(rev.data_ptr()),

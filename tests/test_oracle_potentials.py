@@ -34,8 +34,10 @@ def test_ylm_convention_matches_scipy(orc):
 
 
 def test_gaunt_matches_quadrature(orc):
-    pts, w = RM.sphere_quadrature(12)
-    L = 4
+    # every l up to 6 (the largest lmax the library takes; C3 uses 5): the
+    # quadrature integrates products of degree 3 L = 18 exactly
+    L = 6
+    pts, w = RM.sphere_quadrature(3 * L)
     Y = {(l, m): RM.real_ylm_scipy(l, m, pts) for l in range(L + 1) for m in range(-l, l + 1)}
     worst = 0.0
     for l1 in range(L + 1):
@@ -52,7 +54,7 @@ def test_gaunt_matches_quadrature(orc):
 
 def test_gaunt_special_values(orc):
     # integral of Y_lm Y_lm Y_00 = Y_00 = 1/sqrt(4 pi); odd l-sum vanishes
-    for l in range(5):
+    for l in range(7):
         for m in range(-l, l + 1):
             assert abs(orc.gaunt(0, 0, l, m, l, m) - 1.0 / math.sqrt(4 * math.pi)) < 1e-14
     assert orc.gaunt(1, 0, 1, 0, 1, 0) == pytest.approx(0.0, abs=1e-15)
@@ -64,7 +66,8 @@ def _env(rng, k=14, rmin=2.0, rmax=5.2):
     return u * r[:, None]
 
 
-@pytest.mark.parametrize("el,n,L,bo", [("Fe", 4, 2, 4), ("Fe", 6, 3, 4), ("Si", 4, 2, 3), ("Fe", 5, 4, 4)])
+@pytest.mark.parametrize("el,n,L,bo", [("Fe", 4, 2, 4), ("Fe", 6, 3, 4), ("Si", 4, 2, 3), ("Fe", 5, 4, 4),
+                                      ("Fe", 12, 5, 4), ("Fe", 4, 6, 4)])
 def test_ace_basis_addition_theorem(orc, el, n, L, bo):
     rng = np.random.default_rng(n * 10 + L)
     wl = I.cluster_workload(seed=3, element=el, n_rad=n, l_max=L, body_order=bo)
