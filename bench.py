@@ -53,6 +53,8 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=20)
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-secondary", action="store_true")
+    p.add_argument("--ncu", action="store_true",
+                   help="profiling mode: W warm-up and K steps of the workload at one precision, nothing else")
     p.add_argument("--ref-seconds", type=float, default=90.0)
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--serve-seconds", type=float, default=60.0)
@@ -469,6 +471,44 @@ def gpu_leg(mix, torch, wl, prec, args, flush, peaks, hbm, oracle_seconds, e2e=T
     return blk
 
 
+def profile_run(args):
+    """The command the committed ncu summaries were taken with: one context of
+    the workload (precision auto: bf16 for the screw cylinder, else fp32), W
+    warm-up steps and K steps, synchronised, and a one-line summary."""
+    import torch
+    from paper_2502_19081_gb300 import build as B
+    from paper_2502_19081_gb300 import mix
+    torch.cuda.set_device(0)
+    B.build()
+    if args.workload == "si_replicas_256":
+        from paper_2502_19081_gb300 import inputs as I
+        wls = I.si_replicas(256, seed=4)
+        ctxs = [mix.open_context(w, precision=mix.MIX_FP32) for w in wls]
+        b = mix.Batch(ctxs)
+        b.step(1.0, args.warmup)
+        b.sync()
+        t0 = time.perf_counter()
+        b.step(1.0, args.steps)
+        b.sync()
+        print(json.dumps({"mode": "ncu", "workload": "si_replicas_256", "precision": "f32", "steps": args.steps,
+                          "wall_s": time.perf_counter() - t0, "batch": b.info()}), flush=True)
+        b.close()
+        return
+    wl = make_workload(args.workload, 0)
+    pmap = {"fp32": mix.MIX_FP32, "fp64": mix.MIX_FP64, "bf16": mix.MIX_BF16, "bf16x3": mix.MIX_BF16_SPLIT}
+    prec = pmap.get(args.precision, mix.MIX_BF16 if args.workload == "fe_screw_256000" else mix.MIX_FP32)
+    ctx = mix.open_context(wl, precision=prec)
+    ctx.step(wl.dt, args.warmup)
+    ctx.sync()
+    t0 = time.perf_counter()
+    ctx.step(wl.dt, args.steps)
+    ctx.sync()
+    el = time.perf_counter() - t0
+    print(json.dumps({"mode": "ncu", "workload": wl.name, "precision": mix.PREC_NAMES[prec], "steps": args.steps,
+                      "wall_s": el, "info": ctx.info()}), flush=True)
+    ctx.close()
+
+
 def ours(args):
     import torch
     import torch.distributed as dist
@@ -677,57 +717,42 @@ def batch_bench(args):
     print(json.dumps(out), flush=True)
 
 
-def serve_bench(args):
-    """Serving: a Poisson stream of requests (20 per second; Si or Fe cells of
-    1e3 to 5e5 atoms, log-uniform; 100 to 2000 steps, log-uniform; core 1 to
-    10 % of the atoms; FP32 potentials, FP64 integration) served for a bounded
-    wall-clock window by the library's server (mix_server_*): admission by
-    device memory and an active-atom cap, continuous batching, one step per
-    tick.  value = atom-steps served per second of the window; the per-step
-    latency is the device time of each batched step; queueing delay is
-    admission time minus arrival time.  Requests that arrived but are not yet
-    handed to the server wait in a client-side backlog (system generation is
-    deferred until the server queue has room), counted as queued."""
+def serve_window(mix, I, stream, pots, seconds, precision, max_active_atoms, queue, clocks=None):
+    """Serve the arrival stream for `seconds` of wall clock with one server:
+    requests are generated when they arrive (a client-side backlog holds them
+    while the server's queue is full), the server admits, batches and steps
+    them (one step a tick).  Returns the served throughput and the latencies:
+    per-request per-step (each active request waits one batched step per tick:
+    the step's device time and the tick's wall time, over all (request, step)
+    pairs) and queueing delay (admission minus arrival)."""
     import collections
-    import torch
-    from paper_2502_19081_gb300 import build as B
-    from paper_2502_19081_gb300 import inputs as I
-    from paper_2502_19081_gb300 import mix
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    B.build()
-    pots = I.serve_potentials()
-    stream = list(I.serve_stream(seed=5 + 1000 * rank, rate=args.serve_rate, duration=args.serve_seconds))
-    offered = sum(r["n_target"] * r["nsteps"] for r in stream) / args.serve_seconds
-    srv = mix.Server(1.0, max_active_atoms=args.serve_atoms)
+    srv = mix.Server(1.0, max_active_atoms=max_active_atoms)
     pending = collections.deque(stream)
     backlog = collections.deque()
     arrival = {}
-    step_ms, atoms_per_step, qdelay, done = [], [], [], []
+    step_dev, step_wall, atoms_per_step, qdelay, done = [], [], [], [], []
     served = 0.0
     server_queued = 0
-    clocks = Clocks(local)
-    clocks.start()
-    t_now = 0.0
     t0 = time.perf_counter()
     while True:
         t_now = time.perf_counter() - t0
-        if t_now >= args.serve_seconds:
+        if t_now >= seconds:
             break
         while pending and pending[0]["t"] <= t_now:
             backlog.append(pending.popleft())
-        while backlog and server_queued < args.serve_queue:
+        while backlog and server_queued < queue:
             r = backlog.popleft()
             wl = I.serve_request(r["seed"], r["element"], r["n_target"], r["core_frac"], r["temp_k"], pots)
-            # the synthetic Si model densifies over hundreds of steps (its diamond
-            # lattice is not a minimum): room for twice the lattice's neighbours
-            rid = srv.submit(wl, r["nsteps"], precision=mix.MIX_FP32, nbr_cap=128 if r["element"] == "Si" else 0)
+            rid = srv.submit(wl, r["nsteps"], precision=precision, nbr_cap=128 if r["element"] == "Si" else 0)
             arrival[rid] = r["t"]
             server_queued += 1
+        tw = time.perf_counter()
         t = srv.tick(1)
+        tw = time.perf_counter() - tw
         server_queued = t["queued"]
         if t["steps"]:
-            step_ms.append(t["step_ms"])
+            step_dev += [t["step_ms"]] * t["active"]
+            step_wall += [tw * 1e3] * t["active"]
             atoms_per_step.append(t["active_atoms"])
             served += t["active_atoms"] * t["steps"]
         for rid in list(arrival):
@@ -743,31 +768,70 @@ def serve_bench(args):
         if t["active"] == 0 and t["queued"] == 0 and not backlog and pending:
             time.sleep(max(0.0, min(pending[0]["t"] - (time.perf_counter() - t0), 0.05)))
     wall = time.perf_counter() - t0
-    clk = clocks.stop()
     active_delay = []
     for rid, ta in arrival.items():
         info = srv.request(rid)
         if info["t_admit"] >= 0:
             active_delay.append(info["t_admit"] - ta)
     srv.close()
-    per = np.array(step_ms) if step_ms else np.zeros(1)
+    dev = np.array(step_dev) if step_dev else np.zeros(1)
+    wal = np.array(step_wall) if step_wall else np.zeros(1)
     qd = np.array([q for q in qdelay + active_delay if q == q]) if (qdelay or active_delay) else np.zeros(1)
+    return {
+        "value": served / wall, "wall_s": wall, "ticks": len(atoms_per_step),
+        "per_request_step_ms": {"device_p50": float(np.percentile(dev, 50)), "device_p99": float(np.percentile(dev, 99)),
+                                "wall_p50": float(np.percentile(wal, 50)), "wall_p99": float(np.percentile(wal, 99)),
+                                "pairs": len(step_dev)},
+        "arrived": len(stream) - len(pending), "completed": sum(1 for d in done if d[1] == mix.MIX_REQ_DONE),
+        "failed": sum(1 for d in done if d[1] == mix.MIX_REQ_FAILED),
+        "failed_by_status": dict(collections.Counter(
+            mix.lib().mix_strerror(d[3]).decode() for d in done if d[1] == mix.MIX_REQ_FAILED)),
+        "admitted": len(done) + len(active_delay),
+        "queue_delay_s": {"p50": float(np.percentile(qd, 50)), "p99": float(np.percentile(qd, 99))},
+        "mean_active_atoms": float(np.mean(atoms_per_step)) if atoms_per_step else 0.0,
+    }
+
+
+def serve_bench(args):
+    """Serving: a Poisson stream of requests (20 per second; Si or Fe cells of
+    1e3 to 5e5 atoms, log-uniform; 100 to 2000 steps, log-uniform; core 1 to
+    10 % of the atoms) served for a bounded wall-clock window by the library's
+    server (mix_server_*): admission by device memory and an active-atom cap,
+    continuous batching, one step per tick, FP32 potentials with FP64
+    integration.  The same stream is then served by the plain FP64 unbatched
+    path (every request alone, float64 potentials) for a shorter window, as the
+    comparator.  value = atom-steps served per second of the window."""
+    import torch
+    from paper_2502_19081_gb300 import build as B
+    from paper_2502_19081_gb300 import inputs as I
+    from paper_2502_19081_gb300 import mix
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    B.build()
+    pots = I.serve_potentials()
+    stream = list(I.serve_stream(seed=5 + 1000 * rank, rate=args.serve_rate, duration=args.serve_seconds))
+    offered = sum(r["n_target"] * r["nsteps"] for r in stream) / args.serve_seconds
+    clocks = Clocks(local)
+    clocks.start()
+    main = serve_window(mix, I, stream, pots, args.serve_seconds, mix.MIX_FP32, args.serve_atoms, args.serve_queue)
+    clk = clocks.stop()
+    base_s = max(10.0, args.serve_seconds / 3.0)
+    base = serve_window(mix, I, [r for r in stream if r["t"] < base_s], pots, base_s, mix.MIX_FP64, 1,
+                        args.serve_queue)
     out = {"metric": "served atom-steps/s, Poisson request stream (continuous batching)",
-           "value": served / wall, "unit": UNIT, "n_gpus": world, "steps": len(step_ms), "warmup": 0,
-           "ms_per_step": float(per.mean()), "p50_ms": float(np.percentile(per, 50)),
-           "p99_ms": float(np.percentile(per, 99)), "higher_is_better": True, "dtype": "f32",
+           "value": main["value"], "unit": UNIT, "n_gpus": world, "steps": main["ticks"], "warmup": 0,
+           "p50_ms": main["per_request_step_ms"]["device_p50"], "p99_ms": main["per_request_step_ms"]["device_p99"],
+           "higher_is_better": True, "dtype": "f32",
            "config": {"workload": "serve_poisson", "rate_per_s": args.serve_rate, "window_s": args.serve_seconds,
                       "max_active_atoms": args.serve_atoms, "server_queue": args.serve_queue,
                       "potential_arithmetic": "f32", "integration": "f64",
                       "l2": "working set > L2 (no flush)"},
            "offered_atom_steps_per_s": offered,
-           "arrived": len(stream) - len(pending), "completed": sum(1 for d in done if d[1] == mix.MIX_REQ_DONE),
-           "failed": sum(1 for d in done if d[1] == mix.MIX_REQ_FAILED),
-           "failed_by_status": dict(collections.Counter(
-               mix.lib().mix_strerror(d[3]).decode() for d in done if d[1] == mix.MIX_REQ_FAILED)),
-           "admitted": len(done) + len(active_delay),
-           "queue_delay_s": {"p50": float(np.percentile(qd, 50)), "p99": float(np.percentile(qd, 99))},
-           "mean_active_atoms": float(np.mean(atoms_per_step)) if atoms_per_step else 0.0,
+           "served": {k: v for k, v in main.items() if k != "value"},
+           "fp64_unbatched": dict(base, window_s=base_s,
+                                  note="the plain FP64 path: float64 potentials, one request at a time "
+                                       "(active-atom cap 1), the same arrival stream"),
+           "speedup_over_fp64_unbatched": main["value"] / base["value"] if base["value"] > 0 else None,
            "clocks": clk}
     print(json.dumps(out), flush=True)
 
@@ -830,6 +894,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         reference(args)
+    elif args.ncu:
+        profile_run(args)
     elif args.workload == "si_replicas_256":
         batch_bench(args)
     elif args.workload == "serve_poisson":

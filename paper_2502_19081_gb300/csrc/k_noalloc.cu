@@ -49,6 +49,23 @@ __global__ void k_noalloc_init(int* status, int* cell_count, int ncell) {
     for (int k = t; k < ncell; k += gridDim.x * blockDim.x) cell_count[k] = 0;
 }
 
+// The position checks the context path makes before a build: a non-finite
+// coordinate, or one outside a non-periodic dimension of the box, sets its
+// status bit (the build still runs; every cell index it forms is clamped).
+__global__ void k_noalloc_check(Dev d) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d.n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double4 x = d.x[i];
+        if (!(isfinite(x.x) && isfinite(x.y) && isfinite(x.z))) {
+            set_status(d.status, ST_NONFINITE);
+            continue;
+        }
+        const double xs[3] = {x.x, x.y, x.z};
+        for (int k = 0; k < 3; ++k)
+            if (!d.box.per[k] && (xs[k] < d.box.lo[k] || xs[k] >= d.box.lo[k] + d.box.L[k]))
+                set_status(d.status, ST_OUT_OF_BOX);
+    }
+}
+
 // Device address of the scratch on the current device, looked up once per device.
 int scratch_address(unsigned char** out) {
     int dev = 0;
@@ -86,7 +103,10 @@ extern "C" int mix_neighbours_noalloc(int64_t n_atoms, const double* x_dev, cons
         d.box.L[k] = box_len[k];
         d.box.invL[k] = 1.0 / box_len[k];
         d.box.per[k] = periodic[k] ? 1 : 0;
-        int nc = (int)floor(box_len[k] / r_list);
+        // the cell count is checked as a double before it becomes an int
+        const double ratio = box_len[k] / r_list;
+        if (!(ratio < 1024.0)) return MIX_EINVAL;
+        int nc = (int)floor(ratio);
         if (d.box.per[k]) {
             if (box_lo[k] != 0.0 || nc < 3 || box_len[k] < 2.0 * r_list) return MIX_EINVAL;
         } else if (nc < 1) {
@@ -127,11 +147,14 @@ extern "C" int mix_neighbours_noalloc(int64_t n_atoms, const double* x_dev, cons
         cudaMemcpyAsync(d.x, x_dev, (size_t)n_atoms * sizeof(double4), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         return MIX_ECUDA;
     k_noalloc_init<<<64, 256, 0, s>>>(d.status, d.cell_count, d.cells.ncell);
+    if (n_atoms > 0) k_noalloc_check<<<(int)((n_atoms + 255) / 256), 256, 0, s>>>(d);
     launch_build(d, s);
     if (cudaGetLastError() != cudaSuccess) return MIX_ECUDA;
     int status[SW_COUNT];
     if (cudaMemcpyAsync(status, d.status, sizeof status, cudaMemcpyDeviceToHost, s) != cudaSuccess) return MIX_ECUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return MIX_ECUDA;
+    if (status[SW_STATUS] & ST_NONFINITE) return MIX_ENUMERIC;
+    if (status[SW_STATUS] & ST_OUT_OF_BOX) return MIX_EBOX;
     if (status[SW_STATUS] & ST_NBR_OVERFLOW) return MIX_EOVERFLOW;
     if (status[SW_STATUS] & ST_REV_MISSING) return MIX_EINVAL;
     return MIX_OK;

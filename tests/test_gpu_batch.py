@@ -131,6 +131,16 @@ def test_fused_mixed_elements_with_rebuilds(mx, prec):
         assert c.stats()["rebuilds"] == ra
         assert np.array_equal(x, xa) and np.array_equal(v, va) and np.array_equal(f, fa)
     assert max(r for _, r in alone) > 2     # lists really were rebuilt along the way
+    # the oracle on each member's final bits: sets exactly, forces within the
+    # precision's tolerance (1e-10 eV/A float64, the 1e-3 eV/A gate float)
+    tol = 1e-10 if prec == 0 else 1e-3
+    for wl, c in zip(wls, members):
+        x, _, f, _ = c.get_state()
+        om = oracle.Model(wl)
+        fl, _, _ = c.sets()
+        assert np.array_equal(fl, om.sets(x))
+        FB, _, _ = om.forces(x, oracle.MODE_METHOD)
+        assert np.abs(f[:, :3] - FB[:, :3]).max() < tol
     b.close()
 
 

@@ -5,6 +5,7 @@ without disturbing the others; argument and state errors."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_2502_19081_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
@@ -55,6 +56,9 @@ def test_requests_in_the_mix_equal_alone(mx, precision):
         x, v, f = srv.fetch(rid)
         xa, va, fa = _alone(mx, wl, nsteps, precision)
         assert np.array_equal(x, xa) and np.array_equal(v, va) and np.array_equal(f, fa)
+        # and the oracle on the served request's final bits
+        FB, _, _ = oracle.Model(wl).forces(x, oracle.MODE_METHOD)
+        assert np.abs(f[:, :3] - FB[:, :3]).max() < (1e-10 if precision == 0 else 1e-3)
     srv.close()
 
 

@@ -50,14 +50,69 @@ def test_noalloc_lists_equal_context_lists_two_calls(mx):
         ctx.close()
 
 
+def test_noalloc_allocates_no_device_memory(mx):
+    """After a first call (which loads the library's kernels), further calls
+    leave the device's free memory unchanged."""
+    import torch
+    wl = I.small_fe_box(32, r_core=4.0, ramp=3.0)
+    ctx = mx.open_context(wl)
+    _lists_from_noalloc(mx, torch, ctx, wl)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        st, _, _, _ = _lists_from_noalloc(mx, torch, ctx, wl)
+        assert st == mx.MIX_OK
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    ctx.close()
+
+
+def test_noalloc_reports_bad_positions(mx):
+    """A non-finite coordinate, and one outside a non-periodic dimension, are
+    reported as by the context path (MIX_ENUMERIC, MIX_EBOX)."""
+    import torch
+    wl = I.cluster_workload(33, n=20)
+    s = wl.system
+    nbr = torch.zeros((20, 64), dtype=torch.int32, device="cuda")
+    rev = torch.zeros((20, 64), dtype=torch.int32, device="cuda")
+    nnb = torch.zeros(20, dtype=torch.int32, device="cuda")
+    x = torch.from_numpy(np.ascontiguousarray(s.x)).cuda()
+    assert mx.neighbours_noalloc(x, s.box_lo, s.box_len, s.periodic, 5.8, 64, nnb, nbr, rev) == mx.MIX_OK
+    xn = x.clone()
+    xn[3, 1] = float("nan")
+    assert mx.neighbours_noalloc(xn, s.box_lo, s.box_len, s.periodic, 5.8, 64, nnb, nbr, rev) == mx.MIX_ENUMERIC
+    xo = x.clone()
+    xo[5, 0] = float(s.box_lo[0] + s.box_len[0] + 1.0)
+    assert mx.neighbours_noalloc(xo, s.box_lo, s.box_len, s.periodic, 5.8, 64, nnb, nbr, rev) == mx.MIX_EBOX
+
+
+def test_noalloc_checks_its_arguments(mx):
+    import torch
+    x = torch.zeros((8, 4), dtype=torch.float64, device="cuda")
+    small = torch.zeros((8, 10), dtype=torch.int32, device="cuda")
+    nnb = torch.zeros(8, dtype=torch.int32, device="cuda")
+    with pytest.raises(ValueError):       # nbr smaller than N x cap
+        mx.neighbours_noalloc(x, (0, 0, 0), (50.0, 50.0, 50.0), (1, 1, 1), 5.8, 64, nnb, small, small)
+    with pytest.raises(ValueError):       # float32 positions
+        mx.neighbours_noalloc(x.float(), (0, 0, 0), (50.0, 50.0, 50.0), (1, 1, 1), 5.8, 10, nnb, small, small)
+    with pytest.raises(ValueError):       # [N, 3] positions
+        mx.neighbours_noalloc(x[:, :3].contiguous(), (0, 0, 0), (50.0, 50.0, 50.0), (1, 1, 1), 5.8, 10, nnb,
+                              small, small)
+
+
 def test_noalloc_rejects_sizes_beyond_its_limit(mx):
     import torch
     x = torch.zeros((8, 4), dtype=torch.float64, device="cuda")
-    out = torch.zeros((8, 64), dtype=torch.int32, device="cuda")
+    out = torch.zeros((8, 300), dtype=torch.int32, device="cuda")
+    big = torch.zeros((33000, 64), dtype=torch.int32, device="cuda")
+    nb1 = torch.zeros(33000, dtype=torch.int32, device="cuda")
     too_many = torch.zeros((33000, 4), dtype=torch.float64, device="cuda")
-    st = mx.neighbours_noalloc(too_many, (0, 0, 0), (50.0, 50.0, 50.0), (1, 1, 1), 5.8, 64, out, out, out)
+    st = mx.neighbours_noalloc(too_many, (0, 0, 0), (50.0, 50.0, 50.0), (1, 1, 1), 5.8, 64, nb1, big, big)
     assert st == mx.MIX_EINVAL
     st = mx.neighbours_noalloc(x, (0, 0, 0), (50.0, 50.0, 50.0), (1, 1, 1), 5.8, 300, out, out, out)
     assert st == mx.MIX_EINVAL
     st = mx.neighbours_noalloc(x, (0, 0, 0), (1000.0, 1000.0, 1000.0), (0, 0, 0), 5.8, 64, out, out, out)
     assert st == mx.MIX_EINVAL                     # more cells than the scratch holds
+    st = mx.neighbours_noalloc(x, (0, 0, 0), (1e12, 50.0, 50.0), (0, 0, 0), 5.8, 64, out, out, out)
+    assert st == mx.MIX_EINVAL                     # a cell count beyond int, rejected before conversion
