@@ -509,6 +509,45 @@ def profile_run(args):
     ctx.close()
 
 
+def blended_energy(ctx, mass: float) -> float:
+    """KE + sum_i [w_i E_exp,i + (1 - w_i) E_cheap,i] of a context's current
+    state (eV): the energy force mixing would conserve if it were the gradient
+    of one function (it is not; the drift measures the difference)."""
+    x, v, _, _ = ctx.get_state()
+    ee, ec = ctx.site_energies()
+    _, w = ctx.lam()
+    ke = 0.5 * mass * float(np.sum(v[:, :3] ** 2)) / 9.6485332e-3
+    return ke + float(np.sum(w * ee + (1.0 - w) * ec))
+
+
+def nve_drift(mix, wl, precision, steps, regions=None):
+    """Drift of the blended energy over an NVE run, per atom and as the
+    temperature it amounts to (3/2 k_B per atom), per picosecond."""
+    ctx = mix.open_context(wl, precision=precision, regions=regions)
+    h0 = blended_energy(ctx, wl.system.mass)
+    ctx.step(wl.dt, steps)
+    h1 = blended_energy(ctx, wl.system.mass)
+    ctx.close()
+    n = wl.system.n
+    ps = steps * wl.dt * 1e-3
+    de = (h1 - h0) / n
+    return {"steps": steps, "dt_fs": wl.dt, "dE_per_atom_eV": de, "eV_per_atom_per_ps": de / ps,
+            "K_per_ps": de / (1.5 * 8.617333262e-5) / ps}
+
+
+def drift_block(mix):
+    """Mixed-NVE drift of the Si vacancy cell (100 steps, float64) and the Fe
+    dumbbell cell (1000 steps, float), each beside the same run with the pure
+    cheap potential (no regions): the integrator's own error."""
+    from paper_2502_19081_gb300 import inputs as I
+    out = {}
+    for name, prec, steps in (("si_vacancy_215", mix.MIX_FP64, 100), ("fe_dumbbell_8001", mix.MIX_FP32, 1000)):
+        wl = I.workload(name)
+        out[name] = {"precision": mix.PREC_NAMES[prec], "mixed": nve_drift(mix, wl, prec, steps),
+                     "pure_cheap": nve_drift(mix, wl, prec, steps, regions=[])}
+    return out
+
+
 def ours(args):
     import torch
     import torch.distributed as dist
@@ -647,6 +686,8 @@ def ours(args):
             "mixing": sec["mixing"], "kernels": sec["kernels"], "e2e": sec["e2e"],
             "cpu_baseline": sec.get("cpu_baseline"),
             "evaluated_exp": sec["nstat"]["n_exp"], "evaluated_cheap": sec["nstat"]["n_cheap"]}
+    if not args.no_secondary:
+        out["nve_drift"] = drift_block(mix)
     if not args.no_cpu:
         out["oracle_single_thread"] = oracle_single_thread(["si_vacancy_215", "fe_dumbbell_8001"])
     print(json.dumps(out), flush=True)

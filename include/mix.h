@@ -310,6 +310,9 @@ typedef struct {
     int exp_tensor_cores;   /* 1: the nu = 3 readout runs on the tensor cores (bf16 modes) */
     double tc_flops_per_atom;  /* algorithmic flops of that readout, V = Z W: sum over
                                   l-triples of 2 (2 l3 + 1) n^3 per evaluated atom */
+    int cheap_lanes;        /* lanes per atom of the cheap kernel (8, 16 or 32); a periodic
+                               bulk may narrow after its first evaluation, a 3-body
+                               overflow widens to 32 */
 } mix_info;
 
 int mix_get_info(const mix_ctx* ctx, mix_info* info);

@@ -54,6 +54,8 @@ def main():
             ace, spl = I.element_potentials(el, rng, wl.ace.r_cut, n, L, bo, scale_key=key)
         s0 = float(out.get(f"ace:{key}", {}).get("value", 1.0))
         ace0 = dataclasses.replace(ace, pair=np.zeros(16))
+        if el == "Si" and ace.nu_max >= 2:      # the random part alone, not the stored angular term
+            ace0 = dataclasses.replace(ace0, c2=ace.c2 - I.si_angular_tables(n, L)[1])
         m = oracle.Model(system=wl.system, ace=ace0, spline=spl, regions=wl.regions)
         F, _, _ = m.forces(wl.system.x, oracle.MODE_PURE_EXP)
         rms = _rms(F)
@@ -64,6 +66,8 @@ def main():
         wl = _ref(kind)
         s0 = float(out.get(f"spline3:{el}", {}).get("value", 0.01))
         spl0 = dataclasses.replace(wl.spline, c2=np.zeros(16))
+        if el == "Si":                            # the random 3-body part alone
+            spl0 = dataclasses.replace(spl0, c3=wl.spline.c3 - I.si_angular_tables(wl.ace.n_rad, wl.ace.l_max)[0])
         m = oracle.Model(system=wl.system, ace=wl.ace, spline=spl0, regions=wl.regions)
         F, _, _ = m.forces(wl.system.x, oracle.MODE_PURE_CHEAP)
         rms = _rms(F)

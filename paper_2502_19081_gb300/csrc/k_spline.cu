@@ -74,9 +74,10 @@ __device__ __forceinline__ void spl_fill_tq(unsigned char* tq) {
 
 // One evaluated atom i (an entry of the system's cheap list), by the group of
 // LPA lanes that owns W; the coefficient windows c2w, c3w may sit in shared or
-// global memory.
+// global memory.  Returns the atom's 3-body neighbour count (before any clamp
+// to the on-chip slots).
 template <typename T, int LPA>
-__device__ __forceinline__ void spline_atom(const Dev& d, const SplTab<T>& tab, int i,
+__device__ __forceinline__ int spline_atom(const Dev& d, const SplTab<T>& tab, int i,
                                             const typename Vec4<T>::type* c2w, const typename Vec4<T>::type* c3w,
                                             const unsigned char* tq, SplWarp<T, spl_nb<LPA>()>& W) {
     constexpr int NB = spl_nb<LPA>();
@@ -91,6 +92,7 @@ __device__ __forceinline__ void spline_atom(const Dev& d, const SplTab<T>& tab, 
     const T invh2 = tab.invh2, invh3 = tab.invh3, invhc = tab.invhc;
     const unsigned lt = (1u << lane) - 1u;   // the ballots carry this group's lanes only
     const int cap = d.cap;
+    int n3_all = 0;
     {
         using Pt = typename PairFrame<T>::Pt;
         const PairFrame<T> pf(d, i);
@@ -164,6 +166,7 @@ __device__ __forceinline__ void spline_atom(const Dev& d, const SplTab<T>& tab, 
             }
             n3 += __popc(bal);
         }
+        n3_all = n3;
         if (n3 > NB) {
             if (sub == 0) {
                 set_status(d.status, ST_NB3_OVERFLOW);
@@ -257,6 +260,7 @@ __device__ __forceinline__ void spline_atom(const Dev& d, const SplTab<T>& tab, 
         }
         __syncwarp(mask);
     }
+    return n3_all;
 }
 
 // window counts of the two coefficient tables (4-vectors)
@@ -289,13 +293,17 @@ __global__ void __launch_bounds__(SPL_WARPS * 32, sizeof(T) == 4 ? 6 : 1) k_spli
     const int stride = gridDim.x * SPL_WARPS * G;
     int a = (blockIdx.x * SPL_WARPS + warp) * G + grp;
     int i = a < count ? d.act_c[a] : 0;
+    int nb3 = 0;   // the largest 3-body count this lane's group met
     while (a < count) {   // the next atom's index is loaded ahead
         const int an = a + stride;
         const int in = an < count ? d.act_c[an] : 0;
-        spline_atom<T, LPA>(d, tab, i, c2s, c3s, tq, ws[warp * G + grp]);
+        nb3 = max(nb3, spline_atom<T, LPA>(d, tab, i, c2s, c3s, tq, ws[warp * G + grp]));
         a = an;
         i = in;
     }
+    // one atomic a warp: the context's lane groups are narrowed from it
+    nb3 = __reduce_max_sync(0xffffffffu, nb3);
+    if ((threadIdx.x & 31) == 0 && nb3 > 0) atomicMax(d.status + SW_NB3MAX, nb3);
 }
 
 // Many systems: a lane group per entry {system, atom} of the flattened cheap

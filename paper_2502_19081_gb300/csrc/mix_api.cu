@@ -244,6 +244,8 @@ struct mix_ctx {
     int ace_tcm;                      // 0: CUDA-core nu = 3; 1, 2: tensor-core readout (bf16, bf16 hi/lo)
     int ace_nbuf;                     // tile buffers of the tensor-core kernel
     int spl_lpa;                      // lanes per atom of the cheap kernel (32, 16 or 8)
+    bool spl_bulk;                    // periodic in every dimension (narrow lane groups allowed)
+    bool spl_lpa_settled;             // the lane groups were narrowed or widened once
     int ace_grid_max, spl_grid_max;   // resident CTAs at full occupancy
     int64_t gaunt_nnz, tau_d3_sum, basis_size;
     double nu3_flops;
@@ -700,6 +702,7 @@ int read_status(mix_ctx* c) {
             int grid = 0;
             if (spline_configure(c->precision, 32, &smem, &grid) == cudaSuccess) {
                 c->spl_lpa = 32;
+                c->spl_lpa_settled = true;
                 c->spl_smem = smem;
                 c->spl_grid = c->spl_grid_max = grid;
                 drop_graph(c);
@@ -719,6 +722,28 @@ int read_status(mix_ctx* c) {
     if (st & ST_OUT_OF_BOX) return fail(c, MIX_EBOX, "an atom left the box in a non-periodic dimension");
     if (st & ST_REV_MISSING) return fail(c, MIX_EINVAL, "asymmetric neighbour list");
     if (st & ST_TC_TIMEOUT) return fail(c, MIX_ETIMEOUT, "a wait for the tensor-core readout gave up");
+    // The uniform-density estimate behind the initial lane groups overstates
+    // open lattices (diamond holds half of it inside 3.4 A).  Once an
+    // evaluation has measured the largest 3-body count, a periodic bulk moves
+    // to the narrowest group whose on-chip slots hold twice that count.  No
+    // result depends on the width (every sum keeps its order), and an overflow
+    // widens the groups again; this happens once per context.
+    if (!c->spl_lpa_settled && c->spl_bulk && c->spl_lpa > 8 && c->pinned[SW_NB3MAX] > 0) {
+        c->spl_lpa_settled = true;
+        const int seen = c->pinned[SW_NB3MAX];
+        int want = c->spl_lpa;
+        for (int l : {16, 8})
+            if (l < want && 2 * seen <= spline_nb3(l)) want = l;
+        size_t smem = 0;
+        int grid = 0;
+        if (want < c->spl_lpa && spline_configure(c->precision, want, &smem, &grid) == cudaSuccess) {
+            c->spl_lpa = want;
+            c->spl_smem = smem;
+            c->spl_grid = c->spl_grid_max = grid;
+            drop_graph(c);
+            c->regions_version++;   // any batch holding the context re-plans
+        }
+    }
     return MIX_OK;
 }
 
@@ -871,6 +896,7 @@ int mix_init(const mix_system* sys, const mix_ace* a, const mix_spline* sp, cons
         const double rho = vol > 0 ? (double)sys->n_atoms / vol : 0.0;
         const double n3 = rho * 4.0 / 3.0 * M_PI * sp->r_cut3 * sp->r_cut3 * sp->r_cut3;
         c->spl_lpa = !bulk ? 32 : (n3 * 3.0 <= spline_nb3(8) ? 8 : (n3 * 3.0 <= spline_nb3(16) ? 16 : 32));
+        c->spl_bulk = bulk;
     }
     e = spline_configure(c->precision, c->spl_lpa, &c->spl_smem, &c->spl_grid);
     c->ace_grid_max = c->ace_grid;
@@ -1208,6 +1234,7 @@ int mix_get_info(const mix_ctx* c, mix_info* info) {
     info->buffer_grid = c->dev.grid_buffer;
     info->exp_tensor_cores = c->ace_tcm ? 1 : 0;
     info->tc_flops_per_atom = c->ace_tcm ? 2.0 * (double)c->tau_d3_sum * c->n * c->n * c->n : 0.0;
+    info->cheap_lanes = c->spl_lpa;
     return MIX_OK;
 }
 

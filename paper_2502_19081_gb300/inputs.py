@@ -188,13 +188,15 @@ def _morse_target(r: np.ndarray, depth: float, alpha: float, r0: float, r_taper:
     return phi * taper
 
 
-def pair_control_polygon(r_cut: float, depth: float, alpha: float, r0: float) -> np.ndarray:
+def pair_control_polygon(r_cut: float, depth: float, alpha: float, r0: float,
+                         r_taper: Optional[float] = None) -> np.ndarray:
     """Sixteen B-spline coefficients sampled from the target shape at the knot
     averages (a-1)h of the uniform cubic basis, h = rc/13; the last three are zero
-    so that the pair term and its first two derivatives vanish at rc."""
+    so that the pair term and its first two derivatives vanish at rc.  The
+    target is tapered to zero at r_taper (default 11 h)."""
     h = r_cut / 13.0
     grev = (np.arange(16) - 1.0) * h
-    c = _morse_target(grev, depth, alpha, r0, 11.0 * h)
+    c = _morse_target(grev, depth, alpha, r0, 11.0 * h if r_taper is None else r_taper)
     c[13:] = 0.0
     return c
 
@@ -254,15 +256,45 @@ def _scale(key: str, default: float) -> float:
 
 
 # element pair targets (depth eV, alpha 1/Angstrom, r0 Angstrom = nearest-neighbour distance)
-PAIR_SI = dict(depth=0.8, alpha=1.6, r0=5.431 * math.sqrt(3.0) / 4.0)
+# 3-body cutoff of the cheap Si potential: between the first (2.35 A) and second
+# (3.84 A) shells, so that the angular term's taper is gentle at the bond length
+# (rc 3.5/6 = 2.9 A would put the bond on its steep end)
+SI_RC3 = 3.4
+# Si: a short-ranged well (tapered to zero at 3.4 A, between the first and second
+# shells), so that with the angular term the diamond lattice is a minimum
+PAIR_SI = dict(depth=1.5, alpha=2.0, r0=5.431 * math.sqrt(3.0) / 4.0, r_taper=3.4)
 PAIR_FE = dict(depth=0.5, alpha=1.7, r0=2.855 * math.sqrt(3.0) / 2.0)
 
 
+_SI_ANGULAR_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "si_angular.json")
+
+
+def si_angular_tables(n_rad: int, l_max: int):
+    """The stored angular term of the Si potentials (written by
+    oracle/fit_si_angular.py): additions to the cheap 3-body coefficients
+    [8][8][8], to the expensive nu = 2 coefficients [l_max+1][n][n] and to its
+    pair spline [16].  Zero tables where the file or the shape is absent."""
+    c3 = np.zeros((8, 8, 8))
+    c2 = np.zeros((l_max + 1, n_rad, n_rad))
+    pair = np.zeros(16)
+    if os.path.exists(_SI_ANGULAR_FILE):
+        with open(_SI_ANGULAR_FILE) as fh:
+            tab = json.load(fh)
+        c3 = np.asarray(tab["cheap_c3_add"], dtype=np.float64)
+        ent = tab["ace"].get(f"n{n_rad}_l{l_max}")
+        if ent is not None:
+            c2 = np.asarray(ent["c2_add"], dtype=np.float64)
+            pair = np.asarray(ent["pair_add"], dtype=np.float64)
+    return c3, c2, pair
+
+
 def element_potentials(element: str, rng: np.random.Generator, r_cut: float, n_rad: int, l_max: int,
-                       body_order: int, scale_key: Optional[str] = None):
+                       body_order: int, scale_key: Optional[str] = None, angular: bool = True):
     """Expensive and cheap potentials for one element.  Both pair terms follow
     the same target shape with independent small perturbations, so the two
-    potentials agree in the bulk the way a distilled cheap potential does."""
+    potentials agree in the bulk the way a distilled cheap potential does.
+    Si (angular=True) also carries the stored angular term of both potentials
+    (si_angular_tables), without which the diamond lattice densifies."""
     tgt = PAIR_SI if element == "Si" else PAIR_FE
     base = pair_control_polygon(r_cut, **tgt)
     pert_e = 0.02 * rng.standard_normal(16)
@@ -273,10 +305,16 @@ def element_potentials(element: str, rng: np.random.Generator, r_cut: float, n_r
     pc[13:] = 0.0
     key = scale_key or f"{element}_n{n_rad}_l{l_max}_b{body_order}"
     s_e = _scale(f"ace:{key}", 1.0)
-    r_cut3 = r_cut * 3.5 / 6.0
+    r_cut3 = SI_RC3 if element == "Si" else r_cut * 3.5 / 6.0
     s_3 = _scale(f"spline3:{element}", 0.01)
     ace = make_ace(rng, r_cut, n_rad, l_max, body_order, s_e, pe)
     spl = make_spline(rng, r_cut, r_cut3, s_3, pc)
+    if element == "Si" and angular:
+        c3a, c2a, pa = si_angular_tables(n_rad, l_max)
+        spl = Spline(r_cut=spl.r_cut, r_cut3=spl.r_cut3, c2=spl.c2, c3=spl.c3 + c3a)
+        if ace.nu_max >= 2:
+            ace = Ace(r_cut=ace.r_cut, n_rad=ace.n_rad, l_max=ace.l_max, nu_max=ace.nu_max, c1=ace.c1,
+                      c2=ace.c2 + c2a, c3=ace.c3, pair=ace.pair + pa)
     return ace, spl
 
 
@@ -427,7 +465,8 @@ def si_replica(seed: int, n_target: int, defect: str, temp_k: float, ace: Ace = 
     v = maxwell_boltzmann(rng, pos.shape[0], MASS_SI, temp_k)
     sysm = System(x=_pack(pos), v=v, mass=MASS_SI, box_lo=np.zeros(3), box_len=L, periodic=(1, 1, 1))
     if ace is None or spline is None:
-        ace, spline = element_potentials("Si", np.random.default_rng(1), 5.0, 8, 3, 3)
+        c1 = si_vacancy()
+        ace, spline = c1.ace, c1.spline
     reg = [Region(REGION_SPHERE, tuple(site), (0.0, 0.0, 1.0), 6.0, 2.0)]
     return Workload(f"si_replica_{seed}", sysm, reg, ace, spline, skin=0.3, dt=1.0, steps=200,
                     precision=PRECISION_FP32, seed=seed, extra={"defect": defect, "temp_k": temp_k})
@@ -436,9 +475,10 @@ def si_replica(seed: int, n_target: int, defect: str, temp_k: float, ace: Ace = 
 def si_replicas(n_replicas: int = 256, seed: int = 4, n_min: int = 1000, n_max: int = 20000):
     """The batch of independent Si defect cells: sizes log-uniform on
     [n_min, n_max], vacancy or interstitial with equal probability,
-    temperatures uniform on [300, 1500] K; one shared pair of potentials."""
+    temperatures uniform on [300, 1500] K; the Si vacancy cell's potentials."""
     rng = np.random.default_rng(seed)
-    ace, spl = element_potentials("Si", np.random.default_rng(1), 5.0, 8, 3, 3)
+    c1 = si_vacancy()                       # the Si vacancy cell's potentials
+    ace, spl = c1.ace, c1.spline
     out = []
     for r in range(n_replicas):
         n_t = int(round(math.exp(rng.uniform(math.log(n_min), math.log(n_max)))))
@@ -449,12 +489,13 @@ def si_replicas(n_replicas: int = 256, seed: int = 4, n_min: int = 1000, n_max: 
 
 
 def serve_potentials():
-    """The two potential pairs of the request stream: Si with the silicon
-    vacancy cell's recipe (rc 5 A, n 8, lmax 3, body order 3) and Fe with the
-    dumbbell cell's recipe (rc 5.5 A, n 10, lmax 4, body order 4)."""
-    si = element_potentials("Si", np.random.default_rng(1), 5.0, 8, 3, 3)
-    fe = element_potentials("Fe", np.random.default_rng(2), 5.5, 10, 4, 4)
-    return {"Si": si, "Fe": fe}
+    """The two potential pairs of the request stream: those of the silicon
+    vacancy cell (rc 5 A, n 8, lmax 3, body order 3) and of the Fe dumbbell cell
+    (rc 5.5 A, n 10, lmax 4, body order 4) themselves.  (Each random draw of
+    the many-body terms is a different potential; another draw of the Fe
+    recipe collapses the bcc lattice within 200 steps.)"""
+    si, fe = si_vacancy(), fe_dumbbell()
+    return {"Si": (si.ace, si.spline), "Fe": (fe.ace, fe.spline)}
 
 
 def serve_request(seed: int, element: str, n_target: int, core_frac: float, temp_k: float, pots) -> Workload:

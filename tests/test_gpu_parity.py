@@ -238,36 +238,37 @@ def test_deterministic_and_resumable(mx):
     assert np.abs(d).max() < 1e-12 and _max_abs(vc, va) < 1e-12 and _max_abs(fc, fa) < 1e-10
 
 
-def test_three_body_overflow_widens_the_cheap_lane_groups(mx):
-    """A Si bulk whose mean three-body count puts the cheap potential on
-    quarter-warp lane groups (16 on-chip three-body slots), with a dense spot of
-    18 atoms 0.9 A apart in the vacancy: the first evaluation reports the
-    overflow and widens the groups to a warp; the repeat matches the oracle."""
+def test_three_body_lane_groups_narrow_then_widen(mx):
+    """A Si bulk: the uniform-density estimate puts the cheap kernel on warps,
+    the first evaluation measures at most about 6 three-body neighbours and
+    the context narrows to 8-lane groups (16 on-chip slots).  Moving 18 atoms
+    into a dense spot 0.9 A apart then overflows those groups: the evaluation
+    reports it and widens them to a warp; the repeat matches the oracle."""
     wl = I.si_vacancy(ncell=5)
     s = wl.system
+    ctx = mx.open_context(wl, nbr_cap=128)
+    assert ctx.info()["cheap_lanes"] == 8
+    x, v, _, _ = ctx.get_state()
+    _, _, F0, _ = ctx.get_state()
+    FB0, _, _ = oracle.Model(wl).forces(x, oracle.MODE_METHOD)
+    assert _max_abs(F0[:, :3], FB0[:, :3]) < TOL64      # the narrow groups give the same forces
     g = np.array([[i, j, k] for i in range(3) for j in range(3) for k in range(2)], float) * 0.9
-    extra = s.box_len / 2 + 0.3 + g - g.mean(axis=0)
-    x = np.concatenate([s.x, np.column_stack([extra, np.zeros(len(extra))])])
-    wl.system = dataclasses.replace(s, x=x, v=np.zeros_like(x))
-    ctx = mx.Context(wl)
+    spot = s.box_len / 2 + 0.3 + g - g.mean(axis=0)
+    far = np.argsort(-np.sum((x[:, :3] - s.box_len / 2) ** 2, axis=1))[:18]
+    x2 = x.copy()
+    x2[far, :3] = spot
+    ctx.set_state(x2, v)
     with pytest.raises(mx.MixError) as e:
         ctx.forces()
         ctx.sync()
     assert e.value.code == mx.MIX_EOVERFLOW and "warp per atom" in str(e.value)
+    assert ctx.info()["cheap_lanes"] == 32
     ctx.forces()
     ctx.sync()
-    x1, _, F, _ = ctx.get_state()
-    FB, _, _ = oracle.Model(wl).forces(x1, oracle.MODE_METHOD)
+    x3, _, F, _ = ctx.get_state()
+    FB, _, _ = oracle.Model(wl).forces(x3, oracle.MODE_METHOD)
     assert _max_abs(F[:, :3], FB[:, :3]) < 1e-9 * max(1.0, float(np.abs(FB[:, :3]).max()))
-    cap0 = ctx.cap
     ctx.close()
-    # open_context repeats the evaluation on the widened context instead of
-    # growing the neighbour capacity
-    b = mx.open_context(wl)
-    _, _, Fb, _ = b.get_state()
-    assert b.cap == cap0
-    assert _max_abs(Fb[:, :3], FB[:, :3]) < 1e-9 * max(1.0, float(np.abs(FB[:, :3]).max()))
-    b.close()
 
 
 def test_host_buffer_entry_point_matches_device_path(mx):
