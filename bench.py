@@ -606,7 +606,8 @@ def ours(args):
         roof = {"kernel": "k_ace" if names[dom] == "exp" else "k_spline", "bound": "alu",
                 "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s", "frac": ach / peak,
                 "traffic": (profiled_traffic(f"k_ace_{mix.PREC_NAMES[prec]}_{wl.name}.md",
-                                             ("k_ace.cuh", "k_ace_f32.cu", "k_ace_tc.cuh", "tc.cuh"))
+                                             ("k_ace.cuh", "k_ace_f32.cu") if prec == mix.MIX_FP32 else
+                                             ("k_ace.cuh", "k_ace_tc.cuh", "k_ace_tc1.cu", "tc.cuh"))
                             if names[dom] == "exp" and prec != mix.MIX_FP64 else None),
                 "algorithmic_flops_per_launch": fl,
                 "peak_source": "measured FMA microbenchmark "
