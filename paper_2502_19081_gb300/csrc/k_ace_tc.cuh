@@ -25,8 +25,9 @@ __global__ void __launch_bounds__(TC_ACE_WARPS * 32, 1) k_ace_tc(Dev d, AceTab<f
     extern __shared__ __align__(128) unsigned char smem_tc[];
     __shared__ __align__(8) unsigned long long s_bar;
     __shared__ uint32_t s_tmem;
-    unsigned char* sm =
-        reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_tc) + 127) & ~(uintptr_t)127);
+    // 128-byte aligned base, formed by pointer arithmetic on the shared array so
+    // that the compiler keeps every access through it a shared-memory access
+    unsigned char* sm = smem_tc + ((128u - (smem_u32(smem_tc) & 127u)) & 127u);
     const int tid = threadIdx.x, warp = tid >> 5;
     TcState tc;
     tc.kp = (tab.n * tab.n + 15) & ~15;

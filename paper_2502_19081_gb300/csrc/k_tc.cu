@@ -16,7 +16,7 @@ __global__ void __launch_bounds__(128, 1) k_tc_selftest(const uint16_t* __restri
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) unsigned long long bar;
     __shared__ uint32_t tbase;
-    unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
+    unsigned char* sm = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
     const int kc = k / 8;
     const int sbo_a = kc * TC_LBO_A, sbo_b = kc * TC_LBO_B;
     unsigned char* sa = sm;
