@@ -550,8 +550,8 @@ constexpr int TC_WAIT_POLLS = 1 << 20;
 // for the CTA's TC_ACE_WARPS atoms at once (16 rows (atom, m3) per atom).
 template <typename T, int L, int NP, int TCM = 0>
 __device__ __forceinline__ void ace_group(const Dev& d, const AceTab<T>& tab, int a0, int nexp, unsigned char* smem,
-                                          TcState* tc = nullptr) {
-    constexpr int WN = TCM != 0 ? TC_ACE_WARPS : ace_warps<T>();
+                                          TcState* tc = nullptr, int wn = ACE_GROUP) {
+    const int WN = TCM != 0 ? TC_ACE_WARPS : wn;   // warps (atoms) of the CTA
     constexpr int NLM = (L + 1) * (L + 1);
     constexpr int D = 2 * L + 1;
     constexpr int NQ4 = NP / 4;
@@ -874,12 +874,13 @@ __device__ __forceinline__ void ace_group(const Dev& d, const AceTab<T>& tab, in
 }
 
 template <typename T, int L, int NP>
-__global__ void __launch_bounds__(ace_warps<T>() * 32, ace_min_ctas<T>()) k_ace(Dev d, AceTab<T> tab) {
-    constexpr int WN = ace_warps<T>();
+__global__ void __launch_bounds__(ACE_MAX_WARPS * 32, ace_min_ctas_max<T>()) k_ace(Dev d, AceTab<T> tab) {
+    const int WN = (int)(blockDim.x >> 5);   // ACE_GROUP or ACE_MAX_WARPS atoms a CTA
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int count = d.status[SW_NEXP];
     const int ng = (count + WN - 1) / WN;
-    for (int g = blockIdx.x; g < ng; g += gridDim.x) ace_group<T, L, NP>(d, tab, g * WN, count, smem_raw);
+    for (int g = blockIdx.x; g < ng; g += gridDim.x)
+        ace_group<T, L, NP>(d, tab, g * WN, count, smem_raw, nullptr, WN);
 }
 
 // Many systems: walks the flattened list {system, first atom of a group} of
@@ -915,13 +916,14 @@ __global__ void __launch_bounds__(ace_warps<T>() * 32, ace_min_ctas<T>()) kb_ace
 
 // launch shape: the shared memory of the layout, and as many resident CTAs as fit
 template <typename T, int L, int NP>
-inline cudaError_t ace_shape(const void* kern, int n, int cap, int tile_max, int qb, size_t* smem, int* grid) {
-    const AceLay lay(tile_max, cap, n, qb, L, NP, (int)sizeof(T), ace_warps<T>());
+inline cudaError_t ace_shape(const void* kern, int n, int cap, int tile_max, int qb, size_t* smem, int* grid,
+                             int wn = ACE_GROUP) {
+    const AceLay lay(tile_max, cap, n, qb, L, NP, (int)sizeof(T), wn);
     const size_t bytes = (size_t)lay.total;
     cudaError_t e = raise_smem_limit(kern, bytes);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, ace_warps<T>() * 32, bytes);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, wn * 32, bytes);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     *smem = bytes;
@@ -930,52 +932,55 @@ inline cudaError_t ace_shape(const void* kern, int n, int cap, int tile_max, int
 }
 
 template <typename T, int L, int NP>
-inline cudaError_t ace_cfg(bool batch, int n, int cap, int tile_max, int qb, size_t* smem, int* grid) {
+inline cudaError_t ace_cfg(bool batch, int n, int cap, int tile_max, int qb, size_t* smem, int* grid, int wn) {
     const void* kern = batch ? (const void*)kb_ace<T, L, NP> : (const void*)k_ace<T, L, NP>;
-    return ace_shape<T, L, NP>(kern, n, cap, tile_max, qb, smem, grid);
+    return ace_shape<T, L, NP>(kern, n, cap, tile_max, qb, smem, grid, batch ? ACE_GROUP : wn);
 }
 
 template <typename T, int NP>
-inline cudaError_t ace_cfg_l(bool batch, int L, int n, int cap, int tile_max, int qb, size_t* smem, int* grid) {
+inline cudaError_t ace_cfg_l(bool batch, int L, int n, int cap, int tile_max, int qb, size_t* smem, int* grid,
+                             int wn) {
     switch (L) {
-        case 0: return ace_cfg<T, 0, NP>(batch, n, cap, tile_max, qb, smem, grid);
-        case 1: return ace_cfg<T, 1, NP>(batch, n, cap, tile_max, qb, smem, grid);
-        case 2: return ace_cfg<T, 2, NP>(batch, n, cap, tile_max, qb, smem, grid);
-        case 3: return ace_cfg<T, 3, NP>(batch, n, cap, tile_max, qb, smem, grid);
-        case 4: return ace_cfg<T, 4, NP>(batch, n, cap, tile_max, qb, smem, grid);
-        case 5: return ace_cfg<T, 5, NP>(batch, n, cap, tile_max, qb, smem, grid);
-        case 6: return ace_cfg<T, 6, NP>(batch, n, cap, tile_max, qb, smem, grid);
+        case 0: return ace_cfg<T, 0, NP>(batch, n, cap, tile_max, qb, smem, grid, wn);
+        case 1: return ace_cfg<T, 1, NP>(batch, n, cap, tile_max, qb, smem, grid, wn);
+        case 2: return ace_cfg<T, 2, NP>(batch, n, cap, tile_max, qb, smem, grid, wn);
+        case 3: return ace_cfg<T, 3, NP>(batch, n, cap, tile_max, qb, smem, grid, wn);
+        case 4: return ace_cfg<T, 4, NP>(batch, n, cap, tile_max, qb, smem, grid, wn);
+        case 5: return ace_cfg<T, 5, NP>(batch, n, cap, tile_max, qb, smem, grid, wn);
+        case 6: return ace_cfg<T, 6, NP>(batch, n, cap, tile_max, qb, smem, grid, wn);
     }
     return cudaErrorInvalidValue;
 }
 
 template <typename T>
-inline cudaError_t ace_cfg_t(bool batch, int L, int n, int cap, int tile_max, int qb, size_t* smem, int* grid) {
-    if (n <= 4) return ace_cfg_l<T, 4>(batch, L, n, cap, tile_max, qb, smem, grid);
-    if (n <= 8) return ace_cfg_l<T, 8>(batch, L, n, cap, tile_max, qb, smem, grid);
-    if (n <= 12) return ace_cfg_l<T, 12>(batch, L, n, cap, tile_max, qb, smem, grid);
-    return ace_cfg_l<T, 16>(batch, L, n, cap, tile_max, qb, smem, grid);
+inline cudaError_t ace_cfg_t(bool batch, int L, int n, int cap, int tile_max, int qb, size_t* smem, int* grid,
+                             int wn = ACE_GROUP) {
+    if (n <= 4) return ace_cfg_l<T, 4>(batch, L, n, cap, tile_max, qb, smem, grid, wn);
+    if (n <= 8) return ace_cfg_l<T, 8>(batch, L, n, cap, tile_max, qb, smem, grid, wn);
+    if (n <= 12) return ace_cfg_l<T, 12>(batch, L, n, cap, tile_max, qb, smem, grid, wn);
+    return ace_cfg_l<T, 16>(batch, L, n, cap, tile_max, qb, smem, grid, wn);
 }
 
 template <typename T, int NP>
-inline void ace_launch_l(const Dev& d, const AceTab<T>& tab, int L, size_t smem, int grid, cudaStream_t s) {
+inline void ace_launch_l(const Dev& d, const AceTab<T>& tab, int L, size_t smem, int grid, int wn, cudaStream_t s) {
+    const int th = wn * 32;
     switch (L) {
-        case 0: k_ace<T, 0, NP><<<grid, ace_warps<T>() * 32, smem, s>>>(d, tab); break;
-        case 1: k_ace<T, 1, NP><<<grid, ace_warps<T>() * 32, smem, s>>>(d, tab); break;
-        case 2: k_ace<T, 2, NP><<<grid, ace_warps<T>() * 32, smem, s>>>(d, tab); break;
-        case 3: k_ace<T, 3, NP><<<grid, ace_warps<T>() * 32, smem, s>>>(d, tab); break;
-        case 4: k_ace<T, 4, NP><<<grid, ace_warps<T>() * 32, smem, s>>>(d, tab); break;
-        case 5: k_ace<T, 5, NP><<<grid, ace_warps<T>() * 32, smem, s>>>(d, tab); break;
-        case 6: k_ace<T, 6, NP><<<grid, ace_warps<T>() * 32, smem, s>>>(d, tab); break;
+        case 0: k_ace<T, 0, NP><<<grid, th, smem, s>>>(d, tab); break;
+        case 1: k_ace<T, 1, NP><<<grid, th, smem, s>>>(d, tab); break;
+        case 2: k_ace<T, 2, NP><<<grid, th, smem, s>>>(d, tab); break;
+        case 3: k_ace<T, 3, NP><<<grid, th, smem, s>>>(d, tab); break;
+        case 4: k_ace<T, 4, NP><<<grid, th, smem, s>>>(d, tab); break;
+        case 5: k_ace<T, 5, NP><<<grid, th, smem, s>>>(d, tab); break;
+        case 6: k_ace<T, 6, NP><<<grid, th, smem, s>>>(d, tab); break;
     }
 }
 
 template <typename T>
-inline void ace_launch_t(const Dev& d, const AceTab<T>& tab, int L, size_t smem, int grid, cudaStream_t s) {
-    if (tab.np == 4) ace_launch_l<T, 4>(d, tab, L, smem, grid, s);
-    else if (tab.np == 8) ace_launch_l<T, 8>(d, tab, L, smem, grid, s);
-    else if (tab.np == 12) ace_launch_l<T, 12>(d, tab, L, smem, grid, s);
-    else ace_launch_l<T, 16>(d, tab, L, smem, grid, s);
+inline void ace_launch_t(const Dev& d, const AceTab<T>& tab, int L, size_t smem, int grid, int wn, cudaStream_t s) {
+    if (tab.np == 4) ace_launch_l<T, 4>(d, tab, L, smem, grid, wn, s);
+    else if (tab.np == 8) ace_launch_l<T, 8>(d, tab, L, smem, grid, wn, s);
+    else if (tab.np == 12) ace_launch_l<T, 12>(d, tab, L, smem, grid, wn, s);
+    else ace_launch_l<T, 16>(d, tab, L, smem, grid, wn, s);
 }
 
 template <typename T, int NP>

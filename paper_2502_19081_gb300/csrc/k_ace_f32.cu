@@ -4,12 +4,12 @@
 
 namespace mixd {
 
-cudaError_t ace_configure_f32(int L, int n, int cap, int tile_max, int qb, size_t* smem, int* grid) {
-    return ace_cfg_t<float>(false, L, n, cap, tile_max, qb, smem, grid);
+cudaError_t ace_configure_f32(int L, int n, int cap, int tile_max, int qb, size_t* smem, int* grid, int wn) {
+    return ace_cfg_t<float>(false, L, n, cap, tile_max, qb, smem, grid, wn);
 }
 
-void launch_ace_f32(const Dev& d, const void* tab, int L, size_t smem, int grid, cudaStream_t s) {
-    ace_launch_t<float>(d, *static_cast<const AceTab<float>*>(tab), L, smem, grid, s);
+void launch_ace_f32(const Dev& d, const void* tab, int L, size_t smem, int grid, int wn, cudaStream_t s) {
+    ace_launch_t<float>(d, *static_cast<const AceTab<float>*>(tab), L, smem, grid, wn, s);
 }
 
 cudaError_t ace_batch_configure_f32(int L, int n, int cap, int tile_max, int qb, size_t* smem, int* grid) {

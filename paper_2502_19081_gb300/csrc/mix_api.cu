@@ -241,6 +241,7 @@ struct mix_ctx {
         o_seed, o_core, o_zsum;
     size_t ace_smem, spl_smem;
     int ace_grid, spl_grid;
+    int ace_wn;                       // warps (atoms) a CTA of the CUDA-core expensive kernel
     int ace_tcm;                      // 0: CUDA-core nu = 3; 1, 2: tensor-core readout (bf16, bf16 hi/lo)
     int ace_nbuf;                     // tile buffers of the tensor-core kernel
     int spl_lpa;                      // lanes per atom of the cheap kernel (32, 16 or 8)
@@ -610,7 +611,7 @@ void enqueue_evaluation(mix_ctx* c, cudaStream_t s, int integrate, double dt, in
     launch_spline(c->dev, st, c->precision, c->spl_lpa, c->spl_smem, c->spl_grid, c->aux);
     cudaEventRecord(c->ev_join, c->aux);
     if (c->ace_tcm) launch_ace_tc(c->dev, at, c->ace_tcm, c->L, c->ace_smem, c->ace_grid, c->ace_nbuf, s);
-    else launch_ace(c->dev, at, c->precision, c->L, c->ace_smem, c->ace_grid, s);
+    else launch_ace(c->dev, at, c->precision, c->L, c->ace_smem, c->ace_grid, c->ace_wn, s);
     if (prof) cudaEventRecordWithFlags(c->ev[4], s, ef);
     cudaStreamWaitEvent(s, c->ev_join, 0);
     if (prof) cudaEventRecordWithFlags(c->ev[5], s, ef);
@@ -877,11 +878,15 @@ int mix_init(const mix_system* sys, const mix_ace* a, const mix_spline* sp, cons
         return st;
     }
     layout(c);
+    // large float systems: CTAs of 4 warps share the coefficient tiles between
+    // twice the atoms, so more warps fit an SM (their expensive sets are many
+    // waves large); small sets keep groups of 2, which spread them more evenly
+    c->ace_wn = (c->precision != MIX_FP64 && sys->n_atoms >= 50000) ? ACE_MAX_WARPS : ACE_GROUP;
     cudaError_t e = c->ace_tcm
                         ? ace_tc_configure(c->ace_tcm, c->L, c->n, c->cap, c->tile_max, c->qb, &c->ace_smem,
                                            &c->ace_grid, &c->ace_nbuf)
                         : ace_configure(c->precision, c->L, c->n, c->cap, c->tile_max, c->qb, &c->ace_smem,
-                                        &c->ace_grid);
+                                        &c->ace_grid, c->ace_wn);
     if (e != cudaSuccess) {
         delete c;
         return e == cudaErrorInvalidValue ? MIX_EINVAL : MIX_ECUDA;
@@ -1224,7 +1229,7 @@ int mix_get_info(const mix_ctx* c, mix_info* info) {
     info->workspace_bytes = c->ws_bytes;
     info->exp_smem_bytes = c->ace_smem;
     info->exp_grid = c->ace_grid;
-    info->exp_threads = 32 * (c->ace_tcm ? TC_ACE_WARPS : (c->precision == MIX_FP64 ? ace_warps<double>() : ace_warps<float>()));
+    info->exp_threads = 32 * (c->ace_tcm ? TC_ACE_WARPS : c->ace_wn);
     info->cheap_smem_bytes = c->spl_smem;
     info->cheap_grid = c->spl_grid;
     info->launches_per_evaluation = evals_launches(c);

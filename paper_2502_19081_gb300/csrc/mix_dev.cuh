@@ -222,7 +222,12 @@ template <> struct Vec4<float> { using type = float4; };
 // atoms: at most 10 a SM against 12 with groups of 4); the float kernel's
 // ~36 KB of shared memory a CTA (Fe, n = 10, lmax = 4, 128 neighbour slots)
 // leaves room for 6 CTAs, the float64 kernel's ~71 KB for 3.
+// A single context's CTA may also hold 4 warps (ACE_MAX_WARPS): the two
+// tile buffers are then shared by twice the atoms, which lets more warps fit an
+// SM when the evaluated set is many waves large (the 256,000-atom cylinder:
+// 3 CTAs of 4 warps against 5 of 2).  The batched kernel keeps groups of 2.
 constexpr int ACE_GROUP = 2;
+constexpr int ACE_MAX_WARPS = 4;
 template <typename T>
 __host__ __device__ constexpr int ace_warps() {
     return ACE_GROUP;
@@ -230,6 +235,11 @@ __host__ __device__ constexpr int ace_warps() {
 template <typename T>
 __host__ __device__ constexpr int ace_min_ctas() {
     return sizeof(T) == 4 ? 6 : 2;
+}
+// the same register budget for CTAs of ACE_MAX_WARPS warps
+template <typename T>
+__host__ __device__ constexpr int ace_min_ctas_max() {
+    return ace_min_ctas<T>() * ACE_GROUP / ACE_MAX_WARPS;
 }
 // The tensor-core readout (float, bf16 operands) takes groups of 8 atoms, a
 // warp each: 8 x 16 rows (atom, m3) fill the M = 128 rows of one MMA tile.

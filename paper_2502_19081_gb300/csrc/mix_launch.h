@@ -13,13 +13,15 @@ void launch_build(const Dev& d, cudaStream_t s);
 void launch_sets(const Dev& d, const Regions& r, const SeedRule& sr, cudaStream_t s);
 int sets_launches(const SeedRule& sr);   // kernels launch_sets enqueues
 
-// expensive potential (k_ace.cuh, k_ace_f32.cu, k_ace_f64.cu); returns cudaSuccess or the launch error
-cudaError_t ace_configure(int precision, int L, int n, int cap, int tile_max, int qb, size_t* smem, int* grid);
-void launch_ace(const Dev& d, const void* tab, int precision, int L, size_t smem, int grid, cudaStream_t s);
-cudaError_t ace_configure_f32(int L, int n, int cap, int tile_max, int qb, size_t* smem, int* grid);
-cudaError_t ace_configure_f64(int L, int n, int cap, int tile_max, int qb, size_t* smem, int* grid);
-void launch_ace_f32(const Dev& d, const void* tab, int L, size_t smem, int grid, cudaStream_t s);
-void launch_ace_f64(const Dev& d, const void* tab, int L, size_t smem, int grid, cudaStream_t s);
+// expensive potential (k_ace.cuh, k_ace_f32.cu, k_ace_f64.cu); returns cudaSuccess or the launch error;
+// wn: warps (atoms) a CTA, ACE_GROUP or ACE_MAX_WARPS
+cudaError_t ace_configure(int precision, int L, int n, int cap, int tile_max, int qb, size_t* smem, int* grid,
+                          int wn);
+void launch_ace(const Dev& d, const void* tab, int precision, int L, size_t smem, int grid, int wn, cudaStream_t s);
+cudaError_t ace_configure_f32(int L, int n, int cap, int tile_max, int qb, size_t* smem, int* grid, int wn);
+cudaError_t ace_configure_f64(int L, int n, int cap, int tile_max, int qb, size_t* smem, int* grid, int wn);
+void launch_ace_f32(const Dev& d, const void* tab, int L, size_t smem, int grid, int wn, cudaStream_t s);
+void launch_ace_f64(const Dev& d, const void* tab, int L, size_t smem, int grid, int wn, cudaStream_t s);
 
 // expensive potential with the tensor-core readout (k_ace_tc.cu; float tables
 // with the bf16 operand sections): tcm 1 bf16, 2 bf16 hi/lo.  *nbuf: tile
