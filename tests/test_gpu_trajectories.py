@@ -9,8 +9,9 @@ exactly those positions.
 * Fe dumbbell (8,001 atoms): 1000 steps in float64 and in float, checkpoints
   every 100 steps;
 * screw cylinder (256,000 atoms): 64 sampled atoms (core, ramp, expensive
-  buffer, cheap only) at step 0 and after 100 steps in float64, and every 100
-  steps up to 500 with the bf16 hi/lo readout, the whole set compared exactly.
+  buffer, cheap only) at step 0 and after 100 steps in float64 and in float,
+  and every 100 steps up to 500 with the bf16 hi/lo readout, the whole set
+  compared exactly.
 """
 import numpy as np
 import pytest
@@ -60,7 +61,7 @@ def _sample(rng, lam, fl, k):
     return np.array(pick)
 
 
-@pytest.mark.parametrize("prec,tol,nblocks", [(0, 1e-10, 1), (3, 1e-3, 5)])
+@pytest.mark.parametrize("prec,tol,nblocks", [(0, 1e-10, 1), (1, 1e-3, 1), (3, 1e-3, 5)])
 def test_screw_cylinder_checkpoints(mx, prec, tol, nblocks):
     wl = I.fe_screw()
     ctx = mx.open_context(wl, precision=prec)
