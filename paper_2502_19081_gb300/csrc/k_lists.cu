@@ -171,6 +171,103 @@ __device__ __forceinline__ int pow2_cap(int cap) {
 
 constexpr int NB_RUNS = 18;
 
+// The candidate test of the list build: a float pre-filter (the float distance
+// is within 2e-5 relative of the float64 one for boxes up to a few thousand
+// Angstrom, so only candidates inside a +-2e-4 band around the threshold take
+// the exact float64 test, r^2 formed as in the oracle).
+struct NbTest {
+    float lo2, hi2;
+    float Lf[3], iLf[3];
+    __device__ __forceinline__ explicit NbTest(const Dev& d) {
+        lo2 = (float)(d.rlist2 * (1.0 - 2e-4));
+        hi2 = (float)(d.rlist2 * (1.0 + 2e-4));
+        for (int k = 0; k < 3; ++k) {
+            Lf[k] = (float)d.box.L[k];
+            iLf[k] = (float)d.box.invL[k];
+        }
+    }
+    __device__ __forceinline__ bool accept(const Dev& d, const double4& xi, const float4& xif, const float4& xjf,
+                                           int j) const {
+        float df[3] = {xjf.x - xif.x, xjf.y - xif.y, xjf.z - xif.z};
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            if (d.box.per[k]) df[k] -= Lf[k] * rintf(df[k] * iLf[k]);
+        const float r2f = df[0] * df[0] + df[1] * df[1] + df[2] * df[2];
+        if (r2f < lo2 && !d.exact_lists) return true;
+        if (r2f <= hi2 || d.exact_lists) {
+            double dd[3];
+            delta_rn(d.box, xi, d.x[j], dd);
+            return norm2_rn(dd) < d.rlist2;
+        }
+        return false;
+    }
+};
+
+// The runs of the 27-cell stencil of cell (cx, cy, cz): lane r < NB_RUNS gets
+// run r's first cell_atoms index t0 and length len (0 for an absent run):
+// rows (dz, dy) of three cells along x, one or two runs each.
+__device__ __forceinline__ void nb_run(const Dev& d, int cx, int cy, int cz, int lane, int& t0, int& len) {
+    const int ncx = d.cells.nc[0], ncy = d.cells.nc[1], ncz = d.cells.nc[2];
+    t0 = 0;
+    len = 0;
+    if (lane >= NB_RUNS) return;
+    const int rr = lane >> 1, run = lane & 1;
+    int qz = cz + rr / 3 - 1, qy = cy + rr % 3 - 1;
+    bool in = true;
+    if (d.box.per[2]) qz = (qz + ncz) % ncz;
+    else in = qz >= 0 && qz < ncz;
+    if (d.box.per[1]) qy = (qy + ncy) % ncy;
+    else in = in && qy >= 0 && qy < ncy;
+    // runs of cells along x: [a0, b0] and optionally [a1, b1]
+    int a0, b0, a1 = 1, b1 = 0;
+    if (d.box.per[0]) {
+        if (cx == 0) { a0 = 0; b0 = 1; a1 = ncx - 1; b1 = ncx - 1; }
+        else if (cx == ncx - 1) { a0 = ncx - 2; b0 = ncx - 1; a1 = 0; b1 = 0; }
+        else { a0 = cx - 1; b0 = cx + 1; }
+    } else {
+        a0 = cx > 0 ? cx - 1 : 0;
+        b0 = cx < ncx - 1 ? cx + 1 : ncx - 1;
+    }
+    const int ra = run == 0 ? a0 : a1, rb = run == 0 ? b0 : b1;
+    if (in && ra <= rb) {
+        const int row = (qz * ncy + qy) * ncx;
+        t0 = d.cell_start[row + ra];
+        len = d.cell_start[row + rb + 1] - t0;
+    }
+}
+
+// The row of atom i from its cnt accepted candidates in buf (this warp's
+// capp2 ints): capacity check, then each lane ranks its entries among the row
+// (atom indices are distinct) and stores them at their sorted places.
+__device__ __forceinline__ void nb_write_row(const Dev& d, int64_t i, const double4& xi, int cnt, int* buf, int lane) {
+    const int cap = d.cap;
+    if (lane == 0) {
+        atomicMax(d.status + SW_MAXNB, cnt);
+        if (cnt > cap) set_status(d.status, ST_NBR_OVERFLOW);
+    }
+    const int mlen = cnt < cap ? cnt : cap;
+    // pad to whole 4-vectors with INT_MAX (ranks unaffected): m4 <= capp2
+    const int m4 = (mlen + 3) & ~3;
+    if (mlen + lane < m4) buf[mlen + lane] = INT_MAX;
+    __syncwarp();
+    int* row = d.nbr + i * (int64_t)cap;
+    const int4* b4 = reinterpret_cast<const int4*>(buf);
+    for (int p = lane; p < mlen; p += 32) {
+        const int v = buf[p];
+        int rank = 0;
+        for (int q = 0; q < (m4 >> 2); ++q) {
+            const int4 w = b4[q];
+            rank += (w.x < v) + (w.y < v) + (w.z < v) + (w.w < v);
+        }
+        row[rank] = v;
+    }
+    if (lane == 0) {
+        d.nnb[i] = mlen;
+        d.xb[i] = xi;
+    }
+    __syncwarp();
+}
+
 // AHEAD2: also load the float positions a pass ahead (the batched kernel; the
 // single-context one, on longer candidate runs, measured faster without)
 template <bool AHEAD2>
@@ -183,45 +280,15 @@ __device__ __forceinline__ void neigh_build_body(const Dev& d, int bx, int gx, i
     int* runx = s_runx[warp];
     int* runi = s_runi[warp];
     const unsigned lt = (1u << lane) - 1u;
-    const int ncx = d.cells.nc[0], ncy = d.cells.nc[1], ncz = d.cells.nc[2];
-    const int cap = d.cap;
-    // float pre-filter: the float distance is within 2e-5 relative of the
-    // float64 one for boxes up to a few thousand Angstrom, so only candidates
-    // inside a +-2e-4 band around the threshold need the exact float64 test
-    const float lo2 = (float)(d.rlist2 * (1.0 - 2e-4)), hi2 = (float)(d.rlist2 * (1.0 + 2e-4));
-    const float Lf[3] = {(float)d.box.L[0], (float)d.box.L[1], (float)d.box.L[2]};
-    const float iLf[3] = {(float)d.box.invL[0], (float)d.box.invL[1], (float)d.box.invL[2]};
+    const int ncx = d.cells.nc[0], ncy = d.cells.nc[1];
+    const NbTest test(d);
     for (int64_t i = (int64_t)bx * NB_WARPS + warp; i < d.n; i += (int64_t)gx * NB_WARPS) {
         const double4 xi = d.x[i];
         const float4 xif = d.xf[i];
         const int c = d.cell_of[i];
         const int cx = c % ncx, cy = (c / ncx) % ncy, cz = c / (ncx * ncy);
-        int len = 0, t0 = 0;
-        if (lane < NB_RUNS) {
-            const int rr = lane >> 1, run = lane & 1;
-            int qz = cz + rr / 3 - 1, qy = cy + rr % 3 - 1;
-            bool in = true;
-            if (d.box.per[2]) qz = (qz + ncz) % ncz;
-            else in = qz >= 0 && qz < ncz;
-            if (d.box.per[1]) qy = (qy + ncy) % ncy;
-            else in = in && qy >= 0 && qy < ncy;
-            // runs of cells along x: [a0, b0] and optionally [a1, b1]
-            int a0, b0, a1 = 1, b1 = 0;
-            if (d.box.per[0]) {
-                if (cx == 0) { a0 = 0; b0 = 1; a1 = ncx - 1; b1 = ncx - 1; }
-                else if (cx == ncx - 1) { a0 = ncx - 2; b0 = ncx - 1; a1 = 0; b1 = 0; }
-                else { a0 = cx - 1; b0 = cx + 1; }
-            } else {
-                a0 = cx > 0 ? cx - 1 : 0;
-                b0 = cx < ncx - 1 ? cx + 1 : ncx - 1;
-            }
-            const int ra = run == 0 ? a0 : a1, rb = run == 0 ? b0 : b1;
-            if (in && ra <= rb) {
-                const int row = (qz * ncy + qy) * ncx;
-                t0 = d.cell_start[row + ra];
-                len = d.cell_start[row + rb + 1] - t0;
-            }
-        }
+        int len, t0;
+        nb_run(d, cx, cy, cz, lane, t0, len);
         int inc = len;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -268,18 +335,7 @@ __device__ __forceinline__ void neigh_build_body(const Dev& d, int bx, int gx, i
             bool ok = false;
             if (u < total && j != (int)i) {
                 if (!AHEAD2) xjf = d.xf[j];
-                float df[3] = {xjf.x - xif.x, xjf.y - xif.y, xjf.z - xif.z};
-#pragma unroll
-                for (int k = 0; k < 3; ++k)
-                    if (d.box.per[k]) df[k] -= Lf[k] * rintf(df[k] * iLf[k]);
-                const float r2f = df[0] * df[0] + df[1] * df[1] + df[2] * df[2];
-                if (r2f < lo2 && !d.exact_lists) {
-                    ok = true;
-                } else if (r2f <= hi2 || d.exact_lists) {
-                    double dd[3];
-                    delta_rn(d.box, xi, d.x[j], dd);
-                    ok = norm2_rn(dd) < d.rlist2;
-                }
+                ok = test.accept(d, xi, xif, xjf, j);
             }
             const unsigned m = __ballot_sync(0xffffffffu, ok);
             if (ok) {
@@ -288,37 +344,105 @@ __device__ __forceinline__ void neigh_build_body(const Dev& d, int bx, int gx, i
             }
             cnt += __popc(m);
         }
-        if (lane == 0) {
-            atomicMax(d.status + SW_MAXNB, cnt);
-            if (cnt > cap) set_status(d.status, ST_NBR_OVERFLOW);
-        }
-        const int mlen = cnt < cap ? cnt : cap;
-        // pad to whole 4-vectors with INT_MAX (ranks unaffected): m4 <= capp2
-        const int m4 = (mlen + 3) & ~3;
-        if (mlen + lane < m4) buf[mlen + lane] = INT_MAX;
-        __syncwarp();
-        int* row = d.nbr + i * (int64_t)cap;
-        const int4* b4 = reinterpret_cast<const int4*>(buf);
-        for (int p = lane; p < mlen; p += 32) {
-            const int v = buf[p];
-            int rank = 0;
-            for (int q = 0; q < (m4 >> 2); ++q) {
-                const int4 w = b4[q];
-                rank += (w.x < v) + (w.y < v) + (w.z < v) + (w.w < v);
-            }
-            row[rank] = v;
-        }
-        if (lane == 0) {
-            d.nnb[i] = mlen;
-            d.xb[i] = xi;
-        }
-        __syncwarp();
+        nb_write_row(d, i, xi, cnt, buf, lane);
     }
 }
 
 __global__ void __launch_bounds__(NB_WARPS * 32) k_neigh_build(Dev d, int capp2) {
     extern __shared__ __align__(16) int sbuf[];
     neigh_build_body<false>(d, blockIdx.x, gridDim.x, capp2, sbuf);
+}
+
+// The list build of a single context with neighbour-cell tiles staged in shared
+// memory: a CTA takes a cell at a time, copies the candidates of its 27-cell
+// stencil (atom index and float position, in run order) into shared memory
+// once, and its warps take the cell's atoms, a warp per atom, testing 32
+// staged candidates at a time; the candidates cross L2 once per cell instead
+// of once per atom.  A stencil with more than NB_TILE candidates (a dense
+// spot) is tested from global memory instead.  The same test and row writing
+// as the batched build (neigh_build_body), so the rows are the same.
+constexpr int NB_TILE = 1024;
+
+inline size_t nb_tiled_smem(int capp2) {
+    return (size_t)NB_TILE * (sizeof(float4) + sizeof(int)) + (size_t)NB_WARPS * capp2 * sizeof(int);
+}
+
+__global__ void __launch_bounds__(NB_WARPS * 32) k_neigh_build_tiled(Dev d, int capp2) {
+    if (d.status[SW_REBUILD] == 0) return;
+    extern __shared__ __align__(16) unsigned char nb_smem[];
+    float4* tpos = reinterpret_cast<float4*>(nb_smem);
+    int* tidx = reinterpret_cast<int*>(tpos + NB_TILE);
+    int* sbuf = tidx + NB_TILE;
+    __shared__ int s_runx[NB_RUNS], s_runi[NB_RUNS];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int* buf = sbuf + warp * capp2;
+    const unsigned lt = (1u << lane) - 1u;
+    const int ncx = d.cells.nc[0], ncy = d.cells.nc[1];
+    const int ncell = d.cells.ncell;
+    const NbTest test(d);
+    for (int c = blockIdx.x; c < ncell; c += gridDim.x) {
+        const int a0 = d.cell_start[c], a1 = d.cell_start[c + 1];
+        if (a0 == a1) continue;   // the same for the whole CTA
+        const int cx = c % ncx, cy = (c / ncx) % ncy, cz = c / (ncx * ncy);
+        if (warp == 0) {
+            int t0, len;
+            nb_run(d, cx, cy, cz, lane, t0, len);
+            int inc = len;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += v;
+            }
+            if (lane < NB_RUNS) {
+                s_runi[lane] = inc;
+                s_runx[lane] = t0 - (inc - len);
+            }
+        }
+        __syncthreads();
+        const int total = s_runi[NB_RUNS - 1];
+        const bool staged = total <= NB_TILE;
+        if (staged) {
+            for (int t = threadIdx.x; t < total; t += blockDim.x) {
+                int r = 0;
+                while (t >= s_runi[r]) ++r;
+                const int j = d.cell_atoms[s_runx[r] + t];
+                tidx[t] = j;
+                tpos[t] = d.xf[j];
+            }
+        }
+        __syncthreads();
+        for (int a = a0 + warp; a < a1; a += NB_WARPS) {
+            const int i = d.cell_atoms[a];
+            const double4 xi = d.x[i];
+            const float4 xif = d.xf[i];
+            int cnt = 0;
+            int r = 0;
+            for (int u = lane; u - lane < total; u += 32) {
+                bool ok = false;
+                int j = -1;
+                if (u < total) {
+                    float4 xjf;
+                    if (staged) {
+                        j = tidx[u];
+                        xjf = tpos[u];
+                    } else {
+                        while (u >= s_runi[r]) ++r;
+                        j = d.cell_atoms[s_runx[r] + u];
+                        xjf = d.xf[j];
+                    }
+                    if (j != i) ok = test.accept(d, xi, xif, xjf, j);
+                }
+                const unsigned m = __ballot_sync(0xffffffffu, ok);
+                if (ok) {
+                    const int p = cnt + __popc(m & lt);
+                    if (p < capp2) buf[p] = j;
+                }
+                cnt += __popc(m);
+            }
+            nb_write_row(d, i, xi, cnt, buf, lane);
+        }
+        __syncthreads();   // the tile and the runs are rewritten for the next cell
+    }
 }
 
 // rev[i][s] = position of i in the row of j = nbr[i][s] (binary search in the
@@ -418,10 +542,21 @@ void launch_build(const Dev& d, cudaStream_t s) {
     k_cell_fill<<<nb > 0 ? nb : 1, 256, 0, s>>>(d);
     int capp2 = 32;
     while (capp2 < d.cap) capp2 <<= 1;
-    int64_t want = (d.n + NB_WARPS - 1) / NB_WARPS;
-    int64_t lim = d.grid_build > 0 ? d.grid_build : (int64_t)sm_count() * 16;
-    int grid = (int)(want < lim ? want : lim);
-    k_neigh_build<<<grid > 0 ? grid : 1, NB_WARPS * 32, NB_WARPS * capp2 * sizeof(int), s>>>(d, capp2);
+    // Cells to spare (at least 8 an SM, e.g. 24,000 for the 256,000-atom
+    // cylinder): a CTA a cell with the stencil's candidates staged in shared
+    // memory (C3's full build 631 -> 477 us).  Few cells (324 for the 8,001-atom
+    // dumbbell): a warp per atom over every SM instead (32 against 58 us there).
+    if (d.cells.ncell >= 8 * sm_count()) {
+        const int64_t want = d.cells.ncell;
+        const int64_t lim = d.grid_build > 0 ? d.grid_build : (int64_t)sm_count() * 8;
+        const int grid = (int)(want < lim ? want : lim);
+        k_neigh_build_tiled<<<grid > 0 ? grid : 1, NB_WARPS * 32, nb_tiled_smem(capp2), s>>>(d, capp2);
+    } else {
+        const int64_t want = (d.n + NB_WARPS - 1) / NB_WARPS;
+        const int64_t lim = d.grid_build > 0 ? d.grid_build : (int64_t)sm_count() * 16;
+        const int grid = (int)(want < lim ? want : lim);
+        k_neigh_build<<<grid > 0 ? grid : 1, NB_WARPS * 32, NB_WARPS * capp2 * sizeof(int), s>>>(d, capp2);
+    }
     const int nr = (int)((d.n + 7) / 8);   // a warp per atom
     k_neigh_rev<<<nr > 0 ? nr : 1, 256, 0, s>>>(d);
 }

@@ -78,6 +78,40 @@ def test_lists_and_cells_bit_exact(mx, name):
         assert np.all(nbr[js, rev[i, :nnb[i]]] == i)
 
 
+def _rows_equal(nnb, nbr, onnb, onbr):
+    """Sorted rows equal, compared as whole padded arrays."""
+    if not np.array_equal(nnb, onnb):
+        return False
+    w = int(nnb.max()) if len(nnb) else 0
+    cols = np.arange(w)[None, :]
+    a = np.where(cols < nnb[:, None], nbr[:, :w], -1)
+    b = np.where(cols < onnb[:, None], onbr[:, :w], -1)
+    return bool(np.array_equal(a, b))
+
+
+@pytest.mark.parametrize("kind", ["fe_box_40x40x20", "si_12cubed"])
+def test_lists_bit_exact_cell_tiled_build(mx, kind):
+    """Systems with at least 8 cells an SM take the build that stages each
+    cell's stencil in shared memory: a bcc Fe box of 64,000 atoms (3,249
+    cells) and the Si 12^3 cell (1,728 cells)."""
+    if kind == "fe_box_40x40x20":
+        wl = I.small_fe_box(41, nx=40, ny=40, nz=20, r_core=6.0, ramp=3.0)
+    else:
+        wl = I.si_vacancy(ncell=12, sigma=0.1)
+    s = wl.system
+    ctx = mx.open_context(wl)
+    x, _, _, _ = ctx.get_state()
+    nnb, nbr, rev = ctx.neighbours()
+    onnb, onbr = oracle.neighbours(x, s.box_lo, s.box_len, s.periodic, _rlist(wl), cap=256)
+    assert _rows_equal(nnb, nbr, onnb, onbr)
+    for i in range(0, s.n, 97):
+        js = nbr[i, :nnb[i]]
+        assert np.all(nbr[js, rev[i, :nnb[i]]] == i)
+    fl, _, _ = ctx.sets()
+    assert np.array_equal(fl, oracle.Model(wl).sets(x))
+    ctx.close()
+
+
 @pytest.mark.parametrize("name", CASES)
 def test_lambda_and_sets_bit_exact(mx, name):
     wl = _wl(name)
