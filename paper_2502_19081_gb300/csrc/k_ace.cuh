@@ -259,23 +259,53 @@ __device__ __forceinline__ void tile_fetch(const unsigned char* tiles, const int
     cp_async_commit();
 }
 
-// Reduce-scatter of 16 values over the warp: returns, in every lane, the sum
-// over all 32 lanes of entry (lane >> 1) & 15 (each sum is held by two lanes):
-// four halving exchanges (8 + 4 + 2 + 1 shuffles) and a last pairwise sum, in
-// a fixed order.
-template <typename T>
-__device__ __forceinline__ T warp_reduce_scatter16(T (&v)[16], int lane) {
+// Reduce-scatter of C <= 16 per-lane values over the warp.  At lane bit MASK
+// (16, 8, 4, 2, 1 in turn) the lanes with the bit set keep the upper half of
+// their block (padded with a zero when the count is odd) and send the lower
+// half to their partner, the others the reverse, and each adds what it
+// receives, so the count halves at every bit; once one value is left the
+// remaining bits sum it (both partners add the same two numbers).  The
+// additions are in a fixed order.  rs_entry gives the entry a lane ends with.
+template <typename T, int C, int MASK>
+__device__ __forceinline__ T warp_rs(T* v, int lane) {
+    if constexpr (MASK == 0) {
+        return v[0];
+    } else if constexpr (C == 1) {
+        v[0] += __shfl_xor_sync(0xffffffffu, v[0], MASK);
+        return warp_rs<T, 1, MASK / 2>(v, lane);
+    } else {
+        constexpr int H = (C + 1) / 2;
+        const bool up = (lane & MASK) != 0;
 #pragma unroll
-    for (int h = 8; h >= 1; h >>= 1) {
-        const bool up = (lane & (2 * h)) != 0;
-#pragma unroll
-        for (int i = 0; i < h; ++i) {
-            const T send = up ? v[i] : v[i + h];
-            const T keep = up ? v[i + h] : v[i];
-            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 2 * h);
+        for (int i = 0; i < H; ++i) {
+            const T hi = i + H < C ? v[i + H] : T(0);
+            const T send = up ? v[i] : hi;
+            const T keep = up ? hi : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, MASK);
         }
+        return warp_rs<T, H, MASK / 2>(v, lane);
     }
-    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+// The entry of warp_rs<T, C, 16> a lane holds (idx), and whether the lane is
+// the one of its group that writes it (a real entry, the lowest lane of the
+// lanes that hold the same sum).
+template <int C, int MASK>
+__device__ __forceinline__ void rs_entry(int lane, int& idx, int& real, bool& writer) {
+    if constexpr (MASK == 0) {
+        writer = real >= 1;
+    } else if constexpr (C == 1) {
+        writer = real >= 1 && (lane & (2 * MASK - 1)) == 0;
+    } else {
+        constexpr int H = (C + 1) / 2;
+        if (lane & MASK) {
+            idx += H;
+            real = real > H ? real - H : 0;
+        } else {
+            real = real < H ? real : H;
+        }
+        rs_entry<H, MASK / 2>(lane, idx, real, writer);
+    }
 }
 
 // nu = 3 of one l-triple for this warp's atom, in one pass over lane units
@@ -295,24 +325,20 @@ __device__ __forceinline__ T warp_reduce_scatter16(T (&v)[16], int lane) {
 //             partials of the units of one q1 are summed after the last m3;
 // and, for distinct l's only (omega2 needs it after the pass), stores U.
 // All three l's equal: U is not formed (no adjoint needs it) and the energy is
-// taken as sum A3 (W^T Z), the same sum reordered.
-//
-// TCM != 0 (float only; the tensor-core readout): omega3 and the energy are
-// not formed here.  Z goes, rounded to bf16 (TCM == 2: also its remainder, the
-// lo part), into this atom's rows of the MMA operand tile (row m3, column
-// q1 n + q2 of the K-major layout of tc.cuh), from which the tensor cores form
-// V = Z W (omega3 = mult3 V, E = sum A3 V) after the pass.
-template <typename T, int NP, int QB, int TCM = 0>
+// taken as sum A3 (W^T Z), the same sum reordered.  This is the float64 pass;
+// float runs nu3_units_f, the same arithmetic on packed pairs.
+template <typename T, int NP, int QB>
 __device__ __forceinline__ void nu3_units(const AceTileHdr& h, const T* W, const GEnt<T>* ge, const int* g3o,
                                           const T* A1, const T* A2, const T* A3, int n, int lane, T* U1, T* P1,
-                                          T* o3, T mult3, T& ep, unsigned char* zhi = nullptr,
-                                          unsigned char* zlo = nullptr, int zsbo = 0) {
+                                          T* o3, T mult3, T& ep) {
     constexpr int nqb = NP / QB;
     const int units = n * nqb;
     const int d3 = 2 * h.l3 + 1;
     const bool withu = h.mode != 3;
     const bool keepu = h.mode == 0;
-    const int q3o = (lane >> 1) & 15;   // the omega3 entry this lane receives
+    int q3o = 0, q3real = NP;           // the omega3 entry this lane receives
+    bool q3w = false;
+    rs_entry<NP, 16>(lane, q3o, q3real, q3w);
     for (int u0 = 0; u0 < units; u0 += 32) {
         const int u = u0 + lane;
         const bool uv = u < units;
@@ -386,13 +412,152 @@ __device__ __forceinline__ void nu3_units(const AceTileHdr& h, const T* W, const
             }
             if (withu) {
                 if (cur >= 0 && uv) P1[cur * units + u] += c1;
-                if constexpr (TCM == 0) {
 #pragma unroll
-                    for (int r = 0; r < QB; ++r) ep += uo[r] * z[r];
-                }
+                for (int r = 0; r < QB; ++r) ep += uo[r] * z[r];
                 if (keepu && uv) {
 #pragma unroll
                     for (int r = 0; r < QB; ++r) U1[(m3 * n + q1) * NP + q2 + r] = uo[r];
+                }
+            }
+            // omega3 row m3
+            T pv[16];
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                T s = T(0);
+#pragma unroll
+                for (int r = 0; r < QB; ++r) s += w[r][q] * z[r];
+                pv[q] = s;
+            }
+            const T s3 = warp_rs<T, NP, 16>(pv, lane);
+            if (q3w && q3o < n) {
+                o3[m3 * NP + q3o] += mult3 * s3;
+                if (!withu) ep += A3[m3 * NP + q3o] * s3;
+            }
+        }
+    }
+}
+
+// QB / 2 pairs of consecutive floats from shared memory (QB in {2, 4, 6},
+// 8-byte aligned; QB = 4 16-byte aligned)
+template <int QB>
+__device__ __forceinline__ void ld_pairs(const float* p, float2* out) {
+    if constexpr (QB == 4) {
+        const float4 v = *reinterpret_cast<const float4*>(p);
+        out[0] = make_float2(v.x, v.y);
+        out[1] = make_float2(v.z, v.w);
+    } else {
+#pragma unroll
+        for (int k = 0; k < QB / 2; ++k) out[k] = reinterpret_cast<const float2*>(p)[k];
+    }
+}
+
+// The float unit pass: the arithmetic of nu3_units on packed pairs
+// (__ffma2_rn: two float fused multiply-adds an instruction), which halves the
+// instructions of its dense products.  W rows are held as pairs of
+// consecutive q3: U = W A3 runs as two interleaved sums (even and odd q3)
+// added at the end, and the omega3 partials pair consecutive q3 against a
+// broadcast Z (the same order of additions as the float64 pass).  Z, the
+// omega1 dot product and the energy pair consecutive q2.
+//
+// TCM != 0 (the tensor-core readout): omega3 and the energy are not formed
+// here.  Z goes, rounded to bf16 (TCM == 2: also its remainder, the lo part),
+// into this atom's rows of the MMA operand tile (row m3, column q1 n + q2 of
+// the K-major layout of tc.cuh), from which the tensor cores form V = Z W
+// (omega3 = mult3 V, E = sum A3 V) after the pass.
+template <int NP, int QB, int TCM>
+__device__ __forceinline__ void nu3_units_f(const AceTileHdr& h, const float* W, const GEnt<float>* ge,
+                                            const int* g3o, const float* A1, const float* A2, const float* A3,
+                                            int n, int lane, float* U1, float* P1, float* o3, float mult3,
+                                            float& ep, unsigned char* zhi, unsigned char* zlo, int zsbo) {
+    static_assert(QB % 2 == 0 && NP % 4 == 0, "the float pass works on pairs");
+    constexpr int nqb = NP / QB, NH = NP / 2, QH = QB / 2;
+    const int units = n * nqb;
+    const int d3 = 2 * h.l3 + 1;
+    const bool withu = h.mode != 3;
+    const bool keepu = h.mode == 0;
+    int q3o = 0, q3real = NP;
+    bool q3w = false;
+    rs_entry<NP, 16>(lane, q3o, q3real, q3w);
+    float2 e2 = make_float2(0.f, 0.f);
+    for (int u0 = 0; u0 < units; u0 += 32) {
+        const int u = u0 + lane;
+        const bool uv = u < units;
+        const int uu = uv ? u : 0;
+        const int q1 = uu / nqb;
+        const int q2 = (uu - q1 * nqb) * QB;
+        float2 w[QB][NH];
+#pragma unroll
+        for (int r = 0; r < QB; ++r) {
+            const bool ok = uv && q2 + r < n;
+            const float* wr = W + (q1 * n + (ok ? q2 + r : 0)) * NP;
+#pragma unroll
+            for (int p = 0; p < NP; p += 4) {
+                float4 v = *reinterpret_cast<const float4*>(wr + p);
+                if (!ok) v = make_float4(0.f, 0.f, 0.f, 0.f);
+                w[r][p / 2] = make_float2(v.x, v.y);
+                w[r][p / 2 + 1] = make_float2(v.z, v.w);
+            }
+        }
+        for (int m3 = 0; m3 < d3; ++m3) {
+            float2 uo[QH], z[QH];
+#pragma unroll
+            for (int k = 0; k < QH; ++k) {
+                uo[k] = make_float2(0.f, 0.f);
+                z[k] = make_float2(0.f, 0.f);
+            }
+            if (withu) {
+                float2 a[NH];
+#pragma unroll
+                for (int p = 0; p < NP; p += 4) {
+                    const float4 v = *reinterpret_cast<const float4*>(A3 + m3 * NP + p);
+                    a[p / 2] = make_float2(v.x, v.y);
+                    a[p / 2 + 1] = make_float2(v.z, v.w);
+                }
+#pragma unroll
+                for (int r = 0; r < QB; ++r) {
+                    float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int j = 0; j < NH; ++j) s = __ffma2_rn(w[r][j], a[j], s);
+                    if (r & 1) uo[r / 2].y = s.x + s.y;
+                    else uo[r / 2].x = s.x + s.y;
+                }
+            }
+            const int e1 = g3o[m3 + 1];
+            int cur = -1;
+            float2 c1 = make_float2(0.f, 0.f);
+            for (int e = g3o[m3]; e < e1; ++e) {
+                int pk;
+                float g;
+                ld_gent(ge + e, pk, g);
+                const int m1 = pk & 255;
+                const float ga = g * A1[m1 * NP + q1];
+                const float2 ga2 = make_float2(ga, ga);
+                float2 a2[QH];
+                ld_pairs<QB>(A2 + (pk >> 8) * NP + q2, a2);
+#pragma unroll
+                for (int k = 0; k < QH; ++k) z[k] = __ffma2_rn(ga2, a2[k], z[k]);
+                if (withu) {
+                    if (m1 != cur) {   // uniform over the warp
+                        if (cur >= 0 && uv) P1[cur * units + u] += c1.x + c1.y;
+                        c1 = make_float2(0.f, 0.f);
+                        cur = m1;
+                    }
+                    float2 dd = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int k = 0; k < QH; ++k) dd = __ffma2_rn(a2[k], uo[k], dd);
+                    c1 = __ffma2_rn(make_float2(g, g), dd, c1);
+                }
+            }
+            if (withu) {
+                if (cur >= 0 && uv) P1[cur * units + u] += c1.x + c1.y;
+                if constexpr (TCM == 0) {
+#pragma unroll
+                    for (int k = 0; k < QH; ++k) e2 = __ffma2_rn(uo[k], z[k], e2);
+                }
+                if (keepu && uv) {
+#pragma unroll
+                    for (int k = 0; k < QH; ++k)
+                        *reinterpret_cast<float2*>(U1 + (m3 * n + q1) * NP + q2 + 2 * k) = uo[k];
                 }
             }
             if constexpr (TCM != 0) {
@@ -400,35 +565,39 @@ __device__ __forceinline__ void nu3_units(const AceTileHdr& h, const T* W, const
 #pragma unroll
                     for (int r = 0; r < QB; ++r) {
                         if (q2 + r < n) {
+                            const float zr = (r & 1) ? z[r / 2].y : z[r / 2].x;
                             const int o = tc_off(m3, q1 * n + q2 + r, TC_LBO_A, zsbo);
-                            const __nv_bfloat16 hi = __float2bfloat16_rn((float)z[r]);
+                            const __nv_bfloat16 hi = __float2bfloat16_rn(zr);
                             *reinterpret_cast<__nv_bfloat16*>(zhi + o) = hi;
                             if constexpr (TCM == 2)
                                 *reinterpret_cast<__nv_bfloat16*>(zlo + o) =
-                                    __float2bfloat16_rn((float)z[r] - __bfloat162float(hi));
+                                    __float2bfloat16_rn(zr - __bfloat162float(hi));
                         }
                     }
                 }
             } else {
-            // omega3 row m3
-            T pv[16];
+                // omega3 row m3
+                float pv[16];
 #pragma unroll
-            for (int q = 0; q < 16; ++q) {
-                T s = T(0);
-                if (q < NP) {
+                for (int j = 0; j < NH; ++j) {
+                    float2 s = make_float2(0.f, 0.f);
 #pragma unroll
-                    for (int r = 0; r < QB; ++r) s += w[r][q < NP ? q : 0] * z[r];
+                    for (int r = 0; r < QB; ++r) {
+                        const float zr = (r & 1) ? z[r / 2].y : z[r / 2].x;
+                        s = __ffma2_rn(w[r][j], make_float2(zr, zr), s);
+                    }
+                    pv[2 * j] = s.x;
+                    pv[2 * j + 1] = s.y;
                 }
-                pv[q] = s;
-            }
-            const T s3 = warp_reduce_scatter16<T>(pv, lane);
-            if ((lane & 1) == 0 && q3o < n) {
-                o3[m3 * NP + q3o] += mult3 * s3;
-                if (!withu) ep += A3[m3 * NP + q3o] * s3;
-            }
+                const float s3 = warp_rs<float, NP, 16>(pv, lane);
+                if (q3w && q3o < n) {
+                    o3[m3 * NP + q3o] += mult3 * s3;
+                    if (!withu) ep += A3[m3 * NP + q3o] * s3;
+                }
             }
         }
     }
+    ep += e2.x + e2.y;
 }
 
 // One l-triple for this warp's atom, from the tile in shared memory.
@@ -456,22 +625,26 @@ __device__ __forceinline__ void nu3_tile(const unsigned char* tile, const AceTab
     T* o3 = om + h.l3 * h.l3 * NP;
     const int qb = tab.qb;
     if constexpr ((PART & 1) != 0) {
-    bool done = false;
-    if constexpr (sizeof(T) == 4 && NP == 12) {
-        // n = 11 or 12: 6-wide blocks keep the units within one warp pass
-        if (qb == 6) {
-            nu3_units<T, NP, 6, TCM>(h, W, ge, g3o, A1, A2, A3, n, lane, U1, P1, o3, mult3, ep, zhi, zlo, zsbo);
-            done = true;
+        if constexpr (sizeof(T) == 4) {
+            if constexpr (NP == 12) {
+                // n = 11 or 12: 6-wide blocks keep the units within one warp pass
+                if (qb == 6)
+                    nu3_units_f<NP, 6, TCM>(h, W, ge, g3o, A1, A2, A3, n, lane, U1, P1, o3, mult3, ep, zhi, zlo,
+                                            zsbo);
+            }
+            if (qb == QM)
+                nu3_units_f<NP, QM, TCM>(h, W, ge, g3o, A1, A2, A3, n, lane, U1, P1, o3, mult3, ep, zhi, zlo, zsbo);
+            else if (qb == QM / 2)
+                nu3_units_f<NP, QM / 2, TCM>(h, W, ge, g3o, A1, A2, A3, n, lane, U1, P1, o3, mult3, ep, zhi, zlo,
+                                             zsbo);
+        } else {
+            static_assert(sizeof(T) == 4 || TCM == 0, "the tensor-core readout is float only");
+            if (qb == QM)
+                nu3_units<T, NP, QM>(h, W, ge, g3o, A1, A2, A3, n, lane, U1, P1, o3, mult3, ep);
+            else
+                nu3_units<T, NP, QM / 2>(h, W, ge, g3o, A1, A2, A3, n, lane, U1, P1, o3, mult3, ep);
         }
-    }
-    if (!done) {
-        if (qb == QM)
-            nu3_units<T, NP, QM, TCM>(h, W, ge, g3o, A1, A2, A3, n, lane, U1, P1, o3, mult3, ep, zhi, zlo, zsbo);
-        else
-            nu3_units<T, NP, QM / 2, TCM>(h, W, ge, g3o, A1, A2, A3, n, lane, U1, P1, o3, mult3, ep, zhi, zlo,
-                                          zsbo);
-    }
-    __syncwarp();
+        __syncwarp();
     }
     if constexpr ((PART & 2) == 0) return;
     // omega1 (equal to omega3 when all three l's coincide): sum the unit
@@ -654,10 +827,20 @@ __device__ __forceinline__ void ace_group(const Dev& d, const AceTab<T>& tab, in
                     for (int kl = 0; kl < kc; ++kl) {
                         const T y = cY[kl * NLM + lm];
                         const V4<T> r4 = ld4<T>(cR + kl * NP + q4);
-                        acc[j][0] += y * r4.x;
-                        acc[j][1] += y * r4.y;
-                        acc[j][2] += y * r4.z;
-                        acc[j][3] += y * r4.w;
+                        if constexpr (sizeof(T) == 4) {
+                            const float2 yy = make_float2(y, y);
+                            const float2 lo = __ffma2_rn(yy, make_float2(r4.x, r4.y), make_float2(acc[j][0], acc[j][1]));
+                            const float2 hi = __ffma2_rn(yy, make_float2(r4.z, r4.w), make_float2(acc[j][2], acc[j][3]));
+                            acc[j][0] = lo.x;
+                            acc[j][1] = lo.y;
+                            acc[j][2] = hi.x;
+                            acc[j][3] = hi.y;
+                        } else {
+                            acc[j][0] += y * r4.x;
+                            acc[j][1] += y * r4.y;
+                            acc[j][2] += y * r4.z;
+                            acc[j][3] += y * r4.w;
+                        }
                     }
                 }
             }
@@ -807,11 +990,27 @@ __device__ __forceinline__ void ace_group(const Dev& d, const AceTab<T>& tab, in
                     const int lm = l * l + l + mm;
                     const T* orow = om + lm * NP;
                     T rho = T(0), sig = T(0);
+                    if constexpr (sizeof(T) == 4) {
+                        // even and odd q in packed pairs, added at the end
+                        float2 rr = make_float2(0.f, 0.f), ss = make_float2(0.f, 0.f);
 #pragma unroll
-                    for (int p = 0; p < NP; p += 4) {
-                        const V4<T> o4 = ld4<T>(orow + p);
-                        rho += o4.x * R[p] + o4.y * R[p + 1] + o4.z * R[p + 2] + o4.w * R[p + 3];
-                        sig += o4.x * dR[p] + o4.y * dR[p + 1] + o4.z * dR[p + 2] + o4.w * dR[p + 3];
+                        for (int p = 0; p < NP; p += 4) {
+                            const V4<T> o4 = ld4<T>(orow + p);
+                            const float2 olo = make_float2(o4.x, o4.y), ohi = make_float2(o4.z, o4.w);
+                            rr = __ffma2_rn(olo, make_float2(R[p], R[p + 1]), rr);
+                            rr = __ffma2_rn(ohi, make_float2(R[p + 2], R[p + 3]), rr);
+                            ss = __ffma2_rn(olo, make_float2(dR[p], dR[p + 1]), ss);
+                            ss = __ffma2_rn(ohi, make_float2(dR[p + 2], dR[p + 3]), ss);
+                        }
+                        rho = rr.x + rr.y;
+                        sig = ss.x + ss.y;
+                    } else {
+#pragma unroll
+                        for (int p = 0; p < NP; p += 4) {
+                            const V4<T> o4 = ld4<T>(orow + p);
+                            rho += o4.x * R[p] + o4.y * R[p + 1] + o4.z * R[p + 2] + o4.w * R[p + 3];
+                            sig += o4.x * dR[p] + o4.y * dR[p + 1] + o4.z * dR[p + 2] + o4.w * dR[p + 3];
+                        }
                     }
                     const int mu = mm < 0 ? -mm : mm;
                     const T kk = __ldg(K + lm);
