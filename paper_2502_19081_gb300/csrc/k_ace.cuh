@@ -345,6 +345,8 @@ __device__ __forceinline__ void nu3_units(const AceTileHdr& h, const T* W, const
         const int uu = uv ? u : 0;
         const int q1 = uu / nqb;
         const int q2 = (uu - q1 * nqb) * QB;
+        const T* A1q = A1 + q1;
+        const T* A2q = A2 + q2;
         T w[QB][NP];
 #pragma unroll
         for (int r = 0; r < QB; ++r) {
@@ -386,32 +388,28 @@ __device__ __forceinline__ void nu3_units(const AceTileHdr& h, const T* W, const
                 }
             }
             const int e1 = g3o[m3 + 1];
-            int cur = -1;
             T c1 = T(0);
             for (int e = g3o[m3]; e < e1; ++e) {
                 int pk;
                 T g;
                 ld_gent(ge + e, pk, g);
-                const int m1 = pk & 255;
-                const T ga = g * A1[m1 * NP + q1];
+                const T ga = g * A1q[pk & 255];
                 T a2[QB];
-                ld_blk<T, QB>(A2 + (pk >> 8) * NP + q2, a2);
+                ld_blk<T, QB>(A2q + ((pk >> 8) & 255), a2);
 #pragma unroll
                 for (int r = 0; r < QB; ++r) z[r] += ga * a2[r];
                 if (withu) {
-                    if (m1 != cur) {   // uniform over the warp
-                        if (cur >= 0 && uv) P1[cur * units + u] += c1;
-                        c1 = T(0);
-                        cur = m1;
-                    }
                     T dd = T(0);
 #pragma unroll
                     for (int r = 0; r < QB; ++r) dd += a2[r] * uo[r];
                     c1 += g * dd;
+                    if (pk & GE_RUN_END) {   // uniform over the warp
+                        if (uv) P1[((pk >> 16) & 255) * units + u] += c1;
+                        c1 = T(0);
+                    }
                 }
             }
             if (withu) {
-                if (cur >= 0 && uv) P1[cur * units + u] += c1;
 #pragma unroll
                 for (int r = 0; r < QB; ++r) ep += uo[r] * z[r];
                 if (keepu && uv) {
@@ -485,6 +483,11 @@ __device__ __forceinline__ void nu3_units_f(const AceTileHdr& h, const float* W,
         const int uu = uv ? u : 0;
         const int q1 = uu / nqb;
         const int q2 = (uu - q1 * nqb) * QB;
+        const float* A1q = A1 + q1;
+        const float* A2q = A2 + q2;
+        int e = g3o[0], pkn;   // the entries of all m3 rows follow each other
+        float gn;
+        ld_gent(ge + e, pkn, gn);
         float2 w[QB][NH];
 #pragma unroll
         for (int r = 0; r < QB; ++r) {
@@ -523,33 +526,31 @@ __device__ __forceinline__ void nu3_units_f(const AceTileHdr& h, const float* W,
                 }
             }
             const int e1 = g3o[m3 + 1];
-            int cur = -1;
             float2 c1 = make_float2(0.f, 0.f);
-            for (int e = g3o[m3]; e < e1; ++e) {
-                int pk;
-                float g;
-                ld_gent(ge + e, pk, g);
-                const int m1 = pk & 255;
-                const float ga = g * A1[m1 * NP + q1];
+            for (; e < e1; ++e) {
+                const int pk = pkn;
+                const float g = gn;
+                // the next entry (of this row, the next row, or past the last
+                // row: always inside the tile) is in flight while this one works
+                ld_gent(ge + e + 1, pkn, gn);
+                const float ga = g * A1q[pk & 255];
                 const float2 ga2 = make_float2(ga, ga);
                 float2 a2[QH];
-                ld_pairs<QB>(A2 + (pk >> 8) * NP + q2, a2);
+                ld_pairs<QB>(A2q + ((pk >> 8) & 255), a2);
 #pragma unroll
                 for (int k = 0; k < QH; ++k) z[k] = __ffma2_rn(ga2, a2[k], z[k]);
                 if (withu) {
-                    if (m1 != cur) {   // uniform over the warp
-                        if (cur >= 0 && uv) P1[cur * units + u] += c1.x + c1.y;
-                        c1 = make_float2(0.f, 0.f);
-                        cur = m1;
-                    }
                     float2 dd = make_float2(0.f, 0.f);
 #pragma unroll
                     for (int k = 0; k < QH; ++k) dd = __ffma2_rn(a2[k], uo[k], dd);
                     c1 = __ffma2_rn(make_float2(g, g), dd, c1);
+                    if (pk & GE_RUN_END) {   // uniform over the warp
+                        if (uv) P1[((pk >> 16) & 255) * units + u] += c1.x + c1.y;
+                        c1 = make_float2(0.f, 0.f);
+                    }
                 }
             }
             if (withu) {
-                if (cur >= 0 && uv) P1[cur * units + u] += c1.x + c1.y;
                 if constexpr (TCM == 0) {
 #pragma unroll
                     for (int k = 0; k < QH; ++k) e2 = __ffma2_rn(uo[k], z[k], e2);

@@ -173,10 +173,24 @@ std::vector<unsigned char> ace_tiles(int n, int np, const std::vector<int>& tau,
         T* W = reinterpret_cast<T*>(tile.data() + sizeof(AceTileHdr));
         for (int q12 = 0; q12 < n * n; ++q12)
             for (int q3 = 0; q3 < n; ++q3) W[(size_t)q12 * np + q3] = (T)W3[((size_t)t * n * n + q12) * n + q3];
+        // entries of the ordering by m3 (the first 2 l3 + 1 rows) in the form
+        // the kernel reads them: row offsets of m1 and m2 in the transposed
+        // density (m np), m1, and a flag on the last entry of a run of equal m1
+        // within a row
+        const int ne3 = goff[gb + 2 * l3 + 1] - e0;
         for (int k = 0; k < ne; ++k) {
             GEnt<T> g;
             std::memset(&g, 0, sizeof g);
-            g.pk = gidx[e0 + k];
+            int pk = gidx[e0 + k];
+            if (k < ne3) {
+                const int m1 = pk & 255, m2 = pk >> 8;
+                int row = 0;
+                while (goff[gb + row + 1] - e0 <= k) ++row;
+                const int rend = goff[gb + row + 1] - e0;
+                const bool last = k + 1 >= rend || (gidx[e0 + k + 1] & 255) != m1;
+                pk = (m1 * np) | ((m2 * np) << 8) | (m1 << 16) | (last ? 1 << 24 : 0);
+            }
+            g.pk = pk;
             g.g = (T)gval[e0 + k];
             std::memcpy(tile.data() + h.o_ge + (size_t)k * sizeof g, &g, sizeof g);
         }

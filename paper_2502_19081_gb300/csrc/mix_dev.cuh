@@ -246,7 +246,10 @@ __host__ __device__ constexpr int ace_min_ctas_max() {
 constexpr int TC_ACE_WARPS = 8;
 
 // One Gaunt coefficient with the packed m indices of its two other factors
-// (ma | mb << 8, 0-based), loaded as one 8- or 16-byte word.
+// (ma | mb << 8, 0-based; the ordering by m3 packs more, see AceTileHdr),
+// loaded as one 8- or 16-byte word.
+constexpr int GE_RUN_END = 1 << 24;   // last entry of a run of equal m1 in an m3 row
+
 template <typename T>
 struct __align__(sizeof(T) == 4 ? 8 : 16) GEnt {
     int pk;
@@ -256,8 +259,10 @@ struct __align__(sizeof(T) == 4 ? 8 : 16) GEnt {
 // Header of one l-triple tile of the nu = 3 tables.  A tile is one contiguous,
 // 16-byte aligned block (a multiple of 16 bytes) holding, at these byte offsets:
 //   W[q1 q2][q3]  (n*n rows of np, zero padded) right after the header,
-//   the Gaunt entries GEnt<T> in three orderings (by m3: m1 | m2 << 8 with m1
-//     ascending, by m1: m2 | m3 << 8, by m2: m1 | m3 << 8) at o_ge,
+//   the Gaunt entries GEnt<T> in three orderings at o_ge: by m3 (m1
+//     ascending; m1 np | m2 np << 8 | m1 << 16, bit 24 set on the last entry
+//     of a run of equal m1 within an m3 row), by m1 (m2 | m3 << 8) and by m2
+//     (m1 | m3 << 8),
 //   their offset rows (per ordering 2l+2 ints: the first entry of each m, then
 //     the end; entry indices relative to o_ge) at o_go.
 // mode: 0 l's distinct, 1 l1 == l2, 2 l2 == l3, 3 all equal (W symmetrised over
