@@ -97,19 +97,22 @@ def job_throughput(n_atoms: int, steps: int, world: int, total_ms_max: float) ->
 # algorithmic work model (per evaluated atom)
 
 
-def exp_flops_per_atom(wl, info, nnb_rc: float) -> float:
+def exp_flops_per_atom(wl, info, nnb_rc: float, executed: bool = False) -> float:
     """Linear ACE: density 2 n nlm Nnb; pair gradients (4 n nlm + 8 nlm) Nnb;
     nu=2 readout + adjoint 4 n^2 nlm; nu=3 readout + adjoint as counted by the
-    library from its l-triples (mix_info.nu3_flops_per_atom: U = W A3 and
-    omega3 = W^T Z, Z, E, and the omega1/omega2 terms that coinciding l's do
-    not make redundant)."""
+    library from its l-triples (U = W A3 and omega3 = W^T Z, Z, E, and the
+    omega1/omega2 terms that coinciding l's do not make redundant), with each
+    triple's factors in the potential's own ascending order
+    (mix_info.nu3_flops_ref_per_atom: the fixed algorithmic count), or, with
+    executed=True, in the order the kernel contracts them (smallest l dense,
+    mix_info.nu3_flops_per_atom: less work)."""
     a = wl.ace
     n, nlm = a.n_rad, (a.l_max + 1) ** 2
     f = 2.0 * n * nlm * nnb_rc + (4.0 * n * nlm + 8.0 * nlm) * nnb_rc
     if a.nu_max >= 2:
         f += 4.0 * n * n * nlm
     if a.nu_max >= 3:
-        f += float(info["nu3_flops_per_atom"])
+        f += float(info["nu3_flops_per_atom" if executed else "nu3_flops_ref_per_atom"])
     return f
 
 
@@ -422,6 +425,7 @@ def gpu_leg(mix, torch, wl, prec, args, flush, peaks, hbm, oracle_seconds, e2e=T
     ms_step = total_ms / steps
     phase_ms = tot / max(nev, 1)
     pe = exp_flops_per_atom(wl, info, nst["nnb_exp_rc"])
+    pe_run = exp_flops_per_atom(wl, info, nst["nnb_exp_rc"], executed=True)
     pc = cheap_flops_per_atom(nst["nnb_cheap_rc"], nst["n3_cheap"])
     rf = rebuilds / max(steps, 1)
     kern = {}
@@ -429,6 +433,7 @@ def gpu_leg(mix, torch, wl, prec, args, flush, peaks, hbm, oracle_seconds, e2e=T
         kb = {"ms": float(phase_ms[p]), "share": float(phase_ms[p] / phase_ms.sum())}
         if nm == "exp":
             kb["algorithmic_flops"] = pe * nst["n_exp"]
+            kb["executed_flops"] = pe_run * nst["n_exp"]
             kb["tflops"] = kb["algorithmic_flops"] / (phase_ms[p] * 1e-3) / 1e12 if phase_ms[p] > 0 else 0.0
         elif nm == "cheap":
             # the cheap kernel runs on a second stream beside the expensive one:
@@ -612,6 +617,11 @@ def ours(args):
                 "algorithmic_flops_per_launch": fl,
                 "peak_source": "measured FMA microbenchmark "
                                f"({'fp64' if prec == mix.MIX_FP64 else 'fp32'}), mix_fma_peak (of measured)"}
+        if names[dom] == "exp":
+            # the work the kernel does with the smallest l of each triple dense
+            fx = kern["exp"]["executed_flops"]
+            roof["executed_flops_per_launch"] = fx
+            roof["frac_executed"] = fx / (phase_ms[dom] * 1e-3) / peak
         if names[dom] == "exp" and prec in (mix.MIX_BF16, mix.MIX_BF16_SPLIT):
             # the part of the kernel on the tensor cores: V = Z W per l-triple,
             # 2 d3 n^2 n flops per atom (three products with the split)

@@ -291,8 +291,9 @@ typedef struct {
     int64_t gaunt_nnz;      /* non-zero real Gaunt coefficients over all l-triples */
     int64_t tau_dim3_sum;   /* sum over l-triples of (2 l3 + 1) */
     int64_t basis_size;     /* number of product-basis functions */
-    double nu3_flops_per_atom; /* nu = 3 readout and adjoint per evaluated atom:
-                                  sum over l-triples of U = W A3 and omega3 = W^T Z
+    double nu3_flops_per_atom; /* nu = 3 readout and adjoint per evaluated atom, as
+                                  the kernel contracts them (l1 >= l2 >= l3): sum over
+                                  l-triples of U = W A3 and omega3 = W^T Z
                                   (2 (2l3+1) n^3 each), Z (2 nnz n^2), E (2 (2l3+1) n^2),
                                   omega1 (2 nnz n^2, unless all l equal) and omega2
                                   (2 nnz n^2, only for distinct l's) */
@@ -313,6 +314,12 @@ typedef struct {
     int cheap_lanes;        /* lanes per atom of the cheap kernel (8, 16 or 32); a periodic
                                bulk may narrow after its first evaluation, a 3-body
                                overflow widens to 32 */
+    double nu3_flops_ref_per_atom; /* nu3_flops_per_atom with each l-triple's factors
+                                  in ascending order (l3 the largest), the order the
+                                  potential's coefficients are given in; the kernel
+                                  contracts the factor of smallest l densely instead,
+                                  which does less work (Sec. 2.1: the basis is
+                                  symmetric in its three factors) */
 } mix_info;
 
 int mix_get_info(const mix_ctx* ctx, mix_info* info);

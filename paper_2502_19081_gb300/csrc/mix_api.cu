@@ -263,7 +263,7 @@ struct mix_ctx {
     bool spl_lpa_settled;             // the lane groups were narrowed or widened once
     int ace_grid_max, spl_grid_max;   // resident CTAs at full occupancy
     int64_t gaunt_nnz, tau_d3_sum, basis_size;
-    double nu3_flops;
+    double nu3_flops, nu3_flops_ref;
     int64_t launches;
     bool profiling;
     bool opt_graphs;
@@ -339,10 +339,17 @@ int build_tables(mix_ctx* c, const mix_ace* a, const mix_spline* sp) {
                 Yq.push_back(Y);
                 wq.push_back(gw[iz] * 2.0 * M_PI / nphi);
             }
-        for (int l1 = 0; l1 <= L; ++l1)
-            for (int l2 = l1; l2 <= L; ++l2)
-                for (int l3 = l2; l3 <= L; ++l3) {
-                    if (((l1 + l2 + l3) & 1) || l3 > l1 + l2) continue;
+        // The potential indexes its coefficients by the ascending triple
+        // la <= lb <= lc.  The kernel contracts the third factor densely
+        // (U = W A3 and omega3 = W^T Z cost (2 l3 + 1) n^3 each) and the first
+        // two through the Gaunt-sparse products, and the sum is the same for
+        // any order of the factors, so it takes them in descending order
+        // (l1, l2, l3) = (lc, lb, la): the dense factor has the smallest l.
+        for (int la = 0; la <= L; ++la)
+            for (int lb = la; lb <= L; ++lb)
+                for (int lc = lb; lc <= L; ++lc) {
+                    if (((la + lb + lc) & 1) || lc > la + lb) continue;
+                    const int l1 = lc, l2 = lb, l3 = la;
                     const int d1 = 2 * l1 + 1, d2 = 2 * l2 + 1, d3 = 2 * l3 + 1;
                     std::vector<double> G((size_t)d1 * d2 * d3, 0.0);
                     for (size_t k = 0; k < wq.size(); ++k) {
@@ -394,16 +401,19 @@ int build_tables(mix_ctx* c, const mix_ace* a, const mix_spline* sp) {
                                 }
                     }
                     goff.push_back((int)gidx.size());
-                    // masked coefficients
-                    const size_t id = ((size_t)l1 * L1 + l2) * L1 + l3;
+                    // masked coefficients c[qa][qb][qc] of the ascending triple
+                    // (zero where la == lb and qb < qa, or lb == lc and qc < qb),
+                    // stored as W[q1 q2][q3] with (q1, q2, q3) = (qc, qb, qa)
+                    const size_t id = ((size_t)la * L1 + lb) * L1 + lc;
                     const double* C3 = a->c3 + id * n * n * n;
                     for (int q1 = 0; q1 < n; ++q1)
                         for (int q2 = 0; q2 < n; ++q2)
                             for (int q3 = 0; q3 < n; ++q3) {
+                                const int qa = q3, qb = q2, qc = q1;
                                 bool ok = true;
-                                if (l1 == l2 && q2 < q1) ok = false;
-                                if (l2 == l3 && q3 < q2) ok = false;
-                                W3.push_back(ok ? C3[((size_t)q1 * n + q2) * n + q3] : 0.0);
+                                if (la == lb && qb < qa) ok = false;
+                                if (lb == lc && qc < qb) ok = false;
+                                W3.push_back(ok ? C3[((size_t)qa * n + qb) * n + qc] : 0.0);
                             }
                 }
     }
@@ -452,6 +462,7 @@ int build_tables(mix_ctx* c, const mix_ace* a, const mix_spline* sp) {
         std::copy(S.begin(), S.end(), Wt);
     }
     c->nu3_flops = 0.0;
+    c->nu3_flops_ref = 0.0;
     for (int t = 0; t < c->ntau; ++t) {
         const int l3 = tau[4 * t + 2], gb = tau[4 * t + 3];
         const double nnz = goff[gb + 2 * l3 + 1] - goff[gb], d3 = 2 * l3 + 1, nn = n;
@@ -459,6 +470,14 @@ int build_tables(mix_ctx* c, const mix_ace* a, const mix_spline* sp) {
         if (tmode[t] != 3) f += 2.0 * nnz * nn * nn;
         if (tmode[t] == 0) f += 2.0 * nnz * nn * nn;
         c->nu3_flops += f;
+        // the same count with the factors in ascending order: the dense factor
+        // is then the one of largest l (l1 here), and the coincidences swap
+        const double d1 = 2 * tau[4 * t] + 1;
+        const int mref = tmode[t] == 1 ? 2 : (tmode[t] == 2 ? 1 : tmode[t]);
+        double fr = 4.0 * d1 * nn * nn * nn + 2.0 * nnz * nn * nn + 2.0 * d1 * nn * nn;
+        if (mref != 3) fr += 2.0 * nnz * nn * nn;
+        if (mref == 0) fr += 2.0 * nnz * nn * nn;
+        c->nu3_flops_ref += fr;
     }
     // q2 block of a lane unit (q1, qb consecutive q2) in the nu = 3 pass: every
     // pass of the warp over its units repeats the per-m3 work (a warp-wide
@@ -1254,6 +1273,7 @@ int mix_get_info(const mix_ctx* c, mix_info* info) {
     info->exp_tensor_cores = c->ace_tcm ? 1 : 0;
     info->tc_flops_per_atom = c->ace_tcm ? 2.0 * (double)c->tau_d3_sum * c->n * c->n * c->n : 0.0;
     info->cheap_lanes = c->spl_lpa;
+    info->nu3_flops_ref_per_atom = c->nu3_flops_ref;
     return MIX_OK;
 }
 

@@ -104,7 +104,8 @@ class mix_info(ctypes.Structure):
                 ("cheap_grid", ctypes.c_int), ("launches_per_evaluation", ctypes.c_int),
                 ("launches", ctypes.c_int64), ("gather_grid", ctypes.c_int), ("build_grid", ctypes.c_int),
                 ("buffer_grid", ctypes.c_int), ("exp_tensor_cores", ctypes.c_int),
-                ("tc_flops_per_atom", ctypes.c_double), ("cheap_lanes", ctypes.c_int)]
+                ("tc_flops_per_atom", ctypes.c_double), ("cheap_lanes", ctypes.c_int),
+                ("nu3_flops_ref_per_atom", ctypes.c_double)]
 
 
 class mix_server_options(ctypes.Structure):
