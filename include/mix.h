@@ -341,14 +341,17 @@ int mix_get_profile(mix_ctx* ctx, double* total_ms /*[MIX_PHASES] nullable*/, do
 int mix_fma_peak(int precision, void* cuda_stream, double* flops_per_s);
 
 /* Check of the tensor-core building block of the bf16 readout (no counterpart
- * in the paper; used by the tests): D = A B^T with A [128][k] and B [n][k] bf16
- * (raw 16-bit patterns, row-major) and D [128][n] float32, all caller-owned
- * device memory, formed by one CTA with the shared-memory operand layout,
- * tcgen05.mma instructions and TMEM read-back of the readout kernel.
- * 16 <= n <= 256 and 16 <= k <= 160, both multiples of 16 (else MIX_EINVAL).
- * *status_dev (device int, caller-cleared) gets bit 0 set, and D is NaN, if the
- * bounded wait for the MMAs gave up.  Asynchronous on cuda_stream. */
-int mix_tc_selftest(const void* a_dev, const void* b_dev, int n, int k, float* d_dev, int* status_dev,
+ * in the paper; used by the tests): D = A B^T with A [m][k] and B [n][k] bf16
+ * (raw 16-bit patterns, row-major), m = 128 or 64, formed by one CTA with the
+ * shared-memory operand layout, tcgen05.mma instructions and TMEM read-back of
+ * the readout kernel.  d_dev [128][n] float32 receives TMEM lane l in row l
+ * (for m = 128 row l of D; for m = 64, row r of D lies in lane
+ * 32 (r / 16) + r % 16 and the other lanes hold no result).  All buffers are
+ * caller-owned device memory.  16 <= n <= 256 and 16 <= k <= 160, both
+ * multiples of 16 (else MIX_EINVAL).  *status_dev (device int, caller-cleared)
+ * gets bit 0 set, and d is NaN, if the bounded wait for the MMAs gave up.
+ * Asynchronous on cuda_stream. */
+int mix_tc_selftest(const void* a_dev, const void* b_dev, int m, int n, int k, float* d_dev, int* status_dev,
                     void* cuda_stream);
 
 /* ------------------------------------------------------------------------ */

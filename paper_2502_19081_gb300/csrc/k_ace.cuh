@@ -214,31 +214,38 @@ __device__ __forceinline__ void spline16(const T* __restrict__ c, T invh, T r, T
 
 __host__ __device__ constexpr int ace_a16(int b) { return (b + 15) & ~15; }
 
-// Shared memory (byte offsets, used by the host sizing and the kernels): two
-// tile buffers, then one region per warp.  In a warp region the density chunk
-// (R and Y of 32 neighbours) and the nu = 3 scratch of a triple (U, kept for
-// omega2, and the omega1 partial sums of the lane units) are never live
-// together and share one area.
+// Shared memory (byte offsets, used by the host sizing and the kernels): the
+// tile buffers, then one region per warp: the atom's density A and adjoint
+// omega, and a scratch area holding in turn the density chunk (R and Y of 32
+// neighbours), the nu = 3 scratch of a triple (U, kept for omega2, and the
+// omega1 partials of the lane units) and, for the pair gradients, the
+// compacted unit vectors, distances and list slots.  U is kept only for
+// triples of three distinct l's, whose smallest l (the densely contracted
+// third factor) is at most L - 2: 2 L - 3 rows m3 at most.
 struct AceLay {
-    int tile;                            // bytes of one tile buffer (nbuf buffers)
-    int o_w, wb;                         // first warp region, bytes per warp region
-    int o_u, o_at, o_om, o_scr, o_slot;  // offsets inside a warp region
-    int o_p1;                            // omega1 partials, inside the scratch area
+    int tile;                  // bytes of one tile buffer (nbuf buffers)
+    int o_w, wb;               // first warp region, bytes per warp region
+    int o_at, o_om, o_scr;     // offsets inside a warp region
+    int o_p1;                  // omega1 partials, inside the scratch area
+    int o_slot;                // list slots of the pair-gradient step, inside the scratch area
     int total;
     __host__ __device__ AceLay(int tile_max, int cap, int n, int qb, int L, int NP, int ts, int warps,
                                int nbuf = 2) {
         const int nlm = (L + 1) * (L + 1), D = 2 * L + 1;
+        const int du = 2 * L - 3 > 1 ? 2 * L - 3 : 1;
         tile = ace_a16(tile_max);
         o_w = nbuf * tile;
-        o_u = 0;                                  // [cap][4]: unit vector, r
-        o_at = o_u + ace_a16(4 * cap * ts);       // A[lm][q]
+        o_at = 0;                                 // A[lm][q]
         o_om = o_at + ace_a16(nlm * NP * ts);     // omega[lm][q]
         o_scr = o_om + ace_a16(nlm * NP * ts);
-        o_p1 = ace_a16(D * n * NP * ts);          // after U[m3][q1][q2]; P1[m1][unit]
+        o_p1 = ace_a16(du * n * NP * ts);         // after U[m3][q1][q2]; P1[m1][unit]
         const int nu3 = o_p1 + D * n * (NP / qb) * ts;
         const int chunk = (32 * NP + 32 * nlm) * ts;   // R[32][NP], Y[32][nlm]
-        o_slot = o_scr + ace_a16(nu3 > chunk ? nu3 : chunk);   // list slot per compacted neighbour
-        wb = o_slot + ace_a16(4 * cap);
+        o_slot = ace_a16(4 * cap * ts);           // after [cap][4]: unit vector, r
+        const int pairs = o_slot + 4 * cap;
+        int scr = nu3 > chunk ? nu3 : chunk;
+        scr = scr > pairs ? scr : pairs;
+        wb = o_scr + ace_a16(scr);
         total = o_w + warps * wb;
     }
 };
@@ -739,15 +746,15 @@ __device__ __forceinline__ void ace_group(const Dev& d, const AceTab<T>& tab, in
     if (ntau > 0) tile_fetch(tab.tiles, tab.tile_off, 0, smem);
 
     unsigned char* wreg = smem + lay.o_w + warp * lay.wb;
-    T* su = reinterpret_cast<T*>(wreg + lay.o_u);
     T* At = reinterpret_cast<T*>(wreg + lay.o_at);
     T* om = reinterpret_cast<T*>(wreg + lay.o_om);
     T* scr = reinterpret_cast<T*>(wreg + lay.o_scr);
-    int* slot = reinterpret_cast<int*>(wreg + lay.o_slot);
     T* cR = scr;                 // density chunk
     T* cY = scr + 32 * NP;
     T* U1 = scr;                 // nu = 3
     T* P1 = reinterpret_cast<T*>(wreg + lay.o_scr + lay.o_p1);
+    T* su = scr;                 // pair gradients
+    int* slot = reinterpret_cast<int*>(wreg + lay.o_scr + lay.o_slot);
 
     const int a = a0 + warp;
     const bool has = a < nexp;
@@ -762,14 +769,18 @@ __device__ __forceinline__ void ace_group(const Dev& d, const AceTab<T>& tab, in
     const int* rvr = d.rev + (int64_t)i * cap;
     V* grow = GE + (int64_t)i * cap;
     T ep = T(0);
-    int nb = 0;
+    const T rc2 = (T)d.rce2;
+    const unsigned lt = (1u << lane) - 1u;
+    const int m = has ? d.nnb[i] : 0;
 
     if (has) {
-        // 1. neighbours inside the cutoff, ordered compaction
+        // 1-2. density, 32 list slots at a time: the slots inside the cutoff
+        // are compacted in slot order (ballot) into the chunk, where each lane
+        // then accumulates its (lm, 4 q) outputs over them
         const PairFrame<T> pf(d, i);
-        const T rc2 = (T)d.rce2;
-        const int m = d.nnb[i];
-        const unsigned lt = (1u << lane) - 1u;
+        T acc[NUL][4];
+#pragma unroll
+        for (int j = 0; j < NUL; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = T(0);
         for (int b0 = 0; b0 < m; b0 += 32) {
             const int s = b0 + lane;
             bool ok = false;
@@ -777,42 +788,17 @@ __device__ __forceinline__ void ace_group(const Dev& d, const AceTab<T>& tab, in
             if (s < m) {
                 pf.vec(d, row[s], dv, r2);
                 ok = r2 < rc2;
-                if (!ok) {
-                    V z;
-                    z.x = z.y = z.z = z.w = T(0);
-                    grow[s] = z;
-                    z.w = stamp_as(T(0), stamp);
-                    GIN[(int64_t)row[s] * cap + rvr[s]] = z;   // the partner's incoming row
-                }
             }
             const unsigned bal = __ballot_sync(0xffffffffu, ok);
+            const int kc = __popc(bal);
             if (ok) {
-                const int k = nb + __popc(bal & lt);
+                const int k = __popc(bal & lt);
                 const T r = sqrt(r2), ir = T(1) / r;
-                slot[k] = s;
-                su[4 * k + 0] = dv[0] * ir;
-                su[4 * k + 1] = dv[1] * ir;
-                su[4 * k + 2] = dv[2] * ir;
-                su[4 * k + 3] = r;
-            }
-            nb += __popc(bal);
-        }
-        __syncwarp();
-
-        // 2. density, 32 neighbours at a time
-        T acc[NUL][4];
-#pragma unroll
-        for (int j = 0; j < NUL; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = T(0);
-        for (int k0 = 0; k0 < nb; k0 += 32) {
-            const int kc = nb - k0 < 32 ? nb - k0 : 32;
-            if (lane < kc) {
-                const int k = k0 + lane;
-                const T r = su[4 * k + 3];
                 T R[NP], dR[NP];
                 radial<T, NP>(r, invrc, n, R, dR);
 #pragma unroll
-                for (int p = 0; p < NP; ++p) cR[lane * NP + p] = R[p];
-                ylm_eval<T, L>(su[4 * k], su[4 * k + 1], su[4 * k + 2], tab.ylmk, cY + lane * NLM);
+                for (int p = 0; p < NP; ++p) cR[k * NP + p] = R[p];
+                ylm_eval<T, L>(dv[0] * ir, dv[1] * ir, dv[2] * ir, tab.ylmk, cY + k * NLM);
                 if (tab.has_pair) {
                     T v, dvv;
                     spline16<T>(tab.pair, invh, r, v, dvv);
@@ -908,12 +894,16 @@ __device__ __forceinline__ void ace_group(const Dev& d, const AceTab<T>& tab, in
         // Zhi Wlo); the warps take omega1 and omega2 meanwhile, then wait for
         // the MMAs and read their own rows of V: omega3 += mult3 V,
         // E += sum A3 V (lane-local, summed with the atom's other terms).
-        const int slot_w = 2 * (warp & 3) + (warp >> 2);   // this warp's 16 rows of the MMA tile
+        // this warp's 16 rows of the MMA tile, placed so that their
+        // accumulator rows lie in the TMEM lanes 32 (w % 4) .. + 31 the warp may
+        // read: M = 128 puts row i in lane i, M = 64 rows 16 w .. 16 w + 15 in
+        // lanes 32 w .. 32 w + 15
+        const int slot_w = TC_M == 128 ? 2 * (warp & 3) + (warp >> 2) : warp;
         unsigned char* zh = tc->zhi + 2 * slot_w * tc->sbo;
         unsigned char* zl = TCM == 2 ? tc->zlo + 2 * slot_w * tc->sbo : nullptr;
-        const bool own = (lane >> 4) == (warp >> 2);      // TMEM lane 32 (warp % 4) + lane is this atom's row
+        const bool own = TC_M == 128 ? (lane >> 4) == (warp >> 2) : lane < 16;   // TMEM lane 32 (w % 4) + lane
         const int m3r = lane & 15;
-        const uint32_t idesc = tc_idesc_bf16(128, 16);
+        const uint32_t idesc = tc_idesc_bf16(TC_M, 16);
         const int kp = tc->kp, sbo_b = (kp / 8) * TC_LBO_B;
         for (int t = 0; t < ntau; ++t) {
             unsigned char* tile = smem + (tc->nbuf == 2 ? (t & 1) : 0) * lay.tile;
@@ -974,7 +964,41 @@ __device__ __forceinline__ void ace_group(const Dev& d, const AceTab<T>& tab, in
     if (ntau > 0) __syncthreads();   // both buffers free for the next group's first tile
 
     if (has) {
-        // 5. pair gradients, a lane per neighbour
+        // 5. pair gradients: the neighbours inside the cutoff compacted again
+        // in slot order (unit vector, r and list slot into the scratch area;
+        // the slots outside get zero rows), then a lane per neighbour
+        int nb = 0;
+        {
+            const PairFrame<T> pf(d, i);
+            for (int b0 = 0; b0 < m; b0 += 32) {
+                const int s = b0 + lane;
+                bool ok = false;
+                T dv[3] = {T(0), T(0), T(0)}, r2 = T(0);
+                if (s < m) {
+                    pf.vec(d, row[s], dv, r2);
+                    ok = r2 < rc2;
+                    if (!ok) {
+                        V z;
+                        z.x = z.y = z.z = z.w = T(0);
+                        grow[s] = z;
+                        z.w = stamp_as(T(0), stamp);
+                        GIN[(int64_t)row[s] * cap + rvr[s]] = z;   // the partner's incoming row
+                    }
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, ok);
+                if (ok) {
+                    const int k = nb + __popc(bal & lt);
+                    const T r = sqrt(r2), ir = T(1) / r;
+                    slot[k] = s;
+                    su[4 * k + 0] = dv[0] * ir;
+                    su[4 * k + 1] = dv[1] * ir;
+                    su[4 * k + 2] = dv[2] * ir;
+                    su[4 * k + 3] = r;
+                }
+                nb += __popc(bal);
+            }
+            __syncwarp();
+        }
         const T* K = tab.ylmk;
         for (int k = lane; k < nb; k += 32) {
             const T x = su[4 * k], y = su[4 * k + 1], z = su[4 * k + 2], r = su[4 * k + 3];

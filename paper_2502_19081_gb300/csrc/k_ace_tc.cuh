@@ -1,27 +1,30 @@
 // Expensive potential with the nu = 3 readout on the tensor cores (float
 // arithmetic elsewhere; the body is ace_group in k_ace.cuh with TCM != 0).
 //
-// A CTA of TC_ACE_WARPS = 8 warps takes groups of 8 consecutive atoms of the
-// expensive list, a warp per atom as in the CUDA-core kernel.  Per l-triple the
-// warps write their atom's Z[m3][q1 n + q2] (bf16; with the hi/lo split also
-// the remainders) into rows 16 s + m3 of a shared-memory A operand (s = the
-// warp's slot, 2 (w % 4) + w / 4, so that its rows lie in the TMEM lanes the
-// warp may read), one thread issues kp / 16 tcgen05.mma (K = 16 each; three per
-// slice with the split) against the triple's coefficients W as the B operand
-// (16 rows q3 x kp, streamed with the tile), accumulating V = Z W (128 x 16,
-// f32) in 32 TMEM columns, and commits to an mbarrier; the warps take the
-// Gaunt adjoints omega1 and omega2 meanwhile, wait (bounded), and read their
-// rows of V: omega3 += mult3 V and E += sum A3 V.
-// Shared memory: the A operand(s) (16 row groups x kp / 8 core matrices of
-// TC_LBO_A bytes), then the tile buffers and the warp regions of AceLay.
+// A CTA of TC_ACE_WARPS = 4 warps takes groups of 4 consecutive atoms of the
+// expensive list, a warp per atom as in the CUDA-core kernel, and three CTAs
+// share an SM.  Per l-triple the warps write their atom's Z[m3][q1 n + q2]
+// (bf16; with the hi/lo split also the remainders) into rows 16 w + m3 of a
+// shared-memory A operand (the accumulator rows of an M = 64 product lie in
+// TMEM lanes 32 (r / 16) + r % 16, so warp w's rows are in the lanes it may
+// read), one thread issues kp / 16 tcgen05.mma (K = 16 each; three per slice
+// with the split) against the triple's coefficients W as the B operand (16
+// rows q3 x kp, streamed with the tile), accumulating V = Z W (64 x 16, f32)
+// in 32 TMEM columns, and commits to an mbarrier; the warps take the Gaunt
+// adjoints omega1 and omega2 meanwhile, wait (bounded), and read their rows
+// of V: omega3 += mult3 V and E += sum A3 V.
+// Shared memory: the A operand(s) (TC_M / 8 row groups x kp / 8 core matrices
+// of TC_LBO_A bytes), then the tile buffers and the warp regions of AceLay.
 #pragma once
+
+#include <algorithm>
 
 #include "k_ace.cuh"
 
 namespace mixd {
 
 template <int L, int NP, int TCM>
-__global__ void __launch_bounds__(TC_ACE_WARPS * 32, 1) k_ace_tc(Dev d, AceTab<float> tab, int nbuf) {
+__global__ void __launch_bounds__(TC_ACE_WARPS * 32, TC_MIN_CTAS) k_ace_tc(Dev d, AceTab<float> tab, int nbuf) {
     extern __shared__ __align__(128) unsigned char smem_tc[];
     __shared__ __align__(8) unsigned long long s_bar;
     __shared__ uint32_t s_tmem;
@@ -32,7 +35,7 @@ __global__ void __launch_bounds__(TC_ACE_WARPS * 32, 1) k_ace_tc(Dev d, AceTab<f
     TcState tc;
     tc.kp = (tab.n * tab.n + 15) & ~15;
     tc.sbo = (tc.kp / 8) * TC_LBO_A;
-    const int zbytes = 16 * tc.sbo;
+    const int zbytes = (TC_M / 8) * tc.sbo;
     constexpr int NZ = TCM == 2 ? 2 : 1;
     tc.zhi = sm;
     tc.zlo = TCM == 2 ? sm + zbytes : nullptr;
@@ -65,13 +68,14 @@ __global__ void __launch_bounds__(TC_ACE_WARPS * 32, 1) k_ace_tc(Dev d, AceTab<f
 // dynamic shared memory of k_ace_tc (with 128 bytes for the base alignment)
 inline size_t ace_tc_bytes(int tcm, int L, int NP, int n, int cap, int tile_max, int qb, int nbuf) {
     const int kp = (n * n + 15) & ~15;
-    const size_t zbytes = (size_t)16 * (kp / 8) * TC_LBO_A;
+    const size_t zbytes = (size_t)(TC_M / 8) * (kp / 8) * TC_LBO_A;
     const AceLay lay(tile_max, cap, n, qb, L, NP, 4, TC_ACE_WARPS, nbuf);
     return 128 + (size_t)(tcm == 2 ? 2 : 1) * zbytes + (size_t)lay.total;
 }
 
-// launch shape: two tile buffers if they fit the opt-in shared memory, else
-// one; as many resident CTAs as fit (each holds 32 TMEM columns of 512)
+// launch shape: one or two tile buffers, whichever lets more CTAs share an SM
+// (two on a tie: the next tile then streams in during the current one); as
+// many resident CTAs as fit (each holds 32 TMEM columns of 512)
 template <int L, int NP, int TCM>
 inline cudaError_t ace_tc_shape(int n, int cap, int tile_max, int qb, size_t* smem, int* grid, int* nbuf) {
     const void* kern = (const void*)k_ace_tc<L, NP, TCM>;
@@ -81,22 +85,38 @@ inline cudaError_t ace_tc_shape(int n, int cap, int tile_max, int qb, size_t* sm
     cudaFuncAttributes fa;
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kern);
     if (e != cudaSuccess) return e;
+    int best = 0, best_nb = 0;
+    size_t best_bytes = 0;
     for (int nb = 2; nb >= 1; --nb) {
         const size_t bytes = ace_tc_bytes(TCM, L, NP, n, cap, tile_max, qb, nb);
         if (bytes + fa.sharedSizeBytes > (size_t)optin) continue;
         e = raise_smem_limit(kern, bytes);
         if (e != cudaSuccess) return e;
-        int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TC_ACE_WARPS * 32, bytes);
+        // resident CTAs from the SM's registers, shared memory, threads and
+        // TMEM (16 x 32 columns); the occupancy calculator reports a single CTA
+        // for kernels that allocate tensor memory, whatever each allocates
+        int smem_sm = 0, resv = 0;
+        e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev);
         if (e != cudaSuccess) return e;
-        if (per_sm < 1) continue;
-        if (per_sm > 16) per_sm = 16;   // TMEM: 16 x 32 columns
-        *smem = bytes;
-        *grid = per_sm * sm_count();
-        *nbuf = nb;
-        return cudaSuccess;
+        const int regs_warp = ((fa.numRegs * 32 + 255) / 256) * 256;
+        int per_sm = 65536 / (regs_warp * TC_ACE_WARPS);
+        per_sm = std::min(per_sm, (int)((size_t)smem_sm / (bytes + fa.sharedSizeBytes + (size_t)resv)));
+        per_sm = std::min(per_sm, 2048 / (TC_ACE_WARPS * 32));
+        per_sm = std::min(per_sm, 16);
+        if (per_sm > best) {
+            best = per_sm;
+            best_nb = nb;
+            best_bytes = bytes;
+        }
     }
-    return cudaErrorInvalidValue;
+    if (best < 1) return cudaErrorInvalidValue;
+    e = raise_smem_limit(kern, best_bytes);
+    if (e != cudaSuccess) return e;
+    *smem = best_bytes;
+    *grid = best * sm_count();
+    *nbuf = best_nb;
+    return cudaSuccess;
 }
 
 template <int NP, int TCM>

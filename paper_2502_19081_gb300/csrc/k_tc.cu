@@ -1,9 +1,10 @@
 // Check of the tensor-core building block the expensive kernel's bf16 readout
-// uses (tc.cuh): one CTA forms D = A B^T with M = 128, A [128][K] and
+// uses (tc.cuh): one CTA forms D = A B^T with M = 128 or 64, A [M][K] and
 // B [N][K] bf16 (row-major in global memory, copied by the CTA's threads into
 // the canonical K-major shared-memory layout with the same core-matrix strides
 // as the readout), K / 16 tcgen05.mma instructions accumulating in TMEM, and
-// the rows read back with tcgen05.ld by the four warps.
+// all 128 TMEM lanes read back with tcgen05.ld by the four warps (lane l to
+// row l of the output), so that the caller sees where each row of D lies.
 #include "mix_launch.h"
 #include "tc.cuh"
 
@@ -12,7 +13,7 @@ namespace mixd {
 namespace {
 
 __global__ void __launch_bounds__(128, 1) k_tc_selftest(const uint16_t* __restrict__ a, const uint16_t* __restrict__ b,
-                                                        int n, int k, float* __restrict__ d, int* status) {
+                                                        int m, int n, int k, float* __restrict__ d, int* status) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) unsigned long long bar;
     __shared__ uint32_t tbase;
@@ -22,7 +23,7 @@ __global__ void __launch_bounds__(128, 1) k_tc_selftest(const uint16_t* __restri
     unsigned char* sa = sm;
     unsigned char* sb = sm + 16 * sbo_a;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    for (int e = tid; e < 128 * k; e += blockDim.x) {
+    for (int e = tid; e < m * k; e += blockDim.x) {
         const int r = e / k, c = e - r * k;
         *reinterpret_cast<uint16_t*>(sa + tc_off(r, c, TC_LBO_A, sbo_a)) = a[e];
     }
@@ -40,7 +41,7 @@ __global__ void __launch_bounds__(128, 1) k_tc_selftest(const uint16_t* __restri
     tc_fence_after();
     const uint32_t t0 = tbase;
     if (tid == 0) {
-        const uint32_t idesc = tc_idesc_bf16(128, n);
+        const uint32_t idesc = tc_idesc_bf16(m, n);
         for (int s = 0; s < k / 16; ++s) {
             const uint64_t ad = tc_desc(smem_u32(sa + s * 2 * TC_LBO_A), TC_LBO_A, sbo_a);
             const uint64_t bd = tc_desc(smem_u32(sb + s * 2 * TC_LBO_B), TC_LBO_B, sbo_b);
@@ -70,11 +71,12 @@ __global__ void __launch_bounds__(128, 1) k_tc_selftest(const uint16_t* __restri
 
 size_t tc_selftest_smem(int n, int k) { return (size_t)16 * (k / 8) * TC_LBO_A + (size_t)(n / 8) * (k / 8) * TC_LBO_B + 128; }
 
-cudaError_t tc_selftest(const uint16_t* a, const uint16_t* b, int n, int k, float* d, int* status, cudaStream_t s) {
+cudaError_t tc_selftest(const uint16_t* a, const uint16_t* b, int m, int n, int k, float* d, int* status,
+                        cudaStream_t s) {
     const size_t smem = tc_selftest_smem(n, k);
     cudaError_t e = raise_smem_limit((const void*)k_tc_selftest, smem);
     if (e != cudaSuccess) return e;
-    k_tc_selftest<<<1, 128, smem, s>>>(a, b, n, k, d, status);
+    k_tc_selftest<<<1, 128, smem, s>>>(a, b, m, n, k, d, status);
     return cudaGetLastError();
 }
 

@@ -446,6 +446,8 @@ int build_tables(mix_ctx* c, const mix_ace* a, const mix_spline* sp) {
         const int l1 = tau[4 * t], l2 = tau[4 * t + 1], l3 = tau[4 * t + 2];
         const int mode = (l1 == l2 && l2 == l3) ? 3 : (l1 == l2 ? 1 : (l2 == l3 ? 2 : 0));
         tmode[t] = mode;
+        // the kernel keeps U for distinct l's only, sized for l3 <= L - 2
+        if (mode == 0 && 2 * l3 + 1 > std::max(2 * L - 3, 1)) return fail(c, MIX_EINVAL, "l-triple order");
         double* Wt = W3.data() + (size_t)t * n * n * n;
         std::vector<double> S(Wt, Wt + (size_t)n * n * n);
         auto at = [&](int a, int b, int cc) -> double { return Wt[((size_t)a * n + b) * n + cc]; };
@@ -1314,12 +1316,12 @@ int mix_fma_peak(int precision, void* stream, double* flops) {
     return fma_peak(precision, (cudaStream_t)stream, flops);
 }
 
-int mix_tc_selftest(const void* a_dev, const void* b_dev, int n, int k, float* d_dev, int* status_dev,
+int mix_tc_selftest(const void* a_dev, const void* b_dev, int m, int n, int k, float* d_dev, int* status_dev,
                     void* stream) {
     if (!a_dev || !b_dev || !d_dev || !status_dev) return MIX_EINVAL;
-    if (n < 16 || n > 256 || n % 16 || k < 16 || k > 160 || k % 16) return MIX_EINVAL;
-    const cudaError_t e = tc_selftest(static_cast<const uint16_t*>(a_dev), static_cast<const uint16_t*>(b_dev), n,
-                                      k, d_dev, status_dev, (cudaStream_t)stream);
+    if ((m != 64 && m != 128) || n < 16 || n > 256 || n % 16 || k < 16 || k > 160 || k % 16) return MIX_EINVAL;
+    const cudaError_t e = tc_selftest(static_cast<const uint16_t*>(a_dev), static_cast<const uint16_t*>(b_dev), m,
+                                      n, k, d_dev, status_dev, (cudaStream_t)stream);
     return e == cudaSuccess ? MIX_OK : MIX_ECUDA;
 }
 

@@ -241,9 +241,13 @@ template <typename T>
 __host__ __device__ constexpr int ace_min_ctas_max() {
     return ace_min_ctas<T>() * ACE_GROUP / ACE_MAX_WARPS;
 }
-// The tensor-core readout (float, bf16 operands) takes groups of 8 atoms, a
-// warp each: 8 x 16 rows (atom, m3) fill the M = 128 rows of one MMA tile.
-constexpr int TC_ACE_WARPS = 8;
+// The tensor-core readout (float, bf16 operands) takes groups of 4 atoms, a
+// warp each: 4 x 16 rows (atom, m3) fill the M = 64 rows of one MMA tile, and
+// three such CTAs fit an SM (8 atoms and M = 128 would need a CTA of 8 warps,
+// one an SM).
+constexpr int TC_ACE_WARPS = 4;
+constexpr int TC_M = 16 * TC_ACE_WARPS;
+constexpr int TC_MIN_CTAS = 3;
 
 // One Gaunt coefficient with the packed m indices of its two other factors
 // (ma | mb << 8, 0-based; the ordering by m3 packs more, see AceTileHdr),

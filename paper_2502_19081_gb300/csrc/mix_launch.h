@@ -32,7 +32,8 @@ cudaError_t ace_tc_configure(int tcm, int L, int n, int cap, int tile_max, int q
 void launch_ace_tc(const Dev& d, const void* tab, int tcm, int L, size_t smem, int grid, int nbuf, cudaStream_t s);
 
 // tensor-core building block check (k_tc.cu)
-cudaError_t tc_selftest(const uint16_t* a, const uint16_t* b, int n, int k, float* d, int* status, cudaStream_t s);
+cudaError_t tc_selftest(const uint16_t* a, const uint16_t* b, int m, int n, int k, float* d, int* status,
+                        cudaStream_t s);
 
 // cheap potential (k_spline.cu)
 // lpa: lanes per evaluated atom (32, or 16 or 8 for atoms with few neighbours);

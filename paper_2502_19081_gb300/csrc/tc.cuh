@@ -10,9 +10,10 @@
 // adjacent along M (or N).  One MMA instruction takes K = 16, i.e. two core
 // matrices along K from its descriptor's start address.
 //
-// The accumulator D (M = 128 rows x N columns of f32) lives in TMEM: row i in
-// lane i, column j in column j of the allocation.  Warp w of the CTA may read
-// lanes 32 (w % 4) .. 32 (w % 4) + 31 only.
+// The accumulator D (M rows x N columns of f32) lives in TMEM, column j in
+// column j of the allocation: for M = 128 row i in lane i, for M = 64 row i in
+// lane 32 (i / 16) + i % 16 (the first 16 lanes of each quarter).  Warp w of
+// the CTA may read lanes 32 (w % 4) .. 32 (w % 4) + 31 only.
 #pragma once
 
 #include <cuda_bf16.h>

@@ -187,7 +187,7 @@ def lib():
             L.mix_profile.argtypes = [P, ctypes.c_int]
             L.mix_get_profile.argtypes = [P, dp, dp, i64p]
             L.mix_fma_peak.argtypes = [ctypes.c_int, P, dp]
-            L.mix_tc_selftest.argtypes = [P, P, ctypes.c_int, ctypes.c_int, P, P, P]
+            L.mix_tc_selftest.argtypes = [P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, P]
             L.mix_neighbours_noalloc.argtypes = [ctypes.c_int64, P, dp, dp, ip, ctypes.c_double, ctypes.c_int,
                                                  P, P, P, P]
             L.mix_tune.argtypes = [P, ctypes.c_int]
@@ -503,19 +503,20 @@ def fma_peak(precision: int, stream=None) -> float:
 
 
 def tc_selftest(a, b, d, status, stream=None) -> None:
-    """mix_tc_selftest on torch device tensors: a [128, k] and b [n, k] bfloat16,
-    d [128, n] float32 (written: a @ b.T on the tensor cores), status [1] int32
-    (bit 0 set if the wait for the MMAs gave up).  Asynchronous on `stream`."""
+    """mix_tc_selftest on torch device tensors: a [m, k] (m = 128 or 64) and
+    b [n, k] bfloat16, d [128, n] float32 (written: TMEM lane l of a @ b.T on
+    the tensor cores in row l), status [1] int32 (bit 0 set if the wait for the
+    MMAs gave up).  Asynchronous on `stream`."""
     import torch
     for t, dt, shp in ((a, torch.bfloat16, None), (b, torch.bfloat16, None), (d, torch.float32, None),
                        (status, torch.int32, (1,))):
         if t.dtype != dt or not t.is_cuda or not t.is_contiguous():
             raise ValueError("tc_selftest: a, b bfloat16, d float32, status int32, contiguous CUDA tensors")
-    n, k = int(b.shape[0]), int(b.shape[1])
-    if tuple(a.shape) != (128, k) or tuple(d.shape) != (128, n) or status.numel() < 1:
-        raise ValueError("tc_selftest: shapes a [128, k], b [n, k], d [128, n]")
+    n, k, m = int(b.shape[0]), int(b.shape[1]), int(a.shape[0])
+    if a.dim() != 2 or int(a.shape[1]) != k or tuple(d.shape) != (128, n) or status.numel() < 1:
+        raise ValueError("tc_selftest: shapes a [m, k], b [n, k], d [128, n]")
     s = stream if stream is not None else torch.cuda.current_stream(a.device)
-    st = lib().mix_tc_selftest(ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(b.data_ptr()), n, k,
+    st = lib().mix_tc_selftest(ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(b.data_ptr()), m, n, k,
                                ctypes.c_void_p(d.data_ptr()), ctypes.c_void_p(status.data_ptr()),
                                ctypes.c_void_p(s.cuda_stream))
     if st != MIX_OK:
