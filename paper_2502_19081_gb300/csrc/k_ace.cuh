@@ -569,7 +569,23 @@ __device__ __forceinline__ void nu3_units_f(const AceTileHdr& h, const float* W,
                 }
             }
             if constexpr (TCM != 0) {
-                if (uv) {
+                if (uv && (n & 1) == 0) {
+                    // even n: columns q1 n + q2 + r, r even, are even, so each
+                    // pair lies in one 4-byte word of a core-matrix row
+#pragma unroll
+                    for (int k = 0; k < QH; ++k) {
+                        if (q2 + 2 * k < n) {
+                            const int o = tc_off(m3, q1 * n + q2 + 2 * k, TC_LBO_A, zsbo);
+                            const __nv_bfloat162 hi = __float22bfloat162_rn(z[k]);
+                            *reinterpret_cast<__nv_bfloat162*>(zhi + o) = hi;
+                            if constexpr (TCM == 2) {
+                                const float2 hf = __bfloat1622float2(hi);
+                                *reinterpret_cast<__nv_bfloat162*>(zlo + o) =
+                                    __float22bfloat162_rn(make_float2(z[k].x - hf.x, z[k].y - hf.y));
+                            }
+                        }
+                    }
+                } else if (uv) {
 #pragma unroll
                     for (int r = 0; r < QB; ++r) {
                         if (q2 + r < n) {
