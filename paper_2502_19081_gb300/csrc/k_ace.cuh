@@ -868,15 +868,18 @@ __device__ __forceinline__ void ace_group(const Dev& d, const AceTab<T>& tab, in
                 int l = 0;
                 while ((l + 1) * (l + 1) <= lm) ++l;
                 if (tab.nu >= 2) {
+                    // even and odd q2 in two chains; unrolled over the padded
+                    // count so that the row's coefficient loads are all in flight
                     const T* S2 = tab.S2 + ((int64_t)l * n + q) * n;
                     const T* Ar = At + lm * NP;
                     T v2 = T(0);
-                    int q2 = 0;
-                    for (; q2 + 1 < n; q2 += 2) {
-                        val += __ldg(S2 + q2) * Ar[q2];
-                        v2 += __ldg(S2 + q2 + 1) * Ar[q2 + 1];
+#pragma unroll
+                    for (int q2 = 0; q2 < NP; ++q2) {
+                        if (q2 < n) {
+                            if (q2 & 1) v2 += __ldg(S2 + q2) * Ar[q2];
+                            else val += __ldg(S2 + q2) * Ar[q2];
+                        }
                     }
-                    if (q2 < n) val += __ldg(S2 + q2) * Ar[q2];
                     val += v2;
                 }
                 const T av = At[o];
