@@ -32,6 +32,7 @@ ACE_KEYS = [
     ("Fe_n4_l2_b4", "Fe", 4, 2, 4, "fe"),
     ("Si_n6_l3_b4", "Si", 6, 3, 4, "si"),
     ("Si_n4_l2_b3", "Si", 4, 2, 3, "si"),
+    ("Fe_n14_l6_b4", "Fe", 14, 6, 4, "fe"),
 ]
 
 

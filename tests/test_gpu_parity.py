@@ -43,6 +43,8 @@ def _cases():
         "screw_3000": lambda: I.fe_screw(n_atoms=3000, nrep_z=4),
         # n = 11: 6-wide q2 blocks in the float nu = 3 pass, with a ragged last block
         "fe_box_n11": lambda: I.small_fe_box(15, n_rad=11, l_max=3, r_core=3.0, ramp=2.0),
+        # the largest shapes the library takes: n = 14 (rows padded to 16) and lmax = 6
+        "fe_box_n14_l6": lambda: I.small_fe_box(24, n_rad=14, l_max=6, r_core=3.0, ramp=2.0),
     }
 
 
@@ -145,7 +147,8 @@ def test_forces_fp64_match_oracle(mx, name):
     assert np.all(ee[~me] == 0) and np.all(ec[~mc] == 0)
 
 
-@pytest.mark.parametrize("name", ["si_vacancy_215", "fe_box_685", "fe_box_l4", "cluster_60", "screw_3000", "fe_box_n11"])
+@pytest.mark.parametrize("name", ["si_vacancy_215", "fe_box_685", "fe_box_l4", "cluster_60", "screw_3000", "fe_box_n11",
+                                  "fe_box_n14_l6"])
 def test_forces_fp32_within_gate(mx, name):
     wl = _wl(name)
     ctx = mx.open_context(wl, precision=mx.MIX_FP32)

@@ -93,6 +93,7 @@ def _cases():
         "fe_box_n11": lambda: I.small_fe_box(15, n_rad=11, l_max=3, r_core=3.0, ramp=2.0),
         "fe_box_n12_l5": lambda: I.small_fe_box(21, n_rad=12, l_max=5, r_core=4.0, ramp=3.0),
         "fe_box_n10_l4": lambda: I.small_fe_box(22, n_rad=10, l_max=4, r_core=4.0, ramp=3.0),
+        "fe_box_n14_l6": lambda: I.small_fe_box(24, n_rad=14, l_max=6, r_core=3.0, ramp=2.0),
     }
 
 
