@@ -492,6 +492,9 @@ __device__ __forceinline__ void nu3_units_f(const AceTileHdr& h, const float* W,
         const int q2 = (uu - q1 * nqb) * QB;
         const float* A1q = A1 + q1;
         const float* A2q = A2 + q2;
+        int zcol[TCM != 0 ? QH : 1];   // column part of the operand offset of each pair
+#pragma unroll
+        for (int k = 0; k < (TCM != 0 ? QH : 1); ++k) zcol[k] = tc_off(0, q1 * n + q2 + 2 * k, TC_LBO_A, 0);
         int e = g3o[0], pkn;   // the entries of all m3 rows follow each other
         float gn;
         ld_gent(ge + e, pkn, gn);
@@ -571,11 +574,13 @@ __device__ __forceinline__ void nu3_units_f(const AceTileHdr& h, const float* W,
             if constexpr (TCM != 0) {
                 if (uv && (n & 1) == 0) {
                     // even n: columns q1 n + q2 + r, r even, are even, so each
-                    // pair lies in one 4-byte word of a core-matrix row
+                    // pair lies in one 4-byte word of a core-matrix row; the
+                    // row part of the offset is the m3 one, the column part the unit's
+                    const int orow = tc_off(m3, 0, TC_LBO_A, zsbo);
 #pragma unroll
                     for (int k = 0; k < QH; ++k) {
                         if (q2 + 2 * k < n) {
-                            const int o = tc_off(m3, q1 * n + q2 + 2 * k, TC_LBO_A, zsbo);
+                            const int o = orow + zcol[k];
                             const __nv_bfloat162 hi = __float22bfloat162_rn(z[k]);
                             *reinterpret_cast<__nv_bfloat162*>(zhi + o) = hi;
                             if constexpr (TCM == 2) {

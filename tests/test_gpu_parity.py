@@ -45,6 +45,8 @@ def _cases():
         "fe_box_n11": lambda: I.small_fe_box(15, n_rad=11, l_max=3, r_core=3.0, ramp=2.0),
         # the largest shapes the library takes: n = 14 (rows padded to 16) and lmax = 6
         "fe_box_n14_l6": lambda: I.small_fe_box(24, n_rad=14, l_max=6, r_core=3.0, ramp=2.0),
+        # the smallest padded rows: n = 4, lmax = 2
+        "fe_box_n4_l2": lambda: I.small_fe_box(25, n_rad=4, l_max=2, r_core=3.0, ramp=2.0),
     }
 
 
@@ -148,7 +150,7 @@ def test_forces_fp64_match_oracle(mx, name):
 
 
 @pytest.mark.parametrize("name", ["si_vacancy_215", "fe_box_685", "fe_box_l4", "cluster_60", "screw_3000", "fe_box_n11",
-                                  "fe_box_n14_l6"])
+                                  "fe_box_n14_l6", "fe_box_n4_l2"])
 def test_forces_fp32_within_gate(mx, name):
     wl = _wl(name)
     ctx = mx.open_context(wl, precision=mx.MIX_FP32)
