@@ -42,6 +42,36 @@
 
 namespace mixd {
 
+// The Gaunt coefficients ordered by m3 for every l-triple, shared by all
+// potentials (AceTileHdr): a copy in the constant memory of each module that
+// holds the expensive kernels, so that the warp-uniform entry reads of the
+// nu = 3 pass are constant-bank loads.
+static __constant__ GEnt<float> c_gent_f[GAUNT_ENT_CAP];
+static __constant__ GEnt<double> c_gent_d[GAUNT_ENT_CAP];
+static __constant__ int c_grow[GAUNT_ROW_CAP];
+
+// this module's copy of the table (host side)
+static inline cudaError_t gaunt_upload_module(const void* ent_f, const void* ent_d, int n_ent, const int* rows,
+                                              int n_rows) {
+    if (n_ent > GAUNT_ENT_CAP || n_rows > GAUNT_ROW_CAP) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemcpyToSymbol(c_gent_f, ent_f, (size_t)n_ent * sizeof(GEnt<float>));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_gent_d, ent_d, (size_t)n_ent * sizeof(GEnt<double>));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_grow, rows, (size_t)n_rows * sizeof(int));
+    return e;
+}
+
+// entry i of the constant-memory table
+__device__ __forceinline__ void gent_c(int i, int& pk, float& g) {
+    const GEnt<float> x = c_gent_f[i];
+    pk = x.pk;
+    g = x.g;
+}
+__device__ __forceinline__ void gent_c(int i, int& pk, double& g) {
+    const GEnt<double> x = c_gent_d[i];
+    pk = x.pk;
+    g = x.g;
+}
+
 template <typename T> struct V4;
 template <> struct V4<float> {
     float x, y, z, w;
@@ -335,12 +365,11 @@ __device__ __forceinline__ void rs_entry(int lane, int& idx, int& real, bool& wr
 // taken as sum A3 (W^T Z), the same sum reordered.  This is the float64 pass;
 // float runs nu3_units_f, the same arithmetic on packed pairs.
 template <typename T, int NP, int QB>
-__device__ __forceinline__ void nu3_units(const AceTileHdr& h, const T* W, const GEnt<T>* ge, const int* g3o,
-                                          const T* A1, const T* A2, const T* A3, int n, int lane, T* U1, T* P1,
-                                          T* o3, T mult3, T& ep) {
+__device__ __forceinline__ void nu3_units(const AceTileHdr& h, const T* W, const T* A1, const T* A2, const T* A3,
+                                          int n, int lane, T* U1, T* P1, T* o3, T mult3, T& ep) {
     constexpr int nqb = NP / QB;
     const int units = n * nqb;
-    const int d3 = 2 * h.l3 + 1;
+    const int d3 = 2 * h.l3 + 1, rb = h.cg;
     const bool withu = h.mode != 3;
     const bool keepu = h.mode == 0;
     int q3o = 0, q3real = NP;           // the omega3 entry this lane receives
@@ -394,15 +423,15 @@ __device__ __forceinline__ void nu3_units(const AceTileHdr& h, const T* W, const
                     uo[r] = s;
                 }
             }
-            const int e1 = g3o[m3 + 1];
+            const int e1 = c_grow[rb + m3 + 1];
             T c1 = T(0);
-            for (int e = g3o[m3]; e < e1; ++e) {
+            for (int e = c_grow[rb + m3]; e < e1; ++e) {
                 int pk;
                 T g;
-                ld_gent(ge + e, pk, g);
-                const T ga = g * A1q[pk & 255];
+                gent_c(e, pk, g);
+                const T ga = g * A1q[(pk & 255) * NP];
                 T a2[QB];
-                ld_blk<T, QB>(A2q + ((pk >> 8) & 255), a2);
+                ld_blk<T, QB>(A2q + ((pk >> 8) & 255) * NP, a2);
 #pragma unroll
                 for (int r = 0; r < QB; ++r) z[r] += ga * a2[r];
                 if (withu) {
@@ -411,7 +440,7 @@ __device__ __forceinline__ void nu3_units(const AceTileHdr& h, const T* W, const
                     for (int r = 0; r < QB; ++r) dd += a2[r] * uo[r];
                     c1 += g * dd;
                     if (pk & GE_RUN_END) {   // uniform over the warp
-                        if (uv) P1[((pk >> 16) & 255) * units + u] += c1;
+                        if (uv) P1[(pk & 255) * units + u] += c1;
                         c1 = T(0);
                     }
                 }
@@ -470,14 +499,14 @@ __device__ __forceinline__ void ld_pairs(const float* p, float2* out) {
 // the K-major layout of tc.cuh), from which the tensor cores form V = Z W
 // (omega3 = mult3 V, E = sum A3 V) after the pass.
 template <int NP, int QB, int TCM>
-__device__ __forceinline__ void nu3_units_f(const AceTileHdr& h, const float* W, const GEnt<float>* ge,
-                                            const int* g3o, const float* A1, const float* A2, const float* A3,
-                                            int n, int lane, float* U1, float* P1, float* o3, float mult3,
-                                            float& ep, unsigned char* zhi, unsigned char* zlo, int zsbo) {
+__device__ __forceinline__ void nu3_units_f(const AceTileHdr& h, const float* W, const float* A1, const float* A2,
+                                            const float* A3, int n, int lane, float* U1, float* P1, float* o3,
+                                            float mult3, float& ep, unsigned char* zhi, unsigned char* zlo,
+                                            int zsbo) {
     static_assert(QB % 2 == 0 && NP % 4 == 0, "the float pass works on pairs");
     constexpr int nqb = NP / QB, NH = NP / 2, QH = QB / 2;
     const int units = n * nqb;
-    const int d3 = 2 * h.l3 + 1;
+    const int d3 = 2 * h.l3 + 1, rb = h.cg;
     const bool withu = h.mode != 3;
     const bool keepu = h.mode == 0;
     int q3o = 0, q3real = NP;
@@ -495,9 +524,9 @@ __device__ __forceinline__ void nu3_units_f(const AceTileHdr& h, const float* W,
         int zcol[TCM != 0 ? QH : 1];   // column part of the operand offset of each pair
 #pragma unroll
         for (int k = 0; k < (TCM != 0 ? QH : 1); ++k) zcol[k] = tc_off(0, q1 * n + q2 + 2 * k, TC_LBO_A, 0);
-        int e = g3o[0], pkn;   // the entries of all m3 rows follow each other
+        int e = c_grow[rb], pkn;   // the entries of all m3 rows follow each other
         float gn;
-        ld_gent(ge + e, pkn, gn);
+        gent_c(e, pkn, gn);
         float2 w[QB][NH];
 #pragma unroll
         for (int r = 0; r < QB; ++r) {
@@ -535,18 +564,18 @@ __device__ __forceinline__ void nu3_units_f(const AceTileHdr& h, const float* W,
                     else uo[r / 2].x = s.x + s.y;
                 }
             }
-            const int e1 = g3o[m3 + 1];
+            const int e1 = c_grow[rb + m3 + 1];
             float2 c1 = make_float2(0.f, 0.f);
             for (; e < e1; ++e) {
                 const int pk = pkn;
                 const float g = gn;
-                // the next entry (of this row, the next row, or past the last
-                // row: always inside the tile) is in flight while this one works
-                ld_gent(ge + e + 1, pkn, gn);
-                const float ga = g * A1q[pk & 255];
+                // the next entry (of this row, the next row or triple, or the
+                // zero entry after the last) is in flight while this one works
+                gent_c(e + 1, pkn, gn);
+                const float ga = g * A1q[(pk & 255) * NP];
                 const float2 ga2 = make_float2(ga, ga);
                 float2 a2[QH];
-                ld_pairs<QB>(A2q + ((pk >> 8) & 255), a2);
+                ld_pairs<QB>(A2q + ((pk >> 8) & 255) * NP, a2);
 #pragma unroll
                 for (int k = 0; k < QH; ++k) z[k] = __ffma2_rn(ga2, a2[k], z[k]);
                 if (withu) {
@@ -555,7 +584,7 @@ __device__ __forceinline__ void nu3_units_f(const AceTileHdr& h, const float* W,
                     for (int k = 0; k < QH; ++k) dd = __ffma2_rn(a2[k], uo[k], dd);
                     c1 = __ffma2_rn(make_float2(g, g), dd, c1);
                     if (pk & GE_RUN_END) {   // uniform over the warp
-                        if (uv) P1[((pk >> 16) & 255) * units + u] += c1.x + c1.y;
+                        if (uv) P1[(pk & 255) * units + u] += c1.x + c1.y;
                         c1 = make_float2(0.f, 0.f);
                     }
                 }
@@ -639,12 +668,10 @@ __device__ __forceinline__ void nu3_tile(const unsigned char* tile, const AceTab
     constexpr int QM = 4;     // largest power-of-two q2 block of a lane unit
     const AceTileHdr h = *reinterpret_cast<const AceTileHdr*>(tile);
     const T* W = reinterpret_cast<const T*>(tile + sizeof(AceTileHdr));
-    const GEnt<T>* ge = reinterpret_cast<const GEnt<T>*>(tile + h.o_ge);
-    const int* g3o = reinterpret_cast<const int*>(tile + h.o_go);
+    const GEnt<T>* ge = reinterpret_cast<const GEnt<T>*>(tile + h.o_ge);   // ordered by m2
+    const int* g2o = reinterpret_cast<const int*>(tile + h.o_go);
     const int n = tab.n;
     const int d1 = 2 * h.l1 + 1, d2 = 2 * h.l2 + 1, d3 = 2 * h.l3 + 1;
-    const int* g1o = g3o + d3 + 1;
-    const int* g2o = g1o + d1 + 1;
     // coinciding l's (W symmetrised on the host): scale instead of recompute
     const T mult1 = h.mode == 1 ? T(2) : T(1);
     const T mult3 = h.mode == 3 ? T(3) : (h.mode == 2 ? T(2) : T(1));
@@ -658,20 +685,20 @@ __device__ __forceinline__ void nu3_tile(const unsigned char* tile, const AceTab
             if constexpr (NP == 12) {
                 // n = 11 or 12: 6-wide blocks keep the units within one warp pass
                 if (qb == 6)
-                    nu3_units_f<NP, 6, TCM>(h, W, ge, g3o, A1, A2, A3, n, lane, U1, P1, o3, mult3, ep, zhi, zlo,
+                    nu3_units_f<NP, 6, TCM>(h, W, A1, A2, A3, n, lane, U1, P1, o3, mult3, ep, zhi, zlo,
                                             zsbo);
             }
             if (qb == QM)
-                nu3_units_f<NP, QM, TCM>(h, W, ge, g3o, A1, A2, A3, n, lane, U1, P1, o3, mult3, ep, zhi, zlo, zsbo);
+                nu3_units_f<NP, QM, TCM>(h, W, A1, A2, A3, n, lane, U1, P1, o3, mult3, ep, zhi, zlo, zsbo);
             else if (qb == QM / 2)
-                nu3_units_f<NP, QM / 2, TCM>(h, W, ge, g3o, A1, A2, A3, n, lane, U1, P1, o3, mult3, ep, zhi, zlo,
+                nu3_units_f<NP, QM / 2, TCM>(h, W, A1, A2, A3, n, lane, U1, P1, o3, mult3, ep, zhi, zlo,
                                              zsbo);
         } else {
             static_assert(sizeof(T) == 4 || TCM == 0, "the tensor-core readout is float only");
             if (qb == QM)
-                nu3_units<T, NP, QM>(h, W, ge, g3o, A1, A2, A3, n, lane, U1, P1, o3, mult3, ep);
+                nu3_units<T, NP, QM>(h, W, A1, A2, A3, n, lane, U1, P1, o3, mult3, ep);
             else
-                nu3_units<T, NP, QM / 2>(h, W, ge, g3o, A1, A2, A3, n, lane, U1, P1, o3, mult3, ep);
+                nu3_units<T, NP, QM / 2>(h, W, A1, A2, A3, n, lane, U1, P1, o3, mult3, ep);
         }
         __syncwarp();
     }

@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -98,6 +99,121 @@ void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
     }
 }
 
+// The real Gaunt coefficients G[m1][m2][m3] of every l-triple l1 >= l2 >= l3
+// with l1 <= MIX_MAX_LMAX (the kernels' order of the factors: the third, of
+// smallest l, is contracted densely), by quadrature exact for the degree of
+// the product (Gauss-Legendre in cos(theta) times a uniform grid in phi).  One
+// set serves every potential: the coefficients depend on the l's alone.  Also
+// the ordering the expensive kernels read from constant memory: by m3, m1
+// ascending within a row (m1 | m2 << 8, GE_RUN_END on the last entry of each
+// run of equal m1), with the row offsets of each triple.
+struct GauntAll {
+    std::vector<int> l1, l2, l3;             // the triples
+    std::vector<std::vector<double>> G;      // [t][(m1 d2 + m2) d3 + m3]
+    std::vector<int> row0;                   // [t] first row offset of triple t in rows
+    std::vector<int> rows;                   // entry offsets, 2 l3 + 2 per triple (the last: the end)
+    std::vector<GEnt<float>> ent_f;
+    std::vector<GEnt<double>> ent_d;
+    int index(int a, int b, int c) const {
+        for (size_t t = 0; t < l1.size(); ++t)
+            if (l1[t] == a && l2[t] == b && l3[t] == c) return (int)t;
+        return -1;
+    }
+};
+
+const GauntAll& gaunt_all() {
+    static const GauntAll tab = [] {
+        GauntAll g;
+        const int L = MIX_MAX_LMAX, deg = 3 * L;
+        const int nz = deg / 2 + 2, nphi = deg + 2;
+        std::vector<double> gz, gw;
+        gauss_legendre(nz, gz, gw);
+        std::vector<std::vector<double>> Yq;
+        std::vector<double> wq;
+        for (int iz = 0; iz < nz; ++iz)
+            for (int ip = 0; ip < nphi; ++ip) {
+                const double ph = 2.0 * M_PI * ip / nphi;
+                const double s = std::sqrt(std::max(0.0, 1.0 - gz[iz] * gz[iz]));
+                std::vector<double> Y;
+                host_ylm(L, s * std::cos(ph), s * std::sin(ph), gz[iz], Y);
+                Yq.push_back(Y);
+                wq.push_back(gw[iz] * 2.0 * M_PI / nphi);
+            }
+        for (int l3 = 0; l3 <= L; ++l3)
+            for (int l2 = l3; l2 <= L; ++l2)
+                for (int l1 = l2; l1 <= L; ++l1) {
+                    if (((l1 + l2 + l3) & 1) || l1 > l2 + l3) continue;
+                    const int d1 = 2 * l1 + 1, d2 = 2 * l2 + 1, d3 = 2 * l3 + 1;
+                    std::vector<double> G((size_t)d1 * d2 * d3, 0.0);
+                    for (size_t k = 0; k < wq.size(); ++k) {
+                        const std::vector<double>& Y = Yq[k];
+                        for (int m1 = 0; m1 < d1; ++m1)
+                            for (int m2 = 0; m2 < d2; ++m2) {
+                                const double y12 = wq[k] * Y[l1 * l1 + m1] * Y[l2 * l2 + m2];
+                                for (int m3 = 0; m3 < d3; ++m3) G[((size_t)m1 * d2 + m2) * d3 + m3] += y12 * Y[l3 * l3 + m3];
+                            }
+                    }
+                    g.l1.push_back(l1);
+                    g.l2.push_back(l2);
+                    g.l3.push_back(l3);
+                    g.row0.push_back((int)g.rows.size());
+                    for (int m3 = 0; m3 < d3; ++m3) {
+                        g.rows.push_back((int)g.ent_f.size());
+                        for (int m1 = 0; m1 < d1; ++m1) {
+                            int last = -1;
+                            for (int m2 = 0; m2 < d2; ++m2) {
+                                const double v = G[((size_t)m1 * d2 + m2) * d3 + m3];
+                                if (std::fabs(v) <= GAUNT_ZERO) continue;
+                                last = (int)g.ent_f.size();
+                                GEnt<float> ef;
+                                GEnt<double> ed;
+                                std::memset(&ef, 0, sizeof ef);
+                                std::memset(&ed, 0, sizeof ed);
+                                ef.pk = ed.pk = m1 | (m2 << 8);
+                                ef.g = (float)v;
+                                ed.g = v;
+                                g.ent_f.push_back(ef);
+                                g.ent_d.push_back(ed);
+                            }
+                            if (last >= 0) {
+                                g.ent_f[last].pk |= GE_RUN_END;
+                                g.ent_d[last].pk |= GE_RUN_END;
+                            }
+                        }
+                    }
+                    g.rows.push_back((int)g.ent_f.size());
+                    g.G.push_back(std::move(G));
+                }
+        // one zero entry past the last, which the kernels' prefetch may read
+        GEnt<float> ef;
+        GEnt<double> ed;
+        std::memset(&ef, 0, sizeof ef);
+        std::memset(&ed, 0, sizeof ed);
+        g.ent_f.push_back(ef);
+        g.ent_d.push_back(ed);
+        return g;
+    }();
+    return tab;
+}
+
+// Copies the table into the constant memory of each kernel module on the
+// current device, once per device.
+int gaunt_upload() {
+    static std::mutex mu;
+    static std::vector<int> done;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return MIX_ECUDA;
+    std::lock_guard<std::mutex> lock(mu);
+    if (std::find(done.begin(), done.end(), dev) != done.end()) return MIX_OK;
+    const GauntAll& g = gaunt_all();
+    if ((int)g.ent_f.size() > GAUNT_ENT_CAP || (int)g.rows.size() > GAUNT_ROW_CAP) return MIX_EINVAL;
+    const cudaError_t e = ace_gaunt_upload(g.ent_f.data(), g.ent_d.data(), (int)g.ent_f.size(), g.rows.data(),
+                                           (int)g.rows.size());
+    if (e != cudaSuccess) return MIX_ECUDA;
+    done.push_back(dev);
+    return MIX_OK;
+}
+
 // byte arena for the tables uploaded into the workspace
 struct Arena {
     std::vector<unsigned char> bytes;
@@ -131,14 +247,17 @@ double bf16_value(uint16_t b) {
 
 // The nu = 3 tables as one tile per l-triple (layout in AceTileHdr): W3 holds
 // the symmetrised coefficients [t][q1 q2][q3], tau the triples (l1, l2, l3,
-// first offset row), goff/gidx/gval the Gaunt entries in three orderings.
+// first offset row), tcg each triple's first row in the constant-memory
+// Gaunt table, goff/gidx/gval the Gaunt entries in three orderings (the tile
+// takes the one by m2).
 // tcm (tensor-core readout): 1 appends W as the bf16 B operand, 2 also its
 // bf16 remainders; tiles are then 128-byte multiples.
 template <typename T>
 std::vector<unsigned char> ace_tiles(int n, int np, const std::vector<int>& tau, const std::vector<int>& tmode,
-                                     const std::vector<int>& goff, const std::vector<int>& gidx,
-                                     const std::vector<double>& gval, const std::vector<double>& W3,
-                                     std::vector<int>& off, int& tile_max, int tcm = 0) {
+                                     const std::vector<int>& tcg, const std::vector<int>& goff,
+                                     const std::vector<int>& gidx, const std::vector<double>& gval,
+                                     const std::vector<double>& W3, std::vector<int>& off, int& tile_max,
+                                     int tcm = 0) {
     const int kp = (n * n + 15) & ~15;
     const int sbo_b = (kp / 8) * TC_LBO_B;   // 8 rows of B; two such groups hold the 16 q3 rows
     const int ntau = (int)(tau.size() / 4);
@@ -147,13 +266,18 @@ std::vector<unsigned char> ace_tiles(int n, int np, const std::vector<int>& tau,
     tile_max = 0;
     for (int t = 0; t < ntau; ++t) {
         const int l1 = tau[4 * t], l2 = tau[4 * t + 1], l3 = tau[4 * t + 2], gb = tau[4 * t + 3];
-        const int rows = (2 * l3 + 2) + (2 * l1 + 2) + (2 * l2 + 2);
-        const int e0 = goff[gb], ne = goff[gb + rows - 1] - e0;
+        // the ordering by m2 only (the kernels read the ordering by m3 from the
+        // constant-memory table): its 2 l2 + 2 offset rows follow the 2 l3 + 2
+        // of the ordering by m3 and the 2 l1 + 2 of the ordering by m1
+        const int r2 = gb + (2 * l3 + 2) + (2 * l1 + 2), rows = 2 * l2 + 2;
+        const int e0 = goff[r2], ne = goff[r2 + rows - 1] - e0;
         AceTileHdr h;
+        std::memset(&h, 0, sizeof h);
         h.l1 = l1;
         h.l2 = l2;
         h.l3 = l3;
         h.mode = tmode[t];
+        h.cg = tcg[t];
         size_t o = sizeof(AceTileHdr) + (size_t)n * n * np * sizeof(T);
         h.o_ge = (int)o;
         o += (size_t)ne * sizeof(GEnt<T>);
@@ -173,29 +297,15 @@ std::vector<unsigned char> ace_tiles(int n, int np, const std::vector<int>& tau,
         T* W = reinterpret_cast<T*>(tile.data() + sizeof(AceTileHdr));
         for (int q12 = 0; q12 < n * n; ++q12)
             for (int q3 = 0; q3 < n; ++q3) W[(size_t)q12 * np + q3] = (T)W3[((size_t)t * n * n + q12) * n + q3];
-        // entries of the ordering by m3 (the first 2 l3 + 1 rows) in the form
-        // the kernel reads them: row offsets of m1 and m2 in the transposed
-        // density (m np), m1, and a flag on the last entry of a run of equal m1
-        // within a row
-        const int ne3 = goff[gb + 2 * l3 + 1] - e0;
         for (int k = 0; k < ne; ++k) {
             GEnt<T> g;
             std::memset(&g, 0, sizeof g);
-            int pk = gidx[e0 + k];
-            if (k < ne3) {
-                const int m1 = pk & 255, m2 = pk >> 8;
-                int row = 0;
-                while (goff[gb + row + 1] - e0 <= k) ++row;
-                const int rend = goff[gb + row + 1] - e0;
-                const bool last = k + 1 >= rend || (gidx[e0 + k + 1] & 255) != m1;
-                pk = (m1 * np) | ((m2 * np) << 8) | (m1 << 16) | (last ? 1 << 24 : 0);
-            }
-            g.pk = pk;
+            g.pk = gidx[e0 + k];
             g.g = (T)gval[e0 + k];
             std::memcpy(tile.data() + h.o_ge + (size_t)k * sizeof g, &g, sizeof g);
         }
         for (int r = 0; r < rows; ++r) {
-            const int v = goff[gb + r] - e0;
+            const int v = goff[r2 + r] - e0;
             std::memcpy(tile.data() + h.o_go + (size_t)r * sizeof(int), &v, sizeof v);
         }
         if (tcm) {
@@ -323,22 +433,9 @@ int build_tables(mix_ctx* c, const mix_ace* a, const mix_spline* sp) {
     std::vector<double> W3;
     std::vector<int> goff, gidx;
     std::vector<double> gval;
+    std::vector<int> tcg;   // per triple: its first row in the constant-memory table
     if (a->nu_max >= 3) {
-        const int deg = 3 * L;
-        const int nz = deg / 2 + 2, nphi = deg + 2;
-        std::vector<double> gz, gw;
-        gauss_legendre(nz, gz, gw);
-        std::vector<std::vector<double>> Yq;
-        std::vector<double> wq;
-        for (int iz = 0; iz < nz; ++iz)
-            for (int ip = 0; ip < nphi; ++ip) {
-                const double ph = 2.0 * M_PI * ip / nphi;
-                const double s = std::sqrt(std::max(0.0, 1.0 - gz[iz] * gz[iz]));
-                std::vector<double> Y;
-                host_ylm(L, s * std::cos(ph), s * std::sin(ph), gz[iz], Y);
-                Yq.push_back(Y);
-                wq.push_back(gw[iz] * 2.0 * M_PI / nphi);
-            }
+        const GauntAll& ga = gaunt_all();
         // The potential indexes its coefficients by the ascending triple
         // la <= lb <= lc.  The kernel contracts the third factor densely
         // (U = W A3 and omega3 = W^T Z cost (2 l3 + 1) n^3 each) and the first
@@ -351,16 +448,11 @@ int build_tables(mix_ctx* c, const mix_ace* a, const mix_spline* sp) {
                     if (((la + lb + lc) & 1) || lc > la + lb) continue;
                     const int l1 = lc, l2 = lb, l3 = la;
                     const int d1 = 2 * l1 + 1, d2 = 2 * l2 + 1, d3 = 2 * l3 + 1;
-                    std::vector<double> G((size_t)d1 * d2 * d3, 0.0);
-                    for (size_t k = 0; k < wq.size(); ++k) {
-                        const std::vector<double>& Y = Yq[k];
-                        for (int m1 = 0; m1 < d1; ++m1)
-                            for (int m2 = 0; m2 < d2; ++m2) {
-                                const double y12 = wq[k] * Y[l1 * l1 + m1] * Y[l2 * l2 + m2];
-                                for (int m3 = 0; m3 < d3; ++m3) G[((size_t)m1 * d2 + m2) * d3 + m3] += y12 * Y[l3 * l3 + m3];
-                            }
-                    }
-                    auto nz_ = [&](int m1, int m2, int m3) { return std::fabs(G[((size_t)m1 * d2 + m2) * d3 + m3]) > 1e-12; };
+                    const int tg = ga.index(l1, l2, l3);
+                    if (tg < 0) return fail(c, MIX_EINVAL, "l-triple beyond the Gaunt table");
+                    const std::vector<double>& G = ga.G[tg];
+                    tcg.push_back(ga.row0[tg]);
+                    auto nz_ = [&](int m1, int m2, int m3) { return std::fabs(G[((size_t)m1 * d2 + m2) * d3 + m3]) > GAUNT_ZERO; };
                     auto gv = [&](int m1, int m2, int m3) { return G[((size_t)m1 * d2 + m2) * d3 + m3]; };
                     const int t = (int)(tau.size() / 4);
                     (void)t;
@@ -520,7 +612,7 @@ int build_tables(mix_ctx* c, const mix_ace* a, const mix_spline* sp) {
     if (c->precision == MIX_FP64) {
         c->o_c1 = A.put(c1);
         c->o_S2 = A.put(S2);
-        c->o_tiles = A.put(ace_tiles<double>(n, np, tau, tmode, goff, gidx, gval, W3, toff, c->tile_max));
+        c->o_tiles = A.put(ace_tiles<double>(n, np, tau, tmode, tcg, goff, gidx, gval, W3, toff, c->tile_max));
         c->o_ylmk = A.put(ylmk);
         c->o_pair = A.put(pair);
         c->o_sc2 = A.put(sc2);
@@ -529,7 +621,7 @@ int build_tables(mix_ctx* c, const mix_ace* a, const mix_spline* sp) {
         c->o_c1 = A.put(conv<float>(c1));
         c->o_S2 = A.put(conv<float>(S2));
         c->ace_tcm = c->ntau == 0 ? 0 : (c->precision == MIX_BF16 ? 1 : (c->precision == MIX_BF16_SPLIT ? 2 : 0));
-        c->o_tiles = A.put(ace_tiles<float>(n, np, tau, tmode, goff, gidx, gval, W3, toff, c->tile_max, c->ace_tcm));
+        c->o_tiles = A.put(ace_tiles<float>(n, np, tau, tmode, tcg, goff, gidx, gval, W3, toff, c->tile_max, c->ace_tcm));
         c->o_ylmk = A.put(conv<float>(ylmk));
         c->o_pair = A.put(conv<float>(pair));
         c->o_sc2 = A.put(conv<float>(sc2));
@@ -908,6 +1000,7 @@ int mix_init(const mix_system* sys, const mix_ace* a, const mix_spline* sp, cons
     std::memset(&c->regions, 0, sizeof c->regions);
     c->regions.blend = opt->blend;
     int st = build_tables(c, a, sp);
+    if (st == MIX_OK && c->ntau > 0) st = gaunt_upload();
     if (st) {
         delete c;
         return st;

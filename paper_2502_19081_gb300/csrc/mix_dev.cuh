@@ -250,8 +250,8 @@ constexpr int TC_M = 16 * TC_ACE_WARPS;
 constexpr int TC_MIN_CTAS = 3;
 
 // One Gaunt coefficient with the packed m indices of its two other factors
-// (ma | mb << 8, 0-based; the ordering by m3 packs more, see AceTileHdr),
-// loaded as one 8- or 16-byte word.
+// (ma | mb << 8, 0-based; the ordering by m3 also flags run ends, see
+// AceTileHdr), loaded as one 8- or 16-byte word.
 constexpr int GE_RUN_END = 1 << 24;   // last entry of a run of equal m1 in an m3 row
 
 template <typename T>
@@ -263,12 +263,12 @@ struct __align__(sizeof(T) == 4 ? 8 : 16) GEnt {
 // Header of one l-triple tile of the nu = 3 tables.  A tile is one contiguous,
 // 16-byte aligned block (a multiple of 16 bytes) holding, at these byte offsets:
 //   W[q1 q2][q3]  (n*n rows of np, zero padded) right after the header,
-//   the Gaunt entries GEnt<T> in three orderings at o_ge: by m3 (m1
-//     ascending; m1 np | m2 np << 8 | m1 << 16, bit 24 set on the last entry
-//     of a run of equal m1 within an m3 row), by m1 (m2 | m3 << 8) and by m2
-//     (m1 | m3 << 8),
-//   their offset rows (per ordering 2l+2 ints: the first entry of each m, then
-//     the end; entry indices relative to o_ge) at o_go.
+//   the Gaunt entries GEnt<T> ordered by m2 (m1 | m3 << 8) at o_ge,
+//   their offset rows (2 l2 + 2 ints: the first entry of each m2, then the
+//     end; entry indices relative to o_ge) at o_go.
+// The ordering by m3 (m1 | m2 << 8, m1 ascending within a row, GE_RUN_END on
+// the last entry of each run of equal m1) is the same for every potential and
+// sits in constant memory, from row cg on.
 // mode: 0 l's distinct, 1 l1 == l2, 2 l2 == l3, 3 all equal (W symmetrised over
 // the matching n indices).  Tiles of the tensor-core readout (bf16 modes) also
 // hold, at o_wb (128-byte aligned; 0 otherwise), W as the MMA's B operand: 16
@@ -278,7 +278,16 @@ struct __align__(sizeof(T) == 4 ? 8 : 16) GEnt {
 struct AceTileHdr {
     int l1, l2, l3, mode;
     int o_ge, o_go, bytes, o_wb;
+    int cg;             // first row of the triple in the constant-memory Gaunt table
+    int pad[3];         // 16-byte multiple: W follows
 };
+
+// The constant-memory Gaunt table of the expensive kernels (every l-triple
+// l1 >= l2 >= l3 up to MIX_MAX_LMAX, ordered by m3; built on the host): entry
+// and row capacities, and the magnitude below which a quadrature value is zero.
+constexpr int GAUNT_ENT_CAP = 2048;
+constexpr int GAUNT_ROW_CAP = 192;
+constexpr double GAUNT_ZERO = 1e-12;
 
 template <typename T>
 struct AceTab {
