@@ -203,9 +203,14 @@ class Clocks:
 
 
 def run_precision(mix, torch, wl, precision, steps, warmup, flush, regions=None):
+    """Open a context, warm it up, let the library's autotuner pick its launch
+    shapes (mix_tune: force evaluations at the current positions, the state
+    unchanged), then time `steps` steps with the L2 flushed before each."""
     ctx = mix.open_context(wl, precision=precision, regions=regions)
     for _ in range(warmup):
         ctx.step(wl.dt, 1)
+    ctx.sync()
+    ctx.tune(3)
     ctx.sync()
     launches0 = ctx.info()["launches"]
     rebuilds0 = ctx.stats()["rebuilds"]

@@ -44,18 +44,15 @@ namespace mixd {
 
 // The Gaunt coefficients ordered by m3 for every l-triple, shared by all
 // potentials (AceTileHdr): a copy in the constant memory of each module that
-// holds the expensive kernels, so that the warp-uniform entry reads of the
-// nu = 3 pass are constant-bank loads.
+// holds the float expensive kernels, so that the warp-uniform entry reads of
+// the nu = 3 pass are constant-bank loads.
 static __constant__ GEnt<float> c_gent_f[GAUNT_ENT_CAP];
-static __constant__ GEnt<double> c_gent_d[GAUNT_ENT_CAP];
 static __constant__ int c_grow[GAUNT_ROW_CAP];
 
 // this module's copy of the table (host side)
-static inline cudaError_t gaunt_upload_module(const void* ent_f, const void* ent_d, int n_ent, const int* rows,
-                                              int n_rows) {
+static inline cudaError_t gaunt_upload_module(const void* ent_f, int n_ent, const int* rows, int n_rows) {
     if (n_ent > GAUNT_ENT_CAP || n_rows > GAUNT_ROW_CAP) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemcpyToSymbol(c_gent_f, ent_f, (size_t)n_ent * sizeof(GEnt<float>));
-    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_gent_d, ent_d, (size_t)n_ent * sizeof(GEnt<double>));
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_grow, rows, (size_t)n_rows * sizeof(int));
     return e;
 }
@@ -63,11 +60,6 @@ static inline cudaError_t gaunt_upload_module(const void* ent_f, const void* ent
 // entry i of the constant-memory table
 __device__ __forceinline__ void gent_c(int i, int& pk, float& g) {
     const GEnt<float> x = c_gent_f[i];
-    pk = x.pk;
-    g = x.g;
-}
-__device__ __forceinline__ void gent_c(int i, int& pk, double& g) {
-    const GEnt<double> x = c_gent_d[i];
     pk = x.pk;
     g = x.g;
 }
@@ -365,11 +357,12 @@ __device__ __forceinline__ void rs_entry(int lane, int& idx, int& real, bool& wr
 // taken as sum A3 (W^T Z), the same sum reordered.  This is the float64 pass;
 // float runs nu3_units_f, the same arithmetic on packed pairs.
 template <typename T, int NP, int QB>
-__device__ __forceinline__ void nu3_units(const AceTileHdr& h, const T* W, const T* A1, const T* A2, const T* A3,
-                                          int n, int lane, T* U1, T* P1, T* o3, T mult3, T& ep) {
+__device__ __forceinline__ void nu3_units(const AceTileHdr& h, const T* W, const GEnt<T>* ge3, const int* g3o,
+                                          const T* A1, const T* A2, const T* A3, int n, int lane, T* U1, T* P1,
+                                          T* o3, T mult3, T& ep) {
     constexpr int nqb = NP / QB;
     const int units = n * nqb;
-    const int d3 = 2 * h.l3 + 1, rb = h.cg;
+    const int d3 = 2 * h.l3 + 1;
     const bool withu = h.mode != 3;
     const bool keepu = h.mode == 0;
     int q3o = 0, q3real = NP;           // the omega3 entry this lane receives
@@ -423,12 +416,12 @@ __device__ __forceinline__ void nu3_units(const AceTileHdr& h, const T* W, const
                     uo[r] = s;
                 }
             }
-            const int e1 = c_grow[rb + m3 + 1];
+            const int e1 = g3o[m3 + 1];
             T c1 = T(0);
-            for (int e = c_grow[rb + m3]; e < e1; ++e) {
+            for (int e = g3o[m3]; e < e1; ++e) {
                 int pk;
                 T g;
-                gent_c(e, pk, g);
+                ld_gent(ge3 + e, pk, g);
                 const T ga = g * A1q[(pk & 255) * NP];
                 T a2[QB];
                 ld_blk<T, QB>(A2q + ((pk >> 8) & 255) * NP, a2);
@@ -695,10 +688,13 @@ __device__ __forceinline__ void nu3_tile(const unsigned char* tile, const AceTab
                                              zsbo);
         } else {
             static_assert(sizeof(T) == 4 || TCM == 0, "the tensor-core readout is float only");
+            // float64 reads the ordering by m3 from its tile
+            const GEnt<T>* ge3 = reinterpret_cast<const GEnt<T>*>(tile + h.o_ge3);
+            const int* g3o = reinterpret_cast<const int*>(tile + h.o_go3);
             if (qb == QM)
-                nu3_units<T, NP, QM>(h, W, A1, A2, A3, n, lane, U1, P1, o3, mult3, ep);
+                nu3_units<T, NP, QM>(h, W, ge3, g3o, A1, A2, A3, n, lane, U1, P1, o3, mult3, ep);
             else
-                nu3_units<T, NP, QM / 2>(h, W, A1, A2, A3, n, lane, U1, P1, o3, mult3, ep);
+                nu3_units<T, NP, QM / 2>(h, W, ge3, g3o, A1, A2, A3, n, lane, U1, P1, o3, mult3, ep);
         }
         __syncwarp();
     }
@@ -1148,14 +1144,36 @@ __device__ __forceinline__ void ace_group(const Dev& d, const AceTab<T>& tab, in
     }
 }
 
+// Groups of atoms are handed out one at a time from a counter in the status
+// words, so that CTAs that start late (the cheap kernel shares the SMs on its
+// own stream) take fewer; every group's results are its own, whichever CTA
+// computes them.  The last CTA to finish sets the counter back to zero.
+__device__ __forceinline__ int ace_next_group(const Dev& d, int* s_g) {
+    __syncthreads();   // every thread has read the previous group
+    if (threadIdx.x == 0) *s_g = atomicAdd(d.status + SW_ACE_NEXT, 1);
+    __syncthreads();
+    return *s_g;
+}
+__device__ __forceinline__ void ace_groups_done(const Dev& d) {
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(d.status + SW_ACE_DONE, 1) == (int)gridDim.x - 1) {
+            d.status[SW_ACE_NEXT] = 0;   // every CTA has taken its last group
+            d.status[SW_ACE_DONE] = 0;
+        }
+    }
+}
+
 template <typename T, int L, int NP>
 __global__ void __launch_bounds__(ACE_MAX_WARPS * 32, ace_min_ctas_max<T>()) k_ace(Dev d, AceTab<T> tab) {
     const int WN = (int)(blockDim.x >> 5);   // ACE_GROUP or ACE_MAX_WARPS atoms a CTA
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_g;
     const int count = d.status[SW_NEXP];
     const int ng = (count + WN - 1) / WN;
-    for (int g = blockIdx.x; g < ng; g += gridDim.x)
+    for (int g = ace_next_group(d, &s_g); g < ng; g = ace_next_group(d, &s_g))
         ace_group<T, L, NP>(d, tab, g * WN, count, smem_raw, nullptr, WN);
+    ace_groups_done(d);
 }
 
 // Many systems: walks the flattened list {system, first atom of a group} of

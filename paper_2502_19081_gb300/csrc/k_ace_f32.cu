@@ -4,8 +4,8 @@
 
 namespace mixd {
 
-cudaError_t ace_gaunt_upload_f32(const void* ent_f, const void* ent_d, int n_ent, const int* rows, int n_rows) {
-    return gaunt_upload_module(ent_f, ent_d, n_ent, rows, n_rows);
+cudaError_t ace_gaunt_upload_f32(const void* ent_f, int n_ent, const int* rows, int n_rows) {
+    return gaunt_upload_module(ent_f, n_ent, rows, n_rows);
 }
 
 cudaError_t ace_configure_f32(int L, int n, int cap, int tile_max, int qb, size_t* smem, int* grid, int wn) {

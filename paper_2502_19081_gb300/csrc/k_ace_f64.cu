@@ -4,10 +4,6 @@
 
 namespace mixd {
 
-cudaError_t ace_gaunt_upload_f64(const void* ent_f, const void* ent_d, int n_ent, const int* rows, int n_rows) {
-    return gaunt_upload_module(ent_f, ent_d, n_ent, rows, n_rows);
-}
-
 cudaError_t ace_configure_f64(int L, int n, int cap, int tile_max, int qb, size_t* smem, int* grid, int wn) {
     return ace_cfg_t<double>(false, L, n, cap, tile_max, qb, smem, grid, wn);
 }
@@ -33,11 +29,10 @@ cudaError_t ace_configure(int precision, int L, int n, int cap, int tile_max, in
                                  : ace_configure_f32(L, n, cap, tile_max, qb, smem, grid, wn);
 }
 
-cudaError_t ace_gaunt_upload(const void* ent_f, const void* ent_d, int n_ent, const int* rows, int n_rows) {
-    cudaError_t e = ace_gaunt_upload_f64(ent_f, ent_d, n_ent, rows, n_rows);
-    if (e == cudaSuccess) e = ace_gaunt_upload_f32(ent_f, ent_d, n_ent, rows, n_rows);
-    if (e == cudaSuccess) e = ace_gaunt_upload_tc1(ent_f, ent_d, n_ent, rows, n_rows);
-    if (e == cudaSuccess) e = ace_gaunt_upload_tc2(ent_f, ent_d, n_ent, rows, n_rows);
+cudaError_t ace_gaunt_upload(const void* ent_f, int n_ent, const int* rows, int n_rows) {
+    cudaError_t e = ace_gaunt_upload_f32(ent_f, n_ent, rows, n_rows);
+    if (e == cudaSuccess) e = ace_gaunt_upload_tc1(ent_f, n_ent, rows, n_rows);
+    if (e == cudaSuccess) e = ace_gaunt_upload_tc2(ent_f, n_ent, rows, n_rows);
     return e;
 }
 

@@ -55,8 +55,10 @@ __global__ void __launch_bounds__(TC_ACE_WARPS * 32, TC_MIN_CTAS) k_ace_tc(Dev d
     tc.bar = smem_u32(&s_bar);
     const int count = d.status[SW_NEXP];
     const int ng = (count + TC_ACE_WARPS - 1) / TC_ACE_WARPS;
-    for (int g = blockIdx.x; g < ng; g += gridDim.x)
+    __shared__ int s_g;
+    for (int g = ace_next_group(d, &s_g); g < ng; g = ace_next_group(d, &s_g))
         ace_group<float, L, NP, TCM>(d, tab, g * TC_ACE_WARPS, count, sm + NZ * zbytes, &tc);
+    ace_groups_done(d);
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {

@@ -113,7 +113,6 @@ struct GauntAll {
     std::vector<int> row0;                   // [t] first row offset of triple t in rows
     std::vector<int> rows;                   // entry offsets, 2 l3 + 2 per triple (the last: the end)
     std::vector<GEnt<float>> ent_f;
-    std::vector<GEnt<double>> ent_d;
     int index(int a, int b, int c) const {
         for (size_t t = 0; t < l1.size(); ++t)
             if (l1[t] == a && l2[t] == b && l3[t] == c) return (int)t;
@@ -166,19 +165,12 @@ const GauntAll& gaunt_all() {
                                 if (std::fabs(v) <= GAUNT_ZERO) continue;
                                 last = (int)g.ent_f.size();
                                 GEnt<float> ef;
-                                GEnt<double> ed;
                                 std::memset(&ef, 0, sizeof ef);
-                                std::memset(&ed, 0, sizeof ed);
-                                ef.pk = ed.pk = m1 | (m2 << 8);
+                                ef.pk = m1 | (m2 << 8);
                                 ef.g = (float)v;
-                                ed.g = v;
                                 g.ent_f.push_back(ef);
-                                g.ent_d.push_back(ed);
                             }
-                            if (last >= 0) {
-                                g.ent_f[last].pk |= GE_RUN_END;
-                                g.ent_d[last].pk |= GE_RUN_END;
-                            }
+                            if (last >= 0) g.ent_f[last].pk |= GE_RUN_END;
                         }
                     }
                     g.rows.push_back((int)g.ent_f.size());
@@ -186,18 +178,15 @@ const GauntAll& gaunt_all() {
                 }
         // one zero entry past the last, which the kernels' prefetch may read
         GEnt<float> ef;
-        GEnt<double> ed;
         std::memset(&ef, 0, sizeof ef);
-        std::memset(&ed, 0, sizeof ed);
         g.ent_f.push_back(ef);
-        g.ent_d.push_back(ed);
         return g;
     }();
     return tab;
 }
 
-// Copies the table into the constant memory of each kernel module on the
-// current device, once per device.
+// Copies the table into the constant memory of each float kernel module on
+// the current device, once per device.
 int gaunt_upload() {
     static std::mutex mu;
     static std::vector<int> done;
@@ -207,8 +196,7 @@ int gaunt_upload() {
     if (std::find(done.begin(), done.end(), dev) != done.end()) return MIX_OK;
     const GauntAll& g = gaunt_all();
     if ((int)g.ent_f.size() > GAUNT_ENT_CAP || (int)g.rows.size() > GAUNT_ROW_CAP) return MIX_EINVAL;
-    const cudaError_t e = ace_gaunt_upload(g.ent_f.data(), g.ent_d.data(), (int)g.ent_f.size(), g.rows.data(),
-                                           (int)g.rows.size());
+    const cudaError_t e = ace_gaunt_upload(g.ent_f.data(), (int)g.ent_f.size(), g.rows.data(), (int)g.rows.size());
     if (e != cudaSuccess) return MIX_ECUDA;
     done.push_back(dev);
     return MIX_OK;
@@ -308,6 +296,33 @@ std::vector<unsigned char> ace_tiles(int n, int np, const std::vector<int>& tau,
             const int v = goff[r2 + r] - e0;
             std::memcpy(tile.data() + h.o_go + (size_t)r * sizeof(int), &v, sizeof v);
         }
+        if (sizeof(T) == 8) {
+            // the ordering by m3, with the run-end flags of the constant table
+            const int r3 = 2 * l3 + 2, f0 = goff[gb], nf = goff[gb + r3 - 1] - f0;
+            size_t o3 = tile.size();
+            h.o_ge3 = (int)o3;
+            o3 += (size_t)nf * sizeof(GEnt<T>);
+            h.o_go3 = (int)o3;
+            o3 += (size_t)r3 * sizeof(int);
+            o3 = (o3 + 15) & ~(size_t)15;
+            tile.resize(o3, 0);
+            h.bytes = (int)o3;
+            std::memcpy(tile.data(), &h, sizeof h);
+            for (int r = 0; r + 1 < r3; ++r)
+                for (int k = goff[gb + r] - f0; k < goff[gb + r + 1] - f0; ++k) {
+                    GEnt<T> g;
+                    std::memset(&g, 0, sizeof g);
+                    const int m1 = gidx[f0 + k] & 255;
+                    const bool last = k + 1 >= goff[gb + r + 1] - f0 || (gidx[f0 + k + 1] & 255) != m1;
+                    g.pk = gidx[f0 + k] | (last ? GE_RUN_END : 0);
+                    g.g = (T)gval[f0 + k];
+                    std::memcpy(tile.data() + h.o_ge3 + (size_t)k * sizeof g, &g, sizeof g);
+                }
+            for (int r = 0; r < r3; ++r) {
+                const int v = goff[gb + r] - f0;
+                std::memcpy(tile.data() + h.o_go3 + (size_t)r * sizeof(int), &v, sizeof v);
+            }
+        }
         if (tcm) {
             // B[q3][k] = W[k][q3], k = q1 n + q2 (zero padding stays zero)
             for (int k = 0; k < n * n; ++k)
@@ -324,7 +339,7 @@ std::vector<unsigned char> ace_tiles(int n, int np, const std::vector<int>& tau,
         }
         off[t] = (int)out.size();
         out.insert(out.end(), tile.begin(), tile.end());
-        tile_max = std::max(tile_max, (int)o);
+        tile_max = std::max(tile_max, (int)tile.size());
     }
     off[ntau] = (int)out.size();
     return out;

@@ -34,6 +34,8 @@ enum StatusWord : int {
     SW_EVALS = 11,      // evaluations since the seed rule was set (coordination averaging)
     SW_NSEED = 12,      // number of seed atoms
     SW_EPOCH = 13,      // force evaluations since binding (stamps the incoming gradient rows)
+    SW_ACE_NEXT = 14,   // next group of expensive atoms to hand out (0 between launches)
+    SW_ACE_DONE = 15,   // CTAs of the expensive kernel that have finished (0 between launches)
     SW_COUNT = 64,
 };
 
@@ -268,7 +270,10 @@ struct __align__(sizeof(T) == 4 ? 8 : 16) GEnt {
 //     end; entry indices relative to o_ge) at o_go.
 // The ordering by m3 (m1 | m2 << 8, m1 ascending within a row, GE_RUN_END on
 // the last entry of each run of equal m1) is the same for every potential and
-// sits in constant memory, from row cg on.
+// sits in constant memory, from row cg on; float64 tiles also hold it, at
+// o_ge3 with its 2 l3 + 2 offset rows at o_go3 (the float64 kernel reads it
+// there: its entries are twice the size, and where few warps run a shared-
+// memory read is the quicker).
 // mode: 0 l's distinct, 1 l1 == l2, 2 l2 == l3, 3 all equal (W symmetrised over
 // the matching n indices).  Tiles of the tensor-core readout (bf16 modes) also
 // hold, at o_wb (128-byte aligned; 0 otherwise), W as the MMA's B operand: 16
@@ -279,7 +284,8 @@ struct AceTileHdr {
     int l1, l2, l3, mode;
     int o_ge, o_go, bytes, o_wb;
     int cg;             // first row of the triple in the constant-memory Gaunt table
-    int pad[3];         // 16-byte multiple: W follows
+    int o_ge3, o_go3;   // float64 tiles: their own ordering by m3 and its offset rows (0 in float tiles)
+    int pad;            // 16-byte multiple: W follows
 };
 
 // The constant-memory Gaunt table of the expensive kernels (every l-triple

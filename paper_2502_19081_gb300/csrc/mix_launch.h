@@ -31,13 +31,12 @@ cudaError_t ace_tc_configure(int tcm, int L, int n, int cap, int tile_max, int q
                              int* nbuf);
 void launch_ace_tc(const Dev& d, const void* tab, int tcm, int L, size_t smem, int grid, int nbuf, cudaStream_t s);
 
-// the Gaunt table of the expensive kernels into the constant memory of every
-// module that holds them, on the current device (k_ace_f64.cu dispatches)
-cudaError_t ace_gaunt_upload(const void* ent_f, const void* ent_d, int n_ent, const int* rows, int n_rows);
-cudaError_t ace_gaunt_upload_f32(const void* ent_f, const void* ent_d, int n_ent, const int* rows, int n_rows);
-cudaError_t ace_gaunt_upload_f64(const void* ent_f, const void* ent_d, int n_ent, const int* rows, int n_rows);
-cudaError_t ace_gaunt_upload_tc1(const void* ent_f, const void* ent_d, int n_ent, const int* rows, int n_rows);
-cudaError_t ace_gaunt_upload_tc2(const void* ent_f, const void* ent_d, int n_ent, const int* rows, int n_rows);
+// the Gaunt table of the float expensive kernels into the constant memory of
+// every module that holds them, on the current device (k_ace_f64.cu dispatches)
+cudaError_t ace_gaunt_upload(const void* ent_f, int n_ent, const int* rows, int n_rows);
+cudaError_t ace_gaunt_upload_f32(const void* ent_f, int n_ent, const int* rows, int n_rows);
+cudaError_t ace_gaunt_upload_tc1(const void* ent_f, int n_ent, const int* rows, int n_rows);
+cudaError_t ace_gaunt_upload_tc2(const void* ent_f, int n_ent, const int* rows, int n_rows);
 
 // tensor-core building block check (k_tc.cu)
 cudaError_t tc_selftest(const uint16_t* a, const uint16_t* b, int m, int n, int k, float* d, int* status,
