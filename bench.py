@@ -441,11 +441,18 @@ def gpu_leg(mix, torch, wl, prec, args, flush, peaks, hbm, oracle_seconds, e2e=T
             kb["executed_flops"] = pe_run * nst["n_exp"]
             kb["tflops"] = kb["algorithmic_flops"] / (phase_ms[p] * 1e-3) / 1e12 if phase_ms[p] > 0 else 0.0
         elif nm == "cheap":
-            # the cheap kernel runs on a second stream beside the expensive one:
-            # its phase time is only the part not hidden behind it; its own
-            # throughput comes from the pure-cheap step below
             kb["algorithmic_flops"] = pc * nst["n_cheap"]
-            kb["note"] = "concurrent with exp on a second stream; ms = the part after exp ends"
+            if hinfo["potential_order"] == mix.MIX_ORDER_SERIAL:
+                # one stream: the phase is the cheap kernel's own duration
+                kb["tflops"] = kb["algorithmic_flops"] / (phase_ms[p] * 1e-3) / 1e12 if phase_ms[p] > 0 else 0.0
+                kb["note"] = "after exp on the same stream (order chosen by mix_tune); ms = its own duration"
+            else:
+                # on a second stream beside the expensive kernel: its phase time
+                # is only the part not hidden behind it; its own throughput
+                # comes from the pure-cheap step below
+                first = "cheap" if hinfo["potential_order"] == mix.MIX_ORDER_CHEAP_FIRST else "exp"
+                kb["note"] = (f"concurrent with exp on a second stream, {first} launched first (order chosen by "
+                              "mix_tune); ms = the part after exp ends")
         else:
             kb["algorithmic_bytes"] = phase_bytes(nm, n, nst, rf)
             kb["gbs"] = kb["algorithmic_bytes"] / (phase_ms[p] * 1e-3) / 1e9 if phase_ms[p] > 0 else 0.0
@@ -680,6 +687,8 @@ def ours(args):
                 "force_max_abs_eV_per_A", 1.0) <= GATE)) for p, v in main["others"].items()},
         "roofline": roof,
         "kernels": kern,
+        "launch": {k: main["hinfo"][k] for k in ("potential_order", "exp_grid", "exp_threads", "exp_smem_bytes",
+                                                 "cheap_grid", "cheap_lanes", "gather_grid", "buffer_grid")},
         "mixing": main["mixing"],
         "fma_peak_tflops": {"fp64": peaks[mix.MIX_FP64] / 1e12, "fp32": peaks[mix.MIX_FP32] / 1e12},
         "e2e": main["e2e"],

@@ -148,7 +148,22 @@ typedef struct {
     int nbr_cap;            /* neighbour slots per atom; 0: automatic */
     int no_graphs;          /* 0: mix_step replays each step as one captured CUDA
                                graph launch; nonzero: kernels are launched one by one */
+    int potential_order;    /* how the two potential kernels of an evaluation share
+                               the GPU (MIX_ORDER_*; mix_tune picks the fastest) */
 } mix_options;
+
+/* Orders of the two potential kernels (they write disjoint arrays, so every
+ * order gives the same bits). */
+enum {
+    MIX_ORDER_CHEAP_FIRST = 0, /* two branches, the cheap kernel launched first, so
+                                  that it fills the SMs a small expensive set leaves
+                                  idle (default) */
+    MIX_ORDER_EXP_FIRST = 1,   /* two branches, the expensive kernel launched first;
+                                  the cheap one fills its last wave */
+    MIX_ORDER_SERIAL = 2       /* one stream: the expensive kernel, then the cheap one,
+                                  each with the whole GPU (their phase times are then
+                                  their own durations) */
+};
 
 /* A core region.  d = distance of an atom from the shape (minimum image in
  * periodic dimensions); lambda = 1 for d < r_core, 1 - (d - r_core) / ramp for
@@ -320,6 +335,7 @@ typedef struct {
                                   contracts the factor of smallest l densely instead,
                                   which does less work (Sec. 2.1: the basis is
                                   symmetric in its three factors) */
+    int potential_order;    /* MIX_ORDER_* in use */
 } mix_info;
 
 int mix_get_info(const mix_ctx* ctx, mix_info* info);
@@ -361,8 +377,9 @@ int mix_tc_selftest(const void* a_dev, const void* b_dev, int m, int n, int k, f
 
 /* Autotune one bound context: times force evaluations at the current
  * positions (which leave x, v and f unchanged) while varying, one at a time,
- * the persistent grid of each potential kernel and the grids of the gather and
- * buffer kernels, and keeps the fastest shapes (reported by mix_get_info).
+ * the order of the two potential kernels (MIX_ORDER_*), the persistent grid of
+ * each potential kernel and the grids of the gather and buffer kernels, and
+ * keeps the fastest (reported by mix_get_info).
  * reps: timed evaluations per candidate (median). */
 int mix_tune(mix_ctx* ctx, int reps);
 

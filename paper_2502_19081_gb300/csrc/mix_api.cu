@@ -392,6 +392,7 @@ struct mix_ctx {
     int64_t launches;
     bool profiling;
     bool opt_graphs;
+    int order;                 // MIX_ORDER_* of the two potential kernels
     cudaStream_t cap_stream;
     cudaStream_t aux;          // second branch of an evaluation: the cheap potential
     cudaEvent_t ev_fork, ev_join;
@@ -746,17 +747,32 @@ void enqueue_evaluation(mix_ctx* c, cudaStream_t s, int integrate, double dt, in
     if (prof) cudaEventRecordWithFlags(c->ev[3], s, ef);
     const void* at = c->precision == MIX_FP64 ? (const void*)&c->ace64 : (const void*)&c->ace32;
     const void* st = c->precision == MIX_FP64 ? (const void*)&c->spl64 : (const void*)&c->spl32;
-    // the two potentials write disjoint arrays: the cheap one runs on a second
-    // branch and fills the SMs the expensive kernel's last wave leaves idle
-    cudaEventRecord(c->ev_fork, s);
-    cudaStreamWaitEvent(c->aux, c->ev_fork, 0);
-    launch_spline(c->dev, st, c->precision, c->spl_lpa, c->spl_smem, c->spl_grid, c->aux);
-    cudaEventRecord(c->ev_join, c->aux);
-    if (c->ace_tcm) launch_ace_tc(c->dev, at, c->ace_tcm, c->L, c->ace_smem, c->ace_grid, c->ace_nbuf, s);
-    else launch_ace(c->dev, at, c->precision, c->L, c->ace_smem, c->ace_grid, c->ace_wn, s);
-    if (prof) cudaEventRecordWithFlags(c->ev[4], s, ef);
-    cudaStreamWaitEvent(s, c->ev_join, 0);
-    if (prof) cudaEventRecordWithFlags(c->ev[5], s, ef);
+    auto exp_kernel = [&]() {
+        if (c->ace_tcm) launch_ace_tc(c->dev, at, c->ace_tcm, c->L, c->ace_smem, c->ace_grid, c->ace_nbuf, s);
+        else launch_ace(c->dev, at, c->precision, c->L, c->ace_smem, c->ace_grid, c->ace_wn, s);
+    };
+    if (c->order == MIX_ORDER_SERIAL) {
+        // each kernel has the whole GPU: when the expensive set alone fills
+        // every SM, running the two side by side only delays the expensive one
+        exp_kernel();
+        if (prof) cudaEventRecordWithFlags(c->ev[4], s, ef);
+        launch_spline(c->dev, st, c->precision, c->spl_lpa, c->spl_smem, c->spl_grid, s);
+        if (prof) cudaEventRecordWithFlags(c->ev[5], s, ef);
+    } else {
+        // the two potentials write disjoint arrays: the cheap one runs on a
+        // second branch, launched before the expensive kernel (so that it takes
+        // the SMs a small expensive set leaves idle) or after it (so that it
+        // fills the expensive kernel's last wave)
+        cudaEventRecord(c->ev_fork, s);
+        if (c->order == MIX_ORDER_EXP_FIRST) exp_kernel();
+        cudaStreamWaitEvent(c->aux, c->ev_fork, 0);
+        launch_spline(c->dev, st, c->precision, c->spl_lpa, c->spl_smem, c->spl_grid, c->aux);
+        cudaEventRecord(c->ev_join, c->aux);
+        if (c->order == MIX_ORDER_CHEAP_FIRST) exp_kernel();
+        if (prof) cudaEventRecordWithFlags(c->ev[4], s, ef);
+        cudaStreamWaitEvent(s, c->ev_join, 0);
+        if (prof) cudaEventRecordWithFlags(c->ev[5], s, ef);
+    }
     launch_gather(c->dev, c->precision, integrate, h, s);
     if (prof) cudaEventRecordWithFlags(c->ev[6], s, ef);
 }
@@ -932,6 +948,9 @@ int mix_init(const mix_system* sys, const mix_ace* a, const mix_spline* sp, cons
     c->sys = *sys;
     c->opt = *opt;
     c->opt_graphs = opt->no_graphs == 0;
+    if (opt->potential_order < MIX_ORDER_CHEAP_FIRST || opt->potential_order > MIX_ORDER_SERIAL)
+        return bad("potential_order");
+    c->order = opt->potential_order;
     c->precision = opt->precision;
     c->ace_rc = a->r_cut;
     c->n = a->n_rad;
@@ -1384,6 +1403,7 @@ int mix_get_info(const mix_ctx* c, mix_info* info) {
     info->tc_flops_per_atom = c->ace_tcm ? 2.0 * (double)c->tau_d3_sum * c->n * c->n * c->n : 0.0;
     info->cheap_lanes = c->spl_lpa;
     info->nu3_flops_ref_per_atom = c->nu3_flops_ref;
+    info->potential_order = c->order;
     return MIX_OK;
 }
 
@@ -1884,11 +1904,14 @@ int mix_tune(mix_ctx* c, int reps) {
     std::vector<int> gs = {c->spl_grid_max, c->spl_grid_max / 2, c->spl_grid_max / 4};
     std::vector<int> gg = {sms * 2, sms * 4, sms * 8, sms * 16};
     SeedSave saved;
+    const std::vector<int> orders = {MIX_ORDER_CHEAP_FIRST, MIX_ORDER_EXP_FIRST, MIX_ORDER_SERIAL};
     int st = seed_save(c, &saved);
+    if (!st) st = tune_param(c, reps, &c->order, orders);
     if (!st) st = tune_param(c, reps, &c->ace_grid, ga);
     if (!st) st = tune_param(c, reps, &c->spl_grid, gs);
     if (!st) st = tune_param(c, reps, &c->dev.grid_gather, gg);
     if (!st) st = tune_param(c, reps, &c->dev.grid_buffer, gg);
+    if (!st) st = tune_param(c, reps, &c->order, orders);   // again, at the shapes chosen
     drop_graph(c);
     const int st2 = seed_restore(c, saved);
     return st ? st : st2;

@@ -37,6 +37,9 @@ MIX_BF16_SPLIT = 3    # the same with hi/lo bf16 operand splits (three MMAs per 
 PREC_NAMES = {MIX_FP64: "f64", MIX_FP32: "f32", MIX_BF16: "bf16", MIX_BF16_SPLIT: "bf16x3"}
 MIX_BLEND_LINEAR = 0
 MIX_BLEND_CUBIC = 1
+MIX_ORDER_CHEAP_FIRST = 0   # the two potential kernels on two branches, the cheap one launched first
+MIX_ORDER_EXP_FIRST = 1     # two branches, the expensive one launched first
+MIX_ORDER_SERIAL = 2        # one stream: the expensive kernel, then the cheap one
 
 # functions declared in include/mix.h
 EXPORTS = [
@@ -81,7 +84,7 @@ class mix_spline(ctypes.Structure):
 class mix_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("skin", ctypes.c_double), ("blend", ctypes.c_int),
                 ("buffer_exp", ctypes.c_double), ("buffer_cheap", ctypes.c_double), ("nbr_cap", ctypes.c_int),
-                ("no_graphs", ctypes.c_int)]
+                ("no_graphs", ctypes.c_int), ("potential_order", ctypes.c_int)]
 
 
 class mix_region(ctypes.Structure):
@@ -105,7 +108,7 @@ class mix_info(ctypes.Structure):
                 ("launches", ctypes.c_int64), ("gather_grid", ctypes.c_int), ("build_grid", ctypes.c_int),
                 ("buffer_grid", ctypes.c_int), ("exp_tensor_cores", ctypes.c_int),
                 ("tc_flops_per_atom", ctypes.c_double), ("cheap_lanes", ctypes.c_int),
-                ("nu3_flops_ref_per_atom", ctypes.c_double)]
+                ("nu3_flops_ref_per_atom", ctypes.c_double), ("potential_order", ctypes.c_int)]
 
 
 class mix_server_options(ctypes.Structure):
@@ -217,7 +220,7 @@ def _f64(a) -> np.ndarray:
 
 
 def _init_structs(workload, precision, nbr_cap=0, blend=MIX_BLEND_LINEAR, buffer_exp=0.0, buffer_cheap=0.0,
-                  skin=None, graphs=True):
+                  skin=None, graphs=True, order=MIX_ORDER_CHEAP_FIRST):
     """mix_init arguments for a workload; the returned list keeps the arrays alive."""
     s = workload.system
     keep = []
@@ -232,7 +235,7 @@ def _init_structs(workload, precision, nbr_cap=0, blend=MIX_BLEND_LINEAR, buffer
                    _dp(pair))
     spld = mix_spline(float(sp.r_cut), float(sp.r_cut3), _dp(s2), _dp(s3))
     opt = mix_options(int(precision), float(workload.skin if skin is None else skin), int(blend),
-                      float(buffer_exp), float(buffer_cheap), int(nbr_cap), 0 if graphs else 1)
+                      float(buffer_exp), float(buffer_cheap), int(nbr_cap), 0 if graphs else 1, int(order))
     return sysd, aced, spld, opt, keep
 
 
@@ -253,7 +256,7 @@ class Context:
     def __init__(self, workload: "I.Workload", precision: int = MIX_FP64, device: str = "cuda:0",
                  nbr_cap: int = 0, blend: int = MIX_BLEND_LINEAR, buffer_exp: float = 0.0,
                  buffer_cheap: float = 0.0, skin: Optional[float] = None, regions: Optional[Sequence] = None,
-                 stream=None, graphs: bool = True):
+                 stream=None, graphs: bool = True, order: int = MIX_ORDER_CHEAP_FIRST):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("no CUDA device: the mixed-MD path runs only on the GPU")
@@ -265,7 +268,7 @@ class Context:
         self.n = int(s.n)
         self.precision = precision
         sysd, aced, spld, opt, self._keep = _init_structs(workload, precision, nbr_cap, blend, buffer_exp,
-                                                          buffer_cheap, skin, graphs)
+                                                          buffer_cheap, skin, graphs, order)
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
             h = ctypes.c_void_p()

@@ -277,6 +277,35 @@ def test_deterministic_and_resumable(mx):
     assert np.abs(d).max() < 1e-12 and _max_abs(vc, va) < 1e-12 and _max_abs(fc, fa) < 1e-10
 
 
+@pytest.mark.parametrize("prec", [0, 2])
+def test_potential_orders_give_the_same_bits(mx, prec):
+    """The two potential kernels write disjoint arrays, so launching them on two
+    branches in either order or one after the other on one stream gives the
+    same trajectory bit for bit; the autotuner keeps one of the three orders
+    and the state it found."""
+    wl = I.small_fe_box(16, r_core=4.0, ramp=3.0, sigma=0.15)
+    runs = []
+    for order in (mx.MIX_ORDER_CHEAP_FIRST, mx.MIX_ORDER_EXP_FIRST, mx.MIX_ORDER_SERIAL):
+        c = mx.open_context(wl, precision=prec, order=order)
+        assert c.info()["potential_order"] == order
+        c.step(1.0, 30)
+        runs.append(c.get_state())
+        if order == mx.MIX_ORDER_SERIAL:
+            c.tune(2)
+            assert c.info()["potential_order"] in (0, 1, 2)
+            x0, v0, f0, s0 = runs[-1]
+            x1, v1, f1, s1 = c.get_state()
+            assert s1 == s0 and np.array_equal(x1, x0) and np.array_equal(v1, v0) and np.array_equal(f1, f0)
+            c.step(1.0, 5)
+            assert c.get_state()[3] == 35
+        c.close()
+    for x, v, f, st in runs[1:]:
+        assert st == runs[0][3]
+        assert np.array_equal(x, runs[0][0]) and np.array_equal(v, runs[0][1]) and np.array_equal(f, runs[0][2])
+    with pytest.raises(mx.MixError):
+        mx.Context(wl, precision=prec, order=3)
+
+
 def test_three_body_lane_groups_narrow_then_widen(mx):
     """A Si bulk: the uniform-density estimate puts the cheap kernel on warps,
     the first evaluation measures at most about 6 three-body neighbours and
