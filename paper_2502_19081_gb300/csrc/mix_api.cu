@@ -1479,21 +1479,61 @@ namespace {
 
 // median duration (ms) of `reps` force evaluations at the current positions
 // (integrate = 0 leaves x, v and f as they are), after one untimed evaluation
+// One force evaluation captured as a graph: the form in which mix_step replays
+// its steps, so that the tuner times the candidates as they will run (the
+// order in which the two potential kernels reach the SMs differs between
+// graph replays and launches on streams).
+int capture_eval(mix_ctx* c, cudaGraphExec_t* out) {
+    *out = nullptr;
+    if (!c->cap_stream) {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_fail(c, e, "capture stream");
+    }
+    cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamBeginCapture");
+    enqueue_evaluation(c, c->cap_stream, 0, 0.0, 0, false, true);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(c->cap_stream, &g);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        *out = nullptr;
+        return cuda_fail(c, e, "cudaGraphInstantiate");
+    }
+    return MIX_OK;
+}
+
 int time_force_evals(mix_ctx* c, int reps, float* ms) {
     int st = evaluate(c, 0, 0.0);
     if (st) return st;
     c->forces_valid = true;
+    cudaGraphExec_t gx = nullptr;
+    if (c->opt_graphs) {
+        st = capture_eval(c, &gx);
+        if (st) return st;
+        cudaError_t e = cudaGraphLaunch(gx, c->stream);   // once untimed
+        if (e != cudaSuccess) {
+            cudaGraphExecDestroy(gx);
+            return cuda_fail(c, e, "tuning");
+        }
+    }
     cudaEvent_t e0, e1;
-    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return fail(c, MIX_ECUDA, "event");
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (gx) cudaGraphExecDestroy(gx);
+        return fail(c, MIX_ECUDA, "event");
+    }
     std::vector<float> v;
     for (int r = 0; r < reps; ++r) {
         cudaEventRecord(e0, c->stream);
-        enqueue_evaluation(c, c->stream, 0, 0.0, 0, false);
+        if (gx) cudaGraphLaunch(gx, c->stream);
+        else enqueue_evaluation(c, c->stream, 0, 0.0, 0, false);
         cudaEventRecord(e1, c->stream);
         cudaError_t e = cudaEventSynchronize(e1);
         if (e != cudaSuccess) {
             cudaEventDestroy(e0);
             cudaEventDestroy(e1);
+            if (gx) cudaGraphExecDestroy(gx);
             return cuda_fail(c, e, "tuning");
         }
         float t = 0.f;
@@ -1502,6 +1542,7 @@ int time_force_evals(mix_ctx* c, int reps, float* ms) {
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (gx) cudaGraphExecDestroy(gx);
     std::sort(v.begin(), v.end());
     *ms = v.empty() ? 0.f : v[v.size() / 2];
     return check_stream_error(c, "tuning");
