@@ -11,7 +11,9 @@ exactly those positions.
 * screw cylinder (256,000 atoms): 64 sampled atoms (core, ramp, expensive
   buffer, cheap only) at step 0 and after 100 steps in float64 and in float,
   and every 100 steps up to 500 with the bf16 hi/lo readout, the whole set
-  compared exactly.
+  compared exactly; with the plain bf16 readout every 100 steps up to 500,
+  every atom's force within the gate of the float64 path at the same
+  positions and 64 sampled atoms within the gate of the oracle.
 """
 import numpy as np
 import pytest
@@ -78,3 +80,34 @@ def test_screw_cylinder_checkpoints(mx, prec, tol, nblocks):
         pick = _sample(rng, lam, fl, 16)
         Fs = om.forces_sampled(x, pick)
         assert _max_abs(F[pick, :3], Fs[:, :3]) < tol, step
+
+
+def test_screw_cylinder_plain_bf16_within_gate_500_steps(mx):
+    """The screw cylinder with the plain bf16 readout (the precision its
+    throughput is quoted in) for 500 steps: every 100 steps the evaluated sets
+    equal the oracle's, every atom's force is within the 1e-3 eV/A gate of the
+    float64 path evaluated at the same positions (which itself matches the
+    oracle to 1e-10), and 64 sampled atoms are within the gate of the oracle."""
+    wl = I.fe_screw()
+    ctx = mx.open_context(wl, precision=mx.MIX_BF16)
+    ref = mx.open_context(wl, precision=mx.MIX_FP64)
+    om = oracle.Model(wl)
+    rng = np.random.default_rng(11)
+    for k in range(6):
+        if k:
+            ctx.step(wl.dt, 100)
+        x, v, F, step = ctx.get_state()
+        assert step == 100 * k
+        fl, _, _ = ctx.sets()
+        assert np.array_equal(fl, om.sets(x)), step
+        ref.set_state(x, v, None, step)
+        ref.forces()
+        _, _, F64, _ = ref.get_state()
+        assert _max_abs(F[:, :3], F64[:, :3]) < 1e-3, step
+        lam, _ = ctx.lam()
+        pick = _sample(rng, lam, fl, 16)
+        Fs = om.forces_sampled(x, pick)
+        assert _max_abs(F[pick, :3], Fs[:, :3]) < 1e-3, step
+        assert _max_abs(F64[pick, :3], Fs[:, :3]) < 1e-10, step
+    ctx.close()
+    ref.close()
