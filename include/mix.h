@@ -377,9 +377,13 @@ int mix_tc_selftest(const void* a_dev, const void* b_dev, int m, int n, int k, f
 
 /* Autotune one bound context: times force evaluations at the current
  * positions (which leave x, v and f unchanged) while varying, one at a time,
- * the order of the two potential kernels (MIX_ORDER_*), the persistent grid of
- * each potential kernel and the grids of the gather and buffer kernels, and
- * keeps the fastest (reported by mix_get_info).
+ * the order of the two potential kernels (MIX_ORDER_*), the lane groups of the
+ * cheap kernel (a narrower group is tried only where the largest 3-body
+ * neighbour count measured so far fills at most two thirds of its on-chip
+ * slots; a later overflow reports MIX_EOVERFLOW and widens the groups again),
+ * the persistent grid of each potential kernel and the grids of the gather and
+ * buffer kernels, and keeps the fastest (reported by mix_get_info); the
+ * forces do not depend on any of them.
  * reps: timed evaluations per candidate (median). */
 int mix_tune(mix_ctx* ctx, int reps);
 

@@ -1567,6 +1567,57 @@ int tune_param(mix_ctx* c, int reps, int* param, const std::vector<int>& cand) {
     return MIX_OK;
 }
 
+// The cheap kernel's lane groups: besides the current width, each narrower
+// group whose on-chip 3-body slots the largest count measured so far fills to
+// at most two thirds (so a local rise of half that count still fits; beyond
+// it the evaluation reports MIX_EOVERFLOW and the groups widen again), in any
+// system, periodic or not; the fastest is kept.  The forces do not depend on
+// the width (every per-slot sum keeps its order).
+int tune_cheap_lanes(mix_ctx* c, int reps) {
+    const int seen = c->pinned[SW_NB3MAX], lpa0 = c->spl_lpa;
+    if (seen <= 0) return MIX_OK;
+    std::vector<int> lanes = {lpa0};
+    for (int l : {16, 8})
+        if (l < lpa0 && 3 * seen <= 2 * spline_nb3(l)) lanes.push_back(l);
+    if (lanes.size() < 2) return MIX_OK;
+    const size_t smem0 = c->spl_smem;
+    const int grid0 = c->spl_grid, gmax0 = c->spl_grid_max;
+    int best = lpa0;
+    float tbest = 1e30f;
+    for (int l : lanes) {
+        size_t smem = 0;
+        int grid = 0;
+        if (spline_configure(c->precision, l, &smem, &grid) != cudaSuccess) continue;
+        c->spl_lpa = l;
+        c->spl_smem = smem;
+        c->spl_grid = c->spl_grid_max = grid;
+        float t = 0.f;
+        const int st = time_force_evals(c, reps, &t);
+        if (st) return st;
+        if (t < tbest) {
+            tbest = t;
+            best = l;
+        }
+    }
+    if (best == lpa0) {
+        c->spl_lpa = lpa0;
+        c->spl_smem = smem0;
+        c->spl_grid = grid0;
+        c->spl_grid_max = gmax0;
+        return MIX_OK;
+    }
+    size_t smem = 0;
+    int grid = 0;
+    cudaError_t e = spline_configure(c->precision, best, &smem, &grid);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cheap kernel shape");
+    c->spl_lpa = best;
+    c->spl_smem = smem;
+    c->spl_grid = c->spl_grid_max = grid;
+    c->spl_lpa_settled = true;
+    c->regions_version++;   // any batch holding the context re-plans
+    return MIX_OK;
+}
+
 void set_grid_divisor(mix_ctx* c, int div) {
     c->ace_grid = std::max(1, c->ace_grid_max / div);
     c->spl_grid = std::max(1, c->spl_grid_max / div);
@@ -1942,12 +1993,13 @@ int mix_tune(mix_ctx* c, int reps) {
     if (reps < 1) reps = 3;
     const int sms = sm_count();
     std::vector<int> ga = {c->ace_grid_max, c->ace_grid_max * 3 / 4, c->ace_grid_max / 2, c->ace_grid_max / 4};
-    std::vector<int> gs = {c->spl_grid_max, c->spl_grid_max / 2, c->spl_grid_max / 4};
     std::vector<int> gg = {sms * 2, sms * 4, sms * 8, sms * 16};
     SeedSave saved;
     const std::vector<int> orders = {MIX_ORDER_CHEAP_FIRST, MIX_ORDER_EXP_FIRST, MIX_ORDER_SERIAL};
     int st = seed_save(c, &saved);
     if (!st) st = tune_param(c, reps, &c->order, orders);
+    if (!st) st = tune_cheap_lanes(c, reps);
+    std::vector<int> gs = {c->spl_grid_max, c->spl_grid_max / 2, c->spl_grid_max / 4};
     if (!st) st = tune_param(c, reps, &c->ace_grid, ga);
     if (!st) st = tune_param(c, reps, &c->spl_grid, gs);
     if (!st) st = tune_param(c, reps, &c->dev.grid_gather, gg);

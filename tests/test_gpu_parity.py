@@ -306,6 +306,29 @@ def test_potential_orders_give_the_same_bits(mx, prec):
         mx.Context(wl, precision=prec, order=3)
 
 
+def test_tuning_leaves_the_trajectory_unchanged(mx):
+    """A non-periodic Fe cylinder keeps warps for its cheap atoms until the
+    autotuner, having measured the largest 3-body count, may try half warps;
+    whatever shapes it keeps, the trajectory is the untuned one bit for bit."""
+    wl = _wl("screw_3000")
+    a = mx.open_context(wl, precision=1)
+    b = mx.open_context(wl, precision=1)
+    assert a.info()["cheap_lanes"] == 32
+    a.step(1.0, 10)
+    b.step(1.0, 10)
+    b.sync()
+    b.tune(2)
+    assert b.info()["cheap_lanes"] in (16, 32)
+    a.step(1.0, 30)
+    b.step(1.0, 30)
+    xa, va, fa, sa = a.get_state()
+    xb, vb, fb, sb = b.get_state()
+    assert sa == sb == 40
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb) and np.array_equal(fa, fb)
+    a.close()
+    b.close()
+
+
 def test_three_body_lane_groups_narrow_then_widen(mx):
     """A Si bulk: the uniform-density estimate puts the cheap kernel on warps,
     the first evaluation measures at most about 6 three-body neighbours and
