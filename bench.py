@@ -491,7 +491,10 @@ def gpu_leg(mix, torch, wl, prec, args, flush, peaks, hbm, oracle_seconds, e2e=T
 def profile_run(args):
     """The command the committed ncu summaries were taken with: one context of
     the workload (precision auto: bf16 for the screw cylinder, else fp32), W
-    warm-up steps and K steps, synchronised, and a one-line summary."""
+    warm-up steps, the library's autotuner (as the timed runs use it), and K
+    steps between cudaProfilerStart and cudaProfilerStop (ncu
+    --profile-from-start off captures those alone), synchronised, and a
+    one-line summary."""
     import torch
     from paper_2502_19081_gb300 import build as B
     from paper_2502_19081_gb300 import mix
@@ -517,10 +520,15 @@ def profile_run(args):
     ctx = mix.open_context(wl, precision=prec)
     ctx.step(wl.dt, args.warmup)
     ctx.sync()
+    ctx.tune(3)
+    ctx.sync()
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
     t0 = time.perf_counter()
     ctx.step(wl.dt, args.steps)
     ctx.sync()
     el = time.perf_counter() - t0
+    torch.cuda.profiler.stop()
     print(json.dumps({"mode": "ncu", "workload": wl.name, "precision": mix.PREC_NAMES[prec], "steps": args.steps,
                       "wall_s": el, "info": ctx.info()}), flush=True)
     ctx.close()
