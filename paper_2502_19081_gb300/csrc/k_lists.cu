@@ -32,10 +32,20 @@ __device__ __forceinline__ void disp_body(const Dev& d, int bx, int gx, int inte
             if (force_rebuild) d.status[SW_REBUILD] = 1;
         }
         if (i >= d.n) return;
+        // every load first, so that one memory latency covers them all (the
+        // arrays never overlap, which the compiler cannot know)
         double4 x = d.x[i];
+        double4 v = make_double4(0.0, 0.0, 0.0, 0.0), f = v, xb = v;
+        int c3 = 0;
         if (integrate) {
-            double4 v = d.v[i];
-            const double4 f = d.f[i];
+            v = d.v[i];
+            f = d.f[i];
+        }
+        if (!force_rebuild) {
+            xb = d.xb[i];
+            if (d.xr) c3 = d.cell3[i];
+        }
+        if (integrate) {
             v.x = __dadd_rn(v.x, __dmul_rn(h, f.x));
             v.y = __dadd_rn(v.y, __dmul_rn(h, f.y));
             v.z = __dadd_rn(v.z, __dmul_rn(h, f.z));
@@ -55,11 +65,10 @@ __device__ __forceinline__ void disp_body(const Dev& d, int bx, int gx, int inte
             if (!d.box.per[k] && (xs[k] < d.box.lo[k] || xs[k] >= d.box.lo[k] + d.box.L[k]))
                 set_status(d.status, ST_OUT_OF_BOX);
         if (!force_rebuild) {
-            const double4 xb = d.xb[i];
             const double dx = x.x - xb.x, dy = x.y - xb.y, dz = x.z - xb.z;
             if (dx * dx + dy * dy + dz * dz > d.half_skin2) d.status[SW_REBUILD] = 1;
             // relative to the cell of the last build (recomputed by k_cell_bin on rebuilds)
-            if (d.xr) d.xr[i] = cell_relative(d.box, d.cells, x, d.cell3[i]);
+            if (d.xr) d.xr[i] = cell_relative(d.box, d.cells, x, c3);
         }
     }
 }
@@ -557,7 +566,11 @@ void launch_build(const Dev& d, cudaStream_t s) {
         const int grid = (int)(want < lim ? want : lim);
         k_neigh_build<<<grid > 0 ? grid : 1, NB_WARPS * 32, NB_WARPS * capp2 * sizeof(int), s>>>(d, capp2);
     }
-    const int nr = (int)((d.n + 7) / 8);   // a warp per atom
+    // a warp per atom, striding; the grid is bounded (two waves of 8 CTAs an
+    // SM) so that the steps without a rebuild, where every CTA exits at once,
+    // launch few of them
+    const int64_t want_r = (d.n + 7) / 8, lim_r = (int64_t)sm_count() * 16;
+    const int nr = (int)(want_r < lim_r ? want_r : lim_r);
     k_neigh_rev<<<nr > 0 ? nr : 1, 256, 0, s>>>(d);
 }
 
