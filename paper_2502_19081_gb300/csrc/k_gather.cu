@@ -221,9 +221,15 @@ void launch_gather_batch(const BatchPlan& p, int precision, int integrate, doubl
 void launch_gather(const Dev& d, int precision, int integrate, double h, cudaStream_t s) {
     const int lpa = gather_lpa(d);
     // atoms per warp: enough warps for about half occupancy, at most G_ATOMS, and
-    // with quarter-warp groups at least one atom per group
+    // with quarter-warp groups at least one atom per group; in large systems
+    // small enough that every resident CTA takes about four chunks, so the last
+    // wave of chunks is not a partly empty one (256,000 atoms in chunks of
+    // 8 x 32 are 1.6 waves of the 608 resident CTAs)
     const int64_t warps_wanted = (int64_t)sm_count() * 32;
     int ga = (int)((d.n + warps_wanted - 1) / warps_wanted);
+    const int64_t resident = (int64_t)sm_count() * (precision == MIX_FP64 ? 2 : 4);   // the launch bounds
+    const int64_t ga_waves = (d.n + G_WARPS * resident * 4 - 1) / (G_WARPS * resident * 4);
+    if (ga > ga_waves) ga = (int)ga_waves;
     ga = ga < 32 / lpa ? 32 / lpa : (ga > G_ATOMS ? G_ATOMS : ga);
     const int64_t per_block = (int64_t)G_WARPS * ga;
     int64_t want = (d.n + per_block - 1) / per_block;
