@@ -45,6 +45,13 @@ __device__ __forceinline__ void bspline4(T x, int qmax, int& q, T b[4], T db[4])
     db[3] = T(0.5) * u2;
 }
 
+// An atom's list length and the first list slot and reverse slot of a lane,
+// loaded while the previous atom is evaluated, so that an atom's first partner
+// positions wait on one load rather than three in a chain.
+struct AtomHead {
+    int m, j0, r0;
+};
+
 template <typename T, int NB>
 struct SplWarp {   // per-group shared scratch
     static constexpr int NP = NB * (NB - 1) / 2;
@@ -79,7 +86,8 @@ __device__ __forceinline__ void spl_fill_tq(unsigned char* tq) {
 template <typename T, int LPA>
 __device__ __forceinline__ int spline_atom(const Dev& d, const SplTab<T>& tab, int i,
                                             const typename Vec4<T>::type* c2w, const typename Vec4<T>::type* c3w,
-                                            const unsigned char* tq, SplWarp<T, spl_nb<LPA>()>& W) {
+                                            const unsigned char* tq, SplWarp<T, spl_nb<LPA>()>& W,
+                                            const AtomHead* head = nullptr) {
     constexpr int NB = spl_nb<LPA>();
     using V = typename Vec4<T>::type;
     const int lane = threadIdx.x & 31;
@@ -97,7 +105,7 @@ __device__ __forceinline__ int spline_atom(const Dev& d, const SplTab<T>& tab, i
         using Pt = typename PairFrame<T>::Pt;
         const PairFrame<T> pf(d, i);
         const typename PairFrame<T>::Geo geo = PairFrame<T>::geo(d);   // once per atom, in registers
-        const int m = d.nnb[i];
+        const int m = head ? head->m : d.nnb[i];
         const int* row = d.nbr + (int64_t)i * cap;
         const int* rvr = d.rev + (int64_t)i * cap;
         V* grow = GC + (int64_t)i * cap;
@@ -110,8 +118,8 @@ __device__ __forceinline__ int spline_atom(const Dev& d, const SplTab<T>& tab, i
         int jn = 0, rn = 0;
         Pt ptn{};
         if (sub < m) {
-            jn = row[sub];
-            rn = rvr[sub];
+            jn = head ? head->j0 : row[sub];
+            rn = head ? head->r0 : rvr[sub];
             ptn = PairFrame<T>::load(d, jn);
         }
         for (int c = 0; c * LPA < m; ++c) {
@@ -292,14 +300,34 @@ __global__ void __launch_bounds__(SPL_WARPS * 32, sizeof(T) == 4 ? 6 : 1) k_spli
     const int count = d.status[SW_NCHEAP];
     const int stride = gridDim.x * SPL_WARPS * G;
     int a = (blockIdx.x * SPL_WARPS + warp) * G + grp;
+    const int sub = threadIdx.x & (LPA - 1), cap = d.cap;
+    // an atom's head (list length, this lane's first slot and reverse slot)
+    // is loaded an atom ahead, and the atom index two atoms ahead; the slot
+    // loads do not wait for the length (slot sub < cap lies in the atom's row)
+    auto load_head = [&](int at) {
+        AtomHead hd{0, 0, 0};
+        hd.m = d.nnb[at];
+        if (sub < cap) {
+            hd.j0 = d.nbr[(int64_t)at * cap + sub];
+            hd.r0 = d.rev[(int64_t)at * cap + sub];
+        }
+        return hd;
+    };
     int i = a < count ? d.act_c[a] : 0;
+    AtomHead hd{0, 0, 0};
+    if (a < count) hd = load_head(i);
+    int in = a + stride < count ? d.act_c[a + stride] : 0;
     int nb3 = 0;   // the largest 3-body count this lane's group met
-    while (a < count) {   // the next atom's index is loaded ahead
+    while (a < count) {
         const int an = a + stride;
-        const int in = an < count ? d.act_c[an] : 0;
-        nb3 = max(nb3, spline_atom<T, LPA>(d, tab, i, c2s, c3s, tq, ws[warp * G + grp]));
+        const int inn = an + stride < count ? d.act_c[an + stride] : 0;
+        AtomHead hn{0, 0, 0};
+        if (an < count) hn = load_head(in);
+        nb3 = max(nb3, spline_atom<T, LPA>(d, tab, i, c2s, c3s, tq, ws[warp * G + grp], &hd));
         a = an;
         i = in;
+        in = inn;
+        hd = hn;
     }
     // one atomic a warp: the context's lane groups are narrowed from it
     nb3 = __reduce_max_sync(0xffffffffu, nb3);
