@@ -729,19 +729,38 @@ __device__ __forceinline__ void nu3_tile(const unsigned char* tile, const AceTab
                 ld_gent(ge + e, pk, gv);
                 const T* ar = A1 + (pk & 255) * NP;
                 const T* ur = U1 + (pk >> 8) * n * NP + q2;
-                T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
-                for (int q1 = 0; q1 < n; ++q1) {
-                    const T av = ar[q1];
-                    const V4<T> u4 = ld4<T>(ur + q1 * NP);
-                    s0 += av * u4.x;
-                    s1 += av * u4.y;
-                    s2 += av * u4.z;
-                    s3 += av * u4.w;
+                if constexpr (sizeof(T) == 4) {
+                    // the same fused multiply-adds, two an instruction
+                    float2 s01 = make_float2(0.f, 0.f), s23 = make_float2(0.f, 0.f);
+                    for (int q1 = 0; q1 < n; ++q1) {
+                        const float av = ar[q1];
+                        const float2 a2 = make_float2(av, av);
+                        const V4<T> u4 = ld4<T>(ur + q1 * NP);
+                        s01 = __ffma2_rn(a2, make_float2(u4.x, u4.y), s01);
+                        s23 = __ffma2_rn(a2, make_float2(u4.z, u4.w), s23);
+                    }
+                    const float2 g2 = make_float2(gv, gv);
+                    const float2 c01 = __ffma2_rn(g2, s01, make_float2(c0, c1));
+                    const float2 c23 = __ffma2_rn(g2, s23, make_float2(c2, c3));
+                    c0 = c01.x;
+                    c1 = c01.y;
+                    c2 = c23.x;
+                    c3 = c23.y;
+                } else {
+                    T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+                    for (int q1 = 0; q1 < n; ++q1) {
+                        const T av = ar[q1];
+                        const V4<T> u4 = ld4<T>(ur + q1 * NP);
+                        s0 += av * u4.x;
+                        s1 += av * u4.y;
+                        s2 += av * u4.z;
+                        s3 += av * u4.w;
+                    }
+                    c0 += gv * s0;
+                    c1 += gv * s1;
+                    c2 += gv * s2;
+                    c3 += gv * s3;
                 }
-                c0 += gv * s0;
-                c1 += gv * s1;
-                c2 += gv * s2;
-                c3 += gv * s3;
             }
             T* orow = o2 + m2 * NP + q2;
             orow[0] += c0;
