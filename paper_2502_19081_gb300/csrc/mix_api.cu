@@ -1477,8 +1477,6 @@ const char* mix_last_error(const mix_ctx* c) { return c ? c->err.c_str() : ""; }
 
 namespace {
 
-// median duration (ms) of `reps` force evaluations at the current positions
-// (integrate = 0 leaves x, v and f as they are), after one untimed evaluation
 // One force evaluation captured as a graph: the form in which mix_step replays
 // its steps, so that the tuner times the candidates as they will run (the
 // order in which the two potential kernels reach the SMs differs between
@@ -1504,6 +1502,9 @@ int capture_eval(mix_ctx* c, cudaGraphExec_t* out) {
     return MIX_OK;
 }
 
+// median duration (ms) of `reps` force evaluations at the current positions
+// (integrate = 0 leaves x, v and f as they are), after one untimed evaluation;
+// with graphs enabled each is a replay of one captured evaluation
 int time_force_evals(mix_ctx* c, int reps, float* ms) {
     int st = evaluate(c, 0, 0.0);
     if (st) return st;
