@@ -61,3 +61,41 @@ def test_product_code_does_not_reach_the_oracle():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
                 assert "liboracle" not in txt, f
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every struct the binding passes through the ABI has the size and field
+    offsets the C header gives it (a host C program compiled against
+    include/mix.h prints them; no device involved)."""
+    import shutil
+    import subprocess
+
+    from paper_2502_19081_gb300 import mix
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    structs = [getattr(mix, n) for n in dir(mix)
+               if n.startswith("mix_") and isinstance(getattr(mix, n), type)
+               and issubclass(getattr(mix, n), ctypes.Structure)]
+    assert len(structs) >= 10
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "mix.h"', "int main(void) {"]
+    for s in structs:
+        lines.append(f'    printf("%s sizeof %zu\\n", "{s.__name__}", sizeof({s.__name__}));')
+        for f, _ in s._fields_:
+            lines.append(f'    printf("%s %s %zu\\n", "{s.__name__}", "{f}", offsetof({s.__name__}, {f}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    exe = tmp_path / "layout"
+    src.write_text("\n".join(lines) + "\n")
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    seen = 0
+    for line in out:
+        if not line:
+            continue
+        name, field, val = line.split()
+        s = getattr(mix, name)
+        want = ctypes.sizeof(s) if field == "sizeof" else getattr(s, field).offset
+        assert int(val) == want, (name, field, int(val), want)
+        seen += 1
+    assert seen == sum(len(s._fields_) + 1 for s in structs)
